@@ -1,0 +1,248 @@
+"""CPU oracle for the FeLoG walk + SGNS hot path (test infrastructure).
+
+Only the test suite, the smoke check and the benchmark's CPU-baseline leg may
+import this package.  It wraps ``felog_oracle.c`` (plain C, binary64, no FMA
+contraction), which shares no code with the CUDA library.  See the C file for
+the paper passage each function follows.
+
+Pins that tie it to the paper and to mathematics rather than to itself live in
+``tests/test_oracle_*.py``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "felog_oracle.c")
+_LIB = os.path.join(_HERE, "_felog_oracle.so")
+
+STREAM_WALK, STREAM_PSI, STREAM_NEG, STREAM_INIT = 0, 1, 2, 3
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (binary64, no contraction, no fast-math)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _TrainParams(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("window", ctypes.c_int32),
+                ("negatives", ctypes.c_int32), ("lr0", ctypes.c_double),
+                ("lr_total_tokens", ctypes.c_int64)]
+
+
+class _FeedbackParams(ctypes.Structure):
+    _fields_ = [("enabled", ctypes.c_int32), ("mu", ctypes.c_double), ("ks", ctypes.c_int32),
+                ("max_rounds", ctypes.c_int32), ("reactivate", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        i32, i64, u64, f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+        sig = {
+            "oracle_philox": (None, [u64, P, P]),
+            "oracle_walk": (ctypes.c_int, [P, P, i32, P, i32, i32, i32, u64, i32, P]),
+            "oracle_counts": (None, [P, i64, i32, P]),
+            "oracle_noise_table": (ctypes.c_int, [P, i32, P, P, P, P]),
+            "oracle_draw_negative": (i32, [P, P, i32, u64, u64, i32, i64, i32, i32, i32]),
+            "oracle_init_tables": (None, [i32, i32, u64, P, P]),
+            "oracle_learning_rate": (f64, [f64, i64, i64]),
+            "oracle_pair_update": (f64, [P, P, i32, i32, f64, P]),
+            "oracle_sgns_serial": (f64, [P, i64, i32, i32, P, P, P, u64, u64, i32, i64, P, P]),
+            "oracle_sgns_minibatch": (f64, [P, i64, i32, i32, P, i64, P, P, u64, u64, i32, i64,
+                                            P, P, P]),
+            "oracle_psi_subset": (None, [i64, i32, u64, i32, i32, P]),
+            "oracle_psi_node": (f64, [P, P, P, i32, i32, u64, i32, i32]),
+            "oracle_feedback": (i64, [P, P, i32, P, i32, P, u64, i32, P, P, P]),
+            "oracle_embed": (i32, [P, P, i32, i32, i32, P, P, i32, i64, u64, P, P, P]),
+            "oracle_auc_pairs": (f64, [P, i64, P, i64]),
+            "oracle_link_scores": (None, [P, i32, P, i64, P]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(_lib, name)
+            fn.restype = res
+            fn.argtypes = args
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+# ---------------------------------------------------------------------------
+def philox(seed: int, ctr) -> np.ndarray:
+    """Philox4x32-10 block for counter (x0, x1, x2, x3) and 64-bit key seed."""
+    c = _c(ctr, np.uint32)
+    out = np.zeros(4, np.uint32)
+    lib().oracle_philox(seed, _p(c), _p(out))
+    return out
+
+
+def walk(offsets, cols, starts, L: int, wpr: int, seed: int, round_: int) -> np.ndarray:
+    off, col, st = _c(offsets, np.int32), _c(cols, np.int32), _c(starts, np.int32)
+    out = np.empty((wpr * st.shape[0], L), np.int32)
+    rc = lib().oracle_walk(_p(off), _p(col), off.shape[0] - 1, _p(st), st.shape[0], L, wpr,
+                           seed, round_, _p(out))
+    if rc:
+        raise ValueError(f"oracle_walk failed ({rc})")
+    return out
+
+
+def counts(walks, n: int) -> np.ndarray:
+    w = _c(walks, np.int32)
+    out = np.empty(n, np.uint32)
+    lib().oracle_counts(_p(w), w.size, n, _p(out))
+    return out
+
+
+def noise_table(cnt):
+    """Integer alias table for the unigram^0.75 noise distribution.
+
+    Returns (W, thr, alias, S).
+    """
+    c = _c(cnt, np.uint32)
+    n = c.shape[0]
+    W = np.empty(n, np.uint64)
+    thr = np.empty(n, np.uint64)
+    alias = np.empty(n, np.int32)
+    S = ctypes.c_uint64(0)
+    rc = lib().oracle_noise_table(_p(c), n, _p(W), _p(thr), _p(alias), ctypes.byref(S))
+    if rc:
+        raise RuntimeError(f"oracle_noise_table failed ({rc})")
+    return W, thr, alias, int(S.value)
+
+
+def draw_negative(thr, alias, S: int, seed: int, round_: int, walk_idx: int, pos: int, q: int,
+                  k: int) -> int:
+    return int(lib().oracle_draw_negative(_p(thr), _p(alias), thr.shape[0], S, seed, round_,
+                                          walk_idx, pos, q, k))
+
+
+def init_tables(n: int, d: int, seed: int):
+    phi_in = np.empty((n, d), np.float64)
+    phi_out = np.empty((n, d), np.float64)
+    lib().oracle_init_tables(n, d, seed, _p(phi_in), _p(phi_out))
+    return phi_in, phi_out
+
+
+def learning_rate(lr0: float, t: int, T: int) -> float:
+    return float(lib().oracle_learning_rate(lr0, t, T))
+
+
+def pair_update(in_x: np.ndarray, outs: list, eta: float) -> float:
+    """Apply one Eq. 2 pair update in place; outs[0] is the center's phi_out row."""
+    d = in_x.shape[0]
+    ptrs = (ctypes.c_void_p * len(outs))(*[o.ctypes.data for o in outs])
+    scratch = np.empty(d, np.float64)
+    return float(lib().oracle_pair_update(_p(in_x), ptrs, len(outs), d, eta, _p(scratch)))
+
+
+def _tp(dim, window, negatives, lr0, T):
+    return _TrainParams(dim, window, negatives, lr0, T)
+
+
+def sgns_serial(walks, n: int, dim: int, window: int, negatives: int, lr0: float, T: int,
+                thr, alias, S: int, seed: int, round_: int, clock_base: int,
+                phi_in: np.ndarray, phi_out: np.ndarray) -> float:
+    w = _c(walks, np.int32)
+    assert phi_in.dtype == np.float64 and phi_in.flags.c_contiguous
+    assert phi_out.dtype == np.float64 and phi_out.flags.c_contiguous
+    tp = _tp(dim, window, negatives, lr0, T)
+    return float(lib().oracle_sgns_serial(_p(w), w.shape[0], w.shape[1], n, ctypes.byref(tp),
+                                          _p(thr), _p(alias), S, seed, round_, clock_base,
+                                          _p(phi_in), _p(phi_out)))
+
+
+def sgns_minibatch(walks, n: int, dim: int, window: int, negatives: int, lr0: float, T: int,
+                   B: int, thr, alias, S: int, seed: int, round_: int, clock_base: int,
+                   phi_in: np.ndarray, phi_out: np.ndarray, per_batch: bool = False):
+    w = _c(walks, np.int32)
+    assert phi_in.dtype == np.float64 and phi_in.flags.c_contiguous
+    assert phi_out.dtype == np.float64 and phi_out.flags.c_contiguous
+    tp = _tp(dim, window, negatives, lr0, T)
+    nb = (w.size + B - 1) // B
+    bl = np.zeros(max(nb, 1), np.float64)
+    loss = float(lib().oracle_sgns_minibatch(_p(w), w.shape[0], w.shape[1], n, ctypes.byref(tp),
+                                             B, _p(thr), _p(alias), S, seed, round_, clock_base,
+                                             _p(phi_in), _p(phi_out), _p(bl)))
+    return (loss, bl[:nb]) if per_batch else loss
+
+
+def psi_subset(deg: int, ks: int, seed: int, v: int, round_: int) -> np.ndarray:
+    out = np.empty(ks, np.int64)
+    lib().oracle_psi_subset(deg, ks, seed, v, round_, _p(out))
+    return out
+
+
+def psi_node(offsets, cols, phi: np.ndarray, ks: int, seed: int, round_: int, v: int) -> float:
+    off, col = _c(offsets, np.int32), _c(cols, np.int32)
+    ph = _c(phi, np.float64)
+    return float(lib().oracle_psi_node(_p(off), _p(col), _p(ph), ph.shape[1], ks, seed, round_, v))
+
+
+def feedback(offsets, cols, phi: np.ndarray, active_in, enabled: bool, mu: float, ks: int,
+             reactivate: bool, seed: int, round_: int):
+    """Psi of the evaluated nodes and the next active set (Eq. 4, Eq. 5)."""
+    off, col = _c(offsets, np.int32), _c(cols, np.int32)
+    ph = _c(phi, np.float64)
+    n = off.shape[0] - 1
+    a_in = _c(active_in, np.uint8)
+    a_out = np.empty(n, np.uint8)
+    psi = np.empty(n, np.float64)
+    fp = _FeedbackParams(int(enabled), mu, ks, 0, int(reactivate))
+    cnt = lib().oracle_feedback(_p(off), _p(col), n, _p(ph), ph.shape[1], ctypes.byref(fp), seed,
+                                round_, _p(a_in), _p(a_out), _p(psi))
+    return psi, a_out, int(cnt)
+
+
+def embed(offsets, cols, L: int, wpr: int, dim: int, window: int, negatives: int, lr0: float,
+          feedback_enabled: bool, mu: float, ks: int, max_rounds: int, reactivate: bool,
+          seed: int, mode: str = "serial", B: int = 4096, T: int = 0):
+    """Algorithm 1 end to end; returns (phi_in, phi_out, stats[rounds, 4])."""
+    off, col = _c(offsets, np.int32), _c(cols, np.int32)
+    n = off.shape[0] - 1
+    phi_in = np.empty((n, dim), np.float64)
+    phi_out = np.empty((n, dim), np.float64)
+    stats = np.zeros((max_rounds, 4), np.float64)
+    tp = _tp(dim, window, negatives, lr0, T)
+    fp = _FeedbackParams(int(feedback_enabled), mu, ks, max_rounds, int(reactivate))
+    rounds = lib().oracle_embed(_p(off), _p(col), n, L, wpr, ctypes.byref(tp), ctypes.byref(fp),
+                                0 if mode == "serial" else 1, B, seed, _p(phi_in), _p(phi_out),
+                                _p(stats))
+    return phi_in, phi_out, stats[:rounds]
+
+
+def auc_pairs(pos_scores, neg_scores) -> float:
+    """AUC by its definition over every (positive, negative) pair."""
+    p, q = _c(pos_scores, np.float64), _c(neg_scores, np.float64)
+    return float(lib().oracle_auc_pairs(_p(p), p.shape[0], _p(q), q.shape[0]))
+
+
+def link_scores(phi: np.ndarray, pairs) -> np.ndarray:
+    ph = _c(phi, np.float64)
+    pr = _c(pairs, np.int32)
+    out = np.empty(pr.shape[0], np.float64)
+    lib().oracle_link_scores(_p(ph), ph.shape[1], _p(pr), pr.shape[0], _p(out))
+    return out
+
+
+def link_auc(phi: np.ndarray, pos_pairs, neg_pairs) -> float:
+    return auc_pairs(link_scores(phi, pos_pairs), link_scores(phi, neg_pairs))
