@@ -1,0 +1,488 @@
+#!/usr/bin/env python
+"""Benchmark of the FeLoG walk + SGNS hot path on one B300.
+
+Workload (N=1): R-MAT scale 20 (1,048,576 nodes), edge factor 16,
+(a, b, c, d) = (0.57, 0.19, 0.19, 0.05), symmetrised, deduplicated, 10 % of
+the edges held out for link prediction; walks of 80 nodes, 10 walks per node
+(one per round, 10 rounds), window 10, 5 negatives, d = 128 float tables,
+lock-free (Hogwild) SGNS.
+
+One step = one round of Algorithm 1 over the whole graph: compact V_a, walk
+(corpus counts fused), build the unigram^0.75 alias table, train SGNS,
+compute Psi and the next active set.  The plain form (feedback off) keeps
+every non-isolated node active, so every step does the same work.  The
+tables (2 x 512 MiB) exceed the 126 MB L2, so no L2 flush is needed between
+steps.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
+a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "walk steps/s + SGNS tokens/s at fixed AUC, chosen vs plain form; p50/p99 latency"
+SCALE, EDGE_FACTOR, GRAPH_SEED, SPLIT_SEED = 20, 16, 1, 7
+L, WPR, ROUNDS, WINDOW, NEG, DIM, LR0 = 80, 1, 10, 10, 5, 128, 0.025
+MU, KS = 0.65, 8
+SEED = 2026
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="native", choices=["native", "reference"])
+    p.add_argument("--scale", type=int, default=SCALE, help="R-MAT scale (20 = the benchmark workload)")
+    p.add_argument("--no-quality", action="store_true", help="skip the full-run AUC comparison")
+    p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    return p.parse_args()
+
+
+def _workload(scale, rank=0):
+    from paper_2606_22180_b300 import inputs
+
+    g = inputs.workload_rmat(scale, GRAPH_SEED + 1000 * rank, EDGE_FACTOR)
+    split = inputs.link_split(g, 0.1, SPLIT_SEED + rank)
+    return split
+
+
+def _workload_name(scale):
+    return (f"rmat{scale}-ef{EDGE_FACTOR} (a,b,c,d)=(0.57,0.19,0.19,0.05), 10% edges held out; "
+            f"L={L}, {ROUNDS} walks/node, window {WINDOW}, {NEG} negatives, d={DIM} fp32, hogwild")
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(device_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[3:7]):
+                if val.lower() in ("active", "1"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6400.0, "fallback"
+
+
+def _profile_traffic(kernel_src):
+    """DRAM bytes per launch of the SGNS kernel from the committed ncu
+    summary, or None when the kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "sgns_hogwild_rmat20_fp32.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    src_hash = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    vals = {}
+    for line in txt.splitlines():
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("sgns.cu sha256[:16]") != src_hash:
+        return None
+    try:
+        return float(vals["dram_bytes_per_full_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------------------
+# one round of Algorithm 1 through the C ABI, buffers preallocated
+# ---------------------------------------------------------------------------
+class RoundRunner:
+    KERNELS_PER_ROUND = 13  # compact 3, walk 1, noise table 6, train 2, feedback 1
+
+    def __init__(self, fl, dg, tp, fp, seed):
+        import torch
+
+        self.fl, self.dg, self.tp, self.fp, self.seed = fl, dg, tp, fp, seed
+        self.lib = fl.load()
+        n = dg.n
+        dev = dg.offsets.device
+        self.n = n
+        dt = fl.table_dtype(tp.precision)
+        self.phi_in = torch.empty((n, tp.dim), dtype=dt, device=dev)
+        self.phi_out = torch.empty((n, tp.dim), dtype=dt, device=dev)
+        self.active = [torch.empty(n, dtype=torch.uint8, device=dev) for _ in range(2)]
+        self.starts = torch.empty(n, dtype=torch.int32, device=dev)
+        self.n_active_d = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.n_next_d = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.walks = torch.empty(n * WPR * L, dtype=torch.int32, device=dev)
+        self.counts = torch.empty(n, dtype=torch.int32, device=dev)
+        self.thr = torch.empty(n, dtype=torch.int64, device=dev)
+        self.alias = torch.empty(n, dtype=torch.int32, device=dev)
+        self.S = torch.empty(1, dtype=torch.int64, device=dev)
+        self.loss = torch.empty(1, dtype=torch.float64, device=dev)
+        self.n_active_h = torch.zeros(1, dtype=torch.int32).pin_memory()
+        self.loss_h = torch.zeros(1, dtype=torch.float64).pin_memory()
+        P = ctypes.c_void_p
+        self.cws = torch.empty(self.lib.felog_compact_workspace_bytes(n), dtype=torch.uint8, device=dev)
+        self.nws = torch.empty(self.lib.felog_noise_workspace_bytes(n), dtype=torch.uint8, device=dev)
+        tb = self.lib.felog_train_workspace_bytes(n * WPR, L, n, ctypes.byref(tp))
+        self.tws = torch.empty(max(tb, 256), dtype=torch.uint8, device=dev)
+        self.csr = fl._Csr(dg.offsets.data_ptr(), dg.cols.data_ptr(), n, dg.nnz)
+        self.wp = fl._WalkParams(L, WPR)
+        self.P = P
+        self.cur = 0
+        self.clock = 0
+        self.ev = None
+
+    def reset(self):
+        import torch
+
+        fl = self.fl
+        fl._check(self.lib.felog_init_tables(self.n, self.tp.dim, self.tp.precision, self.seed,
+                                             self.P(self.phi_in.data_ptr()), self.P(self.phi_out.data_ptr()),
+                                             fl._stream()), "init")
+        deg = self.dg.offsets[1:] - self.dg.offsets[:-1]
+        self.active[0].copy_((deg > 0).to(torch.uint8))
+        self.n_live = int((deg > 0).sum().item())
+        self.cur = 0
+        self.clock = 0
+
+    def run(self, r, events=None):
+        """One round; returns (n_active, tokens).  events: 5 CUDA events for phase times."""
+        fl, lib, P = self.fl, self.lib, self.P
+        s = fl._stream()
+        a_in, a_out = self.active[self.cur], self.active[self.cur ^ 1]
+        fl._check(lib.felog_compact_active(P(a_in.data_ptr()), self.n, P(self.starts.data_ptr()),
+                                           P(self.n_active_d.data_ptr()), P(self.cws.data_ptr()),
+                                           self.cws.numel(), s), "compact")
+        self.n_active_h.copy_(self.n_active_d, non_blocking=True)
+        import torch
+
+        torch.cuda.current_stream().synchronize()
+        na = int(self.n_active_h.item())
+        if na == 0:
+            return 0, 0
+        n_walks = na * WPR
+        if events:
+            events[0].record()
+        self.counts.zero_()
+        fl._check(lib.felog_walk(ctypes.byref(self.csr), P(self.starts.data_ptr()), na, ctypes.byref(self.wp),
+                                 self.seed, r, P(self.walks.data_ptr()), P(self.counts.data_ptr()), s), "walk")
+        if events:
+            events[1].record()
+        fl._check(lib.felog_noise_table(P(self.counts.data_ptr()), self.n, P(self.thr.data_ptr()),
+                                        P(self.alias.data_ptr()), P(self.S.data_ptr()), P(self.nws.data_ptr()),
+                                        self.nws.numel(), s), "noise")
+        if events:
+            events[2].record()
+        fl._check(lib.felog_train(P(self.walks.data_ptr()), n_walks, L, self.n, ctypes.byref(self.tp),
+                                  P(self.thr.data_ptr()), P(self.alias.data_ptr()), P(self.S.data_ptr()),
+                                  self.seed, r, self.clock, P(self.phi_in.data_ptr()), P(self.phi_out.data_ptr()),
+                                  P(self.loss.data_ptr()), P(self.tws.data_ptr()), self.tws.numel(), s), "train")
+        if events:
+            events[3].record()
+        fl._check(lib.felog_feedback(ctypes.byref(self.csr), P(self.phi_in.data_ptr()), self.tp.dim,
+                                     self.tp.precision, ctypes.byref(self.fp), self.seed, r, P(a_in.data_ptr()),
+                                     P(a_out.data_ptr()), None, P(self.n_next_d.data_ptr()), s), "feedback")
+        if events:
+            events[4].record()
+        self.clock += n_walks * L
+        self.cur ^= 1
+        return na, n_walks * L
+
+
+def _pairs_per_walk():
+    return sum(min(p, WINDOW) + min(L - 1 - p, WINDOW) for p in range(L))
+
+
+def run_native(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2606_22180_b300 import build, evaluate, felog as fl
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    fl.load()
+
+    split = _workload(args.scale, rank)
+    g = split.train
+    dg = fl.DeviceGraph.from_host(g)
+    n_live = int((g.degrees() > 0).sum())
+    T = ROUNDS * WPR * n_live * L
+    tp = fl.train_params(DIM, WINDOW, NEG, LR0, T, fl.FELOG_SGNS_HOGWILD, 4096, fl.FELOG_FP32)
+    fp_plain = fl.feedback_params(False, MU, KS, ROUNDS, False)
+    runner = RoundRunner(fl, dg, tp, fp_plain, SEED + rank)
+    runner.reset()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for w in range(args.warmup):
+        runner.run(w)
+    # timed region: K plain rounds
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(local)
+    barrier()
+    start.record()
+    tokens = 0
+    for k in range(args.steps):
+        _, tok = runner.run(args.warmup + k, events=ev[k])
+        tokens += tok
+    stop.record()
+    barrier()
+    clocks = sampler.stop()
+    ms = start.elapsed_time(stop)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        tk = torch.tensor([tokens], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tk)
+        tokens_all = float(tk.item())
+    else:
+        tokens_all = float(tokens)
+    phase = {name: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in ev)
+             for i, name in enumerate(["walk", "noise", "train", "feedback"])}
+    steps_per_round = n_live * WPR * (L - 1)
+    value = tokens_all / (ms / 1e3)
+
+    # roofline of the dominant kernel (SGNS): algorithmic bytes per launch
+    row = DIM * 4
+    pairs = n_live * WPR * _pairs_per_walk()
+    alg_bytes = row * (4 * n_live * WPR * L + 2 * NEG * pairs)
+    achieved = alg_bytes / (phase["train"] / 1e3) / 1e9
+    peak, peak_kind = _peaks()
+    traffic = _profile_traffic(os.path.join(ROOT, "paper_2606_22180_b300", "csrc", "sgns.cu"))
+
+    # end to end through the public calls: CSR from pinned host memory, one
+    # round, the round's loss read back
+    off_h = torch.from_numpy(g.offsets).pin_memory()
+    col_h = torch.from_numpy(g.cols).pin_memory()
+    e_start, e_stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e_start.record()
+    e_tokens = 0
+    for k in range(args.steps):
+        dg.offsets.copy_(off_h, non_blocking=True)
+        dg.cols.copy_(col_h, non_blocking=True)
+        _, tok = runner.run(args.warmup + args.steps + k)
+        e_tokens += tok
+        runner.loss_h.copy_(runner.loss, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    e_stop.record()
+    barrier()
+    e_ms = e_start.elapsed_time(e_stop)
+    h2d = (g.offsets.nbytes + g.cols.nbytes)
+    e2e_value = e_tokens * world / (e_ms / 1e3)
+
+    result = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "tokens/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded R-MAT graph; no dataset)",
+        "config": {
+            "workload": _workload_name(args.scale),
+            "nodes": g.n, "directed_csr_entries": g.nnz, "non_isolated": n_live,
+            "step": "one plain round of Algorithm 1 (walk, counts, alias table, SGNS, Psi, V_a)",
+            "l2": "inputs larger than L2 (tables 2 x 512 MiB), no flush",
+            "parallelism": "replicas" if world > 1 else "single GPU",
+        },
+        "walk_steps_per_s": steps_per_round * world / (phase["walk"] / 1e3),
+        "tokens_per_s_sgns_kernel": n_live * WPR * L * world / (phase["train"] / 1e3),
+        "phase_ms": phase,
+        "gpu_launches": RoundRunner.KERNELS_PER_ROUND * args.steps,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "k_sgns_hogwild<128,float,8>", "peak_source": peak_kind},
+        "e2e": {"value": e2e_value, "unit": "tokens/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8},
+        "clocks": clocks,
+    }
+
+    if not args.no_quality and rank == 0:
+        result["quality"] = _quality(fl, evaluate, dg, split, n_live)
+    if not args.no_cpu and rank == 0:
+        result["cpu_baseline"] = _cpu_baseline(split, n_live)
+    if rank == 0:
+        print(json.dumps(result))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _quality(fl, evaluate, dg, split, n_live):
+    """Full runs of Algorithm 1: plain (feedback off, fp32) and chosen
+    (feedback mu = 0.65, bf16 with stochastic rounding); AUC on the held-out
+    edges, wall time of the felog_embed call."""
+    import torch
+
+    out = {}
+    T = ROUNDS * WPR * n_live * L
+    forms = {
+        "plain": (fl.train_params(DIM, WINDOW, NEG, LR0, T, fl.FELOG_SGNS_HOGWILD, 4096, fl.FELOG_FP32),
+                  fl.feedback_params(False, MU, KS, ROUNDS, False)),
+        "chosen": (fl.train_params(DIM, WINDOW, NEG, LR0, T, fl.FELOG_SGNS_HOGWILD, 4096, fl.FELOG_BF16_SR),
+                   fl.feedback_params(True, MU, KS, ROUNDS, False)),
+    }
+    for name, (tp, fp) in forms.items():
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pi, po, st = fl.felog_embed(dg, L, WPR, tp, fp, SEED)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        tokens = sum(s["tokens"] for s in st)
+        out[name] = {
+            "auc": evaluate.link_auc(pi, split.pos, split.neg),
+            "rounds": len(st),
+            "active_per_round": [s["n_active"] for s in st],
+            "tokens": tokens,
+            "seconds": sec,
+            "tokens_per_s": tokens / sec,
+            "loss_per_round": [s["loss"] for s in st],
+        }
+        del pi, po
+    return out
+
+
+def _cpu_baseline(split, n_live, n_starts=2048):
+    """The oracle (single thread, binary64) on the first n_starts walks of a
+    round: walks, counts, alias table, serial SGNS, Psi of the starts."""
+    import oracle
+
+    g = split.train
+    starts = np.nonzero(g.degrees() > 0)[0][:n_starts].astype(np.int32)
+    t0 = time.perf_counter()
+    W = oracle.walk(g.offsets, g.cols, starts, L, WPR, SEED, 0)
+    t_walk = time.perf_counter() - t0
+    _, thr, alias, S = oracle.noise_table(oracle.counts(W, g.n))
+    pi, po = oracle.init_tables(g.n, DIM, SEED)
+    T = ROUNDS * WPR * n_live * L
+    t1 = time.perf_counter()
+    oracle.sgns_serial(W, g.n, DIM, WINDOW, NEG, LR0, T, thr, alias, S, SEED, 0, 0, pi, po)
+    t_train = time.perf_counter() - t1
+    active = np.zeros(g.n, np.uint8)
+    active[starts] = 1
+    oracle.feedback(g.offsets, g.cols, pi, active, True, MU, KS, False, SEED, 0)
+    total = time.perf_counter() - t0
+    tokens = W.size
+    return {"value": tokens / total, "unit": "tokens/s", "cores": 1, "kind": "oracle",
+            "sample": f"{starts.shape[0]} walks of one round (first non-isolated starts), whole round path",
+            "walk_steps_per_s": starts.shape[0] * (L - 1) / t_walk,
+            "sgns_tokens_per_s": tokens / t_train, "seconds": total}
+
+
+def run_reference(args):
+    """The oracle, as it stands, on host cores: each step a bounded sample
+    (512 walks) of the same round."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+
+    split = _workload(args.scale)
+    g = split.train
+    n_live = int((g.degrees() > 0).sum())
+    live = np.nonzero(g.degrees() > 0)[0].astype(np.int32)
+    pi, po = oracle.init_tables(g.n, DIM, SEED)
+    T = ROUNDS * WPR * n_live * L
+    per = 512
+
+    def step(k):
+        starts = live[(k * per) % live.shape[0]:][:per]
+        W = oracle.walk(g.offsets, g.cols, starts, L, WPR, SEED, k % 65536)
+        _, thr, alias, S = oracle.noise_table(oracle.counts(W, g.n))
+        oracle.sgns_serial(W, g.n, DIM, WINDOW, NEG, LR0, T, thr, alias, S, SEED, k % 65536, 0, pi, po)
+        active = np.zeros(g.n, np.uint8)
+        active[starts] = 1
+        oracle.feedback(g.offsets, g.cols, pi, active, False, MU, KS, False, SEED, k % 65536)
+        return W.size
+
+    for k in range(args.warmup):
+        step(k)
+    t0 = time.perf_counter()
+    tokens = sum(step(args.warmup + k) for k in range(args.steps))
+    sec = time.perf_counter() - t0
+    v = tokens / sec
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "tokens/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded R-MAT graph; no dataset)",
+        "config": {"workload": _workload_name(args.scale)},
+        "cpu_baseline": {"value": v, "unit": "tokens/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{per} walks of a round per step (walk, counts, alias table, serial SGNS, Psi)"},
+        "e2e": {"value": v, "unit": "tokens/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+if __name__ == "__main__":
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_native(a)

@@ -1,0 +1,223 @@
+/*
+ * felog.h -- C ABI of the FeLoG walk + SGNS hot path on one B300 (sm_103a).
+ *
+ * The calls follow the paper's Sample / Train / feedback decomposition
+ * (Section 5.1, Algorithm 1; the unified Sample and Train interfaces of
+ * Section 5.4):
+ *
+ *   felog_compact_active  active flags -> ascending start list   (Alg. 1, V_a)
+ *   felog_walk            Sample: uniform truncated walks        (Section 2, Alg. 1 Sampling)
+ *   felog_noise_table     Pn(u) of Eq. 2 as an integer alias table
+ *   felog_init_tables     embedding tables phi_in, phi_out
+ *   felog_train           Train: skip-gram negative sampling     (Eq. 1, Eq. 2; Alg. 1 Training)
+ *   felog_feedback        Psi (Eq. 4) and the next active set (Eq. 5; Alg. 1 Feedback)
+ *   felog_embed           Algorithm 1 end to end
+ *
+ * Conventions (every call):
+ *   - Pointers documented "device" point to CUDA device memory owned by the
+ *     caller; the library never frees caller memory and allocates none of
+ *     its own except where a call says so (felog_embed_host).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are stream-ordered and asynchronous unless stated.
+ *   - Argument errors are reported synchronously by the return status and
+ *     nothing is launched.  FELOG_ERR_CUDA reports a launch or runtime error
+ *     seen by the call (cudaGetLastError); the message is available from
+ *     felog_last_cuda_error().
+ *   - No C++ exception crosses this boundary.
+ *   - Thread-compatible: distinct host threads may call concurrently on
+ *     distinct streams and buffers.
+ *
+ * Random numbers: Philox4x32-10 keyed by the 64-bit seed with counter
+ * (x0, x1, x2, stream); stream 0 = walks, 1 = Psi subsets, 2 = negatives,
+ * 3 = table initialisation, 4 = stochastic rounding.
+ */
+#ifndef FELOG_H_
+#define FELOG_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FELOG_OK = 0,
+    FELOG_ERR_INVALID_ARG = 1, /* a size, pointer or parameter is out of range */
+    FELOG_ERR_BAD_CSR = 2,     /* CSR fails host-side validation */
+    FELOG_ERR_WORKSPACE = 3,   /* workspace missing or smaller than required */
+    FELOG_ERR_CUDA = 4,        /* CUDA launch / runtime error */
+    FELOG_ERR_UNSUPPORTED = 5  /* a parameter combination with no kernel */
+} felog_status;
+
+/* Undirected, unweighted graph (Table 1) in CSR form, device pointers.
+ * offsets[n+1] non-decreasing with offsets[0] = 0 and offsets[n] = nnz;
+ * cols[nnz] in [0, n); each row sorted ascending, symmetric, loop-free. */
+typedef struct {
+    const int32_t *offsets;
+    const int32_t *cols;
+    int32_t n;
+    int64_t nnz;
+} felog_csr;
+
+/* length: nodes per walk (L >= 1); walks_per_round: walks each active node
+ * starts per round (>= 1). */
+typedef struct {
+    int32_t length;
+    int32_t walks_per_round;
+} felog_walk_params;
+
+typedef enum {
+    FELOG_SGNS_HOGWILD = 0,  /* lock-free asynchronous updates (fast form) */
+    FELOG_SGNS_MINIBATCH = 1 /* synchronous minibatch, bitwise reproducible */
+} felog_sgns_mode;
+
+typedef enum {
+    FELOG_FP32 = 0,   /* float tables */
+    FELOG_BF16_SR = 1 /* bfloat16 tables, float math, stochastic rounding on store */
+} felog_precision;
+
+/* dim in {32, 64, 128, 256}; 1 <= window <= 16; 1 <= negatives <= 15;
+ * learning rate lr0 * max(1e-4, 1 - t / lr_total_tokens) on the global token
+ * clock t; minibatch = positions per synchronous batch (MINIBATCH mode). */
+typedef struct {
+    int32_t dim;
+    int32_t window;
+    int32_t negatives;
+    float lr0;
+    int64_t lr_total_tokens;
+    int32_t mode;      /* felog_sgns_mode */
+    int32_t minibatch; /* >= 1 */
+    int32_t precision; /* felog_precision */
+} felog_train_params;
+
+/* enabled = 0 is the plain method (every non-isolated node stays active);
+ * mu: threshold of Eq. 5 (a node stays active iff Psi < mu); ks: subset size
+ * of Eq. 4 (1..32); max_rounds: cap on Algorithm 1's loop; reactivate = 1
+ * evaluates every non-isolated node each round instead of only V_a. */
+typedef struct {
+    int32_t enabled;
+    double mu;
+    int32_t ks;
+    int32_t max_rounds;
+    int32_t reactivate;
+} felog_feedback_params;
+
+/* Per-round record filled by felog_embed (host memory). */
+typedef struct {
+    int32_t round;
+    int32_t n_active;   /* |V_a^r| */
+    int32_t n_next;     /* |V_a^{r+1}| */
+    int32_t reserved;
+    int64_t tokens;     /* corpus positions trained this round */
+    int64_t walk_steps; /* walk transitions this round */
+    double loss;        /* summed pair loss of the round */
+    float ms_walk, ms_noise, ms_train, ms_feedback; /* CUDA-event phase times */
+} felog_round_stats;
+
+const char *felog_status_string(felog_status s);
+/* Text of the last CUDA error seen by a call on this host thread. */
+const char *felog_last_cuda_error(void);
+
+/* Stable compaction of the active set (Algorithm 1's V_a): starts[] receives
+ * the indices v with active[v] != 0 in ascending order, *n_active (device
+ * int32) their count.  active: device uint8[n]; starts: device int32[n].
+ * Workspace: felog_compact_workspace_bytes(n) bytes of device memory. */
+size_t felog_compact_workspace_bytes(int32_t n);
+felog_status felog_compact_active(const uint8_t *active, int32_t n, int32_t *starts,
+                                  int32_t *n_active, void *workspace, size_t workspace_bytes,
+                                  void *stream);
+
+/* Sample (Section 2 "Sampling process"; Section 5.4 Sample interface):
+ * uniform truncated walks.  Walk (round r, rep j, start s = starts[i]) is
+ * written to row j*n_starts + i of walks[n_starts*wpr][L] (device int32,
+ * row-major).  Step t >= 1 draws Philox(x0=t, x1=s, x2=r*wpr+j, 0) and moves
+ * to neighbour floor(u64 * deg / 2^64) (u64 = word1:word0) in CSR order.  A
+ * node without neighbours ends the walk; the rest of its row is -1.
+ * counts (device uint32[n], may be NULL): every written node is added to it
+ * (the corpus histogram used by felog_noise_table).  The CSR is validated on
+ * the host only for its sizes; starts must lie in [0, n). */
+felog_status felog_walk(const felog_csr *g, const int32_t *starts, int32_t n_starts,
+                        const felog_walk_params *wp, uint64_t seed, int32_t round,
+                        int32_t *walks, uint32_t *counts, void *stream);
+
+/* Corpus histogram: counts[v] += occurrences of v in tokens[n_tokens]
+ * (entries < 0 are skipped).  counts must be zeroed by the caller. */
+felog_status felog_count(const int32_t *tokens, int64_t n_tokens, int32_t n, uint32_t *counts,
+                         void *stream);
+
+/* Noise distribution Pn(u) of Eq. 2: unigram counts raised to 0.75, as an
+ * exact integer alias table.  W_v = c_v ? max(1, floor(c^0.75 / cmax^0.75 *
+ * 2^32)) : 0 (c^0.75 = sqrt(c) * sqrt(sqrt(c)) in binary64); S = sum W_v.
+ * thr (device uint64[n]), alias (device int32[n]) and *S (device uint64)
+ * are written; the table equals, entry for entry, the sequential sweep that
+ * pairs light buckets (n W < S) with heavy ones in ascending order.  A draw
+ * takes b = mulhi64(u, n) and keeps b iff mulhi64(u', S) < thr[b], else
+ * alias[b].  Workspace: felog_noise_workspace_bytes(n). */
+size_t felog_noise_workspace_bytes(int32_t n);
+felog_status felog_noise_table(const uint32_t *counts, int32_t n, uint64_t *thr, int32_t *alias,
+                               uint64_t *S, void *workspace, size_t workspace_bytes, void *stream);
+
+/* phi_in[v][i] = (u - 1/2) / dim with u = (Philox(x0=i/4, x1=v, 0, 3) word
+ * i%4 >> 8) * 2^-24 in float; phi_out = 0.  Tables are device [n][dim] of
+ * float (FELOG_FP32) or bfloat16 (FELOG_BF16_SR, rounded to nearest). */
+felog_status felog_init_tables(int32_t n, int32_t dim, int32_t precision, uint64_t seed,
+                               void *phi_in, void *phi_out, void *stream);
+
+/* Train (Eq. 1, Eq. 2; Section 5.4 Train interface): skip-gram with negative
+ * sampling over the corpus walks[n_walks][L] (device int32; -1 = padding).
+ * For every center c = walks[w][p] and window offset o in [-W, W] \ {0}
+ * with a context x = walks[w][p+o] >= 0, the pair maximises
+ *   log sigma(phi_in[x] . phi_out[c]) + sum_k log sigma(-phi_in[x] . phi_out[n_k])
+ * with K negatives n_k drawn from the alias table (thr, alias, *S) by
+ * Philox(x0 = q<<8 | k, x1 = w, x2 = round<<16 | p, 2), q the slot of o;
+ * a negative equal to c is skipped.  The learning rate of a position is
+ * lr0 * max(1e-4, 1 - t / lr_total_tokens), t = clock_base + w*L + p.
+ * HOGWILD applies updates immediately with no locking; MINIBATCH reads the
+ * tables as they stood at the start of each batch of `minibatch` positions,
+ * sums the increments per row exactly (fixed point, order independent) and
+ * applies them at the end of the batch.  *loss (device double) receives the
+ * summed pair loss -log sigma(s+) - sum log sigma(-s_k).
+ * Workspace: felog_train_workspace_bytes(...). */
+size_t felog_train_workspace_bytes(int64_t n_walks, int32_t L, int32_t n,
+                                   const felog_train_params *tp);
+felog_status felog_train(const int32_t *walks, int64_t n_walks, int32_t L, int32_t n,
+                         const felog_train_params *tp, const uint64_t *thr, const int32_t *alias,
+                         const uint64_t *S, uint64_t seed, int32_t round, int64_t clock_base,
+                         void *phi_in, void *phi_out, double *loss, void *workspace,
+                         size_t workspace_bytes, void *stream);
+
+/* Feedback (Eq. 4, Eq. 5): Psi(v) = mean cosine of phi_in[v] with a subset of
+ * min(deg, ks) neighbours (all of them if deg <= ks, else ks distinct CSR
+ * positions by Floyd's algorithm keyed Philox(x0=s, x1=v, x2=round, 1),
+ * sorted ascending), in binary64 with a fixed summation order (partials over
+ * i = l mod 32, then a xor butterfly 16..1).  Evaluated nodes: those with
+ * active_in[v] and deg > 0 (every deg > 0 node when reactivate).
+ * active_out[v] = evaluated && Psi < mu (feedback enabled) or deg > 0
+ * (disabled).  psi (device double[n], may be NULL) gets Psi or NaN for
+ * nodes not evaluated; *n_next (device int32) the size of the next set. */
+felog_status felog_feedback(const felog_csr *g, const void *phi_in, int32_t dim, int32_t precision,
+                            const felog_feedback_params *fp, uint64_t seed, int32_t round,
+                            const uint8_t *active_in, uint8_t *active_out, double *psi,
+                            int32_t *n_next, void *stream);
+
+/* Algorithm 1 end to end on one GPU: V_a <- non-isolated nodes; for each
+ * round: compact V_a, walk (counts fused), noise table, train, feedback,
+ * until V_a is empty or max_rounds.  lr_total_tokens <= 0 selects
+ * max_rounds * wpr * |non-isolated| * L.  phi_in / phi_out (device
+ * [n][dim]) are initialised by the call; phi_in is the embedding.
+ * stats (host, max_rounds entries, may be NULL) and *rounds_run (host, may be
+ * NULL) are filled; the call synchronises `stream` once per round to read
+ * |V_a|.  Workspace: felog_embed_workspace_bytes(...). */
+size_t felog_embed_workspace_bytes(int32_t n, const felog_walk_params *wp,
+                                   const felog_train_params *tp);
+felog_status felog_embed(const felog_csr *g, const felog_walk_params *wp,
+                         const felog_train_params *tp, const felog_feedback_params *fp,
+                         uint64_t seed, void *phi_in, void *phi_out, felog_round_stats *stats,
+                         int32_t *rounds_run, void *workspace, size_t workspace_bytes,
+                         void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FELOG_H_ */

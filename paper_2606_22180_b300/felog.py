@@ -1,0 +1,311 @@
+"""Python binding of ``libfelog.so`` (the C ABI declared in ``include/felog.h``).
+
+Argument marshalling only: every step runs in the library's CUDA kernels.
+PyTorch supplies device memory and the current CUDA stream.  There is no CPU
+fallback; if the library or a CUDA device is missing, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libfelog.so")
+
+FELOG_OK = 0
+FELOG_SGNS_HOGWILD, FELOG_SGNS_MINIBATCH = 0, 1
+FELOG_FP32, FELOG_BF16_SR = 0, 1
+
+# exported symbols (the boundary); tests check each one is present
+SYMBOLS = [
+    "felog_status_string", "felog_last_cuda_error",
+    "felog_compact_workspace_bytes", "felog_compact_active",
+    "felog_walk", "felog_count",
+    "felog_noise_workspace_bytes", "felog_noise_table",
+    "felog_init_tables",
+    "felog_train_workspace_bytes", "felog_train",
+    "felog_feedback",
+    "felog_embed_workspace_bytes", "felog_embed",
+]
+
+
+class FelogError(RuntimeError):
+    pass
+
+
+class _Csr(ctypes.Structure):
+    _fields_ = [("offsets", ctypes.c_void_p), ("cols", ctypes.c_void_p), ("n", ctypes.c_int32),
+                ("nnz", ctypes.c_int64)]
+
+
+class _WalkParams(ctypes.Structure):
+    _fields_ = [("length", ctypes.c_int32), ("walks_per_round", ctypes.c_int32)]
+
+
+class _TrainParams(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("window", ctypes.c_int32), ("negatives", ctypes.c_int32),
+                ("lr0", ctypes.c_float), ("lr_total_tokens", ctypes.c_int64),
+                ("mode", ctypes.c_int32), ("minibatch", ctypes.c_int32),
+                ("precision", ctypes.c_int32)]
+
+
+class _FeedbackParams(ctypes.Structure):
+    _fields_ = [("enabled", ctypes.c_int32), ("mu", ctypes.c_double), ("ks", ctypes.c_int32),
+                ("max_rounds", ctypes.c_int32), ("reactivate", ctypes.c_int32)]
+
+
+class RoundStats(ctypes.Structure):
+    _fields_ = [("round", ctypes.c_int32), ("n_active", ctypes.c_int32), ("n_next", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("tokens", ctypes.c_int64),
+                ("walk_steps", ctypes.c_int64), ("loss", ctypes.c_double),
+                ("ms_walk", ctypes.c_float), ("ms_noise", ctypes.c_float),
+                ("ms_train", ctypes.c_float), ("ms_feedback", ctypes.c_float)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load the CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise FelogError(f"{LIB_PATH} is missing: build it with python -m paper_2606_22180_b300.build")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, i32, i64, u64, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+    sz = ctypes.c_size_t
+    st = ctypes.c_int
+    sig = {
+        "felog_status_string": (ctypes.c_char_p, [st]),
+        "felog_last_cuda_error": (ctypes.c_char_p, []),
+        "felog_compact_workspace_bytes": (sz, [i32]),
+        "felog_compact_active": (st, [P, i32, P, P, P, sz, P]),
+        "felog_walk": (st, [P, P, i32, P, u64, i32, P, P, P]),
+        "felog_count": (st, [P, i64, i32, P, P]),
+        "felog_noise_workspace_bytes": (sz, [i32]),
+        "felog_noise_table": (st, [P, i32, P, P, P, P, sz, P]),
+        "felog_init_tables": (st, [i32, i32, i32, u64, P, P, P]),
+        "felog_train_workspace_bytes": (sz, [i64, i32, i32, P]),
+        "felog_train": (st, [P, i64, i32, i32, P, P, P, P, u64, i32, i64, P, P, P, P, sz, P]),
+        "felog_feedback": (st, [P, P, i32, i32, P, u64, i32, P, P, P, P, P]),
+        "felog_embed_workspace_bytes": (sz, [i32, P, P]),
+        "felog_embed": (st, [P, P, P, P, u64, P, P, P, P, P, sz, P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int, what: str) -> None:
+    if status != FELOG_OK:
+        lib = load()
+        msg = lib.felog_status_string(status).decode()
+        cuda = lib.felog_last_cuda_error().decode()
+        raise FelogError(f"{what}: {msg}" + (f" ({cuda})" if cuda else ""))
+
+
+def _require_cuda(*tensors) -> None:
+    if not torch.cuda.is_available():
+        raise FelogError("no CUDA device: the FeLoG path has no CPU fallback")
+    for t in tensors:
+        if t is not None and not t.is_cuda:
+            raise FelogError("tensors passed to the FeLoG library must live on the GPU")
+        if t is not None and not t.is_contiguous():
+            raise FelogError("tensors passed to the FeLoG library must be contiguous")
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _workspace(nbytes: int, device) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+@dataclasses.dataclass
+class DeviceGraph:
+    """An undirected CSR resident on the GPU (int32 offsets and cols)."""
+
+    offsets: torch.Tensor
+    cols: torch.Tensor
+
+    @property
+    def n(self) -> int:
+        return int(self.offsets.numel() - 1)
+
+    @property
+    def nnz(self) -> int:
+        return int(self.cols.numel())
+
+    @classmethod
+    def from_host(cls, csr, device="cuda") -> "DeviceGraph":
+        off = torch.as_tensor(csr.offsets, dtype=torch.int32).to(device)
+        cols = torch.as_tensor(csr.cols, dtype=torch.int32).to(device)
+        return cls(off, cols)
+
+    def _c(self) -> _Csr:
+        _require_cuda(self.offsets, self.cols)
+        return _Csr(self.offsets.data_ptr(), self.cols.data_ptr() if self.nnz else 0, self.n, self.nnz)
+
+
+def table_dtype(precision: int) -> torch.dtype:
+    return torch.float32 if precision == FELOG_FP32 else torch.bfloat16
+
+
+# ---------------------------------------------------------------------------
+# One wrapper per C entry point, with the same name.
+# ---------------------------------------------------------------------------
+
+def felog_compact_active(active: torch.Tensor):
+    """Ascending indices of the nonzero flags; returns (starts[n], n_active device int32[1])."""
+    _require_cuda(active)
+    lib = load()
+    n = active.numel()
+    starts = torch.empty(max(n, 1), dtype=torch.int32, device=active.device)
+    n_active = torch.empty(1, dtype=torch.int32, device=active.device)
+    ws = _workspace(lib.felog_compact_workspace_bytes(n), active.device)
+    _check(lib.felog_compact_active(_ptr(active), n, _ptr(starts), _ptr(n_active), _ptr(ws),
+                                    ws.numel(), _stream()), "felog_compact_active")
+    return starts, n_active
+
+
+def felog_walk(g: DeviceGraph, starts: torch.Tensor, n_starts: int, length: int,
+               walks_per_round: int, seed: int, round_: int, counts: torch.Tensor | None = None,
+               out: torch.Tensor | None = None) -> torch.Tensor:
+    """Uniform truncated walks; returns int32 [n_starts * walks_per_round, length]."""
+    _require_cuda(starts, counts, out)
+    lib = load()
+    if out is None:
+        out = torch.empty((n_starts * walks_per_round, length), dtype=torch.int32, device=starts.device)
+    wp = _WalkParams(length, walks_per_round)
+    csr = g._c()
+    _check(lib.felog_walk(ctypes.byref(csr), _ptr(starts), n_starts, ctypes.byref(wp), seed, round_,
+                          _ptr(out), _ptr(counts), _stream()), "felog_walk")
+    return out
+
+
+def felog_count(tokens: torch.Tensor, n: int, counts: torch.Tensor | None = None) -> torch.Tensor:
+    _require_cuda(tokens, counts)
+    lib = load()
+    if counts is None:
+        counts = torch.zeros(n, dtype=torch.int32, device=tokens.device)
+    _check(lib.felog_count(_ptr(tokens), tokens.numel(), n, _ptr(counts), _stream()), "felog_count")
+    return counts
+
+
+def felog_noise_table(counts: torch.Tensor):
+    """Alias table of the unigram^0.75 distribution: (thr uint64 as int64, alias int32, S [1])."""
+    _require_cuda(counts)
+    lib = load()
+    n = counts.numel()
+    dev = counts.device
+    thr = torch.empty(n, dtype=torch.int64, device=dev)
+    alias = torch.empty(n, dtype=torch.int32, device=dev)
+    S = torch.empty(1, dtype=torch.int64, device=dev)
+    ws = _workspace(lib.felog_noise_workspace_bytes(n), dev)
+    _check(lib.felog_noise_table(_ptr(counts), n, _ptr(thr), _ptr(alias), _ptr(S), _ptr(ws),
+                                 ws.numel(), _stream()), "felog_noise_table")
+    return thr, alias, S
+
+
+def felog_init_tables(n: int, dim: int, precision: int, seed: int, device="cuda"):
+    _require_cuda()
+    lib = load()
+    dt = table_dtype(precision)
+    phi_in = torch.empty((n, dim), dtype=dt, device=device)
+    phi_out = torch.empty((n, dim), dtype=dt, device=device)
+    _check(lib.felog_init_tables(n, dim, precision, seed, _ptr(phi_in), _ptr(phi_out), _stream()),
+           "felog_init_tables")
+    return phi_in, phi_out
+
+
+def train_params(dim=128, window=10, negatives=5, lr0=0.025, lr_total_tokens=1, mode=FELOG_SGNS_HOGWILD,
+                 minibatch=4096, precision=FELOG_FP32) -> _TrainParams:
+    return _TrainParams(dim, window, negatives, lr0, lr_total_tokens, mode, minibatch, precision)
+
+
+def feedback_params(enabled=True, mu=0.65, ks=8, max_rounds=10, reactivate=False) -> _FeedbackParams:
+    return _FeedbackParams(int(enabled), mu, ks, max_rounds, int(reactivate))
+
+
+def felog_train(walks: torch.Tensor, n: int, tp: _TrainParams, thr: torch.Tensor, alias: torch.Tensor,
+                S: torch.Tensor, seed: int, round_: int, clock_base: int, phi_in: torch.Tensor,
+                phi_out: torch.Tensor, loss: torch.Tensor | None = None,
+                workspace: torch.Tensor | None = None) -> torch.Tensor:
+    """SGNS over walks [n_walks, L]; updates the tables in place; returns loss (device f64 [1])."""
+    _require_cuda(walks, thr, alias, S, phi_in, phi_out, loss, workspace)
+    lib = load()
+    n_walks, L = walks.shape
+    if loss is None:
+        loss = torch.empty(1, dtype=torch.float64, device=walks.device)
+    need = lib.felog_train_workspace_bytes(n_walks, L, n, ctypes.byref(tp))
+    if workspace is None or workspace.numel() < need:
+        workspace = _workspace(need, walks.device)
+    _check(lib.felog_train(_ptr(walks), n_walks, L, n, ctypes.byref(tp), _ptr(thr), _ptr(alias),
+                           _ptr(S), seed, round_, clock_base, _ptr(phi_in), _ptr(phi_out), _ptr(loss),
+                           _ptr(workspace), workspace.numel(), _stream()), "felog_train")
+    return loss
+
+
+def felog_feedback(g: DeviceGraph, phi_in: torch.Tensor, precision: int, fp: _FeedbackParams,
+                   seed: int, round_: int, active_in: torch.Tensor, want_psi: bool = True):
+    """Psi and the next active set; returns (psi f64 [n] or None, active_out u8 [n], n_next [1])."""
+    _require_cuda(phi_in, active_in)
+    lib = load()
+    n = g.n
+    dev = phi_in.device
+    active_out = torch.empty(n, dtype=torch.uint8, device=dev)
+    psi = torch.empty(n, dtype=torch.float64, device=dev) if want_psi else None
+    n_next = torch.empty(1, dtype=torch.int32, device=dev)
+    csr = g._c()
+    _check(lib.felog_feedback(ctypes.byref(csr), _ptr(phi_in), phi_in.shape[1], precision,
+                              ctypes.byref(fp), seed, round_, _ptr(active_in), _ptr(active_out),
+                              _ptr(psi), _ptr(n_next), _stream()), "felog_feedback")
+    return psi, active_out, n_next
+
+
+def embed_workspace_bytes(n: int, length: int, walks_per_round: int, tp: _TrainParams) -> int:
+    lib = load()
+    wp = _WalkParams(length, walks_per_round)
+    return int(lib.felog_embed_workspace_bytes(n, ctypes.byref(wp), ctypes.byref(tp)))
+
+
+def felog_embed(g: DeviceGraph, length: int, walks_per_round: int, tp: _TrainParams,
+                fp: _FeedbackParams, seed: int, phi_in: torch.Tensor | None = None,
+                phi_out: torch.Tensor | None = None, workspace: torch.Tensor | None = None):
+    """Algorithm 1 end to end; returns (phi_in, phi_out, [RoundStats dicts])."""
+    _require_cuda(phi_in, phi_out, workspace)
+    lib = load()
+    dev = g.offsets.device
+    dt = table_dtype(tp.precision)
+    if phi_in is None:
+        phi_in = torch.empty((g.n, tp.dim), dtype=dt, device=dev)
+    if phi_out is None:
+        phi_out = torch.empty((g.n, tp.dim), dtype=dt, device=dev)
+    wp = _WalkParams(length, walks_per_round)
+    need = lib.felog_embed_workspace_bytes(g.n, ctypes.byref(wp), ctypes.byref(tp))
+    if need == 0:
+        raise FelogError("felog_embed: invalid parameters")
+    if workspace is None or workspace.numel() < need:
+        workspace = _workspace(need, dev)
+    stats = (RoundStats * max(fp.max_rounds, 1))()
+    rounds = ctypes.c_int32(0)
+    csr = g._c()
+    _check(lib.felog_embed(ctypes.byref(csr), ctypes.byref(wp), ctypes.byref(tp), ctypes.byref(fp),
+                           seed, _ptr(phi_in), _ptr(phi_out), stats, ctypes.byref(rounds),
+                           _ptr(workspace), workspace.numel(), _stream()), "felog_embed")
+    return phi_in, phi_out, [stats[i].as_dict() for i in range(rounds.value)]

@@ -1,0 +1,362 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Bit-exact: walks, corpus counts, active-set compaction, the alias table,
+table initialisation, Psi and the next active set (given the same table).
+Within 1e-5 relative (Frobenius norm of the tables, and the loss): the
+synchronous-minibatch SGNS (float on the GPU, binary64 in the oracle).
+"""
+import zlib
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2606_22180_b300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+SEED = 11
+
+
+@pytest.fixture(scope="module")
+def fl():
+    from paper_2606_22180_b300 import build, felog
+
+    build.build()
+    felog.load()
+    return felog
+
+
+@pytest.fixture(scope="module")
+def sbm():
+    g, _ = inputs.workload_sbm1000(0)
+    return g
+
+
+@pytest.fixture(scope="module")
+def rmat14():
+    return inputs.rmat(14, 16, seed=5)
+
+
+def _dev(a, dtype=None):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype).cuda()
+
+
+def _live(g):
+    return np.nonzero(g.degrees() > 0)[0].astype(np.int32)
+
+
+# ---------------------------------------------------------------------------
+# compaction
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [1, 31, 4095, 4096, 4097, 100_003, (1 << 20) + 3])
+@pytest.mark.parametrize("density", [0.0, 0.37, 1.0])
+def test_compact_active(fl, n, density):
+    rng = np.random.default_rng(n)
+    flags = (rng.random(n) < density).astype(np.uint8)
+    starts, cnt = fl.felog_compact_active(_dev(flags))
+    k = int(cnt.item())
+    ref = np.nonzero(flags)[0]
+    assert k == ref.shape[0]
+    assert np.array_equal(starts[:k].cpu().numpy(), ref)
+
+
+# ---------------------------------------------------------------------------
+# walks + counts
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("L,wpr,rnd", [(40, 1, 0), (40, 3, 7), (37, 2, 1), (1, 1, 0), (6, 1, 65535)])
+def test_walks_bit_exact_sbm(fl, orc, sbm, L, wpr, rnd):
+    g = sbm
+    dg = fl.DeviceGraph.from_host(g)
+    starts = _live(g)
+    counts = torch.zeros(g.n, dtype=torch.int32, device="cuda")
+    W = fl.felog_walk(dg, _dev(starts), starts.shape[0], L, wpr, SEED, rnd, counts=counts)
+    ref = orc.walk(g.offsets, g.cols, starts, L, wpr, SEED, rnd)
+    assert np.array_equal(W.cpu().numpy(), ref)
+    assert np.array_equal(counts.cpu().numpy().astype(np.uint32), orc.counts(ref, g.n))
+
+
+def test_walks_isolated_and_empty(fl, orc):
+    from conftest import tiny_graph
+
+    g = tiny_graph("with_isolated")
+    dg = fl.DeviceGraph.from_host(g)
+    starts = np.array([3, 0, 4, 2], np.int32)
+    W = fl.felog_walk(dg, _dev(starts), 4, 9, 2, 5, 3)
+    assert np.array_equal(W.cpu().numpy(), orc.walk(g.offsets, g.cols, starts, 9, 2, 5, 3))
+    out = fl.felog_walk(dg, _dev(starts), 0, 9, 2, 5, 3)
+    assert out.shape == (0, 9)
+
+
+def test_walks_rmat_ragged(fl, orc, rmat14):
+    g = rmat14
+    dg = fl.DeviceGraph.from_host(g)
+    starts = _live(g)
+    W = fl.felog_walk(dg, _dev(starts), starts.shape[0], 23, 1, SEED, 2)
+    ref = orc.walk(g.offsets, g.cols, starts, 23, 1, SEED, 2)
+    assert np.array_equal(W.cpu().numpy(), ref)
+
+
+@pytest.mark.slow
+def test_walks_rmat20_sampled(fl, orc):
+    """Full-size R-MAT scale 20, the walk launch of one round (L = 80); rows
+    sampled and recomputed one by one by the oracle."""
+    g = inputs.workload_rmat(20, 1)
+    dg = fl.DeviceGraph.from_host(g)
+    starts = _live(g)
+    counts = torch.zeros(g.n, dtype=torch.int32, device="cuda")
+    W = fl.felog_walk(dg, _dev(starts), starts.shape[0], 80, 1, SEED, 4, counts=counts)
+    rng = np.random.default_rng(0)
+    rows = np.sort(rng.choice(starts.shape[0], 4096, replace=False))
+    ref = orc.walk(g.offsets, g.cols, starts[rows], 80, 1, SEED, 4)
+    assert np.array_equal(W[torch.as_tensor(rows).cuda()].cpu().numpy(), ref)
+    # the fused counts equal the oracle's histogram of the whole round
+    full = orc.counts(orc.walk(g.offsets, g.cols, starts, 80, 1, SEED, 4), g.n)
+    assert np.array_equal(counts.cpu().numpy().astype(np.uint32), full)
+
+
+# ---------------------------------------------------------------------------
+# noise table
+# ---------------------------------------------------------------------------
+def _noise_case(name):
+    rng = np.random.default_rng(zlib.crc32(name.encode()))
+    if name == "zipf":
+        c = rng.zipf(1.6, size=50_000).astype(np.uint32)
+        c[rng.random(c.shape[0]) < 0.2] = 0
+    elif name == "equal":
+        c = np.full(4099, 7, np.uint32)
+    elif name == "single":
+        c = np.zeros(777, np.uint32)
+        c[500] = 9
+    elif name == "zero":
+        c = np.zeros(100, np.uint32)
+    elif name == "wide":  # prefix sums beyond 2^64
+        n = 1 << 20
+        c = np.ones(n, np.uint32)
+        c[n // 2:] = np.uint32(2 ** 31)
+        c = c[rng.permutation(n)]
+    elif name == "tiny":
+        c = np.array([3], np.uint32)
+    return c
+
+
+@pytest.mark.parametrize("name", ["zipf", "equal", "single", "zero", "wide", "tiny"])
+def test_noise_table_bit_exact(fl, orc, name):
+    c = _noise_case(name)
+    thr, alias, S = fl.felog_noise_table(_dev(c.astype(np.int32)))
+    W, thr_ref, alias_ref, S_ref = orc.noise_table(c)
+    assert int(S.item()) == S_ref
+    if S_ref == 0:
+        return
+    assert np.array_equal(thr.cpu().numpy().astype(np.uint64), thr_ref)
+    assert np.array_equal(alias.cpu().numpy(), alias_ref)
+
+
+def test_noise_table_from_walk_counts(fl, orc, sbm):
+    dg = fl.DeviceGraph.from_host(sbm)
+    starts = _live(sbm)
+    counts = torch.zeros(sbm.n, dtype=torch.int32, device="cuda")
+    fl.felog_walk(dg, _dev(starts), starts.shape[0], 40, 1, 3, 0, counts=counts)
+    thr, alias, S = fl.felog_noise_table(counts)
+    ref_counts = orc.counts(orc.walk(sbm.offsets, sbm.cols, starts, 40, 1, 3, 0), sbm.n)
+    _, thr_ref, alias_ref, S_ref = orc.noise_table(ref_counts)
+    assert int(S.item()) == S_ref
+    assert np.array_equal(thr.cpu().numpy().astype(np.uint64), thr_ref)
+    assert np.array_equal(alias.cpu().numpy(), alias_ref)
+
+
+# ---------------------------------------------------------------------------
+# table initialisation
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dim", [32, 64, 128, 256])
+def test_init_tables(fl, orc, dim):
+    n = 1000
+    pi, po = fl.felog_init_tables(n, dim, fl.FELOG_FP32, 123)
+    ri, ro = orc.init_tables(n, dim, 123)
+    assert np.array_equal(pi.cpu().numpy(), ri.astype(np.float32))
+    assert (po == 0).all()
+    bi, bo = fl.felog_init_tables(n, dim, fl.FELOG_BF16_SR, 123)
+    assert torch.equal(bi, torch.from_numpy(ri.astype(np.float32)).to(torch.bfloat16).cuda())
+
+
+# ---------------------------------------------------------------------------
+# SGNS, deterministic minibatch: within 1e-5 of the binary64 oracle
+# ---------------------------------------------------------------------------
+def _round_inputs(orc, g, L, seed, rnd, n_starts=None):
+    starts = _live(g)[:n_starts]
+    W = orc.walk(g.offsets, g.cols, starts, L, 1, seed, rnd)
+    _, thr, alias, S = orc.noise_table(orc.counts(W, g.n))
+    return W, thr, alias, S
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _gpu_train(fl, W, thr, alias, S, g_n, tp, seed, rnd, clock, pi, po):
+    loss = fl.felog_train(_dev(W), g_n, tp, _dev(thr.astype(np.int64)), _dev(alias),
+                          _dev(np.array([S], np.int64)), seed, rnd, clock, pi, po)
+    return float(loss.item())
+
+
+@pytest.mark.parametrize("dim,window,K,B", [(64, 5, 5, 4096), (32, 3, 2, 400), (128, 10, 5, 777),
+                                            (64, 5, 15, 1000)])
+def test_minibatch_sgns_parity_one_round(fl, orc, sbm, dim, window, K, B):
+    g = sbm
+    L = 40
+    W, thr, alias, S = _round_inputs(orc, g, L, SEED, 0)
+    T = 10 * W.size
+    ri, ro = orc.init_tables(g.n, dim, SEED)
+    # give phi_out a nonzero start so every term of Eq. 2 is exercised
+    ro[:] = ri[np.roll(np.arange(g.n), 1)] * 0.5
+    ri = ri.astype(np.float32).astype(np.float64)
+    ro = ro.astype(np.float32).astype(np.float64)
+    pi = torch.from_numpy(ri.astype(np.float32)).cuda()
+    po = torch.from_numpy(ro.astype(np.float32)).cuda()
+    tp = fl.train_params(dim, window, K, 0.025, T, fl.FELOG_SGNS_MINIBATCH, B, fl.FELOG_FP32)
+    lg = _gpu_train(fl, W, thr, alias, S, g.n, tp, SEED, 0, 1234, pi, po)
+    lo = orc.sgns_minibatch(W, g.n, dim, window, K, 0.025, T, B, thr, alias, S, SEED, 0, 1234, ri, ro)
+    assert abs(lg - lo) / lo < 1e-5
+    assert _rel(pi.double().cpu().numpy(), ri) < 1e-5
+    assert _rel(po.double().cpu().numpy(), ro) < 1e-5
+
+
+def test_minibatch_sgns_parity_every_batch(fl, orc, sbm):
+    """Batches of 400 positions (10 walks): compare after each of the first
+    batches and at the end of the round."""
+    g = sbm
+    L, dim, B = 40, 64, 400
+    W, thr, alias, S = _round_inputs(orc, g, L, 5, 2)
+    T = 10 * W.size
+    ri0, ro0 = orc.init_tables(g.n, dim, 5)
+    for k in [1, 2, 3, 7, W.shape[0] // 10]:
+        Wk = W[: 10 * k]
+        pi = torch.from_numpy(ri0.astype(np.float32)).cuda()
+        po = torch.from_numpy(ro0.astype(np.float32)).cuda()
+        ri, ro = ri0.copy(), ro0.copy()
+        tp = fl.train_params(dim, 5, 5, 0.025, T, fl.FELOG_SGNS_MINIBATCH, B, fl.FELOG_FP32)
+        lg = _gpu_train(fl, Wk, thr, alias, S, g.n, tp, 5, 2, 0, pi, po)
+        lo = orc.sgns_minibatch(Wk, g.n, dim, 5, 5, 0.025, T, B, thr, alias, S, 5, 2, 0, ri, ro)
+        assert abs(lg - lo) / lo < 1e-5, k
+        assert _rel(pi.double().cpu().numpy(), ri) < 1e-5, k
+        assert _rel(po.double().cpu().numpy(), ro) < 1e-5, k
+
+
+def test_minibatch_sgns_is_bitwise_reproducible(fl, orc, sbm):
+    g = sbm
+    W, thr, alias, S = _round_inputs(orc, g, 40, 3, 0)
+    tp = fl.train_params(64, 5, 5, 0.025, 10 * W.size, fl.FELOG_SGNS_MINIBATCH, 512, fl.FELOG_FP32)
+    outs = []
+    for _ in range(2):
+        pi, po = fl.felog_init_tables(g.n, 64, fl.FELOG_FP32, 3)
+        lg = _gpu_train(fl, W, thr, alias, S, g.n, tp, 3, 0, 0, pi, po)
+        outs.append((lg, pi.clone(), po.clone()))
+    assert outs[0][0] == outs[1][0]
+    assert torch.equal(outs[0][1], outs[1][1]) and torch.equal(outs[0][2], outs[1][2])
+
+
+@pytest.mark.slow
+def test_minibatch_sgns_parity_rmat20_prefix(fl, orc):
+    """R-MAT scale 20 at the full-size parameters (L 80, window 10, K 5,
+    d 128): a prefix of 2^13 walks of one round against the oracle, with the
+    noise table of the whole round's corpus."""
+    g = inputs.workload_rmat(20, 1)
+    starts = _live(g)
+    W_all = orc.walk(g.offsets, g.cols, starts, 80, 1, SEED, 0)
+    W = W_all[: 1 << 13]
+    _, thr, alias, S = orc.noise_table(orc.counts(W_all, g.n))
+    del W_all
+    ri, ro = orc.init_tables(g.n, 128, SEED)
+    pi = torch.from_numpy(ri.astype(np.float32)).cuda()
+    po = torch.from_numpy(ro.astype(np.float32)).cuda()
+    T = 10 * starts.shape[0] * 80
+    tp = fl.train_params(128, 10, 5, 0.025, T, fl.FELOG_SGNS_MINIBATCH, 4096, fl.FELOG_FP32)
+    lg = _gpu_train(fl, W, thr, alias, S, g.n, tp, SEED, 0, 0, pi, po)
+    lo = orc.sgns_minibatch(W, g.n, 128, 10, 5, 0.025, T, 4096, thr, alias, S, SEED, 0, 0, ri, ro)
+    assert abs(lg - lo) / lo < 1e-5
+    assert _rel(pi.double().cpu().numpy(), ri) < 1e-5
+    assert _rel(po.double().cpu().numpy(), ro) < 1e-5
+
+
+# ---------------------------------------------------------------------------
+# Psi and the next active set: bit-exact given the same table
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("reactivate,enabled", [(False, True), (True, True), (False, False)])
+def test_feedback_bit_exact(fl, orc, rmat14, precision, reactivate, enabled):
+    g = rmat14
+    rng = np.random.default_rng(4)
+    dim = 64
+    phi = (rng.normal(size=(g.n, dim)) + 0.7).astype(np.float32)
+    phi[rng.random(g.n) < 0.01] = 0  # zero rows give cos 0
+    pt = torch.from_numpy(phi).cuda()
+    if precision == 1:
+        pt = pt.to(torch.bfloat16)
+    phi64 = pt.double().cpu().numpy()
+    live = (g.degrees() > 0).astype(np.uint8)
+    active = live * (rng.random(g.n) < 0.7).astype(np.uint8)
+    dg = fl.DeviceGraph.from_host(g)
+    for rnd, mu in [(0, 0.65), (3, 0.9)]:
+        fp = fl.feedback_params(enabled, mu, 8, 10, reactivate)
+        psi, nxt, cnt = fl.felog_feedback(dg, pt, precision, fp, SEED, rnd, _dev(active))
+        psi_ref, nxt_ref, cnt_ref = orc.feedback(g.offsets, g.cols, phi64, active, enabled, mu, 8,
+                                                 reactivate, SEED, rnd)
+        psi = psi.cpu().numpy()
+        assert np.array_equal(np.isnan(psi), np.isnan(psi_ref))
+        ok = ~np.isnan(psi_ref)
+        assert np.array_equal(psi[ok].view(np.int64), psi_ref[ok].view(np.int64))
+        assert np.array_equal(nxt.cpu().numpy(), nxt_ref)
+        assert int(cnt.item()) == cnt_ref
+
+
+@pytest.mark.parametrize("ks", [1, 5, 32])
+def test_feedback_subset_sizes(fl, orc, rmat14, ks):
+    g = rmat14
+    rng = np.random.default_rng(ks)
+    phi = rng.normal(size=(g.n, 32)).astype(np.float32)
+    active = (g.degrees() > 0).astype(np.uint8)
+    fp = fl.feedback_params(True, 0.1, ks, 10, False)
+    psi, nxt, _ = fl.felog_feedback(fl.DeviceGraph.from_host(g), torch.from_numpy(phi).cuda(), 0, fp,
+                                    7, 1, _dev(active))
+    psi_ref, nxt_ref, _ = orc.feedback(g.offsets, g.cols, phi.astype(np.float64), active, True, 0.1, ks,
+                                       False, 7, 1)
+    ok = ~np.isnan(psi_ref)
+    assert np.array_equal(psi.cpu().numpy()[ok].view(np.int64), psi_ref[ok].view(np.int64))
+    assert np.array_equal(nxt.cpu().numpy(), nxt_ref)
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 1 end to end (deterministic SGNS): same schedule as the oracle
+# ---------------------------------------------------------------------------
+def test_embed_minibatch_tracks_oracle(fl, orc, sbm):
+    g = sbm
+    dim, L, R = 32, 20, 4
+    tp = fl.train_params(dim, 3, 3, 0.025, 0, fl.FELOG_SGNS_MINIBATCH, 1000, fl.FELOG_FP32)
+    fp = fl.feedback_params(False, 0.65, 8, R, False)
+    pi, po, st = fl.felog_embed(fl.DeviceGraph.from_host(g), L, 1, tp, fp, 9)
+    ri, ro, rst = orc.embed(g.offsets, g.cols, L, 1, dim, 3, 3, 0.025, False, 0.65, 8, R, False, 9,
+                            mode="minibatch", B=1000)
+    assert len(st) == rst.shape[0] == R
+    for r in range(R):
+        assert st[r]["n_active"] == rst[r, 0] and st[r]["tokens"] == rst[r, 1]
+        assert abs(st[r]["loss"] - rst[r, 2]) / rst[r, 2] < 1e-5
+    assert _rel(pi.double().cpu().numpy(), ri) < 1e-5
+    assert _rel(po.double().cpu().numpy(), ro) < 1e-5
+
+
+def test_embed_feedback_rounds(fl, orc, sbm):
+    """FeeST rounds: |V_a| per round matches the oracle; a decision may flip
+    only where Psi sits within the table tolerance of mu."""
+    g = sbm
+    dim, L, R = 32, 20, 6
+    tp = fl.train_params(dim, 3, 3, 0.025, 0, fl.FELOG_SGNS_MINIBATCH, 1000, fl.FELOG_FP32)
+    fp = fl.feedback_params(True, 0.9, 8, R, False)
+    _, _, st = fl.felog_embed(fl.DeviceGraph.from_host(g), L, 1, tp, fp, 2)
+    _, _, rst = orc.embed(g.offsets, g.cols, L, 1, dim, 3, 3, 0.025, True, 0.9, 8, R, False, 2,
+                          mode="minibatch", B=1000)
+    got = [s["n_active"] for s in st]
+    ref = [int(x) for x in rst[:, 0]]
+    assert got[0] == ref[0]
+    assert len(got) == len(ref)
+    for a, b in zip(got, ref):
+        assert abs(a - b) <= max(2, 0.002 * g.n), (got, ref)

@@ -1,0 +1,52 @@
+"""Hogwild and BF16 forms against the serial oracle by link-prediction AUC
+on the 1,000-node planted partition (10 % of edges held out)."""
+import numpy as np
+import pytest
+
+from paper_2606_22180_b300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+L, DIM, W, K, R = 40, 64, 5, 5, 10
+
+
+@pytest.fixture(scope="module")
+def fl():
+    from paper_2606_22180_b300 import build, felog
+
+    build.build()
+    return felog
+
+
+@pytest.fixture(scope="module")
+def runs(fl, orc):
+    from paper_2606_22180_b300 import evaluate
+
+    res = []
+    for seed in range(5):
+        g, _ = inputs.workload_sbm1000(seed)
+        sp = inputs.link_split(g, 0.1, seed)
+        tr = sp.train
+        ri, _, _ = orc.embed(tr.offsets, tr.cols, L, 1, DIM, W, K, 0.025, False, 0.65, 8, R, False, seed)
+        a_or = orc.link_auc(ri, sp.pos, sp.neg)
+        dg = fl.DeviceGraph.from_host(tr)
+        fp = fl.feedback_params(False, 0.65, 8, R, False)
+        out = {"oracle": a_or}
+        for name, prec in [("hogwild", fl.FELOG_FP32), ("bf16", fl.FELOG_BF16_SR)]:
+            tp = fl.train_params(DIM, W, K, 0.025, 0, fl.FELOG_SGNS_HOGWILD, 4096, prec)
+            pi, _, _ = fl.felog_embed(dg, L, 1, tp, fp, seed)
+            out[name] = evaluate.link_auc(pi, sp.pos, sp.neg)
+        res.append(out)
+    return res
+
+
+def test_hogwild_auc_within_tolerance_of_serial_oracle(runs):
+    d = np.array([r["hogwild"] - r["oracle"] for r in runs])
+    print("hogwild - oracle AUC per seed:", d.round(4))
+    assert abs(d.mean()) <= 0.005
+
+
+def test_bf16_auc_within_tolerance_of_serial_oracle(runs):
+    d = np.array([r["bf16"] - r["oracle"] for r in runs])
+    print("bf16 - oracle AUC per seed:", d.round(4))
+    assert abs(d.mean()) <= 0.005

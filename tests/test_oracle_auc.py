@@ -25,3 +25,15 @@ def test_link_scores_are_dot_products(orc):
     pairs = rng.integers(0, 20, size=(15, 2)).astype(np.int32)
     ref = (phi[pairs[:, 0]] * phi[pairs[:, 1]]).sum(1)
     assert np.allclose(orc.link_scores(phi, pairs), ref, rtol=1e-14, atol=1e-14)
+
+
+def test_package_evaluator_matches_definition(orc):
+    """The rank-based AUC the benchmark uses equals the oracle's pair count."""
+    from paper_2606_22180_b300 import evaluate
+
+    rng = np.random.default_rng(3)
+    phi = rng.normal(size=(60, 8))
+    pos = rng.integers(0, 60, size=(40, 2)).astype(np.int32)
+    neg = rng.integers(0, 60, size=(45, 2)).astype(np.int32)
+    assert abs(evaluate.link_auc(phi, pos, neg) - orc.link_auc(phi, pos, neg)) < 1e-12
+    assert abs(evaluate.auc(np.array([1.0, 1.0]), np.array([1.0])) - 0.5) < 1e-15
