@@ -79,7 +79,10 @@ typedef enum {
 
 /* dim in {32, 64, 128, 256}; 1 <= window <= 16; 1 <= negatives <= 15;
  * learning rate lr0 * max(1e-4, 1 - t / lr_total_tokens) on the global token
- * clock t; minibatch = positions per synchronous batch (MINIBATCH mode). */
+ * clock t; minibatch = positions per synchronous batch (MINIBATCH mode);
+ * hogwild_rows_per_warp (HOGWILD mode, <= 0 selects 16): at most
+ * n / hogwild_rows_per_warp walks are trained concurrently, which bounds the
+ * staleness of lock-free updates on small graphs. */
 typedef struct {
     int32_t dim;
     int32_t window;
@@ -89,6 +92,7 @@ typedef struct {
     int32_t mode;      /* felog_sgns_mode */
     int32_t minibatch; /* >= 1 */
     int32_t precision; /* felog_precision */
+    int32_t hogwild_rows_per_warp;
 } felog_train_params;
 
 /* enabled = 0 is the plain method (every non-isolated node stays active);

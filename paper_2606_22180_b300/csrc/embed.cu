@@ -49,8 +49,17 @@ struct EmbedWorkspace {
     size_t train_bytes;
 };
 
+// lr_total_tokens <= 0 means "derive it"; size and validate with a placeholder
+static felog_train_params sizing_params(const felog_train_params *tp) {
+    felog_train_params t = *tp;
+    if (t.lr_total_tokens <= 0) t.lr_total_tokens = 1;
+    return t;
+}
+
 static EmbedWorkspace carve_embed(Carver &c, int32_t n, const felog_walk_params *wp,
-                                  const felog_train_params *tp) {
+                                  const felog_train_params *tp_in) {
+    const felog_train_params tpv = sizing_params(tp_in);
+    const felog_train_params *tp = &tpv;
     EmbedWorkspace w{};
     const size_t nn = n > 0 ? static_cast<size_t>(n) : 1;
     w.active[0] = c.take<uint8_t>(nn);
@@ -100,7 +109,8 @@ using namespace felog;
 extern "C" size_t felog_embed_workspace_bytes(int32_t n, const felog_walk_params *wp,
                                               const felog_train_params *tp) {
     if (n < 0 || !wp || !tp || wp->length < 1 || wp->walks_per_round < 1) return 0;
-    if (felog_train_workspace_bytes(1, wp->length, n, tp) == 0) return 0;
+    const felog_train_params tpv = sizing_params(tp);
+    if (felog_train_workspace_bytes(1, wp->length, n, &tpv) == 0) return 0;
     Carver c(nullptr, 0);
     carve_embed(c, n, wp, tp);
     return align_up(c.used, 256);

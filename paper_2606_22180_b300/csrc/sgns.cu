@@ -204,15 +204,142 @@ struct SgnsArgs {
 };
 
 // ----------------------------------------------------------------------------
-// HOGWILD: one warp per walk, updates applied immediately.
+// HOGWILD: one warp per walk; every increment is applied at once as an
+// atomic delta, so concurrent updates of a hot row commute instead of
+// overwriting each other (a lost-update race would drop most negative-sample
+// updates when many warps share few rows).  Rows are read through L2
+// (ld.global.cg) so a warp sees its own earlier deltas.
+//   float tables : vector red.global.add (one 16-byte reduction per lane);
+//   bf16 tables  : the lane rounds value-read + delta stochastically and adds
+//                  the resulting bf16 increment with a vector bf16 reduction
+//                  (see sr_increment).
 // ----------------------------------------------------------------------------
-template <int D, class T, int MAXT>
-__global__ void __launch_bounds__(kSgnsThreads)
+
+template <int EPL>
+__device__ __forceinline__ void load_row_cg(const float *__restrict__ p, float (&x)[EPL]) {
+    if constexpr (EPL == 1) {
+        x[0] = __ldcg(p);
+    } else if constexpr (EPL == 2) {
+        const float2 a = __ldcg(reinterpret_cast<const float2 *>(p));
+        x[0] = a.x; x[1] = a.y;
+    } else {
+#pragma unroll
+        for (int i = 0; i < EPL; i += 4) {
+            const float4 a = __ldcg(reinterpret_cast<const float4 *>(p + i));
+            x[i] = a.x; x[i + 1] = a.y; x[i + 2] = a.z; x[i + 3] = a.w;
+        }
+    }
+}
+
+template <int EPL>
+__device__ __forceinline__ void load_row_cg(const __nv_bfloat16 *__restrict__ p, float (&x)[EPL]) {
+    if constexpr (EPL == 1) {
+        x[0] = bf16_bits_to_float(__ldcg(reinterpret_cast<const unsigned short *>(p)));
+    } else if constexpr (EPL == 2) {
+        const uint32_t a = __ldcg(reinterpret_cast<const unsigned int *>(p));
+        x[0] = bf16_bits_to_float(a & 0xffffu); x[1] = bf16_bits_to_float(a >> 16);
+    } else if constexpr (EPL == 4) {
+        const uint2 a = __ldcg(reinterpret_cast<const uint2 *>(p));
+        x[0] = bf16_bits_to_float(a.x & 0xffffu); x[1] = bf16_bits_to_float(a.x >> 16);
+        x[2] = bf16_bits_to_float(a.y & 0xffffu); x[3] = bf16_bits_to_float(a.y >> 16);
+    } else {
+#pragma unroll
+        for (int i = 0; i < EPL; i += 8) {
+            const uint4 a = __ldcg(reinterpret_cast<const uint4 *>(p + i));
+            x[i + 0] = bf16_bits_to_float(a.x & 0xffffu); x[i + 1] = bf16_bits_to_float(a.x >> 16);
+            x[i + 2] = bf16_bits_to_float(a.y & 0xffffu); x[i + 3] = bf16_bits_to_float(a.y >> 16);
+            x[i + 4] = bf16_bits_to_float(a.z & 0xffffu); x[i + 5] = bf16_bits_to_float(a.z >> 16);
+            x[i + 6] = bf16_bits_to_float(a.w & 0xffffu); x[i + 7] = bf16_bits_to_float(a.w >> 16);
+        }
+    }
+}
+
+__device__ __forceinline__ void red_add_v4(float *p, float a, float b, float c, float d) {
+    asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b),
+                 "f"(c), "f"(d)
+                 : "memory");
+}
+__device__ __forceinline__ void red_add_v2(float *p, float a, float b) {
+    asm volatile("red.relaxed.gpu.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b) : "memory");
+}
+
+// float table: add delta; `cur` (the value last read) is not needed
+template <int EPL>
+__device__ __forceinline__ void add_delta(float *__restrict__ p, const float (&cur)[EPL],
+                                          const float (&delta)[EPL], uint32_t) {
+    (void)cur;
+    if constexpr (EPL == 1) {
+        atomicAdd(p, delta[0]);
+    } else if constexpr (EPL == 2) {
+        red_add_v2(p, delta[0], delta[1]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < EPL; i += 4) red_add_v4(p + i, delta[i], delta[i + 1], delta[i + 2], delta[i + 3]);
+    }
+}
+
+__device__ __forceinline__ uint32_t bf16_bits(float x) { return __float_as_uint(x) >> 16; }
+
+__device__ __forceinline__ void red_add_bf16x4(__nv_bfloat16 *p, uint32_t a, uint32_t b, uint32_t c,
+                                               uint32_t d) {
+    const unsigned short ha = static_cast<unsigned short>(a), hb = static_cast<unsigned short>(b);
+    const unsigned short hc = static_cast<unsigned short>(c), hd = static_cast<unsigned short>(d);
+    asm volatile("red.relaxed.gpu.global.add.noftz.v4.bf16 [%0], {%1, %2, %3, %4};" ::"l"(p), "h"(ha),
+                 "h"(hb), "h"(hc), "h"(hd)
+                 : "memory");
+}
+__device__ __forceinline__ void red_add_bf16x2(__nv_bfloat16 *p, uint32_t a, uint32_t b) {
+    const unsigned short ha = static_cast<unsigned short>(a), hb = static_cast<unsigned short>(b);
+    asm volatile("red.relaxed.gpu.global.add.noftz.v2.bf16 [%0], {%1, %2};" ::"l"(p), "h"(ha), "h"(hb)
+                 : "memory");
+}
+
+// bf16 increment of one element: the stochastically rounded new value
+// t = SR(cur + delta) relative to the value `cur` this lane read, returned as
+// the bf16 increment t - cur (exact when cur and t share a binade, rounded to
+// nearest otherwise).  Added atomically (round to nearest) to memory, it
+// reproduces SR(cur + delta) exactly when no other update intervened, and
+// loses no concurrent update when one did.
+__device__ __forceinline__ uint32_t sr_increment(float cur, float delta, uint32_t r16) {
+    const float t = bf16_bits_to_float(sr_bf16(cur + delta, r16));
+    return __bfloat16_as_ushort(__float2bfloat16_rn(t - cur));  // t - cur is exact in float
+}
+
+template <int EPL>
+__device__ __forceinline__ void add_delta(__nv_bfloat16 *__restrict__ p, const float (&cur)[EPL],
+                                          const float (&delta)[EPL], uint32_t r) {
+    uint32_t inc[EPL];
+    bool any = false;
+#pragma unroll
+    for (int i = 0; i < EPL; i += 2) {
+        inc[i] = sr_increment(cur[i], delta[i], r);
+        if (i + 1 < EPL) inc[i + 1] = sr_increment(cur[i + 1], delta[i + 1], r >> 16);
+        r = mix32(r + 0x9E3779B9u);
+    }
+#pragma unroll
+    for (int i = 0; i < EPL; ++i) any |= (inc[i] & 0x7fffu) != 0;
+    if (!any) return;  // every element rounded back to its current value
+    if constexpr (EPL == 1) {
+        atomicAdd(p, __ushort_as_bfloat16(static_cast<unsigned short>(inc[0])));
+    } else if constexpr (EPL == 2) {
+        red_add_bf16x2(p, inc[0], inc[1]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < EPL; i += 4) red_add_bf16x4(p + i, inc[i], inc[i + 1], inc[i + 2], inc[i + 3]);
+    }
+}
+
+// KFIX > 0: the number of negatives is a compile-time constant.
+template <int D, class T, int MAXT, int KFIX>
+__global__ void __launch_bounds__(kSgnsThreads, 3)
     k_sgns_hogwild(SgnsArgs a, T *__restrict__ phi_in, T *__restrict__ phi_out) {
     constexpr int EPL = D / 32;
+    constexpr int SRC_SHIFT = 5 - (MAXT == 8 ? 3 : 4);
+    constexpr bool kBf16 = !std::is_same<T, float>::value;
     extern __shared__ int32_t smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int W = a.window, K = a.K, L = a.L;
+    const int W = a.window, L = a.L;
+    const int K = KFIX > 0 ? KFIX : a.K;
     const int per_warp = L + 2 * W * K;
     int32_t *wk = smem + wib * per_warp;
     int32_t *negs = wk + L;
@@ -239,10 +366,15 @@ __global__ void __launch_bounds__(kSgnsThreads)
             __syncwarp();
             const float tclock = static_cast<float>(a.clock_base + wi * L + p);
             const float eta = a.lr0 * fmaxf(1e-4f, 1.0f - tclock * a.inv_T);
-            float oc[EPL];
+            float oc[EPL], oc0[EPL], doc[EPL];
             float closs = 0.f;
             T *oc_ptr = phi_out + static_cast<int64_t>(c) * D + lane * EPL;
-            load_row<EPL>(oc_ptr, oc);
+            load_row_cg<EPL>(oc_ptr, oc);
+#pragma unroll
+            for (int e = 0; e < EPL; ++e) {
+                oc0[e] = oc[e];
+                doc[e] = 0.f;
+            }
             for (int o = -W; o <= W; ++o) {
                 if (o == 0) continue;
                 const int pp = p + o;
@@ -263,12 +395,13 @@ __global__ void __launch_bounds__(kSgnsThreads)
                 }
                 float ix[EPL];
                 T *ix_ptr = phi_in + static_cast<int64_t>(x) * D + lane * EPL;
-                load_row<EPL>(ix_ptr, ix);
+                load_row_cg<EPL>(ix_ptr, ix);
                 float nr[MAXT][EPL];
 #pragma unroll
                 for (int t = 1; t < MAXT; ++t) {
-                    if (nid[t] >= 0) load_row<EPL>(phi_out + static_cast<int64_t>(nid[t]) * D + lane * EPL, nr[t]);
-                    else {
+                    if (nid[t] >= 0) {
+                        load_row_cg<EPL>(phi_out + static_cast<int64_t>(nid[t]) * D + lane * EPL, nr[t]);
+                    } else {
 #pragma unroll
                         for (int e = 0; e < EPL; ++e) nr[t][e] = 0.f;
                     }
@@ -284,7 +417,6 @@ __global__ void __launch_bounds__(kSgnsThreads)
                     pd[t] = s;
                 }
                 const float dot = reduce_scatter<MAXT>(pd, lane);
-                // this lane's target
                 int32_t my_id = nid[0];
 #pragma unroll
                 for (int t = 1; t < MAXT; ++t)
@@ -298,9 +430,9 @@ __global__ void __launch_bounds__(kSgnsThreads)
                 }
                 float gt[MAXT];
 #pragma unroll
-                for (int t = 0; t < MAXT; ++t) gt[t] = __shfl_sync(kFull, g, t << (5 - (MAXT == 8 ? 3 : 4)));
+                for (int t = 0; t < MAXT; ++t) gt[t] = __shfl_sync(kFull, g, t << SRC_SHIFT);
                 uint32_t rnd[4] = {0, 0, 0, 0};
-                if constexpr (!std::is_same<T, float>::value) {
+                if constexpr (kBf16) {
                     const u32x4 r = philox(a.seed, static_cast<uint32_t>(lane) | (static_cast<uint32_t>(q) << 8),
                                            static_cast<uint32_t>(wi), (a.round << 16) | static_cast<uint32_t>(p),
                                            kStreamSR);
@@ -312,27 +444,29 @@ __global__ void __launch_bounds__(kSgnsThreads)
 #pragma unroll
                 for (int t = 1; t < MAXT; ++t) {
                     if (nid[t] < 0) continue;
+                    float dn[EPL];
 #pragma unroll
                     for (int e = 0; e < EPL; ++e) {
                         din[e] = fmaf(gt[t], nr[t][e], din[e]);
-                        nr[t][e] = fmaf(gt[t], ix[e], nr[t][e]);
+                        dn[e] = gt[t] * ix[e];
                     }
-                    store_row<EPL>(phi_out + static_cast<int64_t>(nid[t]) * D + lane * EPL, nr[t],
+                    add_delta<EPL>(phi_out + static_cast<int64_t>(nid[t]) * D + lane * EPL, nr[t], dn,
                                    mix32(rnd[t & 3] + static_cast<uint32_t>(t)));
                 }
 #pragma unroll
                 for (int e = 0; e < EPL; ++e) {
-                    oc[e] = fmaf(gt[0], ix[e], oc[e]);
-                    ix[e] += din[e];
+                    const float u = gt[0] * ix[e];
+                    oc[e] += u;
+                    doc[e] += u;
                 }
-                store_row<EPL>(ix_ptr, ix, rnd[0]);
+                add_delta<EPL>(ix_ptr, ix, din, rnd[0]);
             }
             uint32_t rc = 0;
-            if constexpr (!std::is_same<T, float>::value) {
+            if constexpr (kBf16) {
                 rc = philox(a.seed, static_cast<uint32_t>(lane) | 0xff00u, static_cast<uint32_t>(wi),
                             (a.round << 16) | static_cast<uint32_t>(p), kStreamSR).x;
             }
-            store_row<EPL>(oc_ptr, oc, rc);
+            add_delta<EPL>(oc_ptr, oc0, doc, rc);
             loss_fx += __float2ll_rn(closs * kLossScaleF);
             __syncwarp();
         }
@@ -601,7 +735,7 @@ static bool params_ok(const felog_train_params *tp) {
     return true;
 }
 
-template <int D, class T, int MAXT>
+template <int D, class T, int MAXT, int KFIX>
 static felog_status launch_train(const SgnsArgs &a, const felog_train_params *tp, void *phi_in,
                                  void *phi_out, TrainWorkspace &w, cudaStream_t s) {
     T *pin = static_cast<T *>(phi_in);
@@ -609,14 +743,19 @@ static felog_status launch_train(const SgnsArgs &a, const felog_train_params *tp
     if (!minibatch_mode(tp)) {
         const size_t smem = sizeof(int32_t) * kWarps * (a.L + 2 * a.window * a.K);
         if (smem > 200 * 1024) return FELOG_ERR_UNSUPPORTED;  // walk too long to stage per warp
-        auto kern = k_sgns_hogwild<D, T, MAXT>;
+        auto kern = k_sgns_hogwild<D, T, MAXT, KFIX>;
         if (smem > 48 * 1024)
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSgnsThreads, smem);
         if (per_sm < 1) per_sm = 1;
+        // resident warps <= n / rows_per_warp: on small graphs this bounds how
+        // many warps update the same rows at once (staleness of lock-free SGD)
+        const int64_t rows_per_warp = tp->hogwild_rows_per_warp > 0 ? tp->hogwild_rows_per_warp : 16;
+        const int64_t cap_blocks = std::max<int64_t>(1, a.n / rows_per_warp / kWarps);
         const int64_t want = (a.n_walks + kWarps - 1) / kWarps;
-        const int blocks = static_cast<int>(std::min<int64_t>(want, static_cast<int64_t>(per_sm) * sm_count()));
+        const int blocks = static_cast<int>(
+            std::min<int64_t>({want, static_cast<int64_t>(per_sm) * sm_count(), cap_blocks}));
         kern<<<blocks, kSgnsThreads, smem, s>>>(a, pin, pout);
         return check_launch("felog_train (hogwild)");
     }
@@ -641,8 +780,9 @@ static felog_status launch_train(const SgnsArgs &a, const felog_train_params *tp
 template <int D, class T>
 static felog_status dispatch_maxt(const SgnsArgs &a, const felog_train_params *tp, void *pi,
                                   void *po, TrainWorkspace &w, cudaStream_t s) {
-    if (tp->negatives + 1 <= 8) return launch_train<D, T, 8>(a, tp, pi, po, w, s);
-    return launch_train<D, T, 16>(a, tp, pi, po, w, s);
+    if (tp->negatives == 5) return launch_train<D, T, 8, 5>(a, tp, pi, po, w, s);
+    if (tp->negatives + 1 <= 8) return launch_train<D, T, 8, 0>(a, tp, pi, po, w, s);
+    return launch_train<D, T, 16, 0>(a, tp, pi, po, w, s);
 }
 
 template <class T>
