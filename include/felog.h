@@ -132,6 +132,29 @@ felog_status felog_compact_active(const uint8_t *active, int32_t n, int32_t *sta
                                   int32_t *n_active, void *workspace, size_t workspace_bytes,
                                   void *stream);
 
+/* Allocation-free compaction (the paper has no counterpart: this is a
+ * deployment convenience).  Same result as felog_compact_active, but it needs
+ * no workspace: its scratch (one int32 count per 4096-flag tile) is a
+ * file-scope device array of 4096 entries (16 KiB) that every GPU loading
+ * this library holds until the process exits.  It is meant for callers that
+ * must not allocate device memory: code running where an allocation could
+ * synchronise the device or break a memory budget (inside a serving loop
+ * with a fixed memory plan, or a host framework that owns all device
+ * allocation).
+ *   - n may not exceed felog_compact_active_noalloc_max_n() = 2^24; larger n
+ *     returns FELOG_ERR_INVALID_ARG and launches nothing.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the one array: calls that can overlap on the GPU (on
+ *     different streams, or from different threads) race and must be
+ *     serialised by the caller.  Every slot a call reads is written earlier
+ *     by the same call, so no clearing is needed between calls.
+ *   - No cudaMalloc, cudaFree or allocating library routine is called. */
+int32_t felog_compact_active_noalloc_max_n(void);
+felog_status felog_compact_active_noalloc(const uint8_t *active, int32_t n, int32_t *starts,
+                                          int32_t *n_active, void *stream);
+
 /* Sample (Section 2 "Sampling process"; Section 5.4 Sample interface):
  * uniform truncated walks.  Walk (round r, rep j, start s = starts[i]) is
  * written to row j*n_starts + i of walks[n_starts*wpr][L] (device int32,

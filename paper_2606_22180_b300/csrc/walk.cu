@@ -8,6 +8,7 @@
 // computed while the previous gather is in flight.
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -141,6 +142,62 @@ extern "C" felog_status felog_compact_active(const uint8_t *active, int32_t n, i
     k_compact_scan<<<1, 1024, 0, s>>>(tile, tiles, n_active);
     k_compact_scatter<<<tiles, kCompactThreads, 0, s>>>(active, n, tile, starts);
     return check_launch("felog_compact_active");
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free compaction.  Same kernels as felog_compact_active; the
+// per-tile counts live in a file-scope device array instead of a caller
+// workspace, so a caller that may not allocate device memory can still run
+// the compaction.  Every tile slot a call uses is written by k_compact_count
+// before it is read, so nothing needs clearing between calls.
+// ---------------------------------------------------------------------------
+namespace felog {
+
+constexpr int kNoAllocMaxTiles = 4096;  // 4096 tiles x 4096 flags = 2^24 nodes
+static __device__ __align__(256) int32_t g_compact_tiles[kNoAllocMaxTiles];
+
+constexpr int kMaxDevices = 64;
+static std::mutex g_noalloc_mu;
+static int32_t *g_noalloc_tiles[kMaxDevices] = {};
+
+// Device address of g_compact_tiles for the current device (host code can
+// only name the symbol, not its device address).
+static felog_status noalloc_tiles(int32_t **out) {
+    int dev = 0;
+    felog_status st = record_cuda_error(cudaGetDevice(&dev), "compact_noalloc");
+    if (st) return st;
+    if (dev < 0 || dev >= kMaxDevices) return FELOG_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_tiles[dev]) {
+        void *p = nullptr;
+        st = record_cuda_error(cudaGetSymbolAddress(&p, g_compact_tiles), "cudaGetSymbolAddress");
+        if (st) return st;
+        g_noalloc_tiles[dev] = static_cast<int32_t *>(p);
+    }
+    *out = g_noalloc_tiles[dev];
+    return FELOG_OK;
+}
+
+}  // namespace felog
+
+extern "C" int32_t felog_compact_active_noalloc_max_n(void) {
+    return static_cast<int32_t>(kNoAllocMaxTiles) * kCompactTile;
+}
+
+extern "C" felog_status felog_compact_active_noalloc(const uint8_t *active, int32_t n, int32_t *starts,
+                                                     int32_t *n_active, void *stream) {
+    if (n < 0 || !n_active || (n > 0 && (!active || !starts))) return FELOG_ERR_INVALID_ARG;
+    if (n > felog_compact_active_noalloc_max_n()) return FELOG_ERR_INVALID_ARG;
+    int32_t *tile = nullptr;
+    felog_status st = noalloc_tiles(&tile);
+    if (st) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (n == 0) return record_cuda_error(cudaMemsetAsync(n_active, 0, sizeof(int32_t), s), "compact");
+    const int tiles = ceil_div(n, kCompactTile);
+    k_compact_count<<<tiles, kCompactThreads, 0, s>>>(active, n, tile);
+    k_compact_scan<<<1, 1024, 0, s>>>(tile, tiles, n_active);
+    k_compact_scatter<<<tiles, kCompactThreads, 0, s>>>(active, n, tile, starts);
+    return check_launch("felog_compact_active_noalloc");
 }
 
 // ---------------------------------------------------------------------------

@@ -23,6 +23,7 @@ FELOG_FP32, FELOG_BF16_SR = 0, 1
 SYMBOLS = [
     "felog_status_string", "felog_last_cuda_error",
     "felog_compact_workspace_bytes", "felog_compact_active",
+    "felog_compact_active_noalloc_max_n", "felog_compact_active_noalloc",
     "felog_walk", "felog_count",
     "felog_noise_workspace_bytes", "felog_noise_table",
     "felog_init_tables",
@@ -87,6 +88,8 @@ def load() -> ctypes.CDLL:
         "felog_last_cuda_error": (ctypes.c_char_p, []),
         "felog_compact_workspace_bytes": (sz, [i32]),
         "felog_compact_active": (st, [P, i32, P, P, P, sz, P]),
+        "felog_compact_active_noalloc_max_n": (i32, []),
+        "felog_compact_active_noalloc": (st, [P, i32, P, P, P]),
         "felog_walk": (st, [P, P, i32, P, u64, i32, P, P, P]),
         "felog_count": (st, [P, i64, i32, P, P]),
         "felog_noise_workspace_bytes": (sz, [i32]),
@@ -180,6 +183,16 @@ def felog_compact_active(active: torch.Tensor):
     ws = _workspace(lib.felog_compact_workspace_bytes(n), active.device)
     _check(lib.felog_compact_active(_ptr(active), n, _ptr(starts), _ptr(n_active), _ptr(ws),
                                     ws.numel(), _stream()), "felog_compact_active")
+    return starts, n_active
+
+
+def felog_compact_active_noalloc(active: torch.Tensor, starts: torch.Tensor, n_active: torch.Tensor):
+    """Compaction without any device allocation by the library (scratch is a
+    static device array); the caller supplies starts[n] and n_active[1]."""
+    _require_cuda(active, starts, n_active)
+    lib = load()
+    _check(lib.felog_compact_active_noalloc(_ptr(active), active.numel(), _ptr(starts), _ptr(n_active),
+                                            _stream()), "felog_compact_active_noalloc")
     return starts, n_active
 
 
