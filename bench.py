@@ -50,6 +50,10 @@ def _args():
     p.add_argument("--scale", type=int, default=SCALE, help="R-MAT scale (20 = the benchmark workload)")
     p.add_argument("--no-quality", action="store_true", help="skip the full-run AUC comparison")
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    p.add_argument("--form", type=int, default=0, choices=[0, 1, 2],
+                   help="Hogwild kernel form: 0 automatic, 1 full warp per pair, 2 half warp per pair")
+    p.add_argument("--precision", default="fp32", choices=["fp32", "bf16"],
+                   help="table precision of the timed rounds (fp32 = the plain form)")
     return p.parse_args()
 
 
@@ -61,9 +65,9 @@ def _workload(scale, rank=0):
     return split
 
 
-def _workload_name(scale):
+def _workload_name(scale, precision="fp32"):
     return (f"rmat{scale}-ef{EDGE_FACTOR} (a,b,c,d)=(0.57,0.19,0.19,0.05), 10% edges held out; "
-            f"L={L}, {ROUNDS} walks/node, window {WINDOW}, {NEG} negatives, d={DIM} fp32, hogwild")
+            f"L={L}, {ROUNDS} walks/node, window {WINDOW}, {NEG} negatives, d={DIM} {precision}, hogwild")
 
 
 # ---------------------------------------------------------------------------
@@ -265,7 +269,8 @@ def run_native(args):
     dg = fl.DeviceGraph.from_host(g)
     n_live = int((g.degrees() > 0).sum())
     T = ROUNDS * WPR * n_live * L
-    tp = fl.train_params(DIM, WINDOW, NEG, LR0, T, fl.FELOG_SGNS_HOGWILD, 4096, fl.FELOG_FP32)
+    prec = fl.FELOG_FP32 if args.precision == "fp32" else fl.FELOG_BF16_SR
+    tp = fl.train_params(DIM, WINDOW, NEG, LR0, T, fl.FELOG_SGNS_HOGWILD, 4096, prec, 0, args.form)
     fp_plain = fl.feedback_params(False, MU, KS, ROUNDS, False)
     runner = RoundRunner(fl, dg, tp, fp_plain, SEED + rank)
     runner.reset()
@@ -306,12 +311,14 @@ def run_native(args):
     value = tokens_all / (ms / 1e3)
 
     # roofline of the dominant kernel (SGNS): algorithmic bytes per launch
-    row = DIM * 4
+    row = DIM * (4 if args.precision == "fp32" else 2)
     pairs = n_live * WPR * _pairs_per_walk()
     alg_bytes = row * (4 * n_live * WPR * L + 2 * NEG * pairs)
     achieved = alg_bytes / (phase["train"] / 1e3) / 1e9
     peak, peak_kind = _peaks()
     traffic = _profile_traffic(os.path.join(ROOT, "paper_2606_22180_b300", "csrc", "sgns.cu"))
+    if args.precision != "fp32" or args.scale != SCALE:
+        traffic = None  # the committed capture is of the fp32 launch at scale 20
 
     # end to end through the public calls: CSR from pinned host memory, one
     # round, the round's loss read back
@@ -345,10 +352,10 @@ def run_native(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32",
+        "dtype": "f32" if args.precision == "fp32" else "bf16 tables, f32 math",
         "data": "synthetic (seeded R-MAT graph; no dataset)",
         "config": {
-            "workload": _workload_name(args.scale),
+            "workload": _workload_name(args.scale, args.precision),
             "nodes": g.n, "directed_csr_entries": g.nnz, "non_isolated": n_live,
             "step": "one plain round of Algorithm 1 (walk, counts, alias table, SGNS, Psi, V_a)",
             "l2": "inputs larger than L2 (tables 2 x 512 MiB), no flush",
@@ -360,7 +367,9 @@ def run_native(args):
         "gpu_launches": RoundRunner.KERNELS_PER_ROUND * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "k_sgns_hogwild<128,float,8>", "peak_source": peak_kind},
+                     "kernel": ("k_sgns_hogwild" if args.form == 1 else "k_sgns_hogwild_hw")
+                               + f"<128,{'float' if args.precision == 'fp32' else 'bf16'},5>",
+                     "peak_source": peak_kind},
         "e2e": {"value": e2e_value, "unit": "tokens/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8},
         "clocks": clocks,
     }

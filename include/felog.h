@@ -82,7 +82,10 @@ typedef enum {
  * clock t; minibatch = positions per synchronous batch (MINIBATCH mode);
  * hogwild_rows_per_warp (HOGWILD mode, <= 0 selects 16): at most
  * n / hogwild_rows_per_warp walks are trained concurrently, which bounds the
- * staleness of lock-free updates on small graphs. */
+ * staleness of lock-free updates on small graphs; hogwild_form selects the
+ * HOGWILD kernel: 0 = automatic (half-warp form where dim <= 128 and
+ * negatives <= 7, full-warp form otherwise), 1 = full warp per pair,
+ * 2 = two pairs per warp (half warp each; dim <= 128, negatives <= 7). */
 typedef struct {
     int32_t dim;
     int32_t window;
@@ -93,6 +96,7 @@ typedef struct {
     int32_t minibatch; /* >= 1 */
     int32_t precision; /* felog_precision */
     int32_t hogwild_rows_per_warp;
+    int32_t hogwild_form;
 } felog_train_params;
 
 /* enabled = 0 is the plain method (every non-isolated node stays active);

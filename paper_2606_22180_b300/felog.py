@@ -50,7 +50,8 @@ class _TrainParams(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int32), ("window", ctypes.c_int32), ("negatives", ctypes.c_int32),
                 ("lr0", ctypes.c_float), ("lr_total_tokens", ctypes.c_int64),
                 ("mode", ctypes.c_int32), ("minibatch", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("hogwild_rows_per_warp", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("hogwild_rows_per_warp", ctypes.c_int32),
+                ("hogwild_form", ctypes.c_int32)]
 
 
 class _FeedbackParams(ctypes.Structure):
@@ -247,9 +248,10 @@ def felog_init_tables(n: int, dim: int, precision: int, seed: int, device="cuda"
 
 
 def train_params(dim=128, window=10, negatives=5, lr0=0.025, lr_total_tokens=1, mode=FELOG_SGNS_HOGWILD,
-                 minibatch=4096, precision=FELOG_FP32, hogwild_rows_per_warp=0) -> _TrainParams:
+                 minibatch=4096, precision=FELOG_FP32, hogwild_rows_per_warp=0,
+                 hogwild_form=0) -> _TrainParams:
     return _TrainParams(dim, window, negatives, lr0, lr_total_tokens, mode, minibatch, precision,
-                        hogwild_rows_per_warp)
+                        hogwild_rows_per_warp, hogwild_form)
 
 
 def feedback_params(enabled=True, mu=0.65, ks=8, max_rounds=10, reactivate=False) -> _FeedbackParams:

@@ -45,9 +45,9 @@ def test_host_side_argument_checks(lib):
     from paper_2606_22180_b300 import felog
 
     assert lib.felog_status_string(0) == b"ok"
-    bad = felog._TrainParams(100, 5, 5, 0.025, 1, 0, 1, 0, 0)  # dim 100 unsupported
+    bad = felog._TrainParams(100, 5, 5, 0.025, 1, 0, 1, 0, 0, 0)  # dim 100 unsupported
     assert lib.felog_train_workspace_bytes(1, 40, 10, ctypes.byref(bad)) == 0
-    good = felog._TrainParams(64, 5, 5, 0.025, 1, 0, 1, 0, 0)
+    good = felog._TrainParams(64, 5, 5, 0.025, 1, 0, 1, 0, 0, 0)
     assert lib.felog_train_workspace_bytes(1, 40, 10, ctypes.byref(good)) > 0
     wp = felog._WalkParams(0, 1)  # zero-length walks rejected
     csr = felog._Csr(1, 1, 4, 4)
