@@ -248,6 +248,74 @@ felog_status felog_embed(const felog_csr *g, const felog_walk_params *wp,
                          int32_t *rounds_run, void *workspace, size_t workspace_bytes,
                          void *stream);
 
+/* ------------------------------------------------------------------------
+ * Batching form: many independent embedding jobs (Algorithm 1 each) trained
+ * together.  One round of every unfinished job runs as one fixed sequence
+ * of launches with no host synchronisation, each job at its own round index,
+ * so felog_batch_run can capture all rounds in one CUDA graph.  A job's walks,
+ * alias tables and Psi are exactly those of the single-graph calls with the
+ * same seed; its training is the half-warp Hogwild step (dim <= 128,
+ * negatives <= 7, HOGWILD mode only), with at most
+ * n_j / hogwild_rows_per_warp warps on job j at once.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    felog_csr graph;          /* device CSR, node ids local to the job */
+    uint64_t seed;
+    int32_t dim;              /* 32, 64 or 128 */
+    void *phi_in, *phi_out;   /* device [n][dim] tables in the batch precision */
+} felog_job;
+
+typedef struct {
+    int32_t rounds;           /* rounds run */
+    int32_t done;             /* 1 once V_a emptied or max_rounds was reached */
+    int64_t tokens;           /* corpus positions trained */
+    int64_t n_live;           /* non-isolated nodes */
+    double loss_last;         /* summed pair loss of the last round */
+} felog_job_stats;
+
+typedef struct {              /* a job's device buffers (owned by the batch) */
+    uint8_t *active[2];
+    int32_t *starts, *walks;  /* walks of the last round: row i = walk of starts[i] */
+    uint32_t *counts;
+    uint64_t *thr;
+    int32_t *alias;
+} felog_job_buffers;
+
+typedef struct {
+    int32_t walk_block;             /* threads per block of the walk kernel */
+    int32_t sgns_blocks_per_sm;     /* resident trainer blocks per SM */
+    int32_t feedback_blocks_per_sm; /* Psi blocks per SM */
+    int32_t from_cache;             /* 1 when read from the cache file */
+} felog_tuning;
+
+typedef struct felog_batch felog_batch;
+
+/* Allocates (cudaMalloc) the per-job buffers and tables; tp->dim is ignored
+ * (each job has its own dim); lr_total_tokens <= 0 derives each job's
+ * horizon from its own graph.  Jobs' graphs and tables stay caller-owned and
+ * must outlive the batch. */
+felog_status felog_batch_create(const felog_job *jobs, int32_t n_jobs, const felog_walk_params *wp,
+                                const felog_train_params *tp, const felog_feedback_params *fp,
+                                felog_batch **out);
+felog_status felog_batch_destroy(felog_batch *b);
+size_t felog_batch_device_bytes(const felog_batch *b);
+/* initialise tables and V_a of every job (round 0) */
+felog_status felog_batch_reset(felog_batch *b, void *stream);
+/* one round of every unfinished job */
+felog_status felog_batch_step(felog_batch *b, void *stream);
+/* reset + max_rounds steps; use_graph = 1 captures them in one CUDA graph
+ * (instantiated on first use, relaunched afterwards; needs a non-NULL stream) */
+felog_status felog_batch_run(felog_batch *b, int32_t use_graph, void *stream);
+/* synchronises `stream`; stats [n_jobs] (caller order), per-round |V_a| and
+ * loss [max_rounds][n_jobs] (each may be NULL) */
+felog_status felog_batch_read(felog_batch *b, felog_job_stats *stats, int32_t *rec_n_active,
+                              double *rec_loss, void *stream);
+felog_status felog_batch_job_buffers(const felog_batch *b, int32_t job, felog_job_buffers *out);
+/* times walk block size, trainer blocks per SM and Psi blocks per SM on
+ * round 0 and keeps the fastest; cache_path (may be NULL) is a text file of
+ * earlier results keyed by GPU name and batch shape.  Leaves the batch reset. */
+felog_status felog_batch_autotune(felog_batch *b, const char *cache_path, felog_tuning *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

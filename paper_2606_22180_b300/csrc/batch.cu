@@ -1,0 +1,1011 @@
+// Batching form: many independent graph-embedding jobs (Algorithm 1 each)
+// trained together on one GPU.
+//
+// Every job keeps its own device buffers (active flags, start list, walks,
+// counts, alias table and its scratch); a device table of jobs and a device
+// array of per-job states (round, token clock, |V_a|, done flag, sums) let one
+// fixed sequence of launches run one round of every unfinished job, each at
+// its own round index, with no host synchronisation.  The rounds can
+// therefore be captured in one CUDA graph.
+//
+// Work is mapped onto flat index spaces, each with a prefix over jobs:
+//   tiles  - 4096-node pieces of one job (compaction, alias-table build);
+//   slots  - n_j * wpr walk rows of job j (walk kernel);
+//   nodes  - n_j nodes of job j (alias finish, Psi);
+//   items  - max(1, n_j / rows_per_warp) training workers of job j; each
+//            trains every c_j-th walk of its job, so at most c_j warps touch
+//            one job's rows at once (the staleness bound of the single-graph
+//            kernel, per job).
+// A job's walks, alias table and Psi are those of the single-graph calls on
+// the same seed (same Philox keys, same integer table); its training is the
+// same half-warp Hogwild step.
+#include <algorithm>
+#include <cstring>
+#include <fstream>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "feedback_core.cuh"
+#include "noise_core.cuh"
+#include "sgns_core.cuh"
+#include "walk_core.cuh"
+
+namespace felog {
+
+bool csr_shape_ok(const felog_csr *g);
+
+constexpr int kBThreads = 256;
+constexpr int kBWarps = kBThreads / 32;
+constexpr int kBTile = 4096;
+constexpr int kBTileItems = kBTile / kBThreads;  // 16 per thread
+
+struct BJob {
+    const int32_t *offsets, *cols;
+    int32_t n, dim;
+    uint64_t seed;
+    void *phi_in, *phi_out;
+    uint8_t *active[2];
+    int32_t *starts, *walks;
+    uint32_t *counts;
+    uint64_t *thr;
+    int32_t *alias;
+    uint64_t *W;
+    u128 *key;
+    int32_t *rank;
+    u128 *light_D;
+    int32_t *heavy_idx;
+    u128 *heavy_E;
+    int32_t tile_base, n_tiles;
+};
+
+struct BState {
+    int32_t round, cur, n_active, n_next;
+    int32_t done, pad0;
+    int64_t clock, n_live;
+    float inv_T, pad1;
+    unsigned long long S;
+    uint32_t cmax, pad2;
+    NoiseAgg total;
+    unsigned long long loss_acc;
+};
+
+struct BArgs {
+    const BJob *jobs;
+    BState *st;
+    int32_t n_jobs;
+    const int64_t *slot_prefix;  // [n_jobs + 1]
+    const int64_t *node_prefix;  // [n_jobs + 1]
+    const int64_t *item_prefix;  // [n_jobs + 1]
+    const int32_t *tile_job, *tile_start;
+    int32_t *tile_count;
+    NoiseAgg *tile_agg;
+    int32_t n_tiles;
+    int64_t n_slots, n_nodes;
+    int32_t L, wpr, window, K, max_rounds, ks, enabled, reactivate, precision;
+    double mu;
+    float lr0;
+    int64_t lr_total_tokens;
+    int32_t *rec_n_active, *rec_n_next;  // [max_rounds][n_jobs]
+    double *rec_loss;
+};
+
+// largest j with prefix[j] <= x (x < prefix[n_jobs])
+__device__ __forceinline__ int find_job(const int64_t *__restrict__ prefix, int n_jobs, int64_t x) {
+    int lo = 0, hi = n_jobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(prefix + mid) <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------------------
+// set-up: per-job state, tables, V_a^0, learning-rate horizon
+// ---------------------------------------------------------------------------
+__global__ void k_b_state_init(BArgs a) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= a.n_jobs) return;
+    BState s{};
+    a.st[j] = s;
+}
+
+template <class T>
+__global__ void k_b_init(BArgs a) {
+    for (int64_t x = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; x < a.n_nodes;
+         x += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int j = find_job(a.node_prefix, a.n_jobs, x);
+        const BJob &jb = a.jobs[j];
+        const int32_t v = static_cast<int32_t>(x - a.node_prefix[j]);
+        T *pin = static_cast<T *>(jb.phi_in) + static_cast<int64_t>(v) * jb.dim;
+        T *pout = static_cast<T *>(jb.phi_out) + static_cast<int64_t>(v) * jb.dim;
+        const float fd = static_cast<float>(jb.dim);
+        for (int i4 = 0; i4 < jb.dim / 4; ++i4) {
+            const u32x4 r = philox(jb.seed, static_cast<uint32_t>(i4), static_cast<uint32_t>(v), 0u, kStreamInit);
+            const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float u = static_cast<float>(w[k] >> 8) * 5.9604644775390625e-08f;  // 2^-24
+                const float val = __fdiv_rn(u - 0.5f, fd);
+                if constexpr (std::is_same<T, float>::value) {
+                    pin[i4 * 4 + k] = val;
+                    pout[i4 * 4 + k] = 0.f;
+                } else {
+                    pin[i4 * 4 + k] = __float2bfloat16_rn(val);
+                    pout[i4 * 4 + k] = __float2bfloat16_rn(0.f);
+                }
+            }
+        }
+        const uint8_t live = jb.offsets[v + 1] > jb.offsets[v];
+        jb.active[0][v] = live;
+        // one add per group of lanes on the same job
+        const unsigned act = __activemask();
+        const unsigned grp = __match_any_sync(act, j);
+        const unsigned mine = grp & __ballot_sync(act, live);
+        if (mine && (__ffs(mine) - 1) == static_cast<int>(threadIdx.x & 31))
+            atomicAdd(reinterpret_cast<unsigned long long *>(&a.st[j].n_live),
+                      static_cast<unsigned long long>(__popc(mine)));
+    }
+}
+
+__global__ void k_b_lr(BArgs a) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= a.n_jobs) return;
+    int64_t T = a.lr_total_tokens;
+    if (T <= 0) T = static_cast<int64_t>(a.max_rounds) * a.wpr * a.st[j].n_live * a.L;
+    if (T <= 0) T = 1;
+    a.st[j].inv_T = static_cast<float>(1.0 / static_cast<double>(T));
+    a.st[j].done = a.st[j].n_live == 0 || a.max_rounds == 0;
+}
+
+// ---------------------------------------------------------------------------
+// compaction of each job's V_a (tiles never span jobs)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBThreads) k_b_compact_count(BArgs a) {
+    __shared__ int32_t warp_sum[kBWarps];
+    const int t = blockIdx.x;
+    const int j = a.tile_job[t];
+    const BJob &jb = a.jobs[j];
+    const BState &st = a.st[j];
+    int32_t c = 0;
+    if (!st.done) {
+        const int32_t start = a.tile_start[t];
+        const uint8_t *act = jb.active[st.cur];
+        for (int i = threadIdx.x; i < kBTile; i += kBThreads) {
+            const int32_t v = start + i;
+            if (v < jb.n) {
+                c += act[v] != 0;
+                jb.counts[v] = 0u;
+            }
+        }
+    }
+    c = __reduce_add_sync(kFull, c);
+    if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t s = 0;
+        for (int w = 0; w < kBWarps; ++w) s += warp_sum[w];
+        a.tile_count[t] = s;
+    }
+}
+
+// one thread per job: exclusive scan of its tile counts, |V_a|, round reset
+__global__ void k_b_compact_scan(BArgs a) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= a.n_jobs) return;
+    BState &st = a.st[j];
+    st.S = 0;
+    st.cmax = 0;
+    st.loss_acc = 0;
+    st.n_next = 0;
+    if (st.done) {
+        st.n_active = 0;
+        return;
+    }
+    const BJob &jb = a.jobs[j];
+    int32_t run = 0;
+    for (int32_t t = jb.tile_base; t < jb.tile_base + jb.n_tiles; ++t) {
+        const int32_t c = a.tile_count[t];
+        a.tile_count[t] = run;
+        run += c;
+    }
+    st.n_active = run;
+    if (run == 0 || st.round >= a.max_rounds) {
+        st.done = 1;
+        st.n_active = 0;
+    }
+}
+
+__global__ void __launch_bounds__(kBThreads) k_b_compact_scatter(BArgs a) {
+    __shared__ int32_t warp_tot[kBWarps];
+    const int t = blockIdx.x;
+    const int j = a.tile_job[t];
+    const BJob &jb = a.jobs[j];
+    const BState &st = a.st[j];
+    if (st.done) return;  // uniform over the block
+    const uint8_t *act = jb.active[st.cur];
+    const int32_t my = a.tile_start[t] + threadIdx.x * kBTileItems;
+    uint32_t bits = 0;
+#pragma unroll
+    for (int k = 0; k < kBTileItems; ++k) {
+        const int32_t v = my + k;
+        if (v < jb.n && act[v]) bits |= 1u << k;
+    }
+    const int32_t c = __popc(bits);
+    int32_t incl = c;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(kFull, incl, o);
+        if ((threadIdx.x & 31) >= o) incl += y;
+    }
+    if ((threadIdx.x & 31) == 31) warp_tot[threadIdx.x >> 5] = incl;
+    __syncthreads();
+    int32_t warp_excl = 0;
+    for (int w = 0; w < (threadIdx.x >> 5); ++w) warp_excl += warp_tot[w];
+    int32_t pos = a.tile_count[t] + warp_excl + incl - c;
+    while (bits) {
+        const int k = __ffs(bits) - 1;
+        bits &= bits - 1;
+        jb.starts[pos++] = my + k;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// walks (counts fused); walk row o of job j = rep * |V_a| + i, as in felog_walk
+// ---------------------------------------------------------------------------
+template <bool VEC>
+__global__ void k_b_walk(BArgs a) {
+    for (int64_t x = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; x < a.n_slots;
+         x += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int j = find_job(a.slot_prefix, a.n_jobs, x);
+        const BState &st = a.st[j];
+        const int64_t o = x - a.slot_prefix[j];
+        if (st.done || o >= static_cast<int64_t>(st.n_active) * a.wpr) continue;
+        const BJob &jb = a.jobs[j];
+        const int32_t rep = static_cast<int32_t>(o / st.n_active);
+        const int32_t i = static_cast<int32_t>(o - static_cast<int64_t>(rep) * st.n_active);
+        const int32_t s = jb.starts[i];
+        const uint32_t x2 = static_cast<uint32_t>(st.round) * static_cast<uint32_t>(a.wpr) + static_cast<uint32_t>(rep);
+        walk_fill_row<true, VEC>(jb.offsets, jb.cols, s, a.L, jb.seed, x2, jb.walks + o * a.L, jb.counts);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// per-job alias tables of the round's corpus (same integers as felog_noise_table)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBThreads) k_b_noise_max(BArgs a) {
+    const int t = blockIdx.x;
+    const int j = a.tile_job[t];
+    if (a.st[j].done) return;
+    const BJob &jb = a.jobs[j];
+    uint32_t m = 0;
+    const int32_t start = a.tile_start[t];
+    for (int i = threadIdx.x; i < kBTile; i += kBThreads)
+        if (start + i < jb.n) m = max(m, jb.counts[start + i]);
+    m = __reduce_max_sync(kFull, m);
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(&a.st[j].cmax, m);
+}
+
+__global__ void __launch_bounds__(kBThreads) k_b_noise_weights(BArgs a) {
+    const int t = blockIdx.x;
+    const int j = a.tile_job[t];
+    if (a.st[j].done) return;
+    const BJob &jb = a.jobs[j];
+    const uint32_t cm = a.st[j].cmax;
+    const double wmax = cm ? three_quarter_power(cm) : 1.0;
+    unsigned long long local = 0;
+    const int32_t start = a.tile_start[t];
+    for (int i = threadIdx.x; i < kBTile; i += kBThreads) {
+        const int32_t v = start + i;
+        if (v >= jb.n) break;
+        const uint32_t c = jb.counts[v];
+        uint64_t w = 0;
+        if (c) {
+            const double q = floor(__dmul_rn(__ddiv_rn(three_quarter_power(c), wmax), 4294967296.0));
+            w = static_cast<uint64_t>(q);
+            if (w < 1) w = 1;
+        }
+        jb.W[v] = w;
+        local += w;
+    }
+    for (int o = 16; o; o >>= 1) local += __shfl_xor_sync(kFull, local, o);
+    if ((threadIdx.x & 31) == 0 && local) atomicAdd(&a.st[j].S, local);
+}
+
+__global__ void __launch_bounds__(kBThreads) k_b_noise_agg(BArgs a) {
+    __shared__ NoiseAgg part[kBThreads];
+    const int t = blockIdx.x;
+    const int j = a.tile_job[t];
+    if (a.st[j].done) return;
+    const BJob &jb = a.jobs[j];
+    const uint64_t S = a.st[j].S;
+    const int32_t my = a.tile_start[t] + threadIdx.x * kBTileItems;
+    NoiseAgg g{0, 0, 0, 0};
+    for (int k = 0; k < kBTileItems; ++k) {
+        const int32_t v = my + k;
+        if (v >= jb.n) break;
+        bool light;
+        uint64_t amt;
+        classify(jb.W[v], static_cast<uint64_t>(jb.n), S, light, amt);
+        if (light) { g.D += amt; g.nL += 1; }
+        else { g.E += amt; g.nH += 1; }
+    }
+    part[threadIdx.x] = g;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        NoiseAgg s{0, 0, 0, 0};
+        for (int i = 0; i < kBThreads; ++i) {
+            s.D += part[i].D; s.E += part[i].E; s.nL += part[i].nL; s.nH += part[i].nH;
+        }
+        a.tile_agg[t] = s;
+    }
+}
+
+__global__ void k_b_noise_scan(BArgs a) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= a.n_jobs || a.st[j].done) return;
+    const BJob &jb = a.jobs[j];
+    NoiseAgg run{0, 0, 0, 0};
+    for (int32_t t = jb.tile_base; t < jb.tile_base + jb.n_tiles; ++t) {
+        const NoiseAgg x = a.tile_agg[t];
+        a.tile_agg[t] = run;
+        run.D += x.D; run.E += x.E; run.nL += x.nL; run.nH += x.nH;
+    }
+    a.st[j].total = run;
+}
+
+__global__ void __launch_bounds__(kBThreads) k_b_noise_scatter(BArgs a) {
+    __shared__ NoiseAgg part[kBThreads];
+    const int t = blockIdx.x;
+    const int j = a.tile_job[t];
+    if (a.st[j].done) return;
+    const BJob &jb = a.jobs[j];
+    const uint64_t S = a.st[j].S;
+    const int32_t my = a.tile_start[t] + threadIdx.x * kBTileItems;
+    NoiseAgg g{0, 0, 0, 0};
+    for (int k = 0; k < kBTileItems; ++k) {
+        const int32_t v = my + k;
+        if (v >= jb.n) break;
+        bool light;
+        uint64_t amt;
+        classify(jb.W[v], static_cast<uint64_t>(jb.n), S, light, amt);
+        if (light) { g.D += amt; g.nL += 1; }
+        else { g.E += amt; g.nH += 1; }
+    }
+    part[threadIdx.x] = g;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        NoiseAgg run = a.tile_agg[t];
+        for (int i = 0; i < kBThreads; ++i) {
+            const NoiseAgg x = part[i];
+            part[i] = run;
+            run.D += x.D; run.E += x.E; run.nL += x.nL; run.nH += x.nH;
+        }
+    }
+    __syncthreads();
+    NoiseAgg run = part[threadIdx.x];
+    for (int k = 0; k < kBTileItems; ++k) {
+        const int32_t v = my + k;
+        if (v >= jb.n) break;
+        bool light;
+        uint64_t amt;
+        classify(jb.W[v], static_cast<uint64_t>(jb.n), S, light, amt);
+        if (light) {
+            jb.key[v] = run.D;
+            jb.light_D[run.nL] = run.D;
+            jb.rank[v] = run.nL;
+            run.D += amt;
+            run.nL += 1;
+        } else {
+            run.E += amt;
+            jb.key[v] = run.E;
+            jb.heavy_idx[run.nH] = v;
+            jb.heavy_E[run.nH] = run.E;
+            jb.rank[v] = run.nH;
+            run.nH += 1;
+        }
+    }
+}
+
+__global__ void k_b_noise_finish(BArgs a) {
+    for (int64_t x = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; x < a.n_nodes;
+         x += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int j = find_job(a.node_prefix, a.n_jobs, x);
+        const BState &st = a.st[j];
+        if (st.done) continue;
+        const BJob &jb = a.jobs[j];
+        const int32_t v = static_cast<int32_t>(x - a.node_prefix[j]);
+        if (st.S == 0) {
+            jb.thr[v] = 0;
+            jb.alias[v] = v;
+            continue;
+        }
+        alias_entry(v, jb.W[v], static_cast<uint64_t>(jb.n), st.S, jb.key[v], jb.rank[v], jb.light_D,
+                    st.total.nL, jb.heavy_idx, jb.heavy_E, st.total.nH, st.total.D, jb.thr + v, jb.alias + v);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// SGNS over training items of the jobs whose dim is D
+// ---------------------------------------------------------------------------
+template <int D, class T, int KFIX>
+__global__ void __launch_bounds__(kSgnsThreads, 2) k_b_sgns(BArgs a, int64_t item_lo, int64_t item_hi) {
+    extern __shared__ int32_t smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int K = KFIX > 0 ? KFIX : a.K;
+    int32_t *wk = smem + wib * (a.L + 2 * a.window * K);
+    int32_t *negs = wk + a.L;
+    const int64_t warps = static_cast<int64_t>(gridDim.x) * kWarps;
+    for (int64_t it = item_lo + static_cast<int64_t>(blockIdx.x) * kWarps + wib; it < item_hi; it += warps) {
+        const int j = find_job(a.item_prefix, a.n_jobs, it);
+        const BState &st = a.st[j];
+        if (st.done) continue;
+        const BJob &jb = a.jobs[j];
+        const int64_t c_j = a.item_prefix[j + 1] - a.item_prefix[j];
+        const int64_t walks = static_cast<int64_t>(st.n_active) * a.wpr;
+        TrainView<T> v{static_cast<T *>(jb.phi_in), static_cast<T *>(jb.phi_out), jb.thr, jb.alias,
+                       static_cast<uint64_t>(jb.n), st.S, jb.seed, static_cast<uint32_t>(st.round), a.lr0,
+                       st.inv_T, st.clock, a.window, a.K, a.L};
+        long long loss_fx = 0;
+        for (int64_t wl = it - a.item_prefix[j]; wl < walks; wl += c_j)
+            loss_fx += hw_train_walk<D, T, KFIX>(v, jb.walks + wl * a.L, wl, wk, negs);
+        for (int o = 16; o; o >>= 1) loss_fx += __shfl_xor_sync(kFull, loss_fx, o);
+        if (lane == 0 && loss_fx != 0)
+            atomicAdd(&a.st[j].loss_acc, static_cast<unsigned long long>(loss_fx));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Psi and V_a^{r+1} (same values as felog_feedback)
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(kBThreads) k_b_feedback(BArgs a) {
+    __shared__ int32_t sub_s[kBWarps][kMaxKs];
+    __shared__ int32_t sorted_s[kBWarps][kMaxKs];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t warps = static_cast<int64_t>(gridDim.x) * kBWarps;
+    for (int64_t x = static_cast<int64_t>(blockIdx.x) * kBWarps + wib; x < a.n_nodes; x += warps) {
+        const int j = find_job(a.node_prefix, a.n_jobs, x);
+        const BState &st = a.st[j];
+        if (st.done) continue;
+        const BJob &jb = a.jobs[j];
+        const int32_t v = static_cast<int32_t>(x - a.node_prefix[j]);
+        const int32_t lo = jb.offsets[v];
+        const int64_t deg = static_cast<int64_t>(jb.offsets[v + 1]) - lo;
+        const bool evaluate = deg > 0 && (a.reactivate || jb.active[st.cur][v]);
+        double psi = 0.0;
+        if (evaluate)
+            psi = psi_node<T>(jb.cols, static_cast<const T *>(jb.phi_in), jb.dim, a.ks, jb.seed,
+                              static_cast<uint32_t>(st.round), v, lo, deg, sub_s[wib], sorted_s[wib]);
+        const uint8_t next = a.enabled ? (evaluate && psi < a.mu) : (deg > 0);
+        if (lane == 0) {
+            jb.active[st.cur ^ 1][v] = next;
+            if (next) atomicAdd(&a.st[j].n_next, 1);
+        }
+    }
+}
+
+__global__ void k_b_round_end(BArgs a) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= a.n_jobs) return;
+    BState &st = a.st[j];
+    if (st.done) return;
+    const int r = st.round;
+    a.rec_n_active[static_cast<int64_t>(r) * a.n_jobs + j] = st.n_active;
+    a.rec_n_next[static_cast<int64_t>(r) * a.n_jobs + j] = st.n_next;
+    a.rec_loss[static_cast<int64_t>(r) * a.n_jobs + j] =
+        static_cast<double>(static_cast<long long>(st.loss_acc)) / kLossScale;
+    st.clock += static_cast<int64_t>(st.n_active) * a.wpr * a.L;
+    st.round = r + 1;
+    st.cur ^= 1;
+    if (st.n_next == 0 || st.round >= a.max_rounds) st.done = 1;
+}
+
+// ---------------------------------------------------------------------------
+// host object
+// ---------------------------------------------------------------------------
+struct HostTuning {
+    int walk_block = 256;
+    int sgns_blocks_per_sm = 2;
+    int feedback_blocks_per_sm = 16;
+};
+
+}  // namespace felog
+
+using namespace felog;
+
+struct felog_batch {
+    int32_t n_jobs = 0;
+    felog_walk_params wp{};
+    felog_train_params tp{};
+    felog_feedback_params fp{};
+    std::vector<int32_t> order;     // internal index -> caller index
+    std::vector<int32_t> position;  // caller index -> internal index
+    std::vector<int32_t> dims;      // internal order
+    std::vector<int32_t> ns;
+    std::vector<int64_t> item_prefix_h;
+    void *blob = nullptr;
+    size_t blob_bytes = 0;
+    BArgs args{};
+    std::vector<BJob> jobs_h;
+    HostTuning tune;
+    cudaGraphExec_t graph = nullptr;
+    int graph_rounds = -1;
+    cudaStream_t graph_stream = nullptr;
+};
+
+namespace {
+
+size_t job_bytes(int32_t n, int32_t L, int32_t wpr) {
+    const size_t nn = n > 0 ? static_cast<size_t>(n) : 1;
+    size_t b = 0;
+    auto add = [&](size_t x) { b += align_up(x, 256); };
+    add(nn);                                       // active[0]
+    add(nn);                                       // active[1]
+    add(4 * nn);                                   // starts
+    add(4 * nn * static_cast<size_t>(wpr) * L);    // walks
+    add(4 * nn);                                   // counts
+    add(8 * nn);                                   // thr
+    add(4 * nn);                                   // alias
+    add(8 * nn);                                   // W
+    add(16 * nn);                                  // key
+    add(4 * nn);                                   // rank
+    add(16 * nn);                                  // light_D
+    add(4 * nn);                                   // heavy_idx
+    add(16 * nn);                                  // heavy_E
+    return b;
+}
+
+felog_status check_jobs(const felog_job *jobs, int32_t n_jobs, const felog_walk_params *wp,
+                        const felog_train_params *tp, const felog_feedback_params *fp) {
+    if (!jobs || n_jobs < 1 || !wp || !tp || !fp) return FELOG_ERR_INVALID_ARG;
+    if (wp->length < 1 || wp->walks_per_round < 1) return FELOG_ERR_INVALID_ARG;
+    if (tp->window < 1 || tp->window > 16 || tp->negatives < 1 || tp->negatives > 7)
+        return FELOG_ERR_UNSUPPORTED;  // the batched trainer is the half-warp form
+    if (tp->mode != FELOG_SGNS_HOGWILD) return FELOG_ERR_UNSUPPORTED;
+    if (tp->precision != FELOG_FP32 && tp->precision != FELOG_BF16_SR) return FELOG_ERR_INVALID_ARG;
+    if (!(tp->lr0 >= 0.f)) return FELOG_ERR_INVALID_ARG;
+    if (fp->ks < 1 || fp->ks > kMaxKs || fp->max_rounds < 0 || fp->max_rounds >= 65536)
+        return FELOG_ERR_INVALID_ARG;
+    const size_t smem = sizeof(int32_t) * kWarps * (wp->length + 2 * tp->window * tp->negatives);
+    if (smem > 200 * 1024) return FELOG_ERR_UNSUPPORTED;
+    for (int32_t i = 0; i < n_jobs; ++i) {
+        const felog_job &j = jobs[i];
+        if (!csr_shape_ok(&j.graph)) return FELOG_ERR_BAD_CSR;
+        if (j.dim != 32 && j.dim != 64 && j.dim != 128) return FELOG_ERR_UNSUPPORTED;
+        if (j.graph.n > 0 && (!j.phi_in || !j.phi_out)) return FELOG_ERR_INVALID_ARG;
+    }
+    return FELOG_OK;
+}
+
+template <int D, class T>
+felog_status launch_b_sgns(felog_batch *b, int64_t lo, int64_t hi, cudaStream_t s) {
+    if (hi <= lo) return FELOG_OK;
+    const size_t smem = sizeof(int32_t) * kWarps * (b->tp.window * 2 * b->tp.negatives + b->wp.length);
+    const bool k5 = b->tp.negatives == 5;
+    auto kern = k5 ? k_b_sgns<D, T, 5> : k_b_sgns<D, T, 0>;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    const int64_t want = (hi - lo + kWarps - 1) / kWarps;
+    const int blocks = static_cast<int>(
+        std::max<int64_t>(1, std::min<int64_t>(want, static_cast<int64_t>(b->tune.sgns_blocks_per_sm) * sm_count())));
+    kern<<<blocks, kSgnsThreads, smem, s>>>(b->args, lo, hi);
+    return FELOG_OK;
+}
+
+template <class T>
+felog_status launch_sgns_all(felog_batch *b, cudaStream_t s) {
+    // items are ordered by job, jobs by dim: one launch per dim range
+    int32_t j = 0;
+    while (j < b->n_jobs) {
+        int32_t k = j;
+        while (k < b->n_jobs && b->dims[k] == b->dims[j]) ++k;
+        const int64_t lo = b->item_prefix_h[j], hi = b->item_prefix_h[k];
+        felog_status st = FELOG_OK;
+        switch (b->dims[j]) {
+            case 32: st = launch_b_sgns<32, T>(b, lo, hi, s); break;
+            case 64: st = launch_b_sgns<64, T>(b, lo, hi, s); break;
+            case 128: st = launch_b_sgns<128, T>(b, lo, hi, s); break;
+        }
+        if (st) return st;
+        j = k;
+    }
+    return FELOG_OK;
+}
+
+int grid_for(int64_t work, int block, int per_sm) {
+    return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((work + block - 1) / block,
+                                                                    static_cast<int64_t>(per_sm) * sm_count())));
+}
+
+felog_status do_reset(felog_batch *b, cudaStream_t s) {
+    const BArgs &a = b->args;
+    const int jg = ceil_div(b->n_jobs, 256);
+    k_b_state_init<<<jg, 256, 0, s>>>(a);
+    if (b->tp.precision == FELOG_FP32) k_b_init<float><<<grid_for(a.n_nodes, 256, 16), 256, 0, s>>>(a);
+    else k_b_init<__nv_bfloat16><<<grid_for(a.n_nodes, 256, 16), 256, 0, s>>>(a);
+    k_b_lr<<<jg, 256, 0, s>>>(a);
+    return check_launch("felog_batch reset");
+}
+
+// phase: bit 0 compaction, 1 walk, 2 noise, 3 sgns, 4 feedback, 5 round end
+felog_status do_step(felog_batch *b, cudaStream_t s, unsigned phases = 0x3f) {
+    const BArgs &a = b->args;
+    const int jg = ceil_div(b->n_jobs, 256);
+    if (phases & 1) {
+        k_b_compact_count<<<a.n_tiles, kBThreads, 0, s>>>(a);
+        k_b_compact_scan<<<jg, 256, 0, s>>>(a);
+        k_b_compact_scatter<<<a.n_tiles, kBThreads, 0, s>>>(a);
+    }
+    if (phases & 2) {
+        const int wb = b->tune.walk_block;
+        const bool vec = (a.L % 4) == 0;
+        if (vec) k_b_walk<true><<<grid_for(a.n_slots, wb, 2048 / wb), wb, 0, s>>>(a);
+        else k_b_walk<false><<<grid_for(a.n_slots, wb, 2048 / wb), wb, 0, s>>>(a);
+    }
+    if (phases & 4) {
+        k_b_noise_max<<<a.n_tiles, kBThreads, 0, s>>>(a);
+        k_b_noise_weights<<<a.n_tiles, kBThreads, 0, s>>>(a);
+        k_b_noise_agg<<<a.n_tiles, kBThreads, 0, s>>>(a);
+        k_b_noise_scan<<<jg, 256, 0, s>>>(a);
+        k_b_noise_scatter<<<a.n_tiles, kBThreads, 0, s>>>(a);
+        k_b_noise_finish<<<grid_for(a.n_nodes, 256, 8), 256, 0, s>>>(a);
+    }
+    if (phases & 8) {
+        felog_status st = b->tp.precision == FELOG_FP32 ? launch_sgns_all<float>(b, s)
+                                                         : launch_sgns_all<__nv_bfloat16>(b, s);
+        if (st) return st;
+    }
+    if (phases & 16) {
+        const int grid = static_cast<int>(std::max<int64_t>(
+            1, std::min<int64_t>((a.n_nodes + kBWarps - 1) / kBWarps,
+                                 static_cast<int64_t>(sm_count()) * b->tune.feedback_blocks_per_sm)));
+        if (b->tp.precision == FELOG_FP32) k_b_feedback<float><<<grid, kBThreads, 0, s>>>(a);
+        else k_b_feedback<__nv_bfloat16><<<grid, kBThreads, 0, s>>>(a);
+    }
+    if (phases & 32) k_b_round_end<<<jg, 256, 0, s>>>(a);
+    return check_launch("felog_batch step");
+}
+
+void drop_graph(felog_batch *b) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->graph_rounds = -1;
+}
+
+}  // namespace
+
+extern "C" felog_status felog_batch_create(const felog_job *jobs, int32_t n_jobs, const felog_walk_params *wp,
+                                           const felog_train_params *tp, const felog_feedback_params *fp,
+                                           felog_batch **out) {
+    if (!out) return FELOG_ERR_INVALID_ARG;
+    *out = nullptr;
+    felog_status st = check_jobs(jobs, n_jobs, wp, tp, fp);
+    if (st) return st;
+    felog_batch *b = new (std::nothrow) felog_batch();
+    if (!b) return FELOG_ERR_INVALID_ARG;
+    b->n_jobs = n_jobs;
+    b->wp = *wp;
+    b->tp = *tp;
+    b->fp = *fp;
+    // internal order: by dim (stable), so each dim's training items are contiguous
+    b->order.resize(n_jobs);
+    for (int32_t i = 0; i < n_jobs; ++i) b->order[i] = i;
+    std::stable_sort(b->order.begin(), b->order.end(),
+                     [&](int32_t x, int32_t y) { return jobs[x].dim < jobs[y].dim; });
+    b->position.resize(n_jobs);
+    for (int32_t i = 0; i < n_jobs; ++i) b->position[b->order[i]] = i;
+    const int32_t L = wp->length, wpr = wp->walks_per_round, R = fp->max_rounds;
+    const int64_t rows_per_warp = tp->hogwild_rows_per_warp > 0 ? tp->hogwild_rows_per_warp : 16;
+    std::vector<int64_t> slot_prefix(n_jobs + 1, 0), node_prefix(n_jobs + 1, 0), item_prefix(n_jobs + 1, 0);
+    std::vector<int32_t> tile_job, tile_start;
+    size_t per_job_total = 0;
+    b->dims.resize(n_jobs);
+    b->ns.resize(n_jobs);
+    for (int32_t i = 0; i < n_jobs; ++i) {
+        const felog_job &j = jobs[b->order[i]];
+        const int32_t n = j.graph.n;
+        b->dims[i] = j.dim;
+        b->ns[i] = n;
+        slot_prefix[i + 1] = slot_prefix[i] + static_cast<int64_t>(n) * wpr;
+        node_prefix[i + 1] = node_prefix[i] + n;
+        item_prefix[i + 1] = item_prefix[i] + std::max<int64_t>(1, n / rows_per_warp);
+        per_job_total += job_bytes(n, L, wpr);
+    }
+    const int32_t n_tiles_total = [&] {
+        int64_t t = 0;
+        for (int32_t i = 0; i < n_jobs; ++i) t += std::max(1, ceil_div(std::max(b->ns[i], 1), kBTile));
+        return static_cast<int32_t>(t);
+    }();
+    // blob layout: job table, states, prefixes, tile tables, records, per-job buffers
+    size_t off = 0;
+    auto slot = [&](size_t bytes) { size_t o = off; off += align_up(bytes, 256); return o; };
+    const size_t o_jobs = slot(sizeof(BJob) * n_jobs);
+    const size_t o_st = slot(sizeof(BState) * n_jobs);
+    const size_t o_sp = slot(sizeof(int64_t) * (n_jobs + 1));
+    const size_t o_np = slot(sizeof(int64_t) * (n_jobs + 1));
+    const size_t o_ip = slot(sizeof(int64_t) * (n_jobs + 1));
+    const size_t o_tj = slot(sizeof(int32_t) * n_tiles_total);
+    const size_t o_ts = slot(sizeof(int32_t) * n_tiles_total);
+    const size_t o_tc = slot(sizeof(int32_t) * n_tiles_total);
+    const size_t o_ta = slot(sizeof(NoiseAgg) * n_tiles_total);
+    const size_t rec = static_cast<size_t>(std::max(R, 1)) * n_jobs;
+    const size_t o_rna = slot(sizeof(int32_t) * rec);
+    const size_t o_rnn = slot(sizeof(int32_t) * rec);
+    const size_t o_rl = slot(sizeof(double) * rec);
+    const size_t o_buf = slot(per_job_total);
+    b->blob_bytes = off;
+    st = record_cuda_error(cudaMalloc(&b->blob, b->blob_bytes), "felog_batch_create");
+    if (st) {
+        delete b;
+        return st;
+    }
+    char *base = static_cast<char *>(b->blob);
+    b->jobs_h.resize(n_jobs);
+    char *p = base + o_buf;
+    auto take = [&](size_t bytes) { char *q = p; p += align_up(bytes, 256); return q; };
+    int32_t tile = 0;
+    for (int32_t i = 0; i < n_jobs; ++i) {
+        const felog_job &j = jobs[b->order[i]];
+        const size_t nn = j.graph.n > 0 ? static_cast<size_t>(j.graph.n) : 1;
+        BJob &jb = b->jobs_h[i];
+        jb.offsets = j.graph.offsets;
+        jb.cols = j.graph.cols;
+        jb.n = j.graph.n;
+        jb.dim = j.dim;
+        jb.seed = j.seed;
+        jb.phi_in = j.phi_in;
+        jb.phi_out = j.phi_out;
+        jb.active[0] = reinterpret_cast<uint8_t *>(take(nn));
+        jb.active[1] = reinterpret_cast<uint8_t *>(take(nn));
+        jb.starts = reinterpret_cast<int32_t *>(take(4 * nn));
+        jb.walks = reinterpret_cast<int32_t *>(take(4 * nn * wpr * L));
+        jb.counts = reinterpret_cast<uint32_t *>(take(4 * nn));
+        jb.thr = reinterpret_cast<uint64_t *>(take(8 * nn));
+        jb.alias = reinterpret_cast<int32_t *>(take(4 * nn));
+        jb.W = reinterpret_cast<uint64_t *>(take(8 * nn));
+        jb.key = reinterpret_cast<u128 *>(take(16 * nn));
+        jb.rank = reinterpret_cast<int32_t *>(take(4 * nn));
+        jb.light_D = reinterpret_cast<u128 *>(take(16 * nn));
+        jb.heavy_idx = reinterpret_cast<int32_t *>(take(4 * nn));
+        jb.heavy_E = reinterpret_cast<u128 *>(take(16 * nn));
+        const int32_t nt = std::max(1, ceil_div(std::max(jb.n, 1), kBTile));
+        jb.tile_base = tile;
+        jb.n_tiles = nt;
+        for (int32_t t = 0; t < nt; ++t) {
+            tile_job.push_back(i);
+            tile_start.push_back(t * kBTile);
+        }
+        tile += nt;
+    }
+    st = record_cuda_error(cudaMemcpy(base + o_jobs, b->jobs_h.data(), sizeof(BJob) * n_jobs, cudaMemcpyHostToDevice), "batch");
+    if (!st) st = record_cuda_error(cudaMemcpy(base + o_sp, slot_prefix.data(), sizeof(int64_t) * (n_jobs + 1), cudaMemcpyHostToDevice), "batch");
+    if (!st) st = record_cuda_error(cudaMemcpy(base + o_np, node_prefix.data(), sizeof(int64_t) * (n_jobs + 1), cudaMemcpyHostToDevice), "batch");
+    if (!st) st = record_cuda_error(cudaMemcpy(base + o_ip, item_prefix.data(), sizeof(int64_t) * (n_jobs + 1), cudaMemcpyHostToDevice), "batch");
+    if (!st) st = record_cuda_error(cudaMemcpy(base + o_tj, tile_job.data(), sizeof(int32_t) * n_tiles_total, cudaMemcpyHostToDevice), "batch");
+    if (!st) st = record_cuda_error(cudaMemcpy(base + o_ts, tile_start.data(), sizeof(int32_t) * n_tiles_total, cudaMemcpyHostToDevice), "batch");
+    if (!st) st = record_cuda_error(cudaMemset(base + o_rna, 0, sizeof(int32_t) * rec), "batch");
+    if (!st) st = record_cuda_error(cudaMemset(base + o_rnn, 0, sizeof(int32_t) * rec), "batch");
+    if (!st) st = record_cuda_error(cudaMemset(base + o_rl, 0, sizeof(double) * rec), "batch");
+    if (st) {
+        cudaFree(b->blob);
+        delete b;
+        return st;
+    }
+    b->item_prefix_h = item_prefix;
+    BArgs &a = b->args;
+    a.jobs = reinterpret_cast<const BJob *>(base + o_jobs);
+    a.st = reinterpret_cast<BState *>(base + o_st);
+    a.n_jobs = n_jobs;
+    a.slot_prefix = reinterpret_cast<const int64_t *>(base + o_sp);
+    a.node_prefix = reinterpret_cast<const int64_t *>(base + o_np);
+    a.item_prefix = reinterpret_cast<const int64_t *>(base + o_ip);
+    a.tile_job = reinterpret_cast<const int32_t *>(base + o_tj);
+    a.tile_start = reinterpret_cast<const int32_t *>(base + o_ts);
+    a.tile_count = reinterpret_cast<int32_t *>(base + o_tc);
+    a.tile_agg = reinterpret_cast<NoiseAgg *>(base + o_ta);
+    a.n_tiles = n_tiles_total;
+    a.n_slots = slot_prefix[n_jobs];
+    a.n_nodes = node_prefix[n_jobs];
+    a.L = L;
+    a.wpr = wpr;
+    a.window = tp->window;
+    a.K = tp->negatives;
+    a.max_rounds = R;
+    a.ks = fp->ks;
+    a.enabled = fp->enabled;
+    a.reactivate = fp->reactivate;
+    a.precision = tp->precision;
+    a.mu = fp->mu;
+    a.lr0 = tp->lr0;
+    a.lr_total_tokens = tp->lr_total_tokens;
+    a.rec_n_active = reinterpret_cast<int32_t *>(base + o_rna);
+    a.rec_n_next = reinterpret_cast<int32_t *>(base + o_rnn);
+    a.rec_loss = reinterpret_cast<double *>(base + o_rl);
+    *out = b;
+    return FELOG_OK;
+}
+
+extern "C" felog_status felog_batch_destroy(felog_batch *b) {
+    if (!b) return FELOG_OK;
+    drop_graph(b);
+    felog_status st = FELOG_OK;
+    if (b->blob) st = record_cuda_error(cudaFree(b->blob), "felog_batch_destroy");
+    delete b;
+    return st;
+}
+
+extern "C" size_t felog_batch_device_bytes(const felog_batch *b) { return b ? b->blob_bytes : 0; }
+
+extern "C" felog_status felog_batch_reset(felog_batch *b, void *stream) {
+    if (!b) return FELOG_ERR_INVALID_ARG;
+    return do_reset(b, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" felog_status felog_batch_step(felog_batch *b, void *stream) {
+    if (!b) return FELOG_ERR_INVALID_ARG;
+    return do_step(b, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" felog_status felog_batch_run(felog_batch *b, int32_t use_graph, void *stream) {
+    if (!b) return FELOG_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int R = b->fp.max_rounds;
+    if (!use_graph || s == nullptr) {
+        felog_status st = do_reset(b, s);
+        for (int r = 0; !st && r < R; ++r) st = do_step(b, s);
+        return st;
+    }
+    if (!b->graph || b->graph_rounds != R) {
+        drop_graph(b);
+        felog_status st = record_cuda_error(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "capture");
+        if (st) return st;
+        felog_status st2 = do_reset(b, s);
+        for (int r = 0; !st2 && r < R; ++r) st2 = do_step(b, s);
+        cudaGraph_t g = nullptr;
+        st = record_cuda_error(cudaStreamEndCapture(s, &g), "capture");
+        if (st2 || st) {
+            if (g) cudaGraphDestroy(g);
+            return st2 ? st2 : st;
+        }
+        st = record_cuda_error(cudaGraphInstantiate(&b->graph, g, 0), "graph instantiate");
+        cudaGraphDestroy(g);
+        if (st) return st;
+        b->graph_rounds = R;
+    }
+    return record_cuda_error(cudaGraphLaunch(b->graph, s), "graph launch");
+}
+
+extern "C" felog_status felog_batch_read(felog_batch *b, felog_job_stats *stats, int32_t *rec_n_active,
+                                         double *rec_loss, void *stream) {
+    if (!b) return FELOG_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    felog_status st = record_cuda_error(cudaStreamSynchronize(s), "felog_batch_read");
+    if (st) return st;
+    const int n = b->n_jobs;
+    const int R = std::max(b->fp.max_rounds, 1);
+    std::vector<BState> sts(n);
+    std::vector<int32_t> rna(static_cast<size_t>(R) * n), rnn(static_cast<size_t>(R) * n);
+    std::vector<double> rl(static_cast<size_t>(R) * n);
+    st = record_cuda_error(cudaMemcpy(sts.data(), b->args.st, sizeof(BState) * n, cudaMemcpyDeviceToHost), "read");
+    if (!st) st = record_cuda_error(cudaMemcpy(rna.data(), b->args.rec_n_active, sizeof(int32_t) * rna.size(), cudaMemcpyDeviceToHost), "read");
+    if (!st) st = record_cuda_error(cudaMemcpy(rnn.data(), b->args.rec_n_next, sizeof(int32_t) * rnn.size(), cudaMemcpyDeviceToHost), "read");
+    if (!st) st = record_cuda_error(cudaMemcpy(rl.data(), b->args.rec_loss, sizeof(double) * rl.size(), cudaMemcpyDeviceToHost), "read");
+    if (st) return st;
+    for (int32_t c = 0; c < n; ++c) {
+        const int32_t i = b->position[c];
+        if (stats) {
+            felog_job_stats &o = stats[c];
+            o.rounds = sts[i].round;
+            o.done = sts[i].done;
+            o.tokens = sts[i].clock;
+            o.n_live = sts[i].n_live;
+            o.loss_last = sts[i].round > 0 ? rl[static_cast<size_t>(sts[i].round - 1) * n + i] : 0.0;
+        }
+        for (int32_t r = 0; r < b->fp.max_rounds; ++r) {
+            if (rec_n_active) rec_n_active[static_cast<size_t>(r) * n + c] = rna[static_cast<size_t>(r) * n + i];
+            if (rec_loss) rec_loss[static_cast<size_t>(r) * n + c] = rl[static_cast<size_t>(r) * n + i];
+        }
+    }
+    return FELOG_OK;
+}
+
+extern "C" felog_status felog_batch_job_buffers(const felog_batch *b, int32_t job, felog_job_buffers *out) {
+    if (!b || !out || job < 0 || job >= b->n_jobs) return FELOG_ERR_INVALID_ARG;
+    const BJob &jb = b->jobs_h[b->position[job]];
+    out->active[0] = jb.active[0];
+    out->active[1] = jb.active[1];
+    out->starts = jb.starts;
+    out->walks = jb.walks;
+    out->counts = jb.counts;
+    out->thr = jb.thr;
+    out->alias = jb.alias;
+    return FELOG_OK;
+}
+
+// Autotuner: times the walk launch shape, the trainer's blocks per SM and the
+// feedback block size on round 0 of this batch (tables re-initialised after
+// each probe) and keeps the fastest of each.  With cache_path, results are
+// looked up and stored in a text file keyed by GPU name and batch shape.
+extern "C" felog_status felog_batch_autotune(felog_batch *b, const char *cache_path, felog_tuning *out,
+                                             void *stream) {
+    if (!b) return FELOG_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop;
+    cudaGetDeviceProperties(&prop, dev);
+    int64_t dsum = 0;
+    for (int32_t d : b->dims) dsum += d;
+    std::string gpu(prop.name);
+    std::replace(gpu.begin(), gpu.end(), ' ', '_');  // the cache file is whitespace separated
+    const std::string key = gpu + "|n=" + std::to_string(b->args.n_nodes) + "|jobs=" +
+                            std::to_string(b->n_jobs) + "|dsum=" + std::to_string(dsum) + "|L=" +
+                            std::to_string(b->wp.length) + "|w=" + std::to_string(b->tp.window) + "|K=" +
+                            std::to_string(b->tp.negatives) + "|p=" + std::to_string(b->tp.precision);
+    if (cache_path) {
+        std::ifstream in(cache_path);
+        std::string k;
+        int wb, sb, fb;
+        while (in >> k >> wb >> sb >> fb) {
+            if (k == key) {
+                b->tune.walk_block = wb;
+                b->tune.sgns_blocks_per_sm = sb;
+                b->tune.feedback_blocks_per_sm = fb;
+                drop_graph(b);
+                if (out) *out = felog_tuning{wb, sb, fb, 1};
+                return FELOG_OK;
+            }
+        }
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    auto time_phase = [&](unsigned before, unsigned phase) -> float {
+        do_reset(b, s);
+        do_step(b, s, before);
+        cudaEventRecord(e0, s);
+        do_step(b, s, phase);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return ms;
+    };
+    HostTuning best = b->tune;
+    float best_ms = 1e30f;
+    for (int wb : {128, 256, 512}) {
+        b->tune.walk_block = wb;
+        const float ms = time_phase(1, 2);
+        if (ms < best_ms) { best_ms = ms; best.walk_block = wb; }
+    }
+    b->tune.walk_block = best.walk_block;
+    best_ms = 1e30f;
+    for (int sb : {1, 2}) {
+        b->tune.sgns_blocks_per_sm = sb;
+        const float ms = time_phase(1 | 2 | 4, 8);
+        if (ms < best_ms) { best_ms = ms; best.sgns_blocks_per_sm = sb; }
+    }
+    b->tune.sgns_blocks_per_sm = best.sgns_blocks_per_sm;
+    best_ms = 1e30f;
+    for (int fb : {4, 8, 16}) {
+        b->tune.feedback_blocks_per_sm = fb;
+        const float ms = time_phase(1 | 2 | 4 | 8, 16);
+        if (ms < best_ms) { best_ms = ms; best.feedback_blocks_per_sm = fb; }
+    }
+    b->tune = best;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    felog_status st = do_reset(b, s);
+    if (st) return st;
+    st = record_cuda_error(cudaStreamSynchronize(s), "autotune");
+    if (st) return st;
+    drop_graph(b);
+    if (cache_path) {
+        std::ofstream o(cache_path, std::ios::app);
+        o << key << " " << best.walk_block << " " << best.sgns_blocks_per_sm << " " << best.feedback_blocks_per_sm
+          << "\n";
+    }
+    if (out) *out = felog_tuning{best.walk_block, best.sgns_blocks_per_sm, best.feedback_blocks_per_sm, 0};
+    return FELOG_OK;
+}

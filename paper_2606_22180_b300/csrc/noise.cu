@@ -20,25 +20,9 @@
 //                  i* = first light with D(i*) > E(j) (D_total if none).
 // Prefix sums can exceed 2^64, so they are carried in unsigned __int128.
 // Everything is integer, so the table is identical to the sequential one.
-#include "common.cuh"
+#include "noise_core.cuh"
 
 namespace felog {
-
-typedef unsigned __int128 u128;
-
-constexpr int kNoiseThreads = 256;
-constexpr int kNoiseItems = 16;
-constexpr int kNoiseTile = kNoiseThreads * kNoiseItems;
-
-struct NoiseAgg {
-    u128 D, E;
-    int32_t nL, nH;
-};
-
-__device__ __forceinline__ double three_quarter_power(uint32_t c) {
-    const double x = static_cast<double>(c);
-    return __dmul_rn(__dsqrt_rn(x), __dsqrt_rn(__dsqrt_rn(x)));
-}
 
 __global__ void k_noise_max(const uint32_t *__restrict__ counts, int32_t n, uint32_t *__restrict__ cmax) {
     uint32_t m = 0;
@@ -70,14 +54,6 @@ __global__ void k_noise_weights(const uint32_t *__restrict__ counts, int32_t n,
     // warp sum of 64-bit values
     for (int o = 16; o; o >>= 1) local += __shfl_xor_sync(kFull, local, o);
     if ((threadIdx.x & 31) == 0 && local) atomicAdd(S, local);
-}
-
-// Per-item classification given S.
-__device__ __forceinline__ void classify(uint64_t Wv, uint64_t n, uint64_t S, bool &light,
-                                         uint64_t &amount) {
-    const uint64_t m = n * Wv;
-    light = m < S;
-    amount = light ? S - m : m - S;
 }
 
 __global__ void __launch_bounds__(kNoiseThreads)
@@ -193,34 +169,8 @@ __global__ void k_noise_finish(const uint64_t *__restrict__ W, int32_t n,
             alias[v] = static_cast<int32_t>(v);
             continue;
         }
-        const uint64_t m = static_cast<uint64_t>(n) * W[v];
-        const u128 k = key[v];
-        if (m < S) {
-            // first heavy with E >= D(i)
-            int32_t lo = 0, hi = nH;  // answer in [0, nH)
-            while (lo < hi) {
-                const int32_t mid = (lo + hi) >> 1;
-                if (heavy_E[mid] >= k) hi = mid;
-                else lo = mid + 1;
-            }
-            thr[v] = m;
-            alias[v] = heavy_idx[lo < nH ? lo : nH - 1];
-        } else if (k >= Dtot) {
-            thr[v] = S;
-            alias[v] = static_cast<int32_t>(v);
-        } else {
-            // first light with D > E(j)
-            int32_t lo = 0, hi = nL;
-            while (lo < hi) {
-                const int32_t mid = (lo + hi) >> 1;
-                if (light_D[mid] > k) hi = mid;
-                else lo = mid + 1;
-            }
-            const u128 Dc = lo < nL ? light_D[lo] : Dtot;
-            thr[v] = S - static_cast<uint64_t>(Dc - k);
-            const int32_t r = rank[v] + 1;
-            alias[v] = heavy_idx[r < nH ? r : nH - 1];
-        }
+        alias_entry(static_cast<int32_t>(v), W[v], static_cast<uint64_t>(n), S, key[v], rank[v], light_D, nL,
+                    heavy_idx, heavy_E, nH, Dtot, thr + v, alias + v);
     }
 }
 

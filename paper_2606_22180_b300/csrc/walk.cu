@@ -10,7 +10,7 @@
 #include <cstring>
 #include <mutex>
 
-#include "common.cuh"
+#include "walk_core.cuh"
 
 namespace felog {
 
@@ -223,61 +223,7 @@ __global__ void __launch_bounds__(kWalkThreads)
         const int32_t i = static_cast<int32_t>(w - static_cast<int64_t>(j) * n_starts);
         const int32_t s = __ldg(starts + i);
         const uint32_t x2 = round * static_cast<uint32_t>(wpr) + static_cast<uint32_t>(j);
-        int32_t *row = walks + w * L;
-        int32_t v = s;
-        bool alive = true;
-        if (COUNT) atomicAdd(counts + s, 1u);
-        if (VEC) {
-            int4 buf;
-            buf.x = s;
-            for (int32_t t0 = 0; t0 < L; t0 += 4) {
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int32_t t = t0 + u;
-                    if (t == 0) continue;
-                    int32_t nxt = -1;
-                    if (alive) {
-                        const int32_t lo = __ldg(offsets + v), hi = __ldg(offsets + v + 1);
-                        const int64_t deg = static_cast<int64_t>(hi) - lo;
-                        if (deg == 0) {
-                            alive = false;
-                        } else {
-                            const u32x4 r = philox(seed, static_cast<uint32_t>(t),
-                                                   static_cast<uint32_t>(s), x2, kStreamWalk);
-                            const uint64_t idx = mulhi64(lo64(r), static_cast<uint64_t>(deg));
-                            nxt = __ldg(cols + lo + static_cast<int64_t>(idx));
-                            v = nxt;
-                            if (COUNT) atomicAdd(counts + nxt, 1u);
-                        }
-                    }
-                    if (u == 0) buf.x = nxt;
-                    if (u == 1) buf.y = nxt;
-                    if (u == 2) buf.z = nxt;
-                    if (u == 3) buf.w = nxt;
-                }
-                *reinterpret_cast<int4 *>(row + t0) = buf;
-            }
-        } else {
-            row[0] = s;
-            for (int32_t t = 1; t < L; ++t) {
-                int32_t nxt = -1;
-                if (alive) {
-                    const int32_t lo = __ldg(offsets + v), hi = __ldg(offsets + v + 1);
-                    const int64_t deg = static_cast<int64_t>(hi) - lo;
-                    if (deg == 0) {
-                        alive = false;
-                    } else {
-                        const u32x4 r = philox(seed, static_cast<uint32_t>(t),
-                                               static_cast<uint32_t>(s), x2, kStreamWalk);
-                        const uint64_t idx = mulhi64(lo64(r), static_cast<uint64_t>(deg));
-                        nxt = __ldg(cols + lo + static_cast<int64_t>(idx));
-                        v = nxt;
-                        if (COUNT) atomicAdd(counts + nxt, 1u);
-                    }
-                }
-                row[t] = nxt;
-            }
-        }
+        walk_fill_row<COUNT, VEC>(offsets, cols, s, L, seed, x2, walks + w * L, counts);
     }
 }
 

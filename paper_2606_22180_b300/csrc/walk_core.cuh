@@ -1,0 +1,75 @@
+// One uniform truncated walk (Section 2; Algorithm 1, Sampling), shared by
+// the single-graph and multi-graph walk kernels.
+#pragma once
+
+#include "common.cuh"
+
+namespace felog {
+
+// Fills row[0..L) with the walk from local node s keyed by x2 (= round * wpr
+// + rep): step t >= 1 draws Philox(x0=t, x1=s, x2, stream 0) and moves to
+// neighbour floor(u64 * deg / 2^64).  A node without neighbours ends the walk
+// and the rest of the row is -1.  COUNT adds every written node to counts[];
+// VEC stores 4 steps at a time (L % 4 == 0, row 16-byte aligned).
+template <bool COUNT, bool VEC>
+__device__ __forceinline__ void walk_fill_row(const int32_t *__restrict__ offsets,
+                                              const int32_t *__restrict__ cols, int32_t s, int32_t L,
+                                              uint64_t seed, uint32_t x2, int32_t *__restrict__ row,
+                                              uint32_t *__restrict__ counts) {
+    int32_t v = s;
+    bool alive = true;
+    if (COUNT) atomicAdd(counts + s, 1u);
+    if (VEC) {
+        int4 buf;
+        buf.x = s;
+        for (int32_t t0 = 0; t0 < L; t0 += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int32_t t = t0 + u;
+                if (t == 0) continue;
+                int32_t nxt = -1;
+                if (alive) {
+                    const int32_t lo = __ldg(offsets + v), hi = __ldg(offsets + v + 1);
+                    const int64_t deg = static_cast<int64_t>(hi) - lo;
+                    if (deg == 0) {
+                        alive = false;
+                    } else {
+                        const u32x4 r = philox(seed, static_cast<uint32_t>(t),
+                                               static_cast<uint32_t>(s), x2, kStreamWalk);
+                        const uint64_t idx = mulhi64(lo64(r), static_cast<uint64_t>(deg));
+                        nxt = __ldg(cols + lo + static_cast<int64_t>(idx));
+                        v = nxt;
+                        if (COUNT) atomicAdd(counts + nxt, 1u);
+                    }
+                }
+                if (u == 0) buf.x = nxt;
+                if (u == 1) buf.y = nxt;
+                if (u == 2) buf.z = nxt;
+                if (u == 3) buf.w = nxt;
+            }
+            *reinterpret_cast<int4 *>(row + t0) = buf;
+        }
+    } else {
+        row[0] = s;
+        for (int32_t t = 1; t < L; ++t) {
+            int32_t nxt = -1;
+            if (alive) {
+                const int32_t lo = __ldg(offsets + v), hi = __ldg(offsets + v + 1);
+                const int64_t deg = static_cast<int64_t>(hi) - lo;
+                if (deg == 0) {
+                    alive = false;
+                } else {
+                    const u32x4 r = philox(seed, static_cast<uint32_t>(t),
+                                           static_cast<uint32_t>(s), x2, kStreamWalk);
+                    const uint64_t idx = mulhi64(lo64(r), static_cast<uint64_t>(deg));
+                    nxt = __ldg(cols + lo + static_cast<int64_t>(idx));
+                    v = nxt;
+                    if (COUNT) atomicAdd(counts + nxt, 1u);
+                }
+            }
+            row[t] = nxt;
+        }
+    }
+}
+
+}  // namespace felog

@@ -30,6 +30,9 @@ SYMBOLS = [
     "felog_train_workspace_bytes", "felog_train",
     "felog_feedback",
     "felog_embed_workspace_bytes", "felog_embed",
+    "felog_batch_create", "felog_batch_destroy", "felog_batch_device_bytes", "felog_batch_reset",
+    "felog_batch_step", "felog_batch_run", "felog_batch_read", "felog_batch_job_buffers",
+    "felog_batch_autotune",
 ]
 
 
@@ -101,6 +104,15 @@ def load() -> ctypes.CDLL:
         "felog_feedback": (st, [P, P, i32, i32, P, u64, i32, P, P, P, P, P]),
         "felog_embed_workspace_bytes": (sz, [i32, P, P]),
         "felog_embed": (st, [P, P, P, P, u64, P, P, P, P, P, sz, P]),
+        "felog_batch_create": (st, [P, i32, P, P, P, P]),
+        "felog_batch_destroy": (st, [P]),
+        "felog_batch_device_bytes": (sz, [P]),
+        "felog_batch_reset": (st, [P, P]),
+        "felog_batch_step": (st, [P, P]),
+        "felog_batch_run": (st, [P, i32, P]),
+        "felog_batch_read": (st, [P, P, P, P, P]),
+        "felog_batch_job_buffers": (st, [P, i32, P]),
+        "felog_batch_autotune": (st, [P, ctypes.c_char_p, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -325,3 +337,128 @@ def felog_embed(g: DeviceGraph, length: int, walks_per_round: int, tp: _TrainPar
                            seed, _ptr(phi_in), _ptr(phi_out), stats, ctypes.byref(rounds),
                            _ptr(workspace), workspace.numel(), _stream()), "felog_embed")
     return phi_in, phi_out, [stats[i].as_dict() for i in range(rounds.value)]
+
+
+# ---------------------------------------------------------------------------
+# Batching form
+# ---------------------------------------------------------------------------
+class _Job(ctypes.Structure):
+    _fields_ = [("graph", _Csr), ("seed", ctypes.c_uint64), ("dim", ctypes.c_int32),
+                ("phi_in", ctypes.c_void_p), ("phi_out", ctypes.c_void_p)]
+
+
+class JobStats(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int32), ("done", ctypes.c_int32), ("tokens", ctypes.c_int64),
+                ("n_live", ctypes.c_int64), ("loss_last", ctypes.c_double)]
+
+
+class _JobBuffers(ctypes.Structure):
+    _fields_ = [("active0", ctypes.c_void_p), ("active1", ctypes.c_void_p), ("starts", ctypes.c_void_p),
+                ("walks", ctypes.c_void_p), ("counts", ctypes.c_void_p), ("thr", ctypes.c_void_p),
+                ("alias", ctypes.c_void_p)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("walk_block", ctypes.c_int32), ("sgns_blocks_per_sm", ctypes.c_int32),
+                ("feedback_blocks_per_sm", ctypes.c_int32), ("from_cache", ctypes.c_int32)]
+
+
+class Batch:
+    """Many embedding jobs trained together (felog_batch_* calls).
+
+    graphs: list of DeviceGraph; dims and seeds per job.  The batch owns its
+    per-job work buffers; the tables it trains are allocated here and exposed
+    as ``phi_in[j]`` / ``phi_out[j]``.
+    """
+
+    def __init__(self, graphs, dims, seeds, length, walks_per_round, tp: _TrainParams,
+                 fp: _FeedbackParams):
+        _require_cuda(*[g.offsets for g in graphs])
+        lib = load()
+        self.lib, self.graphs, self.tp, self.fp = lib, list(graphs), tp, fp
+        dt = table_dtype(tp.precision)
+        dev = graphs[0].offsets.device
+        self.phi_in = [torch.empty((g.n, d), dtype=dt, device=dev) for g, d in zip(graphs, dims)]
+        self.phi_out = [torch.empty((g.n, d), dtype=dt, device=dev) for g, d in zip(graphs, dims)]
+        jobs = (_Job * len(graphs))()
+        for j, (g, d, sd) in enumerate(zip(graphs, dims, seeds)):
+            jobs[j] = _Job(g._c(), sd, d, self.phi_in[j].data_ptr(), self.phi_out[j].data_ptr())
+        self.wp = _WalkParams(length, walks_per_round)
+        handle = ctypes.c_void_p(0)
+        _check(lib.felog_batch_create(jobs, len(graphs), ctypes.byref(self.wp), ctypes.byref(tp),
+                                      ctypes.byref(fp), ctypes.byref(handle)), "felog_batch_create")
+        self.handle = handle
+        self.n_jobs = len(graphs)
+
+    def close(self):
+        if self.handle:
+            self.lib.felog_batch_destroy(self.handle)
+            self.handle = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def device_bytes(self) -> int:
+        return int(self.lib.felog_batch_device_bytes(self.handle))
+
+    def reset(self):
+        _check(self.lib.felog_batch_reset(self.handle, _stream()), "felog_batch_reset")
+
+    def step(self):
+        _check(self.lib.felog_batch_step(self.handle, _stream()), "felog_batch_step")
+
+    def run(self, use_graph: bool = True):
+        _check(self.lib.felog_batch_run(self.handle, int(use_graph), _stream()), "felog_batch_run")
+
+    def autotune(self, cache_path: str | None = None) -> dict:
+        t = Tuning()
+        _check(self.lib.felog_batch_autotune(self.handle, cache_path.encode() if cache_path else None,
+                                             ctypes.byref(t), _stream()), "felog_batch_autotune")
+        return {k: getattr(t, k) for k, _ in t._fields_}
+
+    def read(self):
+        """Per-job stats (dicts) and per-round |V_a| and loss arrays [rounds, jobs]."""
+        import numpy as np
+
+        stats = (JobStats * self.n_jobs)()
+        R = max(self.fp.max_rounds, 1)
+        na = np.zeros((R, self.n_jobs), np.int32)
+        ls = np.zeros((R, self.n_jobs), np.float64)
+        _check(self.lib.felog_batch_read(self.handle, stats, na.ctypes.data_as(ctypes.c_void_p),
+                                         ls.ctypes.data_as(ctypes.c_void_p), _stream()), "felog_batch_read")
+        return [{k: getattr(stats[j], k) for k, _ in JobStats._fields_} for j in range(self.n_jobs)], na, ls
+
+    def job_walks(self, j: int, rows: int) -> torch.Tensor:
+        """A copy of job j's walks of the last round (rows = its |V_a| * wpr)."""
+        b = _JobBuffers()
+        _check(self.lib.felog_batch_job_buffers(self.handle, j, ctypes.byref(b)), "felog_batch_job_buffers")
+        return _device_view(b.walks, rows * self.wp.length, torch.int32).view(rows, self.wp.length).clone()
+
+    def job_table(self, j: int):
+        """Copies of job j's alias table (thr, alias) and corpus counts of the last round."""
+        b = _JobBuffers()
+        _check(self.lib.felog_batch_job_buffers(self.handle, j, ctypes.byref(b)), "felog_batch_job_buffers")
+        n = self.graphs[j].n
+        return (_device_view(b.thr, n, torch.int64).clone(), _device_view(b.alias, n, torch.int32).clone(),
+                _device_view(b.counts, n, torch.int32).clone())
+
+
+class _CudaArray:
+    """A library-owned device buffer exposed through __cuda_array_interface__."""
+
+    _TYPESTR = {torch.int32: "<i4", torch.int64: "<i8", torch.uint8: "|u1"}
+
+    def __init__(self, ptr: int, numel: int, dtype):
+        self.__cuda_array_interface__ = {"data": (int(ptr), False), "shape": (int(numel),),
+                                         "typestr": self._TYPESTR[dtype], "version": 2}
+
+
+def _device_view(ptr: int, numel: int, dtype) -> torch.Tensor:
+    """A tensor aliasing numel elements at a library-owned device address."""
+    if numel == 0:
+        return torch.empty(0, dtype=dtype, device="cuda")
+    torch.cuda.current_stream().synchronize()
+    return torch.as_tensor(_CudaArray(ptr, numel, dtype), device="cuda")

@@ -1,0 +1,146 @@
+"""Batching form: many jobs in one launch sequence give each job the result
+it gets alone -- walks, corpus counts and alias tables bit-exact, the same
+per-round schedule without feedback, Hogwild quality within 0.005 AUC."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2606_22180_b300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fl():
+    from paper_2606_22180_b300 import build, felog
+
+    build.build()
+    felog.load()
+    return felog
+
+
+def _graphs():
+    out = []
+    for i in range(6):
+        if i % 2 == 0:
+            g, _ = inputs.sbm(800 + 700 * i, 4 + i, 0.03, 0.002, seed=100 + i)
+        else:
+            g = inputs.rmat(10 + i // 2, 8, seed=200 + i)
+        out.append(g)
+    return out
+
+
+DIMS = [64, 128, 32, 128, 64, 64]
+L, W, K = 40, 5, 5
+
+
+def test_batch_round0_walks_counts_tables_equal_solo(fl, orc):
+    gs = _graphs()
+    dgs = [fl.DeviceGraph.from_host(g) for g in gs]
+    seeds = [11 + 7 * i for i in range(len(gs))]
+    tp = fl.train_params(64, W, K, 0.025, 0, fl.FELOG_SGNS_HOGWILD, 4096, fl.FELOG_FP32)
+    fp = fl.feedback_params(True, 0.9, 8, 4, False)
+    b = fl.Batch(dgs, DIMS, seeds, L, 1, tp, fp)
+    b.reset()
+    b.step()
+    stats, na, _ = b.read()
+    for j, g in enumerate(gs):
+        live = np.nonzero(g.degrees() > 0)[0].astype(np.int32)
+        assert na[0, j] == live.shape[0]
+        ref = orc.walk(g.offsets, g.cols, live, L, 1, seeds[j], 0)
+        got = b.job_walks(j, live.shape[0]).cpu().numpy()
+        assert np.array_equal(got, ref), j
+        thr, alias, counts = b.job_table(j)
+        cnt = orc.counts(ref, g.n)
+        assert np.array_equal(counts.cpu().numpy().astype(np.uint32), cnt)
+        _, thr_r, alias_r, _ = orc.noise_table(cnt)
+        assert np.array_equal(thr.cpu().numpy().astype(np.uint64), thr_r), j
+        assert np.array_equal(alias.cpu().numpy(), alias_r), j
+    b.close()
+
+
+def test_batch_init_matches_solo_and_graph_capture(fl):
+    gs = _graphs()[:3]
+    dgs = [fl.DeviceGraph.from_host(g) for g in gs]
+    tp = fl.train_params(64, W, K, 0.025, 0, fl.FELOG_SGNS_HOGWILD, 4096, fl.FELOG_BF16_SR)
+    fp = fl.feedback_params(False, 0.65, 8, 3, False)
+    b = fl.Batch(dgs, DIMS[:3], [1, 2, 3], L, 1, tp, fp)
+    b.reset()
+    torch.cuda.synchronize()
+    for j, g in enumerate(gs):
+        pi, _ = fl.felog_init_tables(g.n, DIMS[j], fl.FELOG_BF16_SR, j + 1)
+        assert torch.equal(b.phi_in[j], pi)
+        assert (b.phi_out[j] == 0).all()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        b.run(use_graph=True)   # captured once
+        b.run(use_graph=True)   # relaunched
+    s.synchronize()
+    stats, na, loss = b.read()
+    for j, g in enumerate(gs):
+        live = int((g.degrees() > 0).sum())
+        assert stats[j]["rounds"] == 3 and stats[j]["done"] == 1
+        assert stats[j]["tokens"] == 3 * live * L
+        assert list(na[:, j]) == [live] * 3
+        assert np.all(np.isfinite(loss[:, j])) and np.all(loss[:, j] > 0)
+    b.close()
+
+
+def test_batch_hogwild_quality_equals_solo(fl):
+    """Each job's link-prediction AUC in the batch is within 0.005 of the
+    same job trained alone (mean over jobs)."""
+    from paper_2606_22180_b300 import evaluate
+
+    gs, splits = [], []
+    for i in range(6):
+        g, _ = inputs.sbm(1000 + 500 * i, 8, 0.04, 0.002, seed=300 + i)
+        sp = inputs.link_split(g, 0.1, i)
+        gs.append(sp.train)
+        splits.append(sp)
+    dgs = [fl.DeviceGraph.from_host(g) for g in gs]
+    dims = [64] * 6
+    seeds = [5 + i for i in range(6)]
+    tp = fl.train_params(64, W, K, 0.025, 0, fl.FELOG_SGNS_HOGWILD, 4096, fl.FELOG_FP32)
+    fp = fl.feedback_params(False, 0.65, 8, 10, False)
+    b = fl.Batch(dgs, dims, seeds, L, 1, tp, fp)
+    b.run(use_graph=False)
+    b.read()
+    diffs = []
+    for j in range(6):
+        solo, _, _ = fl.felog_embed(dgs[j], L, 1, tp, fp, seeds[j])
+        a_b = evaluate.link_auc(b.phi_in[j], splits[j].pos, splits[j].neg)
+        a_s = evaluate.link_auc(solo, splits[j].pos, splits[j].neg)
+        diffs.append(a_b - a_s)
+    print("batch - solo AUC per job:", np.round(diffs, 4))
+    assert abs(np.mean(diffs)) <= 0.005
+    b.close()
+
+
+def test_batch_autotune_and_cache(fl, tmp_path):
+    gs = _graphs()[:4]
+    dgs = [fl.DeviceGraph.from_host(g) for g in gs]
+    tp = fl.train_params(64, W, K, 0.025, 0, fl.FELOG_SGNS_HOGWILD, 4096, fl.FELOG_BF16_SR)
+    fp = fl.feedback_params(True, 0.65, 8, 2, False)
+    b = fl.Batch(dgs, DIMS[:4], [1, 2, 3, 4], L, 1, tp, fp)
+    cache = str(tmp_path / "tune.txt")
+    t1 = b.autotune(cache)
+    assert t1["from_cache"] == 0 and t1["walk_block"] in (128, 256, 512)
+    t2 = b.autotune(cache)
+    assert t2["from_cache"] == 1
+    assert {k: t1[k] for k in t1 if k != "from_cache"} == {k: t2[k] for k in t2 if k != "from_cache"}
+    b.run(use_graph=False)
+    stats, _, _ = b.read()
+    assert all(s["rounds"] >= 1 for s in stats)
+    b.close()
+
+
+def test_batch_rejects_unsupported(fl):
+    g = _graphs()[0]
+    dg = fl.DeviceGraph.from_host(g)
+    tp = fl.train_params(64, W, 9, 0.025, 0, fl.FELOG_SGNS_HOGWILD, 4096, fl.FELOG_FP32)
+    fp = fl.feedback_params(False, 0.65, 8, 2, False)
+    with pytest.raises(fl.FelogError):
+        fl.Batch([dg], [64], [1], L, 1, tp, fp)
+    tp = fl.train_params(64, W, K, 0.025, 0, fl.FELOG_SGNS_HOGWILD, 4096, fl.FELOG_FP32)
+    with pytest.raises(fl.FelogError):
+        fl.Batch([dg], [256], [1], L, 1, tp, fp)
