@@ -47,7 +47,8 @@ typedef enum {
     FELOG_ERR_BAD_CSR = 2,     /* CSR fails host-side validation */
     FELOG_ERR_WORKSPACE = 3,   /* workspace missing or smaller than required */
     FELOG_ERR_CUDA = 4,        /* CUDA launch / runtime error */
-    FELOG_ERR_UNSUPPORTED = 5  /* a parameter combination with no kernel */
+    FELOG_ERR_UNSUPPORTED = 5, /* a parameter combination with no kernel */
+    FELOG_ERR_TIMEOUT = 6      /* a bounded wait ran out */
 } felog_status;
 
 /* Undirected, unweighted graph (Table 1) in CSR form, device pointers.
@@ -315,6 +316,72 @@ felog_status felog_batch_job_buffers(const felog_batch *b, int32_t job, felog_jo
  * round 0 and keeps the fastest; cache_path (may be NULL) is a text file of
  * earlier results keyed by GPU name and batch shape.  Leaves the batch reset. */
 felog_status felog_batch_autotune(felog_batch *b, const char *cache_path, felog_tuning *out, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Serving form: a request loop over embedding jobs with continuous batching.
+ * Clients submit host CSRs at any time; a worker thread admits queued jobs
+ * first come first served when their device bytes (CSR, tables, work
+ * buffers; felog_server_job_bytes) fit in the HBM budget beside the
+ * resident jobs, runs one round of Algorithm 1 for all resident jobs
+ * together per iteration (each at its own round, the multi-graph step of the
+ * batching form), and on completion copies the job's phi_in to host memory
+ * and releases its device memory.  A job larger than the whole budget is
+ * rejected.  Times are seconds on the server's steady clock.
+ * ------------------------------------------------------------------------ */
+enum {
+    FELOG_JOB_QUEUED = 0,
+    FELOG_JOB_RUNNING = 1,
+    FELOG_JOB_DONE = 2,
+    FELOG_JOB_REJECTED = 3,
+    FELOG_JOB_FAILED = 4
+};
+
+typedef struct {
+    size_t hbm_budget;          /* bytes of device memory for resident jobs */
+    int32_t max_resident;       /* cap on resident jobs (<= 0: none) */
+    int32_t drain_on_destroy;   /* 1: destroy finishes queued and resident jobs first */
+    felog_walk_params walk;
+    felog_train_params train;   /* dim ignored (per job); HOGWILD, negatives <= 7 */
+    felog_feedback_params feedback;
+} felog_server_config;
+
+typedef struct {
+    int32_t state;              /* FELOG_JOB_* */
+    int32_t rounds;
+    int32_t n, dim;
+    int64_t tokens, n_live;
+    double t_submit, t_admit, t_done;
+    double loss_last;
+} felog_result;
+
+typedef struct {
+    int64_t submitted, admitted, completed, rejected, steps;
+    int32_t resident_jobs, peak_resident_jobs, queued, reserved;
+    size_t resident_bytes, peak_resident_bytes;
+    double busy_seconds;        /* time spent in rounds (device work + readback) */
+} felog_server_stats;
+
+typedef struct felog_server felog_server;
+
+felog_status felog_server_create(const felog_server_config *cfg, felog_server **out);
+/* finishes or abandons pending work (drain_on_destroy), frees everything */
+felog_status felog_server_destroy(felog_server *sv);
+double felog_server_now(const felog_server *sv);
+size_t felog_server_job_bytes(const felog_server *sv, int32_t n, int64_t nnz, int32_t dim);
+/* host CSR (validated: offsets monotone from 0 to nnz, cols in [0, n)),
+ * copied by the call; returns the request id */
+felog_status felog_server_submit(felog_server *sv, const int32_t *offsets, const int32_t *cols, int32_t n,
+                                 int64_t nnz, int32_t dim, uint64_t seed, uint64_t *id);
+felog_status felog_server_poll(felog_server *sv, uint64_t id, felog_result *out);
+/* waits until the request is done, rejected or failed (FELOG_ERR_TIMEOUT
+ * after timeout_s seconds) */
+felog_status felog_server_wait(felog_server *sv, uint64_t id, double timeout_s, felog_result *out);
+/* copies a finished request's phi_in ([n][dim] float, may be NULL) and
+ * forgets the request */
+felog_status felog_server_fetch(felog_server *sv, uint64_t id, float *phi_in_host);
+/* waits until nothing is queued or resident */
+felog_status felog_server_drain(felog_server *sv, double timeout_s);
+felog_status felog_server_get_stats(felog_server *sv, felog_server_stats *out);
 
 #ifdef __cplusplus
 }

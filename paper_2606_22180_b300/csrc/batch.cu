@@ -26,6 +26,7 @@
 #include <string>
 #include <vector>
 
+#include "batch_core.cuh"
 #include "feedback_core.cuh"
 #include "noise_core.cuh"
 #include "sgns_core.cuh"
@@ -34,61 +35,6 @@
 namespace felog {
 
 bool csr_shape_ok(const felog_csr *g);
-
-constexpr int kBThreads = 256;
-constexpr int kBWarps = kBThreads / 32;
-constexpr int kBTile = 4096;
-constexpr int kBTileItems = kBTile / kBThreads;  // 16 per thread
-
-struct BJob {
-    const int32_t *offsets, *cols;
-    int32_t n, dim;
-    uint64_t seed;
-    void *phi_in, *phi_out;
-    uint8_t *active[2];
-    int32_t *starts, *walks;
-    uint32_t *counts;
-    uint64_t *thr;
-    int32_t *alias;
-    uint64_t *W;
-    u128 *key;
-    int32_t *rank;
-    u128 *light_D;
-    int32_t *heavy_idx;
-    u128 *heavy_E;
-    int32_t tile_base, n_tiles;
-};
-
-struct BState {
-    int32_t round, cur, n_active, n_next;
-    int32_t done, pad0;
-    int64_t clock, n_live;
-    float inv_T, pad1;
-    unsigned long long S;
-    uint32_t cmax, pad2;
-    NoiseAgg total;
-    unsigned long long loss_acc;
-};
-
-struct BArgs {
-    const BJob *jobs;
-    BState *st;
-    int32_t n_jobs;
-    const int64_t *slot_prefix;  // [n_jobs + 1]
-    const int64_t *node_prefix;  // [n_jobs + 1]
-    const int64_t *item_prefix;  // [n_jobs + 1]
-    const int32_t *tile_job, *tile_start;
-    int32_t *tile_count;
-    NoiseAgg *tile_agg;
-    int32_t n_tiles;
-    int64_t n_slots, n_nodes;
-    int32_t L, wpr, window, K, max_rounds, ks, enabled, reactivate, precision;
-    double mu;
-    float lr0;
-    int64_t lr_total_tokens;
-    int32_t *rec_n_active, *rec_n_next;  // [max_rounds][n_jobs]
-    double *rec_loss;
-};
 
 // largest j with prefix[j] <= x (x < prefix[n_jobs])
 __device__ __forceinline__ int find_job(const int64_t *__restrict__ prefix, int n_jobs, int64_t x) {
@@ -104,19 +50,13 @@ __device__ __forceinline__ int find_job(const int64_t *__restrict__ prefix, int 
 // ---------------------------------------------------------------------------
 // set-up: per-job state, tables, V_a^0, learning-rate horizon
 // ---------------------------------------------------------------------------
-__global__ void k_b_state_init(BArgs a) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= a.n_jobs) return;
-    BState s{};
-    a.st[j] = s;
-}
-
 template <class T>
 __global__ void k_b_init(BArgs a) {
     for (int64_t x = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; x < a.n_nodes;
          x += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const int j = find_job(a.node_prefix, a.n_jobs, x);
         const BJob &jb = a.jobs[j];
+        if (jb.st->phase != 0) continue;
         const int32_t v = static_cast<int32_t>(x - a.node_prefix[j]);
         T *pin = static_cast<T *>(jb.phi_in) + static_cast<int64_t>(v) * jb.dim;
         T *pout = static_cast<T *>(jb.phi_out) + static_cast<int64_t>(v) * jb.dim;
@@ -144,7 +84,7 @@ __global__ void k_b_init(BArgs a) {
         const unsigned grp = __match_any_sync(act, j);
         const unsigned mine = grp & __ballot_sync(act, live);
         if (mine && (__ffs(mine) - 1) == static_cast<int>(threadIdx.x & 31))
-            atomicAdd(reinterpret_cast<unsigned long long *>(&a.st[j].n_live),
+            atomicAdd(reinterpret_cast<unsigned long long *>(&jb.st->n_live),
                       static_cast<unsigned long long>(__popc(mine)));
     }
 }
@@ -152,11 +92,14 @@ __global__ void k_b_init(BArgs a) {
 __global__ void k_b_lr(BArgs a) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= a.n_jobs) return;
+    BState &st = *a.jobs[j].st;
+    if (st.phase != 0) return;
     int64_t T = a.lr_total_tokens;
-    if (T <= 0) T = static_cast<int64_t>(a.max_rounds) * a.wpr * a.st[j].n_live * a.L;
+    if (T <= 0) T = static_cast<int64_t>(a.max_rounds) * a.wpr * st.n_live * a.L;
     if (T <= 0) T = 1;
-    a.st[j].inv_T = static_cast<float>(1.0 / static_cast<double>(T));
-    a.st[j].done = a.st[j].n_live == 0 || a.max_rounds == 0;
+    st.inv_T = static_cast<float>(1.0 / static_cast<double>(T));
+    st.done = st.n_live == 0 || a.max_rounds == 0;
+    st.phase = 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -167,7 +110,7 @@ __global__ void __launch_bounds__(kBThreads) k_b_compact_count(BArgs a) {
     const int t = blockIdx.x;
     const int j = a.tile_job[t];
     const BJob &jb = a.jobs[j];
-    const BState &st = a.st[j];
+    const BState &st = *a.jobs[j].st;
     int32_t c = 0;
     if (!st.done) {
         const int32_t start = a.tile_start[t];
@@ -194,7 +137,7 @@ __global__ void __launch_bounds__(kBThreads) k_b_compact_count(BArgs a) {
 __global__ void k_b_compact_scan(BArgs a) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= a.n_jobs) return;
-    BState &st = a.st[j];
+    BState &st = *a.jobs[j].st;
     st.S = 0;
     st.cmax = 0;
     st.loss_acc = 0;
@@ -222,7 +165,7 @@ __global__ void __launch_bounds__(kBThreads) k_b_compact_scatter(BArgs a) {
     const int t = blockIdx.x;
     const int j = a.tile_job[t];
     const BJob &jb = a.jobs[j];
-    const BState &st = a.st[j];
+    const BState &st = *a.jobs[j].st;
     if (st.done) return;  // uniform over the block
     const uint8_t *act = jb.active[st.cur];
     const int32_t my = a.tile_start[t] + threadIdx.x * kBTileItems;
@@ -258,7 +201,7 @@ __global__ void k_b_walk(BArgs a) {
     for (int64_t x = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; x < a.n_slots;
          x += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const int j = find_job(a.slot_prefix, a.n_jobs, x);
-        const BState &st = a.st[j];
+        const BState &st = *a.jobs[j].st;
         const int64_t o = x - a.slot_prefix[j];
         if (st.done || o >= static_cast<int64_t>(st.n_active) * a.wpr) continue;
         const BJob &jb = a.jobs[j];
@@ -276,22 +219,22 @@ __global__ void k_b_walk(BArgs a) {
 __global__ void __launch_bounds__(kBThreads) k_b_noise_max(BArgs a) {
     const int t = blockIdx.x;
     const int j = a.tile_job[t];
-    if (a.st[j].done) return;
+    if (a.jobs[j].st->done) return;
     const BJob &jb = a.jobs[j];
     uint32_t m = 0;
     const int32_t start = a.tile_start[t];
     for (int i = threadIdx.x; i < kBTile; i += kBThreads)
         if (start + i < jb.n) m = max(m, jb.counts[start + i]);
     m = __reduce_max_sync(kFull, m);
-    if ((threadIdx.x & 31) == 0 && m) atomicMax(&a.st[j].cmax, m);
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(&a.jobs[j].st->cmax, m);
 }
 
 __global__ void __launch_bounds__(kBThreads) k_b_noise_weights(BArgs a) {
     const int t = blockIdx.x;
     const int j = a.tile_job[t];
-    if (a.st[j].done) return;
+    if (a.jobs[j].st->done) return;
     const BJob &jb = a.jobs[j];
-    const uint32_t cm = a.st[j].cmax;
+    const uint32_t cm = a.jobs[j].st->cmax;
     const double wmax = cm ? three_quarter_power(cm) : 1.0;
     unsigned long long local = 0;
     const int32_t start = a.tile_start[t];
@@ -309,16 +252,16 @@ __global__ void __launch_bounds__(kBThreads) k_b_noise_weights(BArgs a) {
         local += w;
     }
     for (int o = 16; o; o >>= 1) local += __shfl_xor_sync(kFull, local, o);
-    if ((threadIdx.x & 31) == 0 && local) atomicAdd(&a.st[j].S, local);
+    if ((threadIdx.x & 31) == 0 && local) atomicAdd(&a.jobs[j].st->S, local);
 }
 
 __global__ void __launch_bounds__(kBThreads) k_b_noise_agg(BArgs a) {
     __shared__ NoiseAgg part[kBThreads];
     const int t = blockIdx.x;
     const int j = a.tile_job[t];
-    if (a.st[j].done) return;
+    if (a.jobs[j].st->done) return;
     const BJob &jb = a.jobs[j];
-    const uint64_t S = a.st[j].S;
+    const uint64_t S = a.jobs[j].st->S;
     const int32_t my = a.tile_start[t] + threadIdx.x * kBTileItems;
     NoiseAgg g{0, 0, 0, 0};
     for (int k = 0; k < kBTileItems; ++k) {
@@ -343,7 +286,7 @@ __global__ void __launch_bounds__(kBThreads) k_b_noise_agg(BArgs a) {
 
 __global__ void k_b_noise_scan(BArgs a) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= a.n_jobs || a.st[j].done) return;
+    if (j >= a.n_jobs || a.jobs[j].st->done) return;
     const BJob &jb = a.jobs[j];
     NoiseAgg run{0, 0, 0, 0};
     for (int32_t t = jb.tile_base; t < jb.tile_base + jb.n_tiles; ++t) {
@@ -351,16 +294,16 @@ __global__ void k_b_noise_scan(BArgs a) {
         a.tile_agg[t] = run;
         run.D += x.D; run.E += x.E; run.nL += x.nL; run.nH += x.nH;
     }
-    a.st[j].total = run;
+    a.jobs[j].st->total = run;
 }
 
 __global__ void __launch_bounds__(kBThreads) k_b_noise_scatter(BArgs a) {
     __shared__ NoiseAgg part[kBThreads];
     const int t = blockIdx.x;
     const int j = a.tile_job[t];
-    if (a.st[j].done) return;
+    if (a.jobs[j].st->done) return;
     const BJob &jb = a.jobs[j];
-    const uint64_t S = a.st[j].S;
+    const uint64_t S = a.jobs[j].st->S;
     const int32_t my = a.tile_start[t] + threadIdx.x * kBTileItems;
     NoiseAgg g{0, 0, 0, 0};
     for (int k = 0; k < kBTileItems; ++k) {
@@ -411,7 +354,7 @@ __global__ void k_b_noise_finish(BArgs a) {
     for (int64_t x = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; x < a.n_nodes;
          x += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const int j = find_job(a.node_prefix, a.n_jobs, x);
-        const BState &st = a.st[j];
+        const BState &st = *a.jobs[j].st;
         if (st.done) continue;
         const BJob &jb = a.jobs[j];
         const int32_t v = static_cast<int32_t>(x - a.node_prefix[j]);
@@ -438,7 +381,7 @@ __global__ void __launch_bounds__(kSgnsThreads, 2) k_b_sgns(BArgs a, int64_t ite
     const int64_t warps = static_cast<int64_t>(gridDim.x) * kWarps;
     for (int64_t it = item_lo + static_cast<int64_t>(blockIdx.x) * kWarps + wib; it < item_hi; it += warps) {
         const int j = find_job(a.item_prefix, a.n_jobs, it);
-        const BState &st = a.st[j];
+        const BState &st = *a.jobs[j].st;
         if (st.done) continue;
         const BJob &jb = a.jobs[j];
         const int64_t c_j = a.item_prefix[j + 1] - a.item_prefix[j];
@@ -451,7 +394,7 @@ __global__ void __launch_bounds__(kSgnsThreads, 2) k_b_sgns(BArgs a, int64_t ite
             loss_fx += hw_train_walk<D, T, KFIX>(v, jb.walks + wl * a.L, wl, wk, negs);
         for (int o = 16; o; o >>= 1) loss_fx += __shfl_xor_sync(kFull, loss_fx, o);
         if (lane == 0 && loss_fx != 0)
-            atomicAdd(&a.st[j].loss_acc, static_cast<unsigned long long>(loss_fx));
+            atomicAdd(&jb.st->loss_acc, static_cast<unsigned long long>(loss_fx));
     }
 }
 
@@ -466,7 +409,7 @@ __global__ void __launch_bounds__(kBThreads) k_b_feedback(BArgs a) {
     const int64_t warps = static_cast<int64_t>(gridDim.x) * kBWarps;
     for (int64_t x = static_cast<int64_t>(blockIdx.x) * kBWarps + wib; x < a.n_nodes; x += warps) {
         const int j = find_job(a.node_prefix, a.n_jobs, x);
-        const BState &st = a.st[j];
+        const BState &st = *a.jobs[j].st;
         if (st.done) continue;
         const BJob &jb = a.jobs[j];
         const int32_t v = static_cast<int32_t>(x - a.node_prefix[j]);
@@ -480,7 +423,7 @@ __global__ void __launch_bounds__(kBThreads) k_b_feedback(BArgs a) {
         const uint8_t next = a.enabled ? (evaluate && psi < a.mu) : (deg > 0);
         if (lane == 0) {
             jb.active[st.cur ^ 1][v] = next;
-            if (next) atomicAdd(&a.st[j].n_next, 1);
+            if (next) atomicAdd(&jb.st->n_next, 1);
         }
     }
 }
@@ -488,159 +431,248 @@ __global__ void __launch_bounds__(kBThreads) k_b_feedback(BArgs a) {
 __global__ void k_b_round_end(BArgs a) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= a.n_jobs) return;
-    BState &st = a.st[j];
+    BState &st = *a.jobs[j].st;
     if (st.done) return;
     const int r = st.round;
-    a.rec_n_active[static_cast<int64_t>(r) * a.n_jobs + j] = st.n_active;
-    a.rec_n_next[static_cast<int64_t>(r) * a.n_jobs + j] = st.n_next;
-    a.rec_loss[static_cast<int64_t>(r) * a.n_jobs + j] =
-        static_cast<double>(static_cast<long long>(st.loss_acc)) / kLossScale;
+    const BJob &jb = a.jobs[j];
+    jb.rec_n_active[r] = st.n_active;
+    jb.rec_n_next[r] = st.n_next;
+    jb.rec_loss[r] = static_cast<double>(static_cast<long long>(st.loss_acc)) / kLossScale;
     st.clock += static_cast<int64_t>(st.n_active) * a.wpr * a.L;
     st.round = r + 1;
     st.cur ^= 1;
     if (st.n_next == 0 || st.round >= a.max_rounds) st.done = 1;
 }
 
+// gathers every job's state and round records into contiguous arrays
+__global__ void k_b_gather(BArgs a, BState *st_out, int32_t *rna, int32_t *rnn, double *rl) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= a.n_jobs) return;
+    const BJob &jb = a.jobs[j];
+    st_out[j] = *jb.st;
+    for (int r = 0; r < a.max_rounds; ++r) {
+        rna[static_cast<int64_t>(r) * a.n_jobs + j] = jb.rec_n_active[r];
+        rnn[static_cast<int64_t>(r) * a.n_jobs + j] = jb.rec_n_next[r];
+        rl[static_cast<int64_t>(r) * a.n_jobs + j] = jb.rec_loss[r];
+    }
+}
+
 // ---------------------------------------------------------------------------
-// host object
+// host side: job memory, plans (a membership of jobs), init and step
 // ---------------------------------------------------------------------------
-struct HostTuning {
-    int walk_block = 256;
-    int sgns_blocks_per_sm = 2;
-    int feedback_blocks_per_sm = 16;
-};
-
-}  // namespace felog
-
-using namespace felog;
-
-struct felog_batch {
-    int32_t n_jobs = 0;
-    felog_walk_params wp{};
-    felog_train_params tp{};
-    felog_feedback_params fp{};
-    std::vector<int32_t> order;     // internal index -> caller index
-    std::vector<int32_t> position;  // caller index -> internal index
-    std::vector<int32_t> dims;      // internal order
-    std::vector<int32_t> ns;
-    std::vector<int64_t> item_prefix_h;
-    void *blob = nullptr;
-    size_t blob_bytes = 0;
-    BArgs args{};
-    std::vector<BJob> jobs_h;
-    HostTuning tune;
-    cudaGraphExec_t graph = nullptr;
-    int graph_rounds = -1;
-    cudaStream_t graph_stream = nullptr;
-};
-
-namespace {
-
-size_t job_bytes(int32_t n, int32_t L, int32_t wpr) {
+size_t job_work_bytes(int32_t n, const BParams &p) {
     const size_t nn = n > 0 ? static_cast<size_t>(n) : 1;
+    const size_t R = static_cast<size_t>(std::max(p.max_rounds, 1));
     size_t b = 0;
     auto add = [&](size_t x) { b += align_up(x, 256); };
-    add(nn);                                       // active[0]
-    add(nn);                                       // active[1]
-    add(4 * nn);                                   // starts
-    add(4 * nn * static_cast<size_t>(wpr) * L);    // walks
-    add(4 * nn);                                   // counts
-    add(8 * nn);                                   // thr
-    add(4 * nn);                                   // alias
-    add(8 * nn);                                   // W
-    add(16 * nn);                                  // key
-    add(4 * nn);                                   // rank
-    add(16 * nn);                                  // light_D
-    add(4 * nn);                                   // heavy_idx
-    add(16 * nn);                                  // heavy_E
+    add(sizeof(BState));
+    add(4 * R);                                            // rec_n_active
+    add(4 * R);                                            // rec_n_next
+    add(8 * R);                                            // rec_loss
+    add(nn);                                               // active[0]
+    add(nn);                                               // active[1]
+    add(4 * nn);                                           // starts
+    add(4 * nn * static_cast<size_t>(p.wpr) * p.L);        // walks
+    add(4 * nn);                                           // counts
+    add(8 * nn);                                           // thr
+    add(4 * nn);                                           // alias
+    add(8 * nn);                                           // W
+    add(16 * nn);                                          // key
+    add(4 * nn);                                           // rank
+    add(16 * nn);                                          // light_D
+    add(4 * nn);                                           // heavy_idx
+    add(16 * nn);                                          // heavy_E
     return b;
 }
 
-felog_status check_jobs(const felog_job *jobs, int32_t n_jobs, const felog_walk_params *wp,
-                        const felog_train_params *tp, const felog_feedback_params *fp) {
-    if (!jobs || n_jobs < 1 || !wp || !tp || !fp) return FELOG_ERR_INVALID_ARG;
-    if (wp->length < 1 || wp->walks_per_round < 1) return FELOG_ERR_INVALID_ARG;
-    if (tp->window < 1 || tp->window > 16 || tp->negatives < 1 || tp->negatives > 7)
-        return FELOG_ERR_UNSUPPORTED;  // the batched trainer is the half-warp form
-    if (tp->mode != FELOG_SGNS_HOGWILD) return FELOG_ERR_UNSUPPORTED;
-    if (tp->precision != FELOG_FP32 && tp->precision != FELOG_BF16_SR) return FELOG_ERR_INVALID_ARG;
-    if (!(tp->lr0 >= 0.f)) return FELOG_ERR_INVALID_ARG;
-    if (fp->ks < 1 || fp->ks > kMaxKs || fp->max_rounds < 0 || fp->max_rounds >= 65536)
-        return FELOG_ERR_INVALID_ARG;
-    const size_t smem = sizeof(int32_t) * kWarps * (wp->length + 2 * tp->window * tp->negatives);
-    if (smem > 200 * 1024) return FELOG_ERR_UNSUPPORTED;
+void job_carve(BJob &jb, void *mem, int32_t n, const BParams &p) {
+    const size_t nn = n > 0 ? static_cast<size_t>(n) : 1;
+    const size_t R = static_cast<size_t>(std::max(p.max_rounds, 1));
+    char *q = static_cast<char *>(mem);
+    auto take = [&](size_t bytes) { char *r = q; q += align_up(bytes, 256); return r; };
+    jb.st = reinterpret_cast<BState *>(take(sizeof(BState)));
+    jb.rec_n_active = reinterpret_cast<int32_t *>(take(4 * R));
+    jb.rec_n_next = reinterpret_cast<int32_t *>(take(4 * R));
+    jb.rec_loss = reinterpret_cast<double *>(take(8 * R));
+    jb.active[0] = reinterpret_cast<uint8_t *>(take(nn));
+    jb.active[1] = reinterpret_cast<uint8_t *>(take(nn));
+    jb.starts = reinterpret_cast<int32_t *>(take(4 * nn));
+    jb.walks = reinterpret_cast<int32_t *>(take(4 * nn * p.wpr * p.L));
+    jb.counts = reinterpret_cast<uint32_t *>(take(4 * nn));
+    jb.thr = reinterpret_cast<uint64_t *>(take(8 * nn));
+    jb.alias = reinterpret_cast<int32_t *>(take(4 * nn));
+    jb.W = reinterpret_cast<uint64_t *>(take(8 * nn));
+    jb.key = reinterpret_cast<u128 *>(take(16 * nn));
+    jb.rank = reinterpret_cast<int32_t *>(take(4 * nn));
+    jb.light_D = reinterpret_cast<u128 *>(take(16 * nn));
+    jb.heavy_idx = reinterpret_cast<int32_t *>(take(4 * nn));
+    jb.heavy_E = reinterpret_cast<u128 *>(take(16 * nn));
+}
+
+// state and records of a job must start at zero (phase 0 = not initialised)
+felog_status job_clear_state(const BJob &jb, const BParams &p, cudaStream_t s) {
+    const size_t R = static_cast<size_t>(std::max(p.max_rounds, 1));
+    const size_t bytes = align_up(sizeof(BState), 256) + 2 * align_up(4 * R, 256) + 8 * R;
+    return record_cuda_error(cudaMemsetAsync(jb.st, 0, bytes, s), "job state");
+}
+
+felog_status plan_build(BatchPlan &plan, const std::vector<BJob> &jobs_in, const BParams &p, cudaStream_t s) {
+    plan = BatchPlan{};
+    const int32_t n_jobs = static_cast<int32_t>(jobs_in.size());
+    if (n_jobs == 0) return FELOG_OK;
+    std::vector<BJob> jobs = jobs_in;
+    std::vector<int64_t> slot_prefix(n_jobs + 1, 0), node_prefix(n_jobs + 1, 0), item_prefix(n_jobs + 1, 0);
+    std::vector<int32_t> tile_job, tile_start;
+    plan.dims.resize(n_jobs);
+    int32_t tile = 0;
     for (int32_t i = 0; i < n_jobs; ++i) {
-        const felog_job &j = jobs[i];
-        if (!csr_shape_ok(&j.graph)) return FELOG_ERR_BAD_CSR;
-        if (j.dim != 32 && j.dim != 64 && j.dim != 128) return FELOG_ERR_UNSUPPORTED;
-        if (j.graph.n > 0 && (!j.phi_in || !j.phi_out)) return FELOG_ERR_INVALID_ARG;
-    }
-    return FELOG_OK;
-}
-
-template <int D, class T>
-felog_status launch_b_sgns(felog_batch *b, int64_t lo, int64_t hi, cudaStream_t s) {
-    if (hi <= lo) return FELOG_OK;
-    const size_t smem = sizeof(int32_t) * kWarps * (b->tp.window * 2 * b->tp.negatives + b->wp.length);
-    const bool k5 = b->tp.negatives == 5;
-    auto kern = k5 ? k_b_sgns<D, T, 5> : k_b_sgns<D, T, 0>;
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    const int64_t want = (hi - lo + kWarps - 1) / kWarps;
-    const int blocks = static_cast<int>(
-        std::max<int64_t>(1, std::min<int64_t>(want, static_cast<int64_t>(b->tune.sgns_blocks_per_sm) * sm_count())));
-    kern<<<blocks, kSgnsThreads, smem, s>>>(b->args, lo, hi);
-    return FELOG_OK;
-}
-
-template <class T>
-felog_status launch_sgns_all(felog_batch *b, cudaStream_t s) {
-    // items are ordered by job, jobs by dim: one launch per dim range
-    int32_t j = 0;
-    while (j < b->n_jobs) {
-        int32_t k = j;
-        while (k < b->n_jobs && b->dims[k] == b->dims[j]) ++k;
-        const int64_t lo = b->item_prefix_h[j], hi = b->item_prefix_h[k];
-        felog_status st = FELOG_OK;
-        switch (b->dims[j]) {
-            case 32: st = launch_b_sgns<32, T>(b, lo, hi, s); break;
-            case 64: st = launch_b_sgns<64, T>(b, lo, hi, s); break;
-            case 128: st = launch_b_sgns<128, T>(b, lo, hi, s); break;
+        BJob &jb = jobs[i];
+        plan.dims[i] = jb.dim;
+        slot_prefix[i + 1] = slot_prefix[i] + static_cast<int64_t>(jb.n) * p.wpr;
+        node_prefix[i + 1] = node_prefix[i] + jb.n;
+        item_prefix[i + 1] = item_prefix[i] + std::max<int64_t>(1, jb.n / p.rows_per_warp);
+        const int32_t nt = std::max(1, ceil_div(std::max(jb.n, 1), kBTile));
+        jb.tile_base = tile;
+        jb.n_tiles = nt;
+        for (int32_t t = 0; t < nt; ++t) {
+            tile_job.push_back(i);
+            tile_start.push_back(t * kBTile);
         }
-        if (st) return st;
-        j = k;
+        tile += nt;
     }
+    const int32_t R = std::max(p.max_rounds, 1);
+    size_t off = 0;
+    auto slot = [&](size_t bytes) { size_t o = off; off += align_up(bytes, 256); return o; };
+    const size_t o_jobs = slot(sizeof(BJob) * n_jobs);
+    const size_t o_sp = slot(sizeof(int64_t) * (n_jobs + 1));
+    const size_t o_np = slot(sizeof(int64_t) * (n_jobs + 1));
+    const size_t o_ip = slot(sizeof(int64_t) * (n_jobs + 1));
+    const size_t o_tj = slot(sizeof(int32_t) * tile);
+    const size_t o_ts = slot(sizeof(int32_t) * tile);
+    const size_t o_tc = slot(sizeof(int32_t) * tile);
+    const size_t o_ta = slot(sizeof(NoiseAgg) * tile);
+    plan.o_gst = slot(sizeof(BState) * n_jobs);
+    plan.o_gna = slot(sizeof(int32_t) * R * n_jobs);
+    plan.o_gnn = slot(sizeof(int32_t) * R * n_jobs);
+    plan.o_gl = slot(sizeof(double) * R * n_jobs);
+    felog_status st = record_cuda_error(cudaMallocAsync(&plan.mem, off, s), "plan");
+    if (st) return st;
+    plan.bytes = off;
+    char *base = static_cast<char *>(plan.mem);
+    st = record_cuda_error(cudaMemcpyAsync(base + o_jobs, jobs.data(), sizeof(BJob) * n_jobs, cudaMemcpyHostToDevice, s), "plan");
+    if (!st) st = record_cuda_error(cudaMemcpyAsync(base + o_sp, slot_prefix.data(), sizeof(int64_t) * (n_jobs + 1), cudaMemcpyHostToDevice, s), "plan");
+    if (!st) st = record_cuda_error(cudaMemcpyAsync(base + o_np, node_prefix.data(), sizeof(int64_t) * (n_jobs + 1), cudaMemcpyHostToDevice, s), "plan");
+    if (!st) st = record_cuda_error(cudaMemcpyAsync(base + o_ip, item_prefix.data(), sizeof(int64_t) * (n_jobs + 1), cudaMemcpyHostToDevice, s), "plan");
+    if (!st) st = record_cuda_error(cudaMemcpyAsync(base + o_tj, tile_job.data(), sizeof(int32_t) * tile, cudaMemcpyHostToDevice, s), "plan");
+    if (!st) st = record_cuda_error(cudaMemcpyAsync(base + o_ts, tile_start.data(), sizeof(int32_t) * tile, cudaMemcpyHostToDevice, s), "plan");
+    // pageable sources: the copies above have consumed them once the stream reaches this point
+    if (!st) st = record_cuda_error(cudaStreamSynchronize(s), "plan");
+    if (st) {
+        cudaFreeAsync(plan.mem, s);
+        plan.mem = nullptr;
+        return st;
+    }
+    plan.n_jobs = n_jobs;
+    plan.item_prefix = item_prefix;
+    plan.jobs = jobs;
+    BArgs &a = plan.args;
+    a.jobs = reinterpret_cast<const BJob *>(base + o_jobs);
+    a.n_jobs = n_jobs;
+    a.slot_prefix = reinterpret_cast<const int64_t *>(base + o_sp);
+    a.node_prefix = reinterpret_cast<const int64_t *>(base + o_np);
+    a.item_prefix = reinterpret_cast<const int64_t *>(base + o_ip);
+    a.tile_job = reinterpret_cast<const int32_t *>(base + o_tj);
+    a.tile_start = reinterpret_cast<const int32_t *>(base + o_ts);
+    a.tile_count = reinterpret_cast<int32_t *>(base + o_tc);
+    a.tile_agg = reinterpret_cast<NoiseAgg *>(base + o_ta);
+    a.n_tiles = tile;
+    a.n_slots = slot_prefix[n_jobs];
+    a.n_nodes = node_prefix[n_jobs];
+    a.L = p.L;
+    a.wpr = p.wpr;
+    a.window = p.window;
+    a.K = p.K;
+    a.max_rounds = p.max_rounds;
+    a.ks = p.ks;
+    a.enabled = p.enabled;
+    a.reactivate = p.reactivate;
+    a.precision = p.precision;
+    a.mu = p.mu;
+    a.lr0 = p.lr0;
+    a.lr_total_tokens = p.lr_total_tokens;
     return FELOG_OK;
 }
+
+void plan_release(BatchPlan &plan, cudaStream_t s) {
+    if (plan.mem) cudaFreeAsync(plan.mem, s);
+    plan = BatchPlan{};
+}
+
+namespace {
 
 int grid_for(int64_t work, int block, int per_sm) {
     return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((work + block - 1) / block,
                                                                     static_cast<int64_t>(per_sm) * sm_count())));
 }
 
-felog_status do_reset(felog_batch *b, cudaStream_t s) {
-    const BArgs &a = b->args;
-    const int jg = ceil_div(b->n_jobs, 256);
-    k_b_state_init<<<jg, 256, 0, s>>>(a);
-    if (b->tp.precision == FELOG_FP32) k_b_init<float><<<grid_for(a.n_nodes, 256, 16), 256, 0, s>>>(a);
-    else k_b_init<__nv_bfloat16><<<grid_for(a.n_nodes, 256, 16), 256, 0, s>>>(a);
-    k_b_lr<<<jg, 256, 0, s>>>(a);
-    return check_launch("felog_batch reset");
+template <int D, class T>
+void launch_b_sgns(const BatchPlan &plan, const BParams &p, const HostTuning &t, int64_t lo, int64_t hi,
+                   cudaStream_t s) {
+    if (hi <= lo) return;
+    const size_t smem = sizeof(int32_t) * kWarps * (p.window * 2 * p.K + p.L);
+    auto kern = p.K == 5 ? k_b_sgns<D, T, 5> : k_b_sgns<D, T, 0>;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    const int64_t want = (hi - lo + kWarps - 1) / kWarps;
+    const int blocks = static_cast<int>(
+        std::max<int64_t>(1, std::min<int64_t>(want, static_cast<int64_t>(t.sgns_blocks_per_sm) * sm_count())));
+    kern<<<blocks, kSgnsThreads, smem, s>>>(plan.args, lo, hi);
 }
 
-// phase: bit 0 compaction, 1 walk, 2 noise, 3 sgns, 4 feedback, 5 round end
-felog_status do_step(felog_batch *b, cudaStream_t s, unsigned phases = 0x3f) {
-    const BArgs &a = b->args;
-    const int jg = ceil_div(b->n_jobs, 256);
+template <class T>
+void launch_sgns_all(const BatchPlan &plan, const BParams &p, const HostTuning &t, cudaStream_t s) {
+    // items are ordered by job and jobs by dim: one launch per dim range
+    int32_t j = 0;
+    while (j < plan.n_jobs) {
+        int32_t k = j;
+        while (k < plan.n_jobs && plan.dims[k] == plan.dims[j]) ++k;
+        const int64_t lo = plan.item_prefix[j], hi = plan.item_prefix[k];
+        switch (plan.dims[j]) {
+            case 32: launch_b_sgns<32, T>(plan, p, t, lo, hi, s); break;
+            case 64: launch_b_sgns<64, T>(plan, p, t, lo, hi, s); break;
+            case 128: launch_b_sgns<128, T>(plan, p, t, lo, hi, s); break;
+        }
+        j = k;
+    }
+}
+
+}  // namespace
+
+// tables and V_a^0 of the plan's jobs still in phase 0 (the caller clears
+// their state first)
+felog_status plan_init_jobs(const BatchPlan &plan, const BParams &p, cudaStream_t s) {
+    if (plan.n_jobs == 0) return FELOG_OK;
+    const BArgs &a = plan.args;
+    if (p.precision == FELOG_FP32) k_b_init<float><<<grid_for(a.n_nodes, 256, 16), 256, 0, s>>>(a);
+    else k_b_init<__nv_bfloat16><<<grid_for(a.n_nodes, 256, 16), 256, 0, s>>>(a);
+    k_b_lr<<<ceil_div(plan.n_jobs, 256), 256, 0, s>>>(a);
+    return check_launch("felog init jobs");
+}
+
+// phases: bit 0 compaction, 1 walk, 2 noise, 3 sgns, 4 feedback, 5 round end
+felog_status plan_step(const BatchPlan &plan, const BParams &p, const HostTuning &t, cudaStream_t s,
+                       unsigned phases) {
+    if (plan.n_jobs == 0) return FELOG_OK;
+    const BArgs &a = plan.args;
+    const int jg = ceil_div(plan.n_jobs, 256);
     if (phases & 1) {
         k_b_compact_count<<<a.n_tiles, kBThreads, 0, s>>>(a);
         k_b_compact_scan<<<jg, 256, 0, s>>>(a);
         k_b_compact_scatter<<<a.n_tiles, kBThreads, 0, s>>>(a);
     }
     if (phases & 2) {
-        const int wb = b->tune.walk_block;
-        const bool vec = (a.L % 4) == 0;
-        if (vec) k_b_walk<true><<<grid_for(a.n_slots, wb, 2048 / wb), wb, 0, s>>>(a);
+        const int wb = t.walk_block;
+        if (a.L % 4 == 0) k_b_walk<true><<<grid_for(a.n_slots, wb, 2048 / wb), wb, 0, s>>>(a);
         else k_b_walk<false><<<grid_for(a.n_slots, wb, 2048 / wb), wb, 0, s>>>(a);
     }
     if (phases & 4) {
@@ -652,25 +684,118 @@ felog_status do_step(felog_batch *b, cudaStream_t s, unsigned phases = 0x3f) {
         k_b_noise_finish<<<grid_for(a.n_nodes, 256, 8), 256, 0, s>>>(a);
     }
     if (phases & 8) {
-        felog_status st = b->tp.precision == FELOG_FP32 ? launch_sgns_all<float>(b, s)
-                                                         : launch_sgns_all<__nv_bfloat16>(b, s);
-        if (st) return st;
+        if (p.precision == FELOG_FP32) launch_sgns_all<float>(plan, p, t, s);
+        else launch_sgns_all<__nv_bfloat16>(plan, p, t, s);
     }
     if (phases & 16) {
         const int grid = static_cast<int>(std::max<int64_t>(
             1, std::min<int64_t>((a.n_nodes + kBWarps - 1) / kBWarps,
-                                 static_cast<int64_t>(sm_count()) * b->tune.feedback_blocks_per_sm)));
-        if (b->tp.precision == FELOG_FP32) k_b_feedback<float><<<grid, kBThreads, 0, s>>>(a);
+                                 static_cast<int64_t>(sm_count()) * t.feedback_blocks_per_sm)));
+        if (p.precision == FELOG_FP32) k_b_feedback<float><<<grid, kBThreads, 0, s>>>(a);
         else k_b_feedback<__nv_bfloat16><<<grid, kBThreads, 0, s>>>(a);
     }
     if (phases & 32) k_b_round_end<<<jg, 256, 0, s>>>(a);
-    return check_launch("felog_batch step");
+    return check_launch("felog batch step");
 }
+
+// copies states and records of the plan's jobs to the host (synchronises s)
+felog_status plan_gather(const BatchPlan &plan, const BParams &p, cudaStream_t s, std::vector<BState> &sts,
+                         std::vector<int32_t> &rna, std::vector<int32_t> &rnn, std::vector<double> &rl) {
+    const int n = plan.n_jobs;
+    const size_t R = static_cast<size_t>(std::max(p.max_rounds, 1));
+    sts.resize(n);
+    rna.assign(R * n, 0);
+    rnn.assign(R * n, 0);
+    rl.assign(R * n, 0.0);
+    if (n == 0) return FELOG_OK;
+    char *base = static_cast<char *>(plan.mem);
+    k_b_gather<<<ceil_div(n, 256), 256, 0, s>>>(plan.args, reinterpret_cast<BState *>(base + plan.o_gst),
+                                                reinterpret_cast<int32_t *>(base + plan.o_gna),
+                                                reinterpret_cast<int32_t *>(base + plan.o_gnn),
+                                                reinterpret_cast<double *>(base + plan.o_gl));
+    felog_status st = check_launch("gather");
+    if (!st) st = record_cuda_error(cudaMemcpyAsync(sts.data(), base + plan.o_gst, sizeof(BState) * n, cudaMemcpyDeviceToHost, s), "gather");
+    if (!st && p.max_rounds > 0) {
+        st = record_cuda_error(cudaMemcpyAsync(rna.data(), base + plan.o_gna, 4 * R * n, cudaMemcpyDeviceToHost, s), "gather");
+        if (!st) st = record_cuda_error(cudaMemcpyAsync(rnn.data(), base + plan.o_gnn, 4 * R * n, cudaMemcpyDeviceToHost, s), "gather");
+        if (!st) st = record_cuda_error(cudaMemcpyAsync(rl.data(), base + plan.o_gl, 8 * R * n, cudaMemcpyDeviceToHost, s), "gather");
+    }
+    if (!st) st = record_cuda_error(cudaStreamSynchronize(s), "gather");
+    return st;
+}
+
+BParams make_params(const felog_walk_params *wp, const felog_train_params *tp, const felog_feedback_params *fp) {
+    BParams p;
+    p.L = wp->length;
+    p.wpr = wp->walks_per_round;
+    p.window = tp->window;
+    p.K = tp->negatives;
+    p.max_rounds = fp->max_rounds;
+    p.ks = fp->ks;
+    p.enabled = fp->enabled;
+    p.reactivate = fp->reactivate;
+    p.precision = tp->precision;
+    p.mu = fp->mu;
+    p.lr0 = tp->lr0;
+    p.lr_total_tokens = tp->lr_total_tokens;
+    p.rows_per_warp = tp->hogwild_rows_per_warp > 0 ? tp->hogwild_rows_per_warp : 16;
+    return p;
+}
+
+felog_status check_params(const felog_walk_params *wp, const felog_train_params *tp, const felog_feedback_params *fp) {
+    if (!wp || !tp || !fp) return FELOG_ERR_INVALID_ARG;
+    if (wp->length < 1 || wp->walks_per_round < 1) return FELOG_ERR_INVALID_ARG;
+    if (tp->window < 1 || tp->window > 16 || tp->negatives < 1 || tp->negatives > 7)
+        return FELOG_ERR_UNSUPPORTED;  // the batched trainer is the half-warp form
+    if (tp->mode != FELOG_SGNS_HOGWILD) return FELOG_ERR_UNSUPPORTED;
+    if (tp->precision != FELOG_FP32 && tp->precision != FELOG_BF16_SR) return FELOG_ERR_INVALID_ARG;
+    if (!(tp->lr0 >= 0.f)) return FELOG_ERR_INVALID_ARG;
+    if (fp->ks < 1 || fp->ks > kMaxKs || fp->max_rounds < 0 || fp->max_rounds >= 65536) return FELOG_ERR_INVALID_ARG;
+    const size_t smem = sizeof(int32_t) * kWarps * (wp->length + 2 * tp->window * tp->negatives);
+    if (smem > 200 * 1024) return FELOG_ERR_UNSUPPORTED;
+    return FELOG_OK;
+}
+
+felog_status check_job(int32_t n, int64_t nnz, int32_t dim) {
+    if (n < 0 || nnz < 0 || nnz >= (int64_t(1) << 31)) return FELOG_ERR_BAD_CSR;
+    if (dim != 32 && dim != 64 && dim != 128) return FELOG_ERR_UNSUPPORTED;
+    return FELOG_OK;
+}
+
+}  // namespace felog
+
+using namespace felog;
+
+// ---------------------------------------------------------------------------
+// fixed batch (felog_batch_*)
+// ---------------------------------------------------------------------------
+struct felog_batch {
+    int32_t n_jobs = 0;
+    BParams p{};
+    std::vector<int32_t> position;  // caller index -> plan index
+    void *blob = nullptr;           // work memory of all jobs
+    size_t blob_bytes = 0;
+    BatchPlan plan;
+    HostTuning tune;
+    cudaGraphExec_t graph = nullptr;
+    int graph_rounds = -1;
+};
+
+namespace {
 
 void drop_graph(felog_batch *b) {
     if (b->graph) cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
     b->graph_rounds = -1;
+}
+
+felog_status batch_reset(felog_batch *b, cudaStream_t s) {
+    // clear every job's state (contiguous per job), then initialise
+    for (const BJob &jb : b->plan.jobs) {
+        felog_status st = job_clear_state(jb, b->p, s);
+        if (st) return st;
+    }
+    return plan_init_jobs(b->plan, b->p, s);
 }
 
 }  // namespace
@@ -680,75 +805,41 @@ extern "C" felog_status felog_batch_create(const felog_job *jobs, int32_t n_jobs
                                            felog_batch **out) {
     if (!out) return FELOG_ERR_INVALID_ARG;
     *out = nullptr;
-    felog_status st = check_jobs(jobs, n_jobs, wp, tp, fp);
+    if (!jobs || n_jobs < 1) return FELOG_ERR_INVALID_ARG;
+    felog_status st = check_params(wp, tp, fp);
     if (st) return st;
+    for (int32_t i = 0; i < n_jobs; ++i) {
+        if (!csr_shape_ok(&jobs[i].graph)) return FELOG_ERR_BAD_CSR;
+        if ((st = check_job(jobs[i].graph.n, jobs[i].graph.nnz, jobs[i].dim))) return st;
+        if (jobs[i].graph.n > 0 && (!jobs[i].phi_in || !jobs[i].phi_out)) return FELOG_ERR_INVALID_ARG;
+    }
     felog_batch *b = new (std::nothrow) felog_batch();
     if (!b) return FELOG_ERR_INVALID_ARG;
     b->n_jobs = n_jobs;
-    b->wp = *wp;
-    b->tp = *tp;
-    b->fp = *fp;
-    // internal order: by dim (stable), so each dim's training items are contiguous
-    b->order.resize(n_jobs);
-    for (int32_t i = 0; i < n_jobs; ++i) b->order[i] = i;
-    std::stable_sort(b->order.begin(), b->order.end(),
-                     [&](int32_t x, int32_t y) { return jobs[x].dim < jobs[y].dim; });
+    b->p = make_params(wp, tp, fp);
+    // plan order: by dim (stable), so each dim's training items are contiguous
+    std::vector<int32_t> order(n_jobs);
+    for (int32_t i = 0; i < n_jobs; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return jobs[x].dim < jobs[y].dim; });
     b->position.resize(n_jobs);
-    for (int32_t i = 0; i < n_jobs; ++i) b->position[b->order[i]] = i;
-    const int32_t L = wp->length, wpr = wp->walks_per_round, R = fp->max_rounds;
-    const int64_t rows_per_warp = tp->hogwild_rows_per_warp > 0 ? tp->hogwild_rows_per_warp : 16;
-    std::vector<int64_t> slot_prefix(n_jobs + 1, 0), node_prefix(n_jobs + 1, 0), item_prefix(n_jobs + 1, 0);
-    std::vector<int32_t> tile_job, tile_start;
-    size_t per_job_total = 0;
-    b->dims.resize(n_jobs);
-    b->ns.resize(n_jobs);
+    for (int32_t i = 0; i < n_jobs; ++i) b->position[order[i]] = i;
+    std::vector<size_t> offs(n_jobs);
+    size_t total = 0;
     for (int32_t i = 0; i < n_jobs; ++i) {
-        const felog_job &j = jobs[b->order[i]];
-        const int32_t n = j.graph.n;
-        b->dims[i] = j.dim;
-        b->ns[i] = n;
-        slot_prefix[i + 1] = slot_prefix[i] + static_cast<int64_t>(n) * wpr;
-        node_prefix[i + 1] = node_prefix[i] + n;
-        item_prefix[i + 1] = item_prefix[i] + std::max<int64_t>(1, n / rows_per_warp);
-        per_job_total += job_bytes(n, L, wpr);
+        offs[i] = total;
+        total += job_work_bytes(jobs[order[i]].graph.n, b->p);
     }
-    const int32_t n_tiles_total = [&] {
-        int64_t t = 0;
-        for (int32_t i = 0; i < n_jobs; ++i) t += std::max(1, ceil_div(std::max(b->ns[i], 1), kBTile));
-        return static_cast<int32_t>(t);
-    }();
-    // blob layout: job table, states, prefixes, tile tables, records, per-job buffers
-    size_t off = 0;
-    auto slot = [&](size_t bytes) { size_t o = off; off += align_up(bytes, 256); return o; };
-    const size_t o_jobs = slot(sizeof(BJob) * n_jobs);
-    const size_t o_st = slot(sizeof(BState) * n_jobs);
-    const size_t o_sp = slot(sizeof(int64_t) * (n_jobs + 1));
-    const size_t o_np = slot(sizeof(int64_t) * (n_jobs + 1));
-    const size_t o_ip = slot(sizeof(int64_t) * (n_jobs + 1));
-    const size_t o_tj = slot(sizeof(int32_t) * n_tiles_total);
-    const size_t o_ts = slot(sizeof(int32_t) * n_tiles_total);
-    const size_t o_tc = slot(sizeof(int32_t) * n_tiles_total);
-    const size_t o_ta = slot(sizeof(NoiseAgg) * n_tiles_total);
-    const size_t rec = static_cast<size_t>(std::max(R, 1)) * n_jobs;
-    const size_t o_rna = slot(sizeof(int32_t) * rec);
-    const size_t o_rnn = slot(sizeof(int32_t) * rec);
-    const size_t o_rl = slot(sizeof(double) * rec);
-    const size_t o_buf = slot(per_job_total);
-    b->blob_bytes = off;
-    st = record_cuda_error(cudaMalloc(&b->blob, b->blob_bytes), "felog_batch_create");
+    st = record_cuda_error(cudaMalloc(&b->blob, total), "felog_batch_create");
     if (st) {
         delete b;
         return st;
     }
-    char *base = static_cast<char *>(b->blob);
-    b->jobs_h.resize(n_jobs);
-    char *p = base + o_buf;
-    auto take = [&](size_t bytes) { char *q = p; p += align_up(bytes, 256); return q; };
-    int32_t tile = 0;
+    b->blob_bytes = total;
+    std::vector<BJob> bj(n_jobs);
     for (int32_t i = 0; i < n_jobs; ++i) {
-        const felog_job &j = jobs[b->order[i]];
-        const size_t nn = j.graph.n > 0 ? static_cast<size_t>(j.graph.n) : 1;
-        BJob &jb = b->jobs_h[i];
+        const felog_job &j = jobs[order[i]];
+        BJob &jb = bj[i];
+        jb = BJob{};
         jb.offsets = j.graph.offsets;
         jb.cols = j.graph.cols;
         jb.n = j.graph.n;
@@ -756,72 +847,14 @@ extern "C" felog_status felog_batch_create(const felog_job *jobs, int32_t n_jobs
         jb.seed = j.seed;
         jb.phi_in = j.phi_in;
         jb.phi_out = j.phi_out;
-        jb.active[0] = reinterpret_cast<uint8_t *>(take(nn));
-        jb.active[1] = reinterpret_cast<uint8_t *>(take(nn));
-        jb.starts = reinterpret_cast<int32_t *>(take(4 * nn));
-        jb.walks = reinterpret_cast<int32_t *>(take(4 * nn * wpr * L));
-        jb.counts = reinterpret_cast<uint32_t *>(take(4 * nn));
-        jb.thr = reinterpret_cast<uint64_t *>(take(8 * nn));
-        jb.alias = reinterpret_cast<int32_t *>(take(4 * nn));
-        jb.W = reinterpret_cast<uint64_t *>(take(8 * nn));
-        jb.key = reinterpret_cast<u128 *>(take(16 * nn));
-        jb.rank = reinterpret_cast<int32_t *>(take(4 * nn));
-        jb.light_D = reinterpret_cast<u128 *>(take(16 * nn));
-        jb.heavy_idx = reinterpret_cast<int32_t *>(take(4 * nn));
-        jb.heavy_E = reinterpret_cast<u128 *>(take(16 * nn));
-        const int32_t nt = std::max(1, ceil_div(std::max(jb.n, 1), kBTile));
-        jb.tile_base = tile;
-        jb.n_tiles = nt;
-        for (int32_t t = 0; t < nt; ++t) {
-            tile_job.push_back(i);
-            tile_start.push_back(t * kBTile);
-        }
-        tile += nt;
+        job_carve(jb, static_cast<char *>(b->blob) + offs[i], jb.n, b->p);
     }
-    st = record_cuda_error(cudaMemcpy(base + o_jobs, b->jobs_h.data(), sizeof(BJob) * n_jobs, cudaMemcpyHostToDevice), "batch");
-    if (!st) st = record_cuda_error(cudaMemcpy(base + o_sp, slot_prefix.data(), sizeof(int64_t) * (n_jobs + 1), cudaMemcpyHostToDevice), "batch");
-    if (!st) st = record_cuda_error(cudaMemcpy(base + o_np, node_prefix.data(), sizeof(int64_t) * (n_jobs + 1), cudaMemcpyHostToDevice), "batch");
-    if (!st) st = record_cuda_error(cudaMemcpy(base + o_ip, item_prefix.data(), sizeof(int64_t) * (n_jobs + 1), cudaMemcpyHostToDevice), "batch");
-    if (!st) st = record_cuda_error(cudaMemcpy(base + o_tj, tile_job.data(), sizeof(int32_t) * n_tiles_total, cudaMemcpyHostToDevice), "batch");
-    if (!st) st = record_cuda_error(cudaMemcpy(base + o_ts, tile_start.data(), sizeof(int32_t) * n_tiles_total, cudaMemcpyHostToDevice), "batch");
-    if (!st) st = record_cuda_error(cudaMemset(base + o_rna, 0, sizeof(int32_t) * rec), "batch");
-    if (!st) st = record_cuda_error(cudaMemset(base + o_rnn, 0, sizeof(int32_t) * rec), "batch");
-    if (!st) st = record_cuda_error(cudaMemset(base + o_rl, 0, sizeof(double) * rec), "batch");
+    st = plan_build(b->plan, bj, b->p, nullptr);
     if (st) {
         cudaFree(b->blob);
         delete b;
         return st;
     }
-    b->item_prefix_h = item_prefix;
-    BArgs &a = b->args;
-    a.jobs = reinterpret_cast<const BJob *>(base + o_jobs);
-    a.st = reinterpret_cast<BState *>(base + o_st);
-    a.n_jobs = n_jobs;
-    a.slot_prefix = reinterpret_cast<const int64_t *>(base + o_sp);
-    a.node_prefix = reinterpret_cast<const int64_t *>(base + o_np);
-    a.item_prefix = reinterpret_cast<const int64_t *>(base + o_ip);
-    a.tile_job = reinterpret_cast<const int32_t *>(base + o_tj);
-    a.tile_start = reinterpret_cast<const int32_t *>(base + o_ts);
-    a.tile_count = reinterpret_cast<int32_t *>(base + o_tc);
-    a.tile_agg = reinterpret_cast<NoiseAgg *>(base + o_ta);
-    a.n_tiles = n_tiles_total;
-    a.n_slots = slot_prefix[n_jobs];
-    a.n_nodes = node_prefix[n_jobs];
-    a.L = L;
-    a.wpr = wpr;
-    a.window = tp->window;
-    a.K = tp->negatives;
-    a.max_rounds = R;
-    a.ks = fp->ks;
-    a.enabled = fp->enabled;
-    a.reactivate = fp->reactivate;
-    a.precision = tp->precision;
-    a.mu = fp->mu;
-    a.lr0 = tp->lr0;
-    a.lr_total_tokens = tp->lr_total_tokens;
-    a.rec_n_active = reinterpret_cast<int32_t *>(base + o_rna);
-    a.rec_n_next = reinterpret_cast<int32_t *>(base + o_rnn);
-    a.rec_loss = reinterpret_cast<double *>(base + o_rl);
     *out = b;
     return FELOG_OK;
 }
@@ -829,39 +862,40 @@ extern "C" felog_status felog_batch_create(const felog_job *jobs, int32_t n_jobs
 extern "C" felog_status felog_batch_destroy(felog_batch *b) {
     if (!b) return FELOG_OK;
     drop_graph(b);
+    plan_release(b->plan, nullptr);
     felog_status st = FELOG_OK;
     if (b->blob) st = record_cuda_error(cudaFree(b->blob), "felog_batch_destroy");
     delete b;
     return st;
 }
 
-extern "C" size_t felog_batch_device_bytes(const felog_batch *b) { return b ? b->blob_bytes : 0; }
+extern "C" size_t felog_batch_device_bytes(const felog_batch *b) { return b ? b->blob_bytes + b->plan.bytes : 0; }
 
 extern "C" felog_status felog_batch_reset(felog_batch *b, void *stream) {
     if (!b) return FELOG_ERR_INVALID_ARG;
-    return do_reset(b, static_cast<cudaStream_t>(stream));
+    return batch_reset(b, static_cast<cudaStream_t>(stream));
 }
 
 extern "C" felog_status felog_batch_step(felog_batch *b, void *stream) {
     if (!b) return FELOG_ERR_INVALID_ARG;
-    return do_step(b, static_cast<cudaStream_t>(stream));
+    return plan_step(b->plan, b->p, b->tune, static_cast<cudaStream_t>(stream), 0x3f);
 }
 
 extern "C" felog_status felog_batch_run(felog_batch *b, int32_t use_graph, void *stream) {
     if (!b) return FELOG_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int R = b->fp.max_rounds;
+    const int R = b->p.max_rounds;
     if (!use_graph || s == nullptr) {
-        felog_status st = do_reset(b, s);
-        for (int r = 0; !st && r < R; ++r) st = do_step(b, s);
+        felog_status st = batch_reset(b, s);
+        for (int r = 0; !st && r < R; ++r) st = plan_step(b->plan, b->p, b->tune, s, 0x3f);
         return st;
     }
     if (!b->graph || b->graph_rounds != R) {
         drop_graph(b);
         felog_status st = record_cuda_error(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "capture");
         if (st) return st;
-        felog_status st2 = do_reset(b, s);
-        for (int r = 0; !st2 && r < R; ++r) st2 = do_step(b, s);
+        felog_status st2 = batch_reset(b, s);
+        for (int r = 0; !st2 && r < R; ++r) st2 = plan_step(b->plan, b->p, b->tune, s, 0x3f);
         cudaGraph_t g = nullptr;
         st = record_cuda_error(cudaStreamEndCapture(s, &g), "capture");
         if (st2 || st) {
@@ -879,19 +913,12 @@ extern "C" felog_status felog_batch_run(felog_batch *b, int32_t use_graph, void 
 extern "C" felog_status felog_batch_read(felog_batch *b, felog_job_stats *stats, int32_t *rec_n_active,
                                          double *rec_loss, void *stream) {
     if (!b) return FELOG_ERR_INVALID_ARG;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    felog_status st = record_cuda_error(cudaStreamSynchronize(s), "felog_batch_read");
+    std::vector<BState> sts;
+    std::vector<int32_t> rna, rnn;
+    std::vector<double> rl;
+    felog_status st = plan_gather(b->plan, b->p, static_cast<cudaStream_t>(stream), sts, rna, rnn, rl);
     if (st) return st;
     const int n = b->n_jobs;
-    const int R = std::max(b->fp.max_rounds, 1);
-    std::vector<BState> sts(n);
-    std::vector<int32_t> rna(static_cast<size_t>(R) * n), rnn(static_cast<size_t>(R) * n);
-    std::vector<double> rl(static_cast<size_t>(R) * n);
-    st = record_cuda_error(cudaMemcpy(sts.data(), b->args.st, sizeof(BState) * n, cudaMemcpyDeviceToHost), "read");
-    if (!st) st = record_cuda_error(cudaMemcpy(rna.data(), b->args.rec_n_active, sizeof(int32_t) * rna.size(), cudaMemcpyDeviceToHost), "read");
-    if (!st) st = record_cuda_error(cudaMemcpy(rnn.data(), b->args.rec_n_next, sizeof(int32_t) * rnn.size(), cudaMemcpyDeviceToHost), "read");
-    if (!st) st = record_cuda_error(cudaMemcpy(rl.data(), b->args.rec_loss, sizeof(double) * rl.size(), cudaMemcpyDeviceToHost), "read");
-    if (st) return st;
     for (int32_t c = 0; c < n; ++c) {
         const int32_t i = b->position[c];
         if (stats) {
@@ -902,7 +929,7 @@ extern "C" felog_status felog_batch_read(felog_batch *b, felog_job_stats *stats,
             o.n_live = sts[i].n_live;
             o.loss_last = sts[i].round > 0 ? rl[static_cast<size_t>(sts[i].round - 1) * n + i] : 0.0;
         }
-        for (int32_t r = 0; r < b->fp.max_rounds; ++r) {
+        for (int32_t r = 0; r < b->p.max_rounds; ++r) {
             if (rec_n_active) rec_n_active[static_cast<size_t>(r) * n + c] = rna[static_cast<size_t>(r) * n + i];
             if (rec_loss) rec_loss[static_cast<size_t>(r) * n + c] = rl[static_cast<size_t>(r) * n + i];
         }
@@ -912,7 +939,7 @@ extern "C" felog_status felog_batch_read(felog_batch *b, felog_job_stats *stats,
 
 extern "C" felog_status felog_batch_job_buffers(const felog_batch *b, int32_t job, felog_job_buffers *out) {
     if (!b || !out || job < 0 || job >= b->n_jobs) return FELOG_ERR_INVALID_ARG;
-    const BJob &jb = b->jobs_h[b->position[job]];
+    const BJob &jb = b->plan.jobs[b->position[job]];
     out->active[0] = jb.active[0];
     out->active[1] = jb.active[1];
     out->starts = jb.starts;
@@ -924,9 +951,9 @@ extern "C" felog_status felog_batch_job_buffers(const felog_batch *b, int32_t jo
 }
 
 // Autotuner: times the walk launch shape, the trainer's blocks per SM and the
-// feedback block size on round 0 of this batch (tables re-initialised after
-// each probe) and keeps the fastest of each.  With cache_path, results are
-// looked up and stored in a text file keyed by GPU name and batch shape.
+// Psi blocks per SM on round 0 of this batch (the batch is re-initialised
+// before each probe) and keeps the fastest of each.  With cache_path, results
+// are looked up and stored in a text file keyed by GPU name and batch shape.
 extern "C" felog_status felog_batch_autotune(felog_batch *b, const char *cache_path, felog_tuning *out,
                                              void *stream) {
     if (!b) return FELOG_ERR_INVALID_ARG;
@@ -936,13 +963,13 @@ extern "C" felog_status felog_batch_autotune(felog_batch *b, const char *cache_p
     cudaDeviceProp prop;
     cudaGetDeviceProperties(&prop, dev);
     int64_t dsum = 0;
-    for (int32_t d : b->dims) dsum += d;
+    for (int32_t d : b->plan.dims) dsum += d;
     std::string gpu(prop.name);
     std::replace(gpu.begin(), gpu.end(), ' ', '_');  // the cache file is whitespace separated
-    const std::string key = gpu + "|n=" + std::to_string(b->args.n_nodes) + "|jobs=" +
+    const std::string key = gpu + "|n=" + std::to_string(b->plan.args.n_nodes) + "|jobs=" +
                             std::to_string(b->n_jobs) + "|dsum=" + std::to_string(dsum) + "|L=" +
-                            std::to_string(b->wp.length) + "|w=" + std::to_string(b->tp.window) + "|K=" +
-                            std::to_string(b->tp.negatives) + "|p=" + std::to_string(b->tp.precision);
+                            std::to_string(b->p.L) + "|w=" + std::to_string(b->p.window) + "|K=" +
+                            std::to_string(b->p.K) + "|p=" + std::to_string(b->p.precision);
     if (cache_path) {
         std::ifstream in(cache_path);
         std::string k;
@@ -962,10 +989,10 @@ extern "C" felog_status felog_batch_autotune(felog_batch *b, const char *cache_p
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     auto time_phase = [&](unsigned before, unsigned phase) -> float {
-        do_reset(b, s);
-        do_step(b, s, before);
+        batch_reset(b, s);
+        plan_step(b->plan, b->p, b->tune, s, before);
         cudaEventRecord(e0, s);
-        do_step(b, s, phase);
+        plan_step(b->plan, b->p, b->tune, s, phase);
         cudaEventRecord(e1, s);
         cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -996,9 +1023,8 @@ extern "C" felog_status felog_batch_autotune(felog_batch *b, const char *cache_p
     b->tune = best;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    felog_status st = do_reset(b, s);
-    if (st) return st;
-    st = record_cuda_error(cudaStreamSynchronize(s), "autotune");
+    felog_status st = batch_reset(b, s);
+    if (!st) st = record_cuda_error(cudaStreamSynchronize(s), "autotune");
     if (st) return st;
     drop_graph(b);
     if (cache_path) {

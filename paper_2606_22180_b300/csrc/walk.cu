@@ -303,6 +303,7 @@ extern "C" const char *felog_status_string(felog_status st) {
         case FELOG_ERR_WORKSPACE: return "workspace missing or too small";
         case FELOG_ERR_CUDA: return "CUDA error";
         case FELOG_ERR_UNSUPPORTED: return "unsupported parameter combination";
+        case FELOG_ERR_TIMEOUT: return "timed out";
     }
     return "unknown status";
 }

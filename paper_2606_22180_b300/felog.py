@@ -33,6 +33,9 @@ SYMBOLS = [
     "felog_batch_create", "felog_batch_destroy", "felog_batch_device_bytes", "felog_batch_reset",
     "felog_batch_step", "felog_batch_run", "felog_batch_read", "felog_batch_job_buffers",
     "felog_batch_autotune",
+    "felog_server_create", "felog_server_destroy", "felog_server_now", "felog_server_job_bytes",
+    "felog_server_submit", "felog_server_poll", "felog_server_wait", "felog_server_fetch",
+    "felog_server_drain", "felog_server_get_stats",
 ]
 
 
@@ -113,6 +116,16 @@ def load() -> ctypes.CDLL:
         "felog_batch_read": (st, [P, P, P, P, P]),
         "felog_batch_job_buffers": (st, [P, i32, P]),
         "felog_batch_autotune": (st, [P, ctypes.c_char_p, P, P]),
+        "felog_server_create": (st, [P, P]),
+        "felog_server_destroy": (st, [P]),
+        "felog_server_now": (f64, [P]),
+        "felog_server_job_bytes": (sz, [P, i32, i64, i32]),
+        "felog_server_submit": (st, [P, P, P, i32, i64, i32, u64, P]),
+        "felog_server_poll": (st, [P, u64, P]),
+        "felog_server_wait": (st, [P, u64, f64, P]),
+        "felog_server_fetch": (st, [P, u64, P]),
+        "felog_server_drain": (st, [P, f64]),
+        "felog_server_get_stats": (st, [P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -462,3 +475,108 @@ def _device_view(ptr: int, numel: int, dtype) -> torch.Tensor:
         return torch.empty(0, dtype=dtype, device="cuda")
     torch.cuda.current_stream().synchronize()
     return torch.as_tensor(_CudaArray(ptr, numel, dtype), device="cuda")
+
+
+# ---------------------------------------------------------------------------
+# Serving form
+# ---------------------------------------------------------------------------
+JOB_QUEUED, JOB_RUNNING, JOB_DONE, JOB_REJECTED, JOB_FAILED = 0, 1, 2, 3, 4
+
+
+class _ServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_size_t), ("max_resident", ctypes.c_int32),
+                ("drain_on_destroy", ctypes.c_int32), ("walk", _WalkParams), ("train", _TrainParams),
+                ("feedback", _FeedbackParams)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("rounds", ctypes.c_int32), ("n", ctypes.c_int32),
+                ("dim", ctypes.c_int32), ("tokens", ctypes.c_int64), ("n_live", ctypes.c_int64),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("loss_last", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("rejected", ctypes.c_int64), ("steps", ctypes.c_int64), ("resident_jobs", ctypes.c_int32),
+                ("peak_resident_jobs", ctypes.c_int32), ("queued", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("resident_bytes", ctypes.c_size_t), ("peak_resident_bytes", ctypes.c_size_t),
+                ("busy_seconds", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class Server:
+    """Continuous-batching embedding server (felog_server_* calls)."""
+
+    def __init__(self, hbm_budget: int, length: int, walks_per_round: int, tp: _TrainParams,
+                 fp: _FeedbackParams, max_resident: int = 0, drain_on_destroy: bool = False):
+        _require_cuda()
+        self.lib = load()
+        cfg = _ServerConfig(hbm_budget, max_resident, int(drain_on_destroy),
+                            _WalkParams(length, walks_per_round), tp, fp)
+        h = ctypes.c_void_p(0)
+        _check(self.lib.felog_server_create(ctypes.byref(cfg), ctypes.byref(h)), "felog_server_create")
+        self.handle = h
+        self.dims = {}
+
+    def now(self) -> float:
+        return float(self.lib.felog_server_now(self.handle))
+
+    def job_bytes(self, n: int, nnz: int, dim: int) -> int:
+        return int(self.lib.felog_server_job_bytes(self.handle, n, nnz, dim))
+
+    def submit(self, csr, dim: int, seed: int) -> int:
+        import numpy as np
+
+        off = np.ascontiguousarray(csr.offsets, dtype=np.int32)
+        cols = np.ascontiguousarray(csr.cols, dtype=np.int32)
+        rid = ctypes.c_uint64(0)
+        _check(self.lib.felog_server_submit(self.handle, off.ctypes.data_as(ctypes.c_void_p),
+                                            cols.ctypes.data_as(ctypes.c_void_p), off.shape[0] - 1,
+                                            cols.shape[0], dim, seed, ctypes.byref(rid)), "felog_server_submit")
+        self.dims[rid.value] = (off.shape[0] - 1, dim)
+        return rid.value
+
+    def poll(self, rid: int) -> dict:
+        r = Result()
+        _check(self.lib.felog_server_poll(self.handle, rid, ctypes.byref(r)), "felog_server_poll")
+        return r.as_dict()
+
+    def wait(self, rid: int, timeout: float = 600.0) -> dict:
+        r = Result()
+        _check(self.lib.felog_server_wait(self.handle, rid, timeout, ctypes.byref(r)), "felog_server_wait")
+        return r.as_dict()
+
+    def fetch(self, rid: int):
+        import numpy as np
+
+        n, dim = self.dims.pop(rid)
+        out = np.empty((n, dim), np.float32)
+        _check(self.lib.felog_server_fetch(self.handle, rid, out.ctypes.data_as(ctypes.c_void_p)),
+               "felog_server_fetch")
+        return out
+
+    def drain(self, timeout: float = 600.0):
+        _check(self.lib.felog_server_drain(self.handle, timeout), "felog_server_drain")
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(self.lib.felog_server_get_stats(self.handle, ctypes.byref(s)), "felog_server_get_stats")
+        return s.as_dict()
+
+    def close(self):
+        if self.handle:
+            st = self.lib.felog_server_destroy(self.handle)
+            self.handle = ctypes.c_void_p(0)
+            _check(st, "felog_server_destroy")
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
