@@ -52,6 +52,14 @@ def _args():
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     p.add_argument("--form", type=int, default=0, choices=[0, 1, 2],
                    help="Hogwild kernel form: 0 automatic, 1 full warp per pair, 2 half warp per pair")
+    p.add_argument("--mode", default="round", choices=["round", "batch", "serve"],
+                   help="round: one round of Algorithm 1 on R-MAT 20 (default); batch: the 512-graph "
+                        "batching form; serve: the request loop with Poisson arrivals")
+    p.add_argument("--jobs", type=int, default=512, help="batch mode: number of graphs")
+    p.add_argument("--rate", type=float, default=20.0, help="serve mode: arrivals per second")
+    p.add_argument("--duration", type=float, default=20.0, help="serve mode: seconds of arrivals")
+    p.add_argument("--max-nodes", type=int, default=1 << 16, help="serve mode: largest job in nodes")
+    p.add_argument("--no-forms", action="store_true", help="round mode: skip the small batch/serve runs")
     p.add_argument("--precision", default="fp32", choices=["fp32", "bf16"],
                    help="table precision of the timed rounds (fp32 = the plain form)")
     return p.parse_args()
@@ -376,12 +384,134 @@ def run_native(args):
 
     if not args.no_quality and rank == 0:
         result["quality"] = _quality(fl, evaluate, dg, split, n_live)
+        q = result["quality"]
+        result["chosen_vs_plain"] = {
+            "auc_plain": q["plain"]["auc"], "auc_chosen": q["chosen"]["auc"],
+            "auc_delta": q["chosen"]["auc"] - q["plain"]["auc"],
+            "time_plain_s": q["plain"]["seconds"], "time_chosen_s": q["chosen"]["seconds"],
+            "speedup_time_to_result": q["plain"]["seconds"] / q["chosen"]["seconds"],
+            "tokens_plain": q["plain"]["tokens"], "tokens_chosen": q["chosen"]["tokens"],
+            "chosen": "feedback mu=0.65 + bf16-SR tables, same graph and split",
+        }
+    if not args.no_forms and rank == 0:
+        del runner
+        torch.cuda.empty_cache()
+        result["batching_small"] = run_batch(fl, jobs=64, n_hi=20000, warmup=3, steps=3, autotune=True)
+        result["serving_small"] = run_serve(fl, rate=20.0, duration=5.0, max_nodes=1 << 14, sustainable=False)
     if not args.no_cpu and rank == 0:
         result["cpu_baseline"] = _cpu_baseline(split, n_live)
     if rank == 0:
         print(json.dumps(result))
     if world > 1:
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# batching form: many graphs, one captured launch per run
+# ---------------------------------------------------------------------------
+BATCH_L, BATCH_W, BATCH_K, BATCH_ROUNDS = 40, 5, 5, 10
+
+
+def run_batch(fl, jobs=512, n_hi=200000, warmup=1, steps=1, autotune=True, seed=3):
+    """The batching workload: `jobs` graphs (half planted partitions with
+    4..32 communities, half R-MAT), node counts log-uniform in [1e3, n_hi],
+    average degree 8..32, d in {64, 128}, bf16 tables, 10 walks per node of
+    length 40, window 5, 5 negatives; all rounds of all graphs in one
+    captured CUDA graph.  A step is one launch of that graph."""
+    import torch
+
+    from paper_2606_22180_b300 import inputs
+
+    t0 = time.perf_counter()
+    mix = inputs.graph_mix(jobs, seed, 1000, n_hi)
+    gen_s = time.perf_counter() - t0
+    dgs = [fl.DeviceGraph.from_host(g) for g, _ in mix]
+    dims = [d for _, d in mix]
+    tp = fl.train_params(128, BATCH_W, BATCH_K, LR0, 0, fl.FELOG_SGNS_HOGWILD, 4096, fl.FELOG_BF16_SR)
+    fp = fl.feedback_params(False, MU, KS, BATCH_ROUNDS, False)
+    b = fl.Batch(dgs, dims, [SEED + i for i in range(jobs)], BATCH_L, 1, tp, fp)
+    os.makedirs(os.path.join(ROOT, "_build"), exist_ok=True)
+    tuning = b.autotune(os.path.join(ROOT, "_build", "felog_tune.txt")) if autotune else None
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            b.run(use_graph=True)
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            b.run(use_graph=True)
+        e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    stats, na, _ = b.read()
+    tokens = sum(s["tokens"] for s in stats)
+    out = {"workload": f"{jobs} graphs (SBM/R-MAT), |V| log-uniform [1e3, {n_hi}], deg 8-32, d 64/128 bf16, "
+                       f"L={BATCH_L}, {BATCH_ROUNDS} rounds, w={BATCH_W}, K={BATCH_K}",
+           "nodes": int(sum(g.n for g, _ in mix)), "tokens_per_run": int(tokens),
+           "ms_per_run": ms, "tokens_per_s": tokens / (ms / 1e3), "launch": "one CUDA graph per run",
+           "warmup_runs": warmup, "timed_runs": steps, "tuning": tuning, "graph_gen_s": gen_s,
+           "device_bytes": b.device_bytes()}
+    b.close()
+    return out
+
+
+# ---------------------------------------------------------------------------
+# serving form: Poisson arrivals into the continuous-batching server
+# ---------------------------------------------------------------------------
+def run_serve(fl, rate=20.0, duration=20.0, max_nodes=1 << 16, pool_size=48, budget=150 << 30, seed=4,
+              sustainable=True):
+    """Requests arrive as a Poisson process at `rate` per second for
+    `duration` seconds; each is a graph drawn from a pool (half SBM, half
+    R-MAT, node counts log-uniform in [1e3, max_nodes]) with its own seed,
+    trained with the round workload's walk/SGNS parameters, d = 128, bf16
+    tables, feedback mu = 0.65.  Reports latency percentiles over completed
+    requests and offered vs completed load."""
+    from paper_2606_22180_b300 import inputs
+
+    pool = inputs.graph_mix(pool_size, seed, 1000, max_nodes, dims=(128,))
+    tp = fl.train_params(DIM, WINDOW, NEG, LR0, 0, fl.FELOG_SGNS_HOGWILD, 4096, fl.FELOG_BF16_SR)
+    fp = fl.feedback_params(True, MU, KS, ROUNDS, False)
+
+    def one(rate_):
+        rng = np.random.default_rng(seed)
+        sv = fl.Server(budget, L, WPR, tp, fp)
+        t_arr, ids, offered_tokens = 0.0, [], 0
+        start = time.perf_counter()
+        while True:
+            t_arr += rng.exponential(1.0 / rate_)
+            if t_arr > duration:
+                break
+            g, _ = pool[int(rng.integers(0, pool_size))]
+            while time.perf_counter() - start < t_arr:
+                time.sleep(0.0005)
+            ids.append(sv.submit(g, DIM, int(rng.integers(1 << 62))))
+            offered_tokens += int((g.degrees() > 0).sum()) * L * ROUNDS
+        sv.drain(3600)
+        wall = time.perf_counter() - start
+        res = [sv.wait(r, 60) for r in ids]
+        st = sv.stats()
+        sv.close()
+        done = [r for r in res if r["state"] == fl.JOB_DONE]
+        lat = np.array([r["t_done"] - r["t_submit"] for r in done])
+        tokens = sum(r["tokens"] for r in done)
+        return {"rate_per_s": rate_, "requests": len(ids), "completed": len(done),
+                "p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
+                "p99_s": float(np.percentile(lat, 99)) if len(lat) else None,
+                "offered_tokens_per_s_full_schedule": offered_tokens / duration,
+                "completed_tokens_per_s": tokens / wall, "wall_s": wall,
+                "peak_resident_jobs": st["peak_resident_jobs"], "steps": st["steps"],
+                "busy_s": st["busy_seconds"]}
+
+    out = {"workload": f"Poisson {rate}/s for {duration}s, |V| log-uniform [1e3, {max_nodes}] (pool of "
+                       f"{pool_size} SBM/R-MAT graphs), L={L}, w={WINDOW}, K={NEG}, d={DIM} bf16, "
+                       f"feedback mu={MU}, budget {budget >> 30} GiB",
+           "stated": one(rate)}
+    if sustainable:
+        cap = out["stated"]["completed_tokens_per_s"]
+        mean_tokens = np.mean([int((g.degrees() > 0).sum()) * L * ROUNDS for g, _ in pool])
+        out["sustainable"] = one(max(0.5, 0.7 * cap / mean_tokens))
+    return out
 
 
 def _quality(fl, evaluate, dg, split, n_live):
@@ -489,9 +619,34 @@ def run_reference(args):
     }))
 
 
+def run_form(args):
+    """--mode batch / serve: one JSON line for that form."""
+    import torch
+
+    from paper_2606_22180_b300 import build, felog as fl
+
+    build.build()
+    fl.load()
+    torch.cuda.set_device(0)
+    if args.mode == "batch":
+        r = run_batch(fl, jobs=args.jobs, warmup=1, steps=1)
+        line = {"metric": "SGNS tokens/s, batching form", "value": r["tokens_per_s"], "unit": "tokens/s",
+                "n_gpus": 1, "higher_is_better": True, "dtype": "bf16 tables, f32 math",
+                "data": "synthetic (seeded SBM/R-MAT mix)", "config": {"workload": r["workload"]}, "batching": r}
+    else:
+        r = run_serve(fl, rate=args.rate, duration=args.duration, max_nodes=args.max_nodes)
+        line = {"metric": "p50/p99 latency and completed tokens/s, serving form",
+                "value": r["stated"]["completed_tokens_per_s"], "unit": "tokens/s", "n_gpus": 1,
+                "higher_is_better": True, "dtype": "bf16 tables, f32 math",
+                "data": "synthetic (seeded SBM/R-MAT pool)", "config": {"workload": r["workload"]}, "serving": r}
+    print(json.dumps(line))
+
+
 if __name__ == "__main__":
     a = _args()
     if a.impl == "reference":
         run_reference(a)
+    elif a.mode != "round":
+        run_form(a)
     else:
         run_native(a)

@@ -228,3 +228,54 @@ def workload_sbm1000(seed: int = 0) -> tuple[CSR, np.ndarray]:
 def workload_rmat(scale: int, seed: int, edge_factor: int = 16) -> CSR:
     """R-MAT with (a, b, c, d) = (0.57, 0.19, 0.19, 0.05)."""
     return rmat(scale, edge_factor, 0.57, 0.19, 0.19, seed=seed)
+
+
+def sbm_degree(n: int, communities: int, degree: float, seed: int, ratio: float = 20.0) -> CSR:
+    """Planted partition with p_in / p_out = ratio and expected degree ~degree."""
+    size = n / communities
+    p_in = degree / ((size - 1) + (n - size) / ratio)
+    p_in = min(p_in, 1.0)
+    g, _ = sbm(n, communities, p_in, p_in / ratio, seed)
+    return g
+
+
+def rmat_nodes(n: int, degree: float, seed: int, a=0.57, b=0.19, c=0.19) -> CSR:
+    """R-MAT on the smallest power of two >= n, restricted to nodes < n,
+    with about degree * n / 2 drawn edges kept."""
+    scale = max(1, int(np.ceil(np.log2(n))))
+    N = 1 << scale
+    keep_frac = (n / N) ** 2
+    m = int(degree * n / 2 / max(keep_frac, 1e-3))
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ab, abc = a + b, a + b + c
+    s = np.zeros(m, dtype=np.int64)
+    t = np.zeros(m, dtype=np.int64)
+    for _level in range(scale):
+        r = rng.random(m, dtype=np.float32)
+        s = (s << 1) | (r >= ab)
+        t = (t << 1) | (((r >= a) & (r < ab)) | (r >= abc))
+    perm = rng.permutation(N).astype(np.int64)
+    s, t = perm[s], perm[t]
+    ok = (s < n) & (t < n)
+    return csr_from_edges(n, s[ok], t[ok])
+
+
+def graph_mix(count: int, seed: int, n_lo: int, n_hi: int, deg_lo: float = 8.0, deg_hi: float = 32.0,
+              dims=(64, 128)):
+    """A mix of jobs for the batching and serving forms: half planted
+    partitions (4..32 communities), half R-MAT; node counts log-uniform in
+    [n_lo, n_hi], average degree uniform in [deg_lo, deg_hi], embedding
+    dimension drawn from dims.  Returns a list of (CSR, dim)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(count):
+        n = int(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi))))
+        deg = float(rng.uniform(deg_lo, deg_hi))
+        dim = int(dims[int(rng.integers(0, len(dims)))])
+        if i % 2 == 0:
+            k = int(rng.integers(4, 33))
+            g = sbm_degree(n, k, deg, seed=int(rng.integers(1 << 31)))
+        else:
+            g = rmat_nodes(n, deg, seed=int(rng.integers(1 << 31)))
+        out.append((g, dim))
+    return out
