@@ -250,6 +250,20 @@ class RoundRunner:
         return na, n_walks * L
 
 
+def reduce_over_ranks(ms: float, tokens: float, device) -> tuple[float, float]:
+    """Whole-job aggregation of independent replicas: the slowest rank's time
+    and the tokens of all ranks (no collective on the data path; this is the
+    only exchange)."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    k = torch.tensor([tokens], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(k, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(k.item())
+
+
 def _pairs_per_walk():
     return sum(min(p, WINDOW) + min(L - 1 - p, WINDOW) for p in range(L))
 
@@ -305,12 +319,7 @@ def run_native(args):
     clocks = sampler.stop()
     ms = start.elapsed_time(stop)
     if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        tk = torch.tensor([tokens], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tk)
-        tokens_all = float(tk.item())
+        ms, tokens_all = reduce_over_ranks(ms, tokens, "cuda")
     else:
         tokens_all = float(tokens)
     phase = {name: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in ev)
@@ -346,8 +355,11 @@ def run_native(args):
     e_stop.record()
     barrier()
     e_ms = e_start.elapsed_time(e_stop)
+    e_tokens_all = float(e_tokens)
+    if world > 1:
+        e_ms, e_tokens_all = reduce_over_ranks(e_ms, e_tokens, "cuda")
     h2d = (g.offsets.nbytes + g.cols.nbytes)
-    e2e_value = e_tokens * world / (e_ms / 1e3)
+    e2e_value = e_tokens_all / (e_ms / 1e3)
 
     result = {
         "metric": METRIC,
