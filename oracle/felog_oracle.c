@@ -30,6 +30,7 @@
 #define STREAM_PSI 1u
 #define STREAM_NEG 2u
 #define STREAM_INIT 3u
+#define STREAM_TILE 7u
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10 (SC 2011): ten rounds of two 32x32->64 multiplies; the key  */
@@ -402,6 +403,121 @@ double oracle_sgns_minibatch(const int32_t *walks, int64_t n_walks, int32_t L, i
     }
     free(din); free(dout); free(touched_in); free(touched_out);
     free(list_in); free(list_out); free(tg); free(g);
+    return loss;
+}
+
+/* The Ns shared negatives of tile t (reading of the tile form below):       */
+/* draw j takes Philox(x0 = j, x1 = t, x2 = round, stream 7) and the alias   */
+/* table as a per-pair draw does.                                            */
+void oracle_tile_negatives(const uint64_t *thr, const int32_t *alias, int32_t n, uint64_t S,
+                           uint64_t seed, int32_t round, int64_t t, int32_t Ns, int32_t *out) {
+    for (int32_t j = 0; j < Ns; ++j) {
+        uint32_t r4[4];
+        philox4(seed, (uint32_t)j, (uint32_t)t, (uint32_t)round, STREAM_TILE, r4);
+        uint64_t b = mulhi64(lo_word64(r4), (uint64_t)n);
+        uint64_t coin = mulhi64(hi_word64(r4), S);
+        out[j] = coin < thr[b] ? (int32_t)b : alias[b];
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Shared-negatives tile form of Eq. 2 (an estimator variant; the paper      */
+/* prescribes per-pair draws).  Reading taken:                               */
+/*  - tile t holds the centers at corpus positions [t*T, min(t*T+T, N)),     */
+/*    positions numbered walk*L + pos, pairs formed as in the serial form;  */
+/*  - the tile draws Ns negatives once: draw j uses Philox(x0 = j,           */
+/*    x1 = t, x2 = round, stream 7) and the alias table exactly like a      */
+/*    per-pair draw; every pair of the tile uses all Ns of them, each with  */
+/*    weight K/Ns, so the expected negative term of a pair equals that of   */
+/*    K independent draws; a shared negative equal to the pair's center is   */
+/*    skipped for that pair (the per-pair skip rule);                       */
+/*  - eta is the rate of the tile's first center position;                   */
+/*  - all scores of a tile read the tables as they stood when the tile       */
+/*    began and the summed increments are added when it ends (tiles run in  */
+/*    order).                                                               */
+/* Per pair (x, c): loss -log sigma(f+) - (K/Ns) sum_j log sigma(-f_j),       */
+/* increments g+ = eta (1 - sigma(f+)), g_j = -eta (K/Ns) sigma(f_j) applied */
+/* as phi_in[x] += g phi_out[target], phi_out[target] += g phi_in[x].         */
+/* tile_loss (may be NULL) receives each tile's loss.                        */
+/* ------------------------------------------------------------------------ */
+double oracle_sgns_tile(const int32_t *walks, int64_t n_walks, int32_t L, int32_t n,
+                        const oracle_train_params *tp, int32_t T, int32_t Ns,
+                        const uint64_t *thr, const int32_t *alias, uint64_t S, uint64_t seed,
+                        int32_t round, int64_t clock_base, double *phi_in, double *phi_out,
+                        double *tile_loss) {
+    const int32_t d = tp->dim, w = tp->window, K = tp->negatives;
+    const double omega = (double)K / (double)Ns;
+    double *din = (double *)calloc((size_t)n * d, sizeof(double));
+    double *dout = (double *)calloc((size_t)n * d, sizeof(double));
+    uint8_t *touched_in = (uint8_t *)calloc((size_t)n, 1);
+    uint8_t *touched_out = (uint8_t *)calloc((size_t)n, 1);
+    int32_t *list_in = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *list_out = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *neg = (int32_t *)malloc(sizeof(int32_t) * (size_t)Ns);
+    const int64_t total = n_walks * L;
+    double loss = 0.0;
+    int64_t t = 0;
+    for (int64_t b0 = 0; b0 < total; b0 += T, ++t) {
+        int64_t b1 = b0 + T < total ? b0 + T : total;
+        double eta = oracle_learning_rate(tp->lr0, clock_base + b0, tp->lr_total_tokens);
+        oracle_tile_negatives(thr, alias, n, S, seed, round, t, Ns, neg);
+        int32_t n_in = 0, n_out = 0;
+        double tl = 0.0;
+        for (int64_t tok = b0; tok < b1; ++tok) {
+            int64_t wi = tok / L;
+            int32_t p = (int32_t)(tok % L);
+            const int32_t *row = walks + wi * L;
+            int32_t c = row[p];
+            if (c < 0) continue;
+            for (int32_t o = -w; o <= w; ++o) {
+                if (o == 0) continue;
+                int32_t pp = p + o;
+                if (pp < 0 || pp >= L || row[pp] < 0) continue;
+                int32_t x = row[pp];
+                const double *ix = phi_in + (int64_t)x * d;
+                double *dx = din + (int64_t)x * d;
+                if (!touched_in[x]) { touched_in[x] = 1; list_in[n_in++] = x; }
+                for (int32_t j = -1; j < Ns; ++j) {
+                    int32_t target = j < 0 ? c : neg[j];
+                    if (j >= 0 && target == c) continue;
+                    const double *ot = phi_out + (int64_t)target * d;
+                    double f = dot(ix, ot, d);
+                    double g;
+                    if (j < 0) {
+                        tl += neg_log_sigmoid(f);
+                        g = eta * (1.0 - sigmoid(f));
+                    } else {
+                        tl += omega * neg_log_sigmoid(-f);
+                        g = -eta * omega * sigmoid(f);
+                    }
+                    double *dt = dout + (int64_t)target * d;
+                    for (int32_t i = 0; i < d; ++i) dx[i] += g * ot[i];
+                    for (int32_t i = 0; i < d; ++i) dt[i] += g * ix[i];
+                    if (!touched_out[target]) { touched_out[target] = 1; list_out[n_out++] = target; }
+                }
+            }
+        }
+        for (int32_t a = 0; a < n_in; ++a) {
+            int64_t r = list_in[a];
+            for (int32_t i = 0; i < d; ++i) {
+                phi_in[r * d + i] += din[r * d + i];
+                din[r * d + i] = 0.0;
+            }
+            touched_in[r] = 0;
+        }
+        for (int32_t a = 0; a < n_out; ++a) {
+            int64_t r = list_out[a];
+            for (int32_t i = 0; i < d; ++i) {
+                phi_out[r * d + i] += dout[r * d + i];
+                dout[r * d + i] = 0.0;
+            }
+            touched_out[r] = 0;
+        }
+        if (tile_loss) tile_loss[t] = tl;
+        loss += tl;
+    }
+    free(din); free(dout); free(touched_in); free(touched_out);
+    free(list_in); free(list_out); free(neg);
     return loss;
 }
 
