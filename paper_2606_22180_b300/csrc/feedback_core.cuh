@@ -58,28 +58,53 @@ __device__ __forceinline__ double psi_node(const int32_t *__restrict__ cols, con
         }
     }
     __syncwarp();
+    // elements l, l+32, ... of phi[v] (dim <= 256, so at most 8 per lane)
     const T *pv = phi + v * dim;
+    const int per_lane = dim >> 5;
+    double xv[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) xv[c] = c < per_lane ? elem(pv, lane + 32 * c) : 0.0;
     double nv = 0.0;
-    for (int i = lane; i < dim; i += 32) {
-        const double x = elem(pv, i);
-        nv = __dadd_rn(nv, __dmul_rn(x, x));
-    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+        if (c < per_lane) nv = __dadd_rn(nv, __dmul_rn(xv[c], xv[c]));
     nv = butterfly(nv);
+    // neighbours in groups of 4 so that their row loads overlap; each dot
+    // product keeps the fixed per-lane order and butterfly, and the cosines
+    // are added in ascending subset order
+    constexpr int G = 4;
     double sum = 0.0;
-    for (int a = 0; a < m; ++a) {
-        const int32_t u = cols[lo + sorted[a]];
-        const T *pu = phi + static_cast<int64_t>(u) * dim;
-        double nu = 0.0, dt = 0.0;
-        for (int i = lane; i < dim; i += 32) {
-            const double y = elem(pu, i);
-            nu = __dadd_rn(nu, __dmul_rn(y, y));
-            dt = __dadd_rn(dt, __dmul_rn(elem(pv, i), y));
+    for (int a0 = 0; a0 < m; a0 += G) {
+        const T *pu[G];
+#pragma unroll
+        for (int b = 0; b < G; ++b) {
+            const int32_t u = a0 + b < m ? cols[lo + sorted[a0 + b]] : 0;
+            pu[b] = phi + static_cast<int64_t>(u) * dim;
         }
-        nu = butterfly(nu);
-        dt = butterfly(dt);
-        double cs = 0.0;
-        if (nv > 0.0 && nu > 0.0) cs = __ddiv_rn(dt, __dmul_rn(__dsqrt_rn(nv), __dsqrt_rn(nu)));
-        sum = __dadd_rn(sum, cs);
+        double nu[G], dt[G];
+#pragma unroll
+        for (int b = 0; b < G; ++b) nu[b] = dt[b] = 0.0;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            if (c >= per_lane) break;
+            double y[G];
+#pragma unroll
+            for (int b = 0; b < G; ++b) y[b] = elem(pu[b], lane + 32 * c);
+#pragma unroll
+            for (int b = 0; b < G; ++b) {
+                nu[b] = __dadd_rn(nu[b], __dmul_rn(y[b], y[b]));
+                dt[b] = __dadd_rn(dt[b], __dmul_rn(xv[c], y[b]));
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < G; ++b) {
+            if (a0 + b >= m) break;
+            const double n2 = butterfly(nu[b]);
+            const double d2 = butterfly(dt[b]);
+            double cs = 0.0;
+            if (nv > 0.0 && n2 > 0.0) cs = __ddiv_rn(d2, __dmul_rn(__dsqrt_rn(nv), __dsqrt_rn(n2)));
+            sum = __dadd_rn(sum, cs);
+        }
     }
     const double psi = __ddiv_rn(sum, static_cast<double>(m));
     __syncwarp();
