@@ -70,7 +70,8 @@ typedef struct {
 
 typedef enum {
     FELOG_SGNS_HOGWILD = 0,  /* lock-free asynchronous updates (fast form) */
-    FELOG_SGNS_MINIBATCH = 1 /* synchronous minibatch, bitwise reproducible */
+    FELOG_SGNS_MINIBATCH = 1, /* synchronous minibatch, bitwise reproducible */
+    FELOG_SGNS_TILE = 2       /* shared-negatives tiles on the tensor cores */
 } felog_sgns_mode;
 
 typedef enum {
@@ -86,7 +87,12 @@ typedef enum {
  * staleness of lock-free updates on small graphs; hogwild_form selects the
  * HOGWILD kernel: 0 = automatic (half-warp form where dim <= 128 and
  * negatives <= 7, full-warp form otherwise), 1 = full warp per pair,
- * 2 = two pairs per warp (half warp each; dim <= 128, negatives <= 7). */
+ * 2 = two pairs per warp (half warp each; dim <= 128, negatives <= 7).
+ * TILE mode (dim in {32, 64, 128}): tile_negatives = shared negatives per
+ * tile (32, 64, 96 or 128; 0 selects 64); tile_ctas = concurrent tiles
+ * (0 = min(SMs, max(1, n / 2048)), which bounds how many stale tile updates
+ * meet on the rows of a small graph; 1 = tiles strictly in order, the
+ * reproducible form). */
 typedef struct {
     int32_t dim;
     int32_t window;
@@ -98,6 +104,8 @@ typedef struct {
     int32_t precision; /* felog_precision */
     int32_t hogwild_rows_per_warp;
     int32_t hogwild_form;
+    int32_t tile_negatives;
+    int32_t tile_ctas;
 } felog_train_params;
 
 /* enabled = 0 is the plain method (every non-isolated node stays active);
@@ -208,8 +216,18 @@ felog_status felog_init_tables(int32_t n, int32_t dim, int32_t precision, uint64
  * HOGWILD applies updates immediately with no locking; MINIBATCH reads the
  * tables as they stood at the start of each batch of `minibatch` positions,
  * sums the increments per row exactly (fixed point, order independent) and
- * applies them at the end of the batch.  *loss (device double) receives the
- * summed pair loss -log sigma(s+) - sum log sigma(-s_k).
+ * applies them at the end of the batch.  TILE replaces the per-pair draws
+ * by Ns = tile_negatives draws shared by all pairs whose center lies in one
+ * tile of Tc = 128 - 2W consecutive corpus positions (tile t: positions
+ * [t*Tc, t*Tc + Tc)): draw j is Philox(x0 = j, x1 = t, x2 = round, 7) through
+ * the alias table, each shared negative has weight K / Ns, one equal to the
+ * pair's center is skipped; eta is that of the tile's first position; the
+ * scores of a tile read the tables as gathered at its start and its summed
+ * increments are added at its end; products run in bf16 on the tensor
+ * cores with f32 accumulation.  *loss (device double) receives the summed
+ * pair loss -log sigma(s+) - sum log sigma(-s_k) (TILE: negatives weighted
+ * by K / Ns); it is NaN if a TILE launch gave up waiting for the tensor
+ * cores (the launch then stops early).
  * Workspace: felog_train_workspace_bytes(...). */
 size_t felog_train_workspace_bytes(int64_t n_walks, int32_t L, int32_t n,
                                    const felog_train_params *tp);

@@ -388,8 +388,10 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-__global__ void k_loss_finish(const unsigned long long *__restrict__ acc, double *__restrict__ loss) {
-    *loss = static_cast<double>(static_cast<long long>(*acc)) / kLossScale;
+__global__ void k_loss_finish(const unsigned long long *__restrict__ acc, const int32_t *__restrict__ timeout,
+                              double *__restrict__ loss) {
+    *loss = *timeout ? __longlong_as_double(0x7ff8000000000000LL)
+                     : static_cast<double>(static_cast<long long>(*acc)) / kLossScale;
 }
 
 // ----------------------------------------------------------------------------
@@ -427,14 +429,22 @@ __global__ void k_init_tables(int32_t n, int32_t dim, uint64_t seed, T *__restri
 // ----------------------------------------------------------------------------
 struct TrainWorkspace {
     unsigned long long *loss_acc;
+    int32_t *timeout;  // set by a TILE launch whose tensor-core wait gave up
     MbState mb;
 };
+
+felog_status launch_tile(const int32_t *walks, int64_t n_walks, int32_t L, int32_t n,
+                         const felog_train_params *tp, const uint64_t *thr, const int32_t *alias,
+                         const uint64_t *S, uint64_t seed, int32_t round, int64_t clock_base,
+                         void *phi_in, void *phi_out, unsigned long long *loss_acc, int32_t *timeout,
+                         cudaStream_t s);
 
 static bool minibatch_mode(const felog_train_params *tp) { return tp->mode == FELOG_SGNS_MINIBATCH; }
 
 static TrainWorkspace carve_train(Carver &c, int32_t n, const felog_train_params *tp) {
     TrainWorkspace w{};
     w.loss_acc = c.take<unsigned long long>(1);
+    w.timeout = c.take<int32_t>(1);
     if (minibatch_mode(tp)) {
         const size_t nn = n > 0 ? static_cast<size_t>(n) : 1;
         w.mb.acc_in = c.take<long long>(nn * tp->dim);
@@ -452,7 +462,15 @@ static bool params_ok(const felog_train_params *tp) {
     if (!tp) return false;
     if (tp->dim != 32 && tp->dim != 64 && tp->dim != 128 && tp->dim != 256) return false;
     if (tp->window < 1 || tp->window > 16 || tp->negatives < 1 || tp->negatives > 15) return false;
-    if (tp->mode != FELOG_SGNS_HOGWILD && tp->mode != FELOG_SGNS_MINIBATCH) return false;
+    if (tp->mode != FELOG_SGNS_HOGWILD && tp->mode != FELOG_SGNS_MINIBATCH && tp->mode != FELOG_SGNS_TILE)
+        return false;
+    if (tp->mode == FELOG_SGNS_TILE) {
+        if (tp->dim > 128) return false;
+        if (tp->tile_negatives != 0 && (tp->tile_negatives < 32 || tp->tile_negatives > 128 ||
+                                        tp->tile_negatives % 32 != 0))
+            return false;
+        if (tp->tile_ctas < 0) return false;
+    }
     if (tp->precision != FELOG_FP32 && tp->precision != FELOG_BF16_SR) return false;
     if (tp->mode == FELOG_SGNS_MINIBATCH && tp->minibatch < 1) return false;
     if (tp->hogwild_form < 0 || tp->hogwild_form > 2) return false;
@@ -557,6 +575,7 @@ extern "C" felog_status felog_train(const int32_t *walks, int64_t n_walks, int32
     Carver c(workspace, workspace_bytes);
     TrainWorkspace w = carve_train(c, n, tp);
     felog_status st = record_cuda_error(cudaMemsetAsync(w.loss_acc, 0, sizeof(unsigned long long), s), "train");
+    if (!st) st = record_cuda_error(cudaMemsetAsync(w.timeout, 0, sizeof(int32_t), s), "train");
     if (st) return st;
     if (minibatch_mode(tp)) {
         st = record_cuda_error(cudaMemsetAsync(w.mb.mark_in, 0, sizeof(uint32_t) * n, s), "train");
@@ -565,7 +584,11 @@ extern "C" felog_status felog_train(const int32_t *walks, int64_t n_walks, int32
         if (!st) st = record_cuda_error(cudaMemsetAsync(w.mb.acc_out, 0, sizeof(long long) * n * tp->dim, s), "train");
         if (st) return st;
     }
-    if (n_walks > 0) {
+    if (n_walks > 0 && tp->mode == FELOG_SGNS_TILE) {
+        st = launch_tile(walks, n_walks, L, n, tp, thr, alias, S, seed, round, clock_base, phi_in, phi_out,
+                         w.loss_acc, w.timeout, s);
+        if (st) return st;
+    } else if (n_walks > 0) {
         SgnsArgs a;
         a.walks = walks;
         a.n_walks = n_walks;
@@ -586,7 +609,7 @@ extern "C" felog_status felog_train(const int32_t *walks, int64_t n_walks, int32
                                          : dispatch_dim<__nv_bfloat16>(a, tp, phi_in, phi_out, w, s);
         if (st) return st;
     }
-    k_loss_finish<<<1, 1, 0, s>>>(w.loss_acc, loss);
+    k_loss_finish<<<1, 1, 0, s>>>(w.loss_acc, w.timeout, loss);
     return check_launch("felog_train");
 }
 

@@ -1,0 +1,459 @@
+// Shared-negatives tile form of Eq. 2 on the tensor cores (tcgen05).
+//
+// Estimator (a variant of the per-pair draws of Eq. 2): tile t holds the
+// centers at corpus positions [t*Tc, t*Tc + Tc) (position = walk*L + pos,
+// Tc = 128 - 2w); the tile draws Ns negatives once, draw j from
+// Philox(x0 = j, x1 = t, x2 = round, stream 7) and the alias table; every
+// pair (context x, center c) of the tile uses all Ns of them with weight
+// K / Ns, skipping a negative equal to c.  eta is the rate of the tile's
+// first center.  Scores read the tables as they stood when the tile's rows
+// were gathered; the summed increments are added when the tile ends.
+//
+// One CTA of 4 warps per SM works through tiles.  A tile's 128 rows are the
+// positions [t*Tc - w, t*Tc - w + 128): every context of the tile's centers
+// lies among them.  With X = phi_in of those positions (128 x d) and
+// Y = [phi_out of the positions; phi_out of the Ns negatives] (128 + Ns
+// rows), three bf16 contractions with f32 accumulation in tensor memory do
+// the dense work:
+//   S  = X Y^T        scores of every (position, target) pair
+//   G  = grad(S)      epilogue on CUDA cores: positives on the band
+//                     |p - q| <= w of the same walk, negatives weighted by
+//                     K/Ns times the row's pair count (minus pairs whose
+//                     center equals the negative)
+//   dX = G Y          increments of phi_in rows
+//   dY = G^T X        increments of phi_out rows
+// The increments are added to the tables with vector reductions (bf16
+// tables: stochastically rounded increments against the gathered values).
+//
+// Shared memory (no-swizzle core-matrix layout, see tc_core.cuh): X
+// 128 x d, Y 256 x d, G 128 x 256, all bf16.  Tensor memory: 512 columns;
+// S in columns [0, 128 + Ns), dX in [256, 256 + d), dY (positions, then
+// negatives) reuses [0, 2d) once S has been read.
+#include <algorithm>
+
+#include "sgns_core.cuh"
+#include "tc_core.cuh"
+
+namespace felog {
+
+constexpr uint32_t kStreamTile = 7;
+constexpr int kTileThreads = 128;
+constexpr int kTileRows = 128;
+constexpr uint32_t kTileWaitLimit = 1u << 26;  // polls of an mbarrier before reporting a timeout
+
+struct TileArgs {
+    const int32_t *walks;
+    int64_t total;  // n_walks * L
+    int64_t n_tiles;
+    int32_t L, n, window, K, Ns, Tc;
+    float lr0;
+    double inv_total;  // 1 / lr_total_tokens
+    int64_t clock_base;
+    const uint64_t *thr;
+    const int32_t *alias;
+    const uint64_t *S;
+    uint64_t seed;
+    uint32_t round;
+    unsigned long long *loss_acc;
+    int32_t *timeout;
+};
+
+template <int D>
+struct TileSmem {
+    static constexpr uint32_t kX = 0;
+    static constexpr uint32_t kY = kX + kTileRows * D * 2;
+    static constexpr uint32_t kG = kY + 256 * D * 2;
+    static constexpr uint32_t kEnd = kG + kTileRows * 256 * 2;
+    // requested size: at least 120 KB so that one CTA holds an SM and its
+    // 512 tensor-memory columns
+    static constexpr uint32_t kBytes = kEnd > 122880 ? kEnd : 122880;
+};
+
+__device__ __forceinline__ float sigmoidf_fast(float s) { return 1.f / (1.f + __expf(-s)); }
+
+// 8 floats -> 8 bf16 (round to nearest) packed in 4 words
+__device__ __forceinline__ uint4 pack8(const float4 &a, const float4 &b) {
+    uint4 r;
+    __nv_bfloat162 h;
+    h = __floats2bfloat162_rn(a.x, a.y); r.x = *reinterpret_cast<uint32_t *>(&h);
+    h = __floats2bfloat162_rn(a.z, a.w); r.y = *reinterpret_cast<uint32_t *>(&h);
+    h = __floats2bfloat162_rn(b.x, b.y); r.z = *reinterpret_cast<uint32_t *>(&h);
+    h = __floats2bfloat162_rn(b.z, b.w); r.w = *reinterpret_cast<uint32_t *>(&h);
+    return r;
+}
+
+__device__ __forceinline__ uint4 ld_row8(const float *p) {
+    float4 a, b;
+    asm volatile("ld.global.cg.v4.f32 {%0,%1,%2,%3}, [%4];" : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w) : "l"(p));
+    asm volatile("ld.global.cg.v4.f32 {%0,%1,%2,%3}, [%4];" : "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w) : "l"(p + 4));
+    return pack8(a, b);
+}
+__device__ __forceinline__ uint4 ld_row8(const __nv_bfloat16 *p) {
+    uint4 r;
+    asm volatile("ld.global.cg.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(p));
+    return r;
+}
+
+// Adds 8 increments (f32) to table elements p[0..8); `snap` holds the 8
+// gathered values as packed bf16 (used by bf16 tables for stochastic
+// rounding of gathered value + increment).
+__device__ __forceinline__ void add8(float *p, const float *d, uint4, uint32_t) {
+    red_add_v4(p, d[0], d[1], d[2], d[3]);
+    red_add_v4(p + 4, d[4], d[5], d[6], d[7]);
+}
+__device__ __forceinline__ void add8(__nv_bfloat16 *p, const float *d, uint4 snap, uint32_t w) {
+    const uint32_t raw[4] = {snap.x, snap.y, snap.z, snap.w};
+    float dd[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) dd[i] = d[i];
+    add_delta_raw<8>(p, raw, dd, w);
+}
+
+template <int D, class T>
+__global__ void __launch_bounds__(kTileThreads, 1)
+    k_sgns_tile(TileArgs a, T *__restrict__ phi_in, T *__restrict__ phi_out) {
+    using Lay = TileSmem<D>;
+    extern __shared__ __align__(1024) uint8_t sm[];
+    __shared__ int32_t node_s[kTileRows];     // node of each row position (-1: none)
+    __shared__ uint32_t walk_s[kTileRows];    // walk index of each row position
+    __shared__ int32_t neg_s[kTileRows];      // shared negatives (Ns used)
+    __shared__ uint8_t colused_s[2 * kTileRows];  // Y row received a nonzero gradient column
+    __shared__ uint8_t hit_s[kTileRows];      // center equals one of the negatives
+    __shared__ uint32_t bloom_s[32];
+    __shared__ __align__(8) uint64_t bar_s;
+    __shared__ uint32_t tmem_s;
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t base = smem_addr(sm);
+    const uint32_t xs = base + Lay::kX, ys = base + Lay::kY, gs = base + Lay::kG;
+    const uint32_t bar = smem_addr(&bar_s);
+    const int w = a.window, Ns = a.Ns, NY = kTileRows + Ns;
+    const uint64_t nn = static_cast<uint64_t>(a.n), Ssum = *a.S;
+    const float omega = static_cast<float>(a.K) / static_cast<float>(Ns);
+
+    // zero the parts of Y and G that no tile writes (negative rows beyond Ns,
+    // gradient columns beyond 128 + Ns)
+    for (int e = tid; e < (256 - NY) * D / 8; e += kTileThreads) {
+        const int r = NY + e / (D / 8), c = (e % (D / 8)) * 8;
+        *reinterpret_cast<uint4 *>(sm + Lay::kY + core_offset(r, c, 256)) = make_uint4(0, 0, 0, 0);
+    }
+    for (int e = tid; e < kTileRows * (256 - NY) / 8; e += kTileThreads) {
+        const int r = e / ((256 - NY) / 8), c = NY + (e % ((256 - NY) / 8)) * 8;
+        *reinterpret_cast<uint4 *>(sm + Lay::kG + core_offset(r, c, kTileRows)) = make_uint4(0, 0, 0, 0);
+    }
+    if (tid == 0) mbar_init(bar, 1);
+    if (warp == 0) tmem_alloc(smem_addr(&tmem_s), 512);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tm = tmem_s;
+    const uint32_t lane_base = tm + (static_cast<uint32_t>(warp * 32) << 16);
+    uint32_t phase = 0;
+    double loss = 0.0;
+    bool failed = false;
+
+    for (int64_t t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
+        const int64_t pos0 = t * a.Tc - w;  // corpus position of row 0
+        // ---- rows, negatives ------------------------------------------------
+        {
+            const int64_t pos = pos0 + tid;
+            int32_t v = -1;
+            uint32_t wk = 0xffffffffu;
+            if (pos >= 0 && pos < a.total) {
+                v = __ldg(a.walks + pos);
+                wk = static_cast<uint32_t>(pos / a.L);
+            }
+            node_s[tid] = v;
+            walk_s[tid] = wk;
+            colused_s[tid] = 0;
+            colused_s[kTileRows + tid] = 0;
+            if (tid < 32) bloom_s[tid] = 0;
+        }
+        __syncthreads();
+        if (tid < Ns) {
+            const u32x4 r = philox(a.seed, static_cast<uint32_t>(tid), static_cast<uint32_t>(t), a.round, kStreamTile);
+            const uint64_t b = mulhi64(lo64(r), nn);
+            const uint64_t coin = mulhi64(hi64(r), Ssum);
+            const uint64_t th = __ldg(reinterpret_cast<const unsigned long long *>(a.thr) + b);
+            const int32_t v = coin < th ? static_cast<int32_t>(b) : __ldg(a.alias + b);
+            neg_s[tid] = v;
+            atomicOr(&bloom_s[(static_cast<uint32_t>(v) * 0x9E3779B1u) >> 27], 1u << (v & 31));
+        }
+        // ---- gather X (phi_in of positions) and Y (phi_out of centers and
+        //      negatives) into the core-matrix layout, as bf16 ------------------
+        __syncthreads();
+        {
+            const int lane = tid & 31;
+            const int r8 = lane & 7, cq = lane >> 3;  // row within group, chunk within 4
+            constexpr int kChunks = D / 8;            // 16-byte bf16 chunks per row
+            constexpr int kUnitsPerGroup = kChunks / 4;
+            const int groups = kTileRows / 8 + NY / 8;  // X row groups, then Y row groups
+            for (int u = warp; u < groups * kUnitsPerGroup; u += 4) {
+                const int gi = u / kUnitsPerGroup, c = ((u % kUnitsPerGroup) * 4 + cq) * 8;
+                const bool isx = gi < kTileRows / 8;
+                const int r = (isx ? gi : gi - kTileRows / 8) * 8 + r8;
+                int32_t v;
+                if (isx) v = node_s[r];
+                else if (r < kTileRows) v = (r >= w && r < w + a.Tc) ? node_s[r] : -1;  // centers only
+                else v = neg_s[r - kTileRows];
+                uint4 val = make_uint4(0, 0, 0, 0);
+                if (v >= 0) val = ld_row8((isx ? phi_in : phi_out) + static_cast<int64_t>(v) * D + c);
+                const uint32_t off = isx ? Lay::kX + core_offset(r, c, kTileRows) : Lay::kY + core_offset(r, c, 256);
+                *reinterpret_cast<uint4 *>(sm + off) = val;
+            }
+        }
+        // centers equal to a negative (exact check behind a bloom filter)
+        {
+            const int32_t v = node_s[tid];
+            uint8_t hit = 0;
+            if (v >= 0 && tid >= w && tid < w + a.Tc &&
+                (bloom_s[(static_cast<uint32_t>(v) * 0x9E3779B1u) >> 27] >> (v & 31) & 1u))
+                for (int j = 0; j < Ns; ++j) hit |= neg_s[j] == v;
+            hit_s[tid] = hit;
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        // ---- S = X Y^T ---------------------------------------------------------
+        if (tid == 0) {
+#pragma unroll
+            for (int s = 0; s < D / 16; ++s)
+                mma_bf16(tm, smem_desc(xs + 2 * s * (kTileRows * 16), kTileRows * 16, 128),
+                         smem_desc(ys + 2 * s * (256 * 16), 256 * 16, 128), mma_idesc_bf16(128, NY, 0, 0), s > 0);
+            mma_commit(bar);
+        }
+        failed = !mbar_wait(bar, phase, kTileWaitLimit);
+        phase ^= 1;
+        tc_fence_after();
+        if (__syncthreads_or(failed)) break;
+        // ---- epilogue: gradient G (bf16) ------------------------------------
+        const int q = tid;
+        const int32_t vq = node_s[q];
+        const uint32_t wq = walk_s[q];
+        const float eta = static_cast<float>(
+            static_cast<double>(a.lr0) *
+            fmax(1e-4, 1.0 - static_cast<double>(a.clock_base + t * a.Tc) * a.inv_total));
+        int cnt = 0;        // pairs with context at row q
+        bool any_hit = false;
+        float row_loss = 0.f;
+#pragma unroll 1
+        for (int c = 0; c < 4; ++c) {  // positive band, columns 32c .. 32c+31
+            uint32_t packed[16];
+            const bool near = c >= warp - 1 && c <= warp + 1;  // warp-uniform
+            if (near) {
+                uint32_t r[32];
+                tmem_ld32(lane_base + 32 * c, r);
+                tmem_wait_ld();
+#pragma unroll
+                for (int i = 0; i < 32; i += 2) {
+                    float g2[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int p = 32 * c + i + h;
+                        const int dqp = p - q;
+                        float g = 0.f;
+                        if (vq >= 0 && dqp != 0 && dqp >= -w && dqp <= w && p >= w && p < w + a.Tc &&
+                            node_s[p] >= 0 && walk_s[p] == wq) {
+                            const float s = __uint_as_float(r[i + h]);
+                            g = eta * (1.f - sigmoidf_fast(s));
+                            row_loss += softplus_neg(s);
+                            ++cnt;
+                            any_hit |= hit_s[p] != 0;
+                            colused_s[p] = 1;
+                        }
+                        g2[h] = g;
+                    }
+                    __nv_bfloat162 hv = __floats2bfloat162_rn(g2[0], g2[1]);
+                    packed[i / 2] = *reinterpret_cast<uint32_t *>(&hv);
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) packed[i] = 0;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                *reinterpret_cast<uint4 *>(sm + Lay::kG + core_offset(q, 32 * c + 8 * k, kTileRows)) =
+                    make_uint4(packed[4 * k], packed[4 * k + 1], packed[4 * k + 2], packed[4 * k + 3]);
+        }
+#pragma unroll 1
+        for (int c = 0; c < Ns / 32; ++c) {  // shared negatives, columns 128 + 32c ..
+            uint32_t r[32];
+            tmem_ld32(lane_base + kTileRows + 32 * c, r);
+            tmem_wait_ld();
+            uint32_t packed[16];
+#pragma unroll
+            for (int i = 0; i < 32; i += 2) {
+                float g2[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int k = 32 * c + i + h;
+                    int m = cnt;
+                    if (any_hit) {  // pairs whose center is this negative do not count
+                        const int32_t nk = neg_s[k];
+                        for (int p = max(w, q - w); p <= min(w + a.Tc - 1, q + w); ++p)
+                            if (p != q && hit_s[p] && node_s[p] == nk && walk_s[p] == wq) --m;
+                    }
+                    float g = 0.f;
+                    if (m > 0) {
+                        const float s = __uint_as_float(r[i + h]);
+                        const float wm = omega * static_cast<float>(m);
+                        g = -eta * wm * sigmoidf_fast(s);
+                        row_loss += wm * softplus_neg(-s);
+                        colused_s[kTileRows + k] = 1;
+                    }
+                    g2[h] = g;
+                }
+                __nv_bfloat162 hv = __floats2bfloat162_rn(g2[0], g2[1]);
+                packed[i / 2] = *reinterpret_cast<uint32_t *>(&hv);
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                *reinterpret_cast<uint4 *>(sm + Lay::kG + core_offset(q, kTileRows + 32 * c + 8 * k, kTileRows)) =
+                    make_uint4(packed[4 * k], packed[4 * k + 1], packed[4 * k + 2], packed[4 * k + 3]);
+        }
+        loss += static_cast<double>(row_loss);
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        // ---- dX = G Y, dY = G^T X -------------------------------------------
+        if (tid == 0) {
+            for (int s = 0; s < NY / 16; ++s)
+                mma_bf16(tm + 256, smem_desc(gs + 2 * s * (kTileRows * 16), kTileRows * 16, 128),
+                         smem_desc(ys + 2 * s * 128, 128, 256 * 16), mma_idesc_bf16(128, D, 0, 1), s > 0);
+            for (int h = 0; h < 2; ++h) {
+#pragma unroll
+                for (int s = 0; s < kTileRows / 16; ++s)
+                    mma_bf16(tm + h * D, smem_desc(gs + h * 16 * (kTileRows * 16) + 2 * s * 128, 128, kTileRows * 16),
+                             smem_desc(xs + 2 * s * 128, 128, kTileRows * 16), mma_idesc_bf16(128, D, 1, 1), s > 0);
+            }
+            mma_commit(bar);
+        }
+        failed = !mbar_wait(bar, phase, kTileWaitLimit);
+        phase ^= 1;
+        tc_fence_after();
+        if (__syncthreads_or(failed)) break;
+        // ---- add the increments to the tables --------------------------------
+        {
+            const u32x4 rw = philox(a.seed, static_cast<uint32_t>(t), static_cast<uint32_t>(q), a.round, kStreamSR);
+            uint32_t sr0 = rw.x | 1u, sr1 = rw.y | 1u, sr2 = rw.z | 1u;
+            const bool do_x = vq >= 0 && cnt > 0;
+            const bool do_c = colused_s[q] != 0;
+            const bool do_n = q < Ns && colused_s[kTileRows + q] != 0;
+            T *px = phi_in + static_cast<int64_t>(max(vq, 0)) * D;
+            T *pc = phi_out + static_cast<int64_t>(max(node_s[q], 0)) * D;
+            T *pn = phi_out + static_cast<int64_t>(q < Ns ? neg_s[q] : 0) * D;
+#pragma unroll 1
+            for (int c = 0; c < D / 32; ++c) {
+                uint32_t rx[32], rc[32], rn[32];
+                tmem_ld32(lane_base + 256 + 32 * c, rx);
+                tmem_ld32(lane_base + 32 * c, rc);
+                tmem_ld32(lane_base + D + 32 * c, rn);
+                tmem_wait_ld();
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int col = 32 * c + 8 * k;
+                    float d8[8];
+                    if (do_x) {
+                        const uint4 snap = *reinterpret_cast<const uint4 *>(sm + Lay::kX + core_offset(q, col, kTileRows));
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) d8[i] = __uint_as_float(rx[8 * k + i]);
+                        add8(px + col, d8, snap, xorshift32(sr0));
+                    }
+                    if (do_c) {
+                        const uint4 snap = *reinterpret_cast<const uint4 *>(sm + Lay::kY + core_offset(q, col, 256));
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) d8[i] = __uint_as_float(rc[8 * k + i]);
+                        add8(pc + col, d8, snap, xorshift32(sr1));
+                    }
+                    if (do_n) {
+                        const uint4 snap =
+                            *reinterpret_cast<const uint4 *>(sm + Lay::kY + core_offset(kTileRows + q, col, 256));
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) d8[i] = __uint_as_float(rn[8 * k + i]);
+                        add8(pn + col, d8, snap, xorshift32(sr2));
+                    }
+                }
+            }
+        }
+        // the next tile's gather reads what these reductions wrote
+        __threadfence();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+    }
+    if (failed && tid == 0) atomicExch(a.timeout, 1);
+    long long fx = __double2ll_rn(loss * kLossScale);
+    for (int o = 16; o; o >>= 1) fx += __shfl_xor_sync(kFull, fx, o);
+    if ((tid & 31) == 0 && fx != 0) atomicAdd(a.loss_acc, static_cast<unsigned long long>(fx));
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tm, 512);
+}
+
+template <int D, class T>
+static felog_status launch_tile_dim(const TileArgs &a, int ctas, void *pi, void *po, cudaStream_t s) {
+    auto kern = k_sgns_tile<D, T>;
+    const int bytes = static_cast<int>(TileSmem<D>::kBytes);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return record_cuda_error(e, "felog_train (tile)");
+    kern<<<ctas, kTileThreads, bytes, s>>>(a, static_cast<T *>(pi), static_cast<T *>(po));
+    return check_launch("felog_train (tile)");
+}
+
+// Rows per concurrent tile under the automatic cap: a tile adds its summed
+// increments to ~300 rows at once, computed from values gathered when it
+// began, so too many tiles in flight on a small graph pile stale steps onto
+// the same rows and training diverges (1,000 nodes with one tile per SM
+// does); at most n / kTileRowsPerCta tiles run at once.
+constexpr int64_t kTileRowsPerCta = 2048;
+
+// Launches the tile trainer over walks[n_walks][L]; called by felog_train
+// after argument checks.  tile_ctas <= 0: min(SMs, max(1, n / 2048)) tiles
+// at once; 1 runs the tiles in order (the reproducible form).
+felog_status launch_tile(const int32_t *walks, int64_t n_walks, int32_t L, int32_t n,
+                         const felog_train_params *tp, const uint64_t *thr, const int32_t *alias,
+                         const uint64_t *S, uint64_t seed, int32_t round, int64_t clock_base,
+                         void *phi_in, void *phi_out, unsigned long long *loss_acc, int32_t *timeout,
+                         cudaStream_t s) {
+    TileArgs a;
+    a.walks = walks;
+    a.total = n_walks * L;
+    a.L = L;
+    a.n = n;
+    a.window = tp->window;
+    a.K = tp->negatives;
+    a.Ns = tp->tile_negatives > 0 ? tp->tile_negatives : 64;
+    a.Tc = kTileRows - 2 * tp->window;
+    a.n_tiles = (a.total + a.Tc - 1) / a.Tc;
+    a.lr0 = tp->lr0;
+    a.inv_total = 1.0 / static_cast<double>(tp->lr_total_tokens);
+    a.clock_base = clock_base;
+    a.thr = thr;
+    a.alias = alias;
+    a.S = S;
+    a.seed = seed;
+    a.round = static_cast<uint32_t>(round);
+    a.loss_acc = loss_acc;
+    a.timeout = timeout;
+    if (a.n_tiles == 0) return FELOG_OK;
+    if (a.n_tiles > 0xffffffffLL) return FELOG_ERR_INVALID_ARG;
+    int ctas = tp->tile_ctas > 0
+                   ? std::min(tp->tile_ctas, sm_count())
+                   : static_cast<int>(std::min<int64_t>(sm_count(), std::max<int64_t>(1, n / kTileRowsPerCta)));
+    ctas = static_cast<int>(std::min<int64_t>(ctas, a.n_tiles));
+    const bool f32 = tp->precision == FELOG_FP32;
+    switch (tp->dim) {
+        case 32: return f32 ? launch_tile_dim<32, float>(a, ctas, phi_in, phi_out, s)
+                            : launch_tile_dim<32, __nv_bfloat16>(a, ctas, phi_in, phi_out, s);
+        case 64: return f32 ? launch_tile_dim<64, float>(a, ctas, phi_in, phi_out, s)
+                            : launch_tile_dim<64, __nv_bfloat16>(a, ctas, phi_in, phi_out, s);
+        case 128: return f32 ? launch_tile_dim<128, float>(a, ctas, phi_in, phi_out, s)
+                             : launch_tile_dim<128, __nv_bfloat16>(a, ctas, phi_in, phi_out, s);
+    }
+    return FELOG_ERR_UNSUPPORTED;
+}
+
+}  // namespace felog

@@ -16,7 +16,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libfelog.so")
 
 FELOG_OK = 0
-FELOG_SGNS_HOGWILD, FELOG_SGNS_MINIBATCH = 0, 1
+FELOG_SGNS_HOGWILD, FELOG_SGNS_MINIBATCH, FELOG_SGNS_TILE = 0, 1, 2
 FELOG_FP32, FELOG_BF16_SR = 0, 1
 
 # exported symbols (the boundary); tests check each one is present
@@ -57,7 +57,8 @@ class _TrainParams(ctypes.Structure):
                 ("lr0", ctypes.c_float), ("lr_total_tokens", ctypes.c_int64),
                 ("mode", ctypes.c_int32), ("minibatch", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("hogwild_rows_per_warp", ctypes.c_int32),
-                ("hogwild_form", ctypes.c_int32)]
+                ("hogwild_form", ctypes.c_int32), ("tile_negatives", ctypes.c_int32),
+                ("tile_ctas", ctypes.c_int32)]
 
 
 class _FeedbackParams(ctypes.Structure):
@@ -274,9 +275,9 @@ def felog_init_tables(n: int, dim: int, precision: int, seed: int, device="cuda"
 
 def train_params(dim=128, window=10, negatives=5, lr0=0.025, lr_total_tokens=1, mode=FELOG_SGNS_HOGWILD,
                  minibatch=4096, precision=FELOG_FP32, hogwild_rows_per_warp=0,
-                 hogwild_form=0) -> _TrainParams:
+                 hogwild_form=0, tile_negatives=0, tile_ctas=0) -> _TrainParams:
     return _TrainParams(dim, window, negatives, lr0, lr_total_tokens, mode, minibatch, precision,
-                        hogwild_rows_per_warp, hogwild_form)
+                        hogwild_rows_per_warp, hogwild_form, tile_negatives, tile_ctas)
 
 
 def feedback_params(enabled=True, mu=0.65, ks=8, max_rounds=10, reactivate=False) -> _FeedbackParams:
