@@ -52,8 +52,9 @@ def _args():
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     p.add_argument("--form", type=int, default=0, choices=[0, 1, 2],
                    help="Hogwild kernel form: 0 automatic, 1 full warp per pair, 2 half warp per pair")
-    p.add_argument("--mode", default="round", choices=["round", "batch", "serve"],
-                   help="round: one round of Algorithm 1 on R-MAT 20 (default); batch: the 512-graph "
+    p.add_argument("--mode", default="round", choices=["round", "tile", "batch", "serve"],
+                   help="round: one round of Algorithm 1 on R-MAT 20 (default); tile: rounds with the "
+                        "shared-negatives tile trainer; batch: the 512-graph "
                         "batching form; serve: the request loop with Poisson arrivals")
     p.add_argument("--jobs", type=int, default=512, help="batch mode: number of graphs")
     p.add_argument("--rate", type=float, default=20.0, help="serve mode: arrivals per second")
@@ -408,6 +409,8 @@ def run_native(args):
     if not args.no_forms and rank == 0:
         del runner
         torch.cuda.empty_cache()
+        result["tile_form"] = _tile_form(fl, dg, n_live, T)
+        torch.cuda.empty_cache()
         result["batching_small"] = run_batch(fl, jobs=64, n_hi=20000, warmup=3, steps=3, autotune=True)
         result["serving_small"] = run_serve(fl, rate=20.0, duration=5.0, max_nodes=1 << 14, sustainable=False)
     if not args.no_cpu and rank == 0:
@@ -526,6 +529,72 @@ def run_serve(fl, rate=20.0, duration=20.0, max_nodes=1 << 16, pool_size=48, bud
     return out
 
 
+TILE_NS = 64
+
+
+def _tile_flops(n_tiles, dim, ns):
+    """Tensor-core FLOPs of the tile trainer: per tile S = X Y^T and
+    dX = G Y (128 x dim x (128 + Ns) each) and dY = G^T X (256 x dim x 128)."""
+    ny = 128 + ns
+    return n_tiles * 2 * 128 * dim * (2 * ny + 256)
+
+
+def _tile_form(fl, dg, n_live, T, steps=3, warmup=2, scale=SCALE):
+    """The shared-negatives tile trainer (TILE mode, bf16 tables) on the same
+    graph: plain rounds timed with CUDA events per phase; its tensor FLOP/s
+    against the measured bf16 peak and its gathered/added row bytes against
+    HBM bandwidth."""
+    import torch
+
+    tp = fl.train_params(DIM, WINDOW, NEG, LR0, T, fl.FELOG_SGNS_TILE, 1, fl.FELOG_BF16_SR,
+                         tile_negatives=TILE_NS)
+    runner = RoundRunner(fl, dg, tp, fl.feedback_params(False, MU, KS, ROUNDS, False), SEED)
+    runner.reset()
+    for w in range(warmup):
+        runner.run(w)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(steps)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tokens = 0
+    for k in range(steps):
+        _, tok = runner.run(warmup + k, events=ev[k])
+        tokens += tok
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    train_ms = statistics.mean(e[2].elapsed_time(e[3]) for e in ev)
+    tok_round = tokens / steps
+    tc = 128 - 2 * WINDOW
+    n_tiles = -(-tok_round // tc)
+    flops = _tile_flops(n_tiles, DIM, TILE_NS)
+    row = DIM * 2
+    alg_bytes = n_tiles * 2 * (128 + tc + TILE_NS) * row
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    bf16_peak = float(peaks.get("bf16_tflops_sustained", 1400.0))
+    hbm_peak, _ = _peaks()
+    tflops = flops / (train_ms / 1e3) / 1e12
+    gbs = alg_bytes / (train_ms / 1e3) / 1e9
+    out = {
+        "workload": f"{_workload_name(scale, 'bf16')}, TILE mode, Ns={TILE_NS} shared negatives per tile of {tc} centers",
+        "tokens_per_round": tok_round,
+        "round_tokens_per_s": tokens / sec,
+        "train_ms": train_ms,
+        "tokens_per_s_train_kernel": tok_round / (train_ms / 1e3),
+        "tiles_per_launch": n_tiles,
+        "tensor": {"achieved": tflops, "peak": bf16_peak, "unit": "TFLOP/s", "frac": tflops / bf16_peak,
+                   "flops_per_launch": flops, "peak_source": "measured bf16 sustained (cuBLAS)"},
+        "rows": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                 "bytes_per_launch": alg_bytes},
+        "kernel": "k_sgns_tile<128,bf16>",
+    }
+    del runner
+    return out
+
+
 def _quality(fl, evaluate, dg, split, n_live):
     """Full runs of Algorithm 1: plain (feedback off, fp32) and chosen
     (feedback mu = 0.65, bf16 with stochastic rounding); AUC on the held-out
@@ -539,6 +608,9 @@ def _quality(fl, evaluate, dg, split, n_live):
                   fl.feedback_params(False, MU, KS, ROUNDS, False)),
         "chosen": (fl.train_params(DIM, WINDOW, NEG, LR0, T, fl.FELOG_SGNS_HOGWILD, 4096, fl.FELOG_BF16_SR),
                    fl.feedback_params(True, MU, KS, ROUNDS, False)),
+        "tile": (fl.train_params(DIM, WINDOW, NEG, LR0, T, fl.FELOG_SGNS_TILE, 1, fl.FELOG_BF16_SR,
+                                 tile_negatives=TILE_NS),
+                 fl.feedback_params(False, MU, KS, ROUNDS, False)),
     }
     for name, (tp, fp) in forms.items():
         torch.cuda.synchronize()
@@ -632,7 +704,7 @@ def run_reference(args):
 
 
 def run_form(args):
-    """--mode batch / serve: one JSON line for that form."""
+    """--mode tile / batch / serve: one JSON line for that form."""
     import torch
 
     from paper_2606_22180_b300 import build, felog as fl
@@ -640,7 +712,17 @@ def run_form(args):
     build.build()
     fl.load()
     torch.cuda.set_device(0)
-    if args.mode == "batch":
+    if args.mode == "tile":
+        split = _workload(args.scale)
+        dg = fl.DeviceGraph.from_host(split.train)
+        n_live = int((split.train.degrees() > 0).sum())
+        r = _tile_form(fl, dg, n_live, ROUNDS * WPR * n_live * L, steps=args.steps, warmup=args.warmup,
+                       scale=args.scale)
+        line = {"metric": "SGNS tokens/s, shared-negatives tile form", "value": r["round_tokens_per_s"],
+                "unit": "tokens/s", "n_gpus": 1, "higher_is_better": True, "dtype": "bf16 tables, f32 math",
+                "data": "synthetic (seeded R-MAT graph; no dataset)", "config": {"workload": r["workload"]},
+                "tile_form": r}
+    elif args.mode == "batch":
         r = run_batch(fl, jobs=args.jobs, warmup=1, steps=1)
         line = {"metric": "SGNS tokens/s, batching form", "value": r["tokens_per_s"], "unit": "tokens/s",
                 "n_gpus": 1, "higher_is_better": True, "dtype": "bf16 tables, f32 math",

@@ -9,7 +9,9 @@
 // first center.  Scores read the tables as they stood when the tile's rows
 // were gathered; the summed increments are added when the tile ends.
 //
-// One CTA of 4 warps per SM works through tiles.  A tile's 128 rows are the
+// One CTA of 8 warps per SM works through tiles (warps g and g + 4 share
+// the tensor-memory lanes of rows 32g .. 32g + 31 and split each epilogue's
+// columns between them).  A tile's 128 rows are the
 // positions [t*Tc - w, t*Tc - w + 128): every context of the tile's centers
 // lies among them.  With X = phi_in of those positions (128 x d) and
 // Y = [phi_out of the positions; phi_out of the Ns negatives] (128 + Ns
@@ -37,7 +39,7 @@
 namespace felog {
 
 constexpr uint32_t kStreamTile = 7;
-constexpr int kTileThreads = 128;
+constexpr int kTileThreads = 256;  // 8 warps; warps g and g + 4 share TMEM lanes 32g ..
 constexpr int kTileRows = 128;
 constexpr uint32_t kTileWaitLimit = 1u << 26;  // polls of an mbarrier before reporting a timeout
 
@@ -68,8 +70,6 @@ struct TileSmem {
     // 512 tensor-memory columns
     static constexpr uint32_t kBytes = kEnd > 122880 ? kEnd : 122880;
 };
-
-__device__ __forceinline__ float sigmoidf_fast(float s) { return 1.f / (1.f + __expf(-s)); }
 
 // 8 floats -> 8 bf16 (round to nearest) packed in 4 words
 __device__ __forceinline__ uint4 pack8(const float4 &a, const float4 &b) {
@@ -109,13 +109,21 @@ __device__ __forceinline__ void add8(__nv_bfloat16 *p, const float *d, uint4 sna
     add_delta_raw<8>(p, raw, dd, w);
 }
 
+// sigma(s) and log(1 + exp(-|s|)) from one exponential
+__device__ __forceinline__ void sigmoid_softplus(float s, float &sig, float &l1p) {
+    const float e = __expf(-fabsf(s));
+    const float r = __fdividef(1.f, 1.f + e);
+    sig = s >= 0.f ? r : e * r;
+    l1p = __logf(1.f + e);
+}
+
 template <int D, class T>
 __global__ void __launch_bounds__(kTileThreads, 1)
     k_sgns_tile(TileArgs a, T *__restrict__ phi_in, T *__restrict__ phi_out) {
     using Lay = TileSmem<D>;
     extern __shared__ __align__(1024) uint8_t sm[];
     __shared__ int32_t node_s[kTileRows];     // node of each row position (-1: none)
-    __shared__ uint32_t walk_s[kTileRows];    // walk index of each row position
+    __shared__ int16_t lo_s[kTileRows], hi_s[kTileRows];  // rows of the same walk as row q
     __shared__ int32_t neg_s[kTileRows];      // shared negatives (Ns used)
     __shared__ uint8_t colused_s[2 * kTileRows];  // Y row received a nonzero gradient column
     __shared__ uint8_t hit_s[kTileRows];      // center equals one of the negatives
@@ -123,13 +131,16 @@ __global__ void __launch_bounds__(kTileThreads, 1)
     __shared__ __align__(8) uint64_t bar_s;
     __shared__ uint32_t tmem_s;
 
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t base = smem_addr(sm);
     const uint32_t xs = base + Lay::kX, ys = base + Lay::kY, gs = base + Lay::kG;
     const uint32_t bar = smem_addr(&bar_s);
     const int w = a.window, Ns = a.Ns, NY = kTileRows + Ns;
     const uint64_t nn = static_cast<uint64_t>(a.n), Ssum = *a.S;
     const float omega = static_cast<float>(a.K) / static_cast<float>(Ns);
+    // epilogue roles: warps g and g + 4 share TMEM lanes 32g .. 32g + 31
+    const int quarter = warp & 3, half = warp >> 2;
+    const int q = quarter * 32 + lane;  // row of this thread in the epilogues
 
     // zero the parts of Y and G that no tile writes (negative rows beyond Ns,
     // gradient columns beyond 128 + Ns)
@@ -147,48 +158,54 @@ __global__ void __launch_bounds__(kTileThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tm = tmem_s;
-    const uint32_t lane_base = tm + (static_cast<uint32_t>(warp * 32) << 16);
+    const uint32_t lane_base = tm + (static_cast<uint32_t>(quarter * 32) << 16);
     uint32_t phase = 0;
     double loss = 0.0;
     bool failed = false;
 
     for (int64_t t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
         const int64_t pos0 = t * a.Tc - w;  // corpus position of row 0
-        // ---- rows, negatives ------------------------------------------------
-        {
+        // ---- rows (threads 0..127), shared negatives (threads 128..) ---------
+        if (tid < kTileRows) {
             const int64_t pos = pos0 + tid;
             int32_t v = -1;
-            uint32_t wk = 0xffffffffu;
+            int lo = 1, hi = 0;
             if (pos >= 0 && pos < a.total) {
                 v = __ldg(a.walks + pos);
-                wk = static_cast<uint32_t>(pos / a.L);
+                const int64_t wstart = pos - pos % a.L;  // first position of this walk
+                const int64_t wend = (wstart + a.L < a.total ? wstart + a.L : a.total) - 1;  // last position
+                lo = wstart > pos0 ? static_cast<int>(wstart - pos0) : 0;
+                hi = wend - pos0 < kTileRows - 1 ? static_cast<int>(wend - pos0) : kTileRows - 1;
             }
             node_s[tid] = v;
-            walk_s[tid] = wk;
+            lo_s[tid] = static_cast<int16_t>(lo);
+            hi_s[tid] = static_cast<int16_t>(hi);
             colused_s[tid] = 0;
             colused_s[kTileRows + tid] = 0;
             if (tid < 32) bloom_s[tid] = 0;
         }
         __syncthreads();
-        if (tid < Ns) {
-            const u32x4 r = philox(a.seed, static_cast<uint32_t>(tid), static_cast<uint32_t>(t), a.round, kStreamTile);
+        if (tid >= kTileRows && tid < kTileRows + Ns) {
+            const int j = tid - kTileRows;
+            const u32x4 r = philox(a.seed, static_cast<uint32_t>(j), static_cast<uint32_t>(t), a.round, kStreamTile);
             const uint64_t b = mulhi64(lo64(r), nn);
             const uint64_t coin = mulhi64(hi64(r), Ssum);
             const uint64_t th = __ldg(reinterpret_cast<const unsigned long long *>(a.thr) + b);
             const int32_t v = coin < th ? static_cast<int32_t>(b) : __ldg(a.alias + b);
-            neg_s[tid] = v;
+            neg_s[j] = v;
             atomicOr(&bloom_s[(static_cast<uint32_t>(v) * 0x9E3779B1u) >> 27], 1u << (v & 31));
         }
+        __syncthreads();
         // ---- gather X (phi_in of positions) and Y (phi_out of centers and
         //      negatives) into the core-matrix layout, as bf16 ------------------
-        __syncthreads();
         {
-            const int lane = tid & 31;
             const int r8 = lane & 7, cq = lane >> 3;  // row within group, chunk within 4
             constexpr int kChunks = D / 8;            // 16-byte bf16 chunks per row
             constexpr int kUnitsPerGroup = kChunks / 4;
             const int groups = kTileRows / 8 + NY / 8;  // X row groups, then Y row groups
-            for (int u = warp; u < groups * kUnitsPerGroup; u += 4) {
+            const int units = groups * kUnitsPerGroup;
+#pragma unroll 2
+            for (int u = warp; u < units; u += kTileThreads / 32) {
                 const int gi = u / kUnitsPerGroup, c = ((u % kUnitsPerGroup) * 4 + cq) * 8;
                 const bool isx = gi < kTileRows / 8;
                 const int r = (isx ? gi : gi - kTileRows / 8) * 8 + r8;
@@ -203,7 +220,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
             }
         }
         // centers equal to a negative (exact check behind a bloom filter)
-        {
+        if (tid < kTileRows) {
             const int32_t v = node_s[tid];
             uint8_t hit = 0;
             if (v >= 0 && tid >= w && tid < w + a.Tc &&
@@ -227,57 +244,63 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         phase ^= 1;
         tc_fence_after();
         if (__syncthreads_or(failed)) break;
-        // ---- epilogue: gradient G (bf16) ------------------------------------
-        const int q = tid;
+        // ---- epilogue: gradient G (bf16).  Row q pairs with the centers
+        //      p in [plo, phi] \ {q} whose node is >= 0 ----------------------------
         const int32_t vq = node_s[q];
-        const uint32_t wq = walk_s[q];
         const float eta = static_cast<float>(
             static_cast<double>(a.lr0) *
             fmax(1e-4, 1.0 - static_cast<double>(a.clock_base + t * a.Tc) * a.inv_total));
-        int cnt = 0;        // pairs with context at row q
+        int plo = max(max(q - w, w), static_cast<int>(lo_s[q]));
+        int phi = min(min(q + w, w + a.Tc - 1), static_cast<int>(hi_s[q]));
+        if (vq < 0) phi = plo - 1;
+        int cnt = 0;
         bool any_hit = false;
-        float row_loss = 0.f;
-#pragma unroll 1
-        for (int c = 0; c < 4; ++c) {  // positive band, columns 32c .. 32c+31
-            uint32_t packed[16];
-            const bool near = c >= warp - 1 && c <= warp + 1;  // warp-uniform
-            if (near) {
-                uint32_t r[32];
-                tmem_ld32(lane_base + 32 * c, r);
-                tmem_wait_ld();
-#pragma unroll
-                for (int i = 0; i < 32; i += 2) {
-                    float g2[2];
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int p = 32 * c + i + h;
-                        const int dqp = p - q;
-                        float g = 0.f;
-                        if (vq >= 0 && dqp != 0 && dqp >= -w && dqp <= w && p >= w && p < w + a.Tc &&
-                            node_s[p] >= 0 && walk_s[p] == wq) {
-                            const float s = __uint_as_float(r[i + h]);
-                            g = eta * (1.f - sigmoidf_fast(s));
-                            row_loss += softplus_neg(s);
-                            ++cnt;
-                            any_hit |= hit_s[p] != 0;
-                            colused_s[p] = 1;
-                        }
-                        g2[h] = g;
-                    }
-                    __nv_bfloat162 hv = __floats2bfloat162_rn(g2[0], g2[1]);
-                    packed[i / 2] = *reinterpret_cast<uint32_t *>(&hv);
-                }
-            } else {
-#pragma unroll
-                for (int i = 0; i < 16; ++i) packed[i] = 0;
+        for (int p = plo; p <= phi; ++p)
+            if (p != q && node_s[p] >= 0) {
+                ++cnt;
+                any_hit |= hit_s[p] != 0;
             }
+        float row_loss = 0.f;
+        if (half == 0) {
+#pragma unroll 1
+            for (int c = 0; c < 4; ++c) {  // positive band, columns 32c .. 32c+31
+                uint32_t packed[16];
+                if (c >= quarter - 1 && c <= quarter + 1) {  // warp-uniform
+                    uint32_t r[32];
+                    tmem_ld32(lane_base + 32 * c, r);
+                    tmem_wait_ld();
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
-                *reinterpret_cast<uint4 *>(sm + Lay::kG + core_offset(q, 32 * c + 8 * k, kTileRows)) =
-                    make_uint4(packed[4 * k], packed[4 * k + 1], packed[4 * k + 2], packed[4 * k + 3]);
+                    for (int i = 0; i < 32; i += 2) {
+                        float g2[2];
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int p = 32 * c + i + h;
+                            float g = 0.f;
+                            if (p >= plo && p <= phi && p != q && node_s[p] >= 0) {
+                                const float s = __uint_as_float(r[i + h]);
+                                float sig, l1p;
+                                sigmoid_softplus(s, sig, l1p);
+                                g = eta * (1.f - sig);
+                                row_loss += fmaxf(-s, 0.f) + l1p;  // -log sigma(s)
+                                colused_s[p] = 1;
+                            }
+                            g2[h] = g;
+                        }
+                        __nv_bfloat162 hv = __floats2bfloat162_rn(g2[0], g2[1]);
+                        packed[i / 2] = *reinterpret_cast<uint32_t *>(&hv);
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) packed[i] = 0;
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    *reinterpret_cast<uint4 *>(sm + Lay::kG + core_offset(q, 32 * c + 8 * k, kTileRows)) =
+                        make_uint4(packed[4 * k], packed[4 * k + 1], packed[4 * k + 2], packed[4 * k + 3]);
+            }
         }
 #pragma unroll 1
-        for (int c = 0; c < Ns / 32; ++c) {  // shared negatives, columns 128 + 32c ..
+        for (int c = half; c < Ns / 32; c += 2) {  // shared negatives, columns 128 + 32c ..
             uint32_t r[32];
             tmem_ld32(lane_base + kTileRows + 32 * c, r);
             tmem_wait_ld();
@@ -291,15 +314,16 @@ __global__ void __launch_bounds__(kTileThreads, 1)
                     int m = cnt;
                     if (any_hit) {  // pairs whose center is this negative do not count
                         const int32_t nk = neg_s[k];
-                        for (int p = max(w, q - w); p <= min(w + a.Tc - 1, q + w); ++p)
-                            if (p != q && hit_s[p] && node_s[p] == nk && walk_s[p] == wq) --m;
+                        for (int p = plo; p <= phi; ++p) m -= (p != q && hit_s[p] && node_s[p] == nk);
                     }
                     float g = 0.f;
                     if (m > 0) {
                         const float s = __uint_as_float(r[i + h]);
                         const float wm = omega * static_cast<float>(m);
-                        g = -eta * wm * sigmoidf_fast(s);
-                        row_loss += wm * softplus_neg(-s);
+                        float sig, l1p;
+                        sigmoid_softplus(s, sig, l1p);
+                        g = -eta * wm * sig;
+                        row_loss += wm * (fmaxf(s, 0.f) + l1p);  // -log sigma(-s)
                         colused_s[kTileRows + k] = 1;
                     }
                     g2[h] = g;
@@ -334,45 +358,40 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         phase ^= 1;
         tc_fence_after();
         if (__syncthreads_or(failed)) break;
-        // ---- add the increments to the tables --------------------------------
+        // ---- add the increments to the tables: half 0 adds dX of row q and dY
+        //      of negative q, half 1 dY of position q ----------------------------
         {
             const u32x4 rw = philox(a.seed, static_cast<uint32_t>(t), static_cast<uint32_t>(q), a.round, kStreamSR);
-            uint32_t sr0 = rw.x | 1u, sr1 = rw.y | 1u, sr2 = rw.z | 1u;
-            const bool do_x = vq >= 0 && cnt > 0;
-            const bool do_c = colused_s[q] != 0;
-            const bool do_n = q < Ns && colused_s[kTileRows + q] != 0;
-            T *px = phi_in + static_cast<int64_t>(max(vq, 0)) * D;
-            T *pc = phi_out + static_cast<int64_t>(max(node_s[q], 0)) * D;
-            T *pn = phi_out + static_cast<int64_t>(q < Ns ? neg_s[q] : 0) * D;
+            uint32_t sr0 = (half ? rw.z : rw.x) | 1u, sr1 = rw.y | 1u;
+            const bool first = half == 0 ? (vq >= 0 && cnt > 0) : colused_s[q] != 0;
+            const bool second = half == 0 && q < Ns && colused_s[kTileRows + q] != 0;
+            T *p1 = (half == 0 ? phi_in : phi_out) + static_cast<int64_t>(max(vq, 0)) * D;
+            T *p2 = phi_out + static_cast<int64_t>(q < Ns ? neg_s[q] : 0) * D;
+            const uint32_t t1 = half == 0 ? lane_base + 256 : lane_base;  // dX or dY(positions)
+            const uint32_t s1 = half == 0 ? Lay::kX + 0 : Lay::kY + 0;
+            const int R1 = half == 0 ? kTileRows : 256;
 #pragma unroll 1
             for (int c = 0; c < D / 32; ++c) {
-                uint32_t rx[32], rc[32], rn[32];
-                tmem_ld32(lane_base + 256 + 32 * c, rx);
-                tmem_ld32(lane_base + 32 * c, rc);
-                tmem_ld32(lane_base + D + 32 * c, rn);
+                uint32_t r1[32], r2[32];
+                tmem_ld32(t1 + 32 * c, r1);
+                if (half == 0) tmem_ld32(lane_base + D + 32 * c, r2);
                 tmem_wait_ld();
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const int col = 32 * c + 8 * k;
                     float d8[8];
-                    if (do_x) {
-                        const uint4 snap = *reinterpret_cast<const uint4 *>(sm + Lay::kX + core_offset(q, col, kTileRows));
+                    if (first) {
+                        const uint4 snap = *reinterpret_cast<const uint4 *>(sm + s1 + core_offset(q, col, R1));
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) d8[i] = __uint_as_float(rx[8 * k + i]);
-                        add8(px + col, d8, snap, xorshift32(sr0));
+                        for (int i = 0; i < 8; ++i) d8[i] = __uint_as_float(r1[8 * k + i]);
+                        add8(p1 + col, d8, snap, xorshift32(sr0));
                     }
-                    if (do_c) {
-                        const uint4 snap = *reinterpret_cast<const uint4 *>(sm + Lay::kY + core_offset(q, col, 256));
-#pragma unroll
-                        for (int i = 0; i < 8; ++i) d8[i] = __uint_as_float(rc[8 * k + i]);
-                        add8(pc + col, d8, snap, xorshift32(sr1));
-                    }
-                    if (do_n) {
+                    if (second) {
                         const uint4 snap =
                             *reinterpret_cast<const uint4 *>(sm + Lay::kY + core_offset(kTileRows + q, col, 256));
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) d8[i] = __uint_as_float(rn[8 * k + i]);
-                        add8(pn + col, d8, snap, xorshift32(sr2));
+                        for (int i = 0; i < 8; ++i) d8[i] = __uint_as_float(r2[8 * k + i]);
+                        add8(p2 + col, d8, snap, xorshift32(sr1));
                     }
                 }
             }
@@ -386,7 +405,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
     if (failed && tid == 0) atomicExch(a.timeout, 1);
     long long fx = __double2ll_rn(loss * kLossScale);
     for (int o = 16; o; o >>= 1) fx += __shfl_xor_sync(kFull, fx, o);
-    if ((tid & 31) == 0 && fx != 0) atomicAdd(a.loss_acc, static_cast<unsigned long long>(fx));
+    if (lane == 0 && fx != 0) atomicAdd(a.loss_acc, static_cast<unsigned long long>(fx));
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
