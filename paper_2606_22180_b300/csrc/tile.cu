@@ -32,6 +32,7 @@
 // S in columns [0, 128 + Ns), dX in [256, 256 + d), dY (positions, then
 // negatives) reuses [0, 2d) once S has been read.
 #include <algorithm>
+#include <type_traits>
 
 #include "sgns_core.cuh"
 #include "tc_core.cuh"
@@ -94,6 +95,29 @@ __device__ __forceinline__ uint4 ld_row8(const __nv_bfloat16 *p) {
     return r;
 }
 
+// 16-byte asynchronous copy global -> shared (L2 only); src_bytes = 0
+// writes zeros without reading.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+// number of set bits of the 128-bit mask m[0..4) at positions lo..hi
+__device__ __forceinline__ int popc_range(const uint32_t *m, int lo, int hi) {
+    int c = 0;
+#pragma unroll
+    for (int wd = 0; wd < 4; ++wd) {
+        const int a = max(lo - 32 * wd, 0), b = min(hi - 32 * wd, 31);
+        if (a <= b) {
+            const uint32_t sel = (b - a == 31) ? 0xffffffffu : (((1u << (b - a + 1)) - 1u) << a);
+            c += __popc(m[wd] & sel);
+        }
+    }
+    return c;
+}
+
 // Adds 8 increments (f32) to table elements p[0..8); `snap` holds the 8
 // gathered values as packed bf16 (used by bf16 tables for stochastic
 // rounding of gathered value + increment).
@@ -125,8 +149,10 @@ __global__ void __launch_bounds__(kTileThreads, 1)
     __shared__ int32_t node_s[kTileRows];     // node of each row position (-1: none)
     __shared__ int16_t lo_s[kTileRows], hi_s[kTileRows];  // rows of the same walk as row q
     __shared__ int32_t neg_s[kTileRows];      // shared negatives (Ns used)
-    __shared__ uint8_t colused_s[2 * kTileRows];  // Y row received a nonzero gradient column
-    __shared__ uint8_t hit_s[kTileRows];      // center equals one of the negatives
+    __shared__ uint32_t valid_s[4];           // bit p: row p is a center with a node
+    __shared__ uint32_t hitm_s[4];            // bit p: that center equals a shared negative
+    __shared__ uint32_t nodem_s[4];           // bit p: row p holds a node
+    __shared__ uint32_t negm_s[kTileRows][4];  // center p: bit j set where negative j equals it
     __shared__ uint32_t bloom_s[32];
     __shared__ __align__(8) uint64_t bar_s;
     __shared__ uint32_t tmem_s;
@@ -180,8 +206,6 @@ __global__ void __launch_bounds__(kTileThreads, 1)
             node_s[tid] = v;
             lo_s[tid] = static_cast<int16_t>(lo);
             hi_s[tid] = static_cast<int16_t>(hi);
-            colused_s[tid] = 0;
-            colused_s[kTileRows + tid] = 0;
             if (tid < 32) bloom_s[tid] = 0;
         }
         __syncthreads();
@@ -204,7 +228,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
             constexpr int kUnitsPerGroup = kChunks / 4;
             const int groups = kTileRows / 8 + NY / 8;  // X row groups, then Y row groups
             const int units = groups * kUnitsPerGroup;
-#pragma unroll 2
+#pragma unroll 4
             for (int u = warp; u < units; u += kTileThreads / 32) {
                 const int gi = u / kUnitsPerGroup, c = ((u % kUnitsPerGroup) * 4 + cq) * 8;
                 const bool isx = gi < kTileRows / 8;
@@ -213,20 +237,40 @@ __global__ void __launch_bounds__(kTileThreads, 1)
                 if (isx) v = node_s[r];
                 else if (r < kTileRows) v = (r >= w && r < w + a.Tc) ? node_s[r] : -1;  // centers only
                 else v = neg_s[r - kTileRows];
-                uint4 val = make_uint4(0, 0, 0, 0);
-                if (v >= 0) val = ld_row8((isx ? phi_in : phi_out) + static_cast<int64_t>(v) * D + c);
                 const uint32_t off = isx ? Lay::kX + core_offset(r, c, kTileRows) : Lay::kY + core_offset(r, c, 256);
-                *reinterpret_cast<uint4 *>(sm + off) = val;
+                const T *src = (isx ? phi_in : phi_out) + static_cast<int64_t>(max(v, 0)) * D + c;
+                if constexpr (std::is_same<T, __nv_bfloat16>::value) {
+                    cp_async16(base + off, src, v >= 0 ? 16u : 0u);
+                } else {
+                    uint4 val = make_uint4(0, 0, 0, 0);
+                    if (v >= 0) val = ld_row8(src);
+                    *reinterpret_cast<uint4 *>(sm + off) = val;
+                }
             }
+            if constexpr (std::is_same<T, __nv_bfloat16>::value) cp_async_wait_all();
         }
-        // centers equal to a negative (exact check behind a bloom filter)
+        // valid centers, and centers equal to a negative (exact check behind
+        // a bloom filter), as 128-bit masks
         if (tid < kTileRows) {
             const int32_t v = node_s[tid];
-            uint8_t hit = 0;
-            if (v >= 0 && tid >= w && tid < w + a.Tc &&
-                (bloom_s[(static_cast<uint32_t>(v) * 0x9E3779B1u) >> 27] >> (v & 31) & 1u))
-                for (int j = 0; j < Ns; ++j) hit |= neg_s[j] == v;
-            hit_s[tid] = hit;
+            const bool valid = v >= 0 && tid >= w && tid < w + a.Tc;
+            bool hit = false;
+            if (valid && (bloom_s[(static_cast<uint32_t>(v) * 0x9E3779B1u) >> 27] >> (v & 31) & 1u)) {
+                uint32_t mw[4] = {0, 0, 0, 0};
+#pragma unroll
+                for (int wd = 0; wd < 4; ++wd)
+                    for (int b = 0; b < 32 && 32 * wd + b < Ns; ++b) mw[wd] |= (neg_s[32 * wd + b] == v ? 1u : 0u) << b;
+                hit = (mw[0] | mw[1] | mw[2] | mw[3]) != 0;
+#pragma unroll
+                for (int wd = 0; wd < 4; ++wd) negm_s[tid][wd] = mw[wd];
+            }
+            const uint32_t vb = __ballot_sync(kFull, valid), hb = __ballot_sync(kFull, hit);
+            const uint32_t nb = __ballot_sync(kFull, v >= 0);
+            if (lane == 0) {
+                valid_s[warp] = vb;
+                hitm_s[warp] = hb;
+                nodem_s[warp] = nb;
+            }
         }
         fence_async_smem();
         tc_fence_before();
@@ -253,56 +297,82 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         int plo = max(max(q - w, w), static_cast<int>(lo_s[q]));
         int phi = min(min(q + w, w + a.Tc - 1), static_cast<int>(hi_s[q]));
         if (vq < 0) phi = plo - 1;
-        int cnt = 0;
-        bool any_hit = false;
-        for (int p = plo; p <= phi; ++p)
-            if (p != q && node_s[p] >= 0) {
-                ++cnt;
-                any_hit |= hit_s[p] != 0;
-            }
+        uint32_t vm[4], hm[4], nm[4];
+#pragma unroll
+        for (int wd = 0; wd < 4; ++wd) {
+            vm[wd] = valid_s[wd];
+            hm[wd] = hitm_s[wd];
+            nm[wd] = nodem_s[wd];
+        }
+        const bool q_in = q >= plo && q <= phi;
+        const int cnt = popc_range(vm, plo, phi) - (q_in ? static_cast<int>(valid_s[q >> 5] >> (q & 31) & 1u) : 0);
+        const bool any_hit = popc_range(hm, plo, phi) - (q_in ? static_cast<int>(hitm_s[q >> 5] >> (q & 31) & 1u) : 0) > 0;
         float row_loss = 0.f;
-        if (half == 0) {
+        // positive band, columns 32c .. 32c+31: half 0 takes the warp's own
+        // chunk, half 1 the other three (two band edges and a zero chunk).
+        // Scores outside a row's pairs get coefficient 0 (no branches).
 #pragma unroll 1
-            for (int c = 0; c < 4; ++c) {  // positive band, columns 32c .. 32c+31
-                uint32_t packed[16];
-                if (c >= quarter - 1 && c <= quarter + 1) {  // warp-uniform
-                    uint32_t r[32];
-                    tmem_ld32(lane_base + 32 * c, r);
-                    tmem_wait_ld();
+        for (int c = 0; c < 4; ++c) {
+            if ((c == quarter) != (half == 0)) continue;  // warp-uniform
+            uint32_t packed[16];
+            if (c >= quarter - 1 && c <= quarter + 1) {
+                uint32_t r[32];
+                tmem_ld32(lane_base + 32 * c, r);
+                // pairs of row q among columns 32c .. 32c+31
+                uint32_t pm = valid_s[c];
+                const int a0 = plo - 32 * c, b0 = phi - 32 * c;
+                pm &= (a0 <= 0 ? 0xffffffffu : (a0 >= 32 ? 0u : (0xffffffffu << a0)));
+                pm &= (b0 >= 31 ? 0xffffffffu : (b0 < 0 ? 0u : (0xffffffffu >> (31 - b0))));
+                if (q >= 32 * c && q < 32 * c + 32) pm &= ~(1u << (q - 32 * c));
+                tmem_wait_ld();
 #pragma unroll
-                    for (int i = 0; i < 32; i += 2) {
-                        float g2[2];
+                for (int i = 0; i < 32; i += 2) {
+                    float g2[2];
 #pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            const int p = 32 * c + i + h;
-                            float g = 0.f;
-                            if (p >= plo && p <= phi && p != q && node_s[p] >= 0) {
-                                const float s = __uint_as_float(r[i + h]);
-                                float sig, l1p;
-                                sigmoid_softplus(s, sig, l1p);
-                                g = eta * (1.f - sig);
-                                row_loss += fmaxf(-s, 0.f) + l1p;  // -log sigma(s)
-                                colused_s[p] = 1;
-                            }
-                            g2[h] = g;
-                        }
-                        __nv_bfloat162 hv = __floats2bfloat162_rn(g2[0], g2[1]);
-                        packed[i / 2] = *reinterpret_cast<uint32_t *>(&hv);
+                    for (int h = 0; h < 2; ++h) {
+                        const float on = static_cast<float>(pm >> (i + h) & 1u);
+                        const float s = __uint_as_float(r[i + h]);
+                        float sig, l1p;
+                        sigmoid_softplus(s, sig, l1p);
+                        g2[h] = on * eta * (1.f - sig);
+                        row_loss += on * (fmaxf(-s, 0.f) + l1p);  // -log sigma(s)
                     }
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) packed[i] = 0;
+                    __nv_bfloat162 hv = __floats2bfloat162_rn(g2[0], g2[1]);
+                    packed[i / 2] = *reinterpret_cast<uint32_t *>(&hv);
                 }
+            } else {
 #pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    *reinterpret_cast<uint4 *>(sm + Lay::kG + core_offset(q, 32 * c + 8 * k, kTileRows)) =
-                        make_uint4(packed[4 * k], packed[4 * k + 1], packed[4 * k + 2], packed[4 * k + 3]);
+                for (int i = 0; i < 16; ++i) packed[i] = 0;
             }
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                *reinterpret_cast<uint4 *>(sm + Lay::kG + core_offset(q, 32 * c + 8 * k, kTileRows)) =
+                    make_uint4(packed[4 * k], packed[4 * k + 1], packed[4 * k + 2], packed[4 * k + 3]);
         }
 #pragma unroll 1
         for (int c = half; c < Ns / 32; c += 2) {  // shared negatives, columns 128 + 32c ..
             uint32_t r[32];
             tmem_ld32(lane_base + kTileRows + 32 * c, r);
+            float mk[32];  // pair count of row q that counts negative 32c + i
+#pragma unroll
+            for (int i = 0; i < 32; ++i) mk[i] = static_cast<float>(cnt);
+            if (any_hit) {  // pairs whose center is this negative do not count
+#pragma unroll
+                for (int wd = 0; wd < 4; ++wd) {
+                    const int a0 = plo - 32 * wd, b0 = phi - 32 * wd;
+                    uint32_t hb = hm[wd];
+                    hb &= (a0 <= 0 ? 0xffffffffu : (a0 >= 32 ? 0u : (0xffffffffu << a0)));
+                    hb &= (b0 >= 31 ? 0xffffffffu : (b0 < 0 ? 0u : (0xffffffffu >> (31 - b0))));
+                    if ((q >> 5) == wd) hb &= ~(1u << (q & 31));
+                    while (hb) {
+                        const int p = 32 * wd + __ffs(hb) - 1;
+                        hb &= hb - 1;
+                        const uint32_t mw = negm_s[p][c];
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) mk[i] -= static_cast<float>(mw >> i & 1u);
+                    }
+                }
+            }
             tmem_wait_ld();
             uint32_t packed[16];
 #pragma unroll
@@ -310,23 +380,11 @@ __global__ void __launch_bounds__(kTileThreads, 1)
                 float g2[2];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const int k = 32 * c + i + h;
-                    int m = cnt;
-                    if (any_hit) {  // pairs whose center is this negative do not count
-                        const int32_t nk = neg_s[k];
-                        for (int p = plo; p <= phi; ++p) m -= (p != q && hit_s[p] && node_s[p] == nk);
-                    }
-                    float g = 0.f;
-                    if (m > 0) {
-                        const float s = __uint_as_float(r[i + h]);
-                        const float wm = omega * static_cast<float>(m);
-                        float sig, l1p;
-                        sigmoid_softplus(s, sig, l1p);
-                        g = -eta * wm * sig;
-                        row_loss += wm * (fmaxf(s, 0.f) + l1p);  // -log sigma(-s)
-                        colused_s[kTileRows + k] = 1;
-                    }
-                    g2[h] = g;
+                    const float s = __uint_as_float(r[i + h]);
+                    float sig, l1p;
+                    sigmoid_softplus(s, sig, l1p);
+                    g2[h] = -eta * omega * mk[i + h] * sig;
+                    row_loss += omega * mk[i + h] * (fmaxf(s, 0.f) + l1p);  // -log sigma(-s)
                 }
                 __nv_bfloat162 hv = __floats2bfloat162_rn(g2[0], g2[1]);
                 packed[i / 2] = *reinterpret_cast<uint32_t *>(&hv);
@@ -363,8 +421,18 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         {
             const u32x4 rw = philox(a.seed, static_cast<uint32_t>(t), static_cast<uint32_t>(q), a.round, kStreamSR);
             uint32_t sr0 = (half ? rw.z : rw.x) | 1u, sr1 = rw.y | 1u;
-            const bool first = half == 0 ? (vq >= 0 && cnt > 0) : colused_s[q] != 0;
-            const bool second = half == 0 && q < Ns && colused_s[kTileRows + q] != 0;
+            // position q is a center of some pair iff it is a valid center with
+            // another node of its walk within w; a negative row is always added
+            // (a zero increment leaves a table unchanged)
+            bool first;
+            if (half == 0) {
+                first = vq >= 0 && cnt > 0;
+            } else {
+                const bool vc = valid_s[q >> 5] >> (q & 31) & 1u;
+                const int clo = max(q - w, static_cast<int>(lo_s[q])), chi = min(q + w, static_cast<int>(hi_s[q]));
+                first = vc && popc_range(nm, clo, chi) > 1;
+            }
+            const bool second = half == 0 && q < Ns;
             T *p1 = (half == 0 ? phi_in : phi_out) + static_cast<int64_t>(max(vq, 0)) * D;
             T *p2 = phi_out + static_cast<int64_t>(q < Ns ? neg_s[q] : 0) * D;
             const uint32_t t1 = half == 0 ? lane_base + 256 : lane_base;  // dX or dY(positions)
