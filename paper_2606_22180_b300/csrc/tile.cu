@@ -28,9 +28,12 @@
 // tables: stochastically rounded increments against the gathered values).
 //
 // Shared memory (no-swizzle core-matrix layout, see tc_core.cuh): X
-// 128 x d, Y 256 x d, G 128 x 256, all bf16.  Tensor memory: 512 columns;
-// S in columns [0, 128 + Ns), dX in [256, 256 + d), dY (positions, then
-// negatives) reuses [0, 2d) once S has been read.
+// 128 x d, Y (128 + Ns) x d, G 128 x (128 + Ns), all bf16; with bf16 tables
+// and tiles allowed to overlap, a second X/Y stage receives the next tile's
+// rows (cp.async) while this tile computes.  Tensor memory: 512 columns; S
+// in columns [0, 128 + Ns), dX in [256, 256 + d), dY reuses [0, 2d) once S
+// has been read (positions 0..127, then rows NY - 128 .. NY - 1 of G^T X,
+// whose last Ns are the negatives).
 #include <algorithm>
 #include <type_traits>
 
@@ -59,17 +62,7 @@ struct TileArgs {
     uint32_t round;
     unsigned long long *loss_acc;
     int32_t *timeout;
-};
-
-template <int D>
-struct TileSmem {
-    static constexpr uint32_t kX = 0;
-    static constexpr uint32_t kY = kX + kTileRows * D * 2;
-    static constexpr uint32_t kG = kY + 256 * D * 2;
-    static constexpr uint32_t kEnd = kG + kTileRows * 256 * 2;
-    // requested size: at least 120 KB so that one CTA holds an SM and its
-    // 512 tensor-memory columns
-    static constexpr uint32_t kBytes = kEnd > 122880 ? kEnd : 122880;
+    int32_t prefetch;  // gather the next tile while this one computes (2 stages)
 };
 
 // 8 floats -> 8 bf16 (round to nearest) packed in 4 words
@@ -141,57 +134,53 @@ __device__ __forceinline__ void sigmoid_softplus(float s, float &sig, float &l1p
     l1p = __logf(1.f + e);
 }
 
+// Per-stage tile bookkeeping (shared memory).
+struct TileStage {
+    int32_t node[kTileRows];       // node of each row position (-1: none)
+    int16_t lo[kTileRows], hi[kTileRows];  // rows of the same walk as row q
+    int32_t neg[kTileRows];        // shared negatives (Ns used)
+    uint32_t negm[kTileRows][4];   // center p: bit j set where negative j equals it
+    uint32_t valid[4];             // bit p: row p is a center with a node
+    uint32_t hitm[4];              // bit p: that center equals a shared negative
+    uint32_t nodem[4];             // bit p: row p holds a node
+    uint32_t bloom[32];
+};
+
+// Dynamic shared memory: `stages` copies of [X (128 x d) | Y (128 + Ns rows
+// x d)], then G (128 x (128 + Ns)), all bf16 in the core-matrix layout.
+__host__ __device__ inline uint32_t tile_stage_bytes(int D, int NY) { return (kTileRows + NY) * D * 2; }
+__host__ __device__ inline uint32_t tile_smem_bytes(int D, int NY, int stages) {
+    const uint32_t b = stages * tile_stage_bytes(D, NY) + kTileRows * NY * 2;
+    return b > 122880 ? b : 122880;  // at least 120 KB: one CTA (and its 512 TMEM columns) per SM
+}
+
 template <int D, class T>
 __global__ void __launch_bounds__(kTileThreads, 1)
     k_sgns_tile(TileArgs a, T *__restrict__ phi_in, T *__restrict__ phi_out) {
-    using Lay = TileSmem<D>;
+    constexpr bool kAsync = std::is_same<T, __nv_bfloat16>::value;
     extern __shared__ __align__(1024) uint8_t sm[];
-    __shared__ int32_t node_s[kTileRows];     // node of each row position (-1: none)
-    __shared__ int16_t lo_s[kTileRows], hi_s[kTileRows];  // rows of the same walk as row q
-    __shared__ int32_t neg_s[kTileRows];      // shared negatives (Ns used)
-    __shared__ uint32_t valid_s[4];           // bit p: row p is a center with a node
-    __shared__ uint32_t hitm_s[4];            // bit p: that center equals a shared negative
-    __shared__ uint32_t nodem_s[4];           // bit p: row p holds a node
-    __shared__ uint32_t negm_s[kTileRows][4];  // center p: bit j set where negative j equals it
-    __shared__ uint32_t bloom_s[32];
+    __shared__ TileStage st_s[2];
     __shared__ __align__(8) uint64_t bar_s;
     __shared__ uint32_t tmem_s;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t base = smem_addr(sm);
-    const uint32_t xs = base + Lay::kX, ys = base + Lay::kY, gs = base + Lay::kG;
     const uint32_t bar = smem_addr(&bar_s);
     const int w = a.window, Ns = a.Ns, NY = kTileRows + Ns;
+    const int stages = a.prefetch ? 2 : 1;
+    const uint32_t xbytes = kTileRows * D * 2, sbytes = tile_stage_bytes(D, NY);
+    const uint32_t goff = stages * sbytes;  // G
     const uint64_t nn = static_cast<uint64_t>(a.n), Ssum = *a.S;
     const float omega = static_cast<float>(a.K) / static_cast<float>(Ns);
     // epilogue roles: warps g and g + 4 share TMEM lanes 32g .. 32g + 31
     const int quarter = warp & 3, half = warp >> 2;
     const int q = quarter * 32 + lane;  // row of this thread in the epilogues
+    const int neg_lane0 = 256 - NY;     // dY lane of the first negative (second half of G^T X)
 
-    // zero the parts of Y and G that no tile writes (negative rows beyond Ns,
-    // gradient columns beyond 128 + Ns)
-    for (int e = tid; e < (256 - NY) * D / 8; e += kTileThreads) {
-        const int r = NY + e / (D / 8), c = (e % (D / 8)) * 8;
-        *reinterpret_cast<uint4 *>(sm + Lay::kY + core_offset(r, c, 256)) = make_uint4(0, 0, 0, 0);
-    }
-    for (int e = tid; e < kTileRows * (256 - NY) / 8; e += kTileThreads) {
-        const int r = e / ((256 - NY) / 8), c = NY + (e % ((256 - NY) / 8)) * 8;
-        *reinterpret_cast<uint4 *>(sm + Lay::kG + core_offset(r, c, kTileRows)) = make_uint4(0, 0, 0, 0);
-    }
-    if (tid == 0) mbar_init(bar, 1);
-    if (warp == 0) tmem_alloc(smem_addr(&tmem_s), 512);
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tm = tmem_s;
-    const uint32_t lane_base = tm + (static_cast<uint32_t>(quarter * 32) << 16);
-    uint32_t phase = 0;
-    double loss = 0.0;
-    bool failed = false;
-
-    for (int64_t t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
+    // Rows, shared negatives and masks of tile t into stage `sg`.
+    auto setup = [&](int sg, int64_t t) {
+        TileStage &S = st_s[sg];
         const int64_t pos0 = t * a.Tc - w;  // corpus position of row 0
-        // ---- rows (threads 0..127), shared negatives (threads 128..) ---------
         if (tid < kTileRows) {
             const int64_t pos = pos0 + tid;
             int32_t v = -1;
@@ -203,10 +192,10 @@ __global__ void __launch_bounds__(kTileThreads, 1)
                 lo = wstart > pos0 ? static_cast<int>(wstart - pos0) : 0;
                 hi = wend - pos0 < kTileRows - 1 ? static_cast<int>(wend - pos0) : kTileRows - 1;
             }
-            node_s[tid] = v;
-            lo_s[tid] = static_cast<int16_t>(lo);
-            hi_s[tid] = static_cast<int16_t>(hi);
-            if (tid < 32) bloom_s[tid] = 0;
+            S.node[tid] = v;
+            S.lo[tid] = static_cast<int16_t>(lo);
+            S.hi[tid] = static_cast<int16_t>(hi);
+            if (tid < 32) S.bloom[tid] = 0;
         }
         __syncthreads();
         if (tid >= kTileRows && tid < kTileRows + Ns) {
@@ -216,73 +205,102 @@ __global__ void __launch_bounds__(kTileThreads, 1)
             const uint64_t coin = mulhi64(hi64(r), Ssum);
             const uint64_t th = __ldg(reinterpret_cast<const unsigned long long *>(a.thr) + b);
             const int32_t v = coin < th ? static_cast<int32_t>(b) : __ldg(a.alias + b);
-            neg_s[j] = v;
-            atomicOr(&bloom_s[(static_cast<uint32_t>(v) * 0x9E3779B1u) >> 27], 1u << (v & 31));
+            S.neg[j] = v;
+            atomicOr(&S.bloom[(static_cast<uint32_t>(v) * 0x9E3779B1u) >> 27], 1u << (v & 31));
         }
         __syncthreads();
-        // ---- gather X (phi_in of positions) and Y (phi_out of centers and
-        //      negatives) into the core-matrix layout, as bf16 ------------------
-        {
-            const int r8 = lane & 7, cq = lane >> 3;  // row within group, chunk within 4
-            constexpr int kChunks = D / 8;            // 16-byte bf16 chunks per row
-            constexpr int kUnitsPerGroup = kChunks / 4;
-            const int groups = kTileRows / 8 + NY / 8;  // X row groups, then Y row groups
-            const int units = groups * kUnitsPerGroup;
-#pragma unroll 4
-            for (int u = warp; u < units; u += kTileThreads / 32) {
-                const int gi = u / kUnitsPerGroup, c = ((u % kUnitsPerGroup) * 4 + cq) * 8;
-                const bool isx = gi < kTileRows / 8;
-                const int r = (isx ? gi : gi - kTileRows / 8) * 8 + r8;
-                int32_t v;
-                if (isx) v = node_s[r];
-                else if (r < kTileRows) v = (r >= w && r < w + a.Tc) ? node_s[r] : -1;  // centers only
-                else v = neg_s[r - kTileRows];
-                const uint32_t off = isx ? Lay::kX + core_offset(r, c, kTileRows) : Lay::kY + core_offset(r, c, 256);
-                const T *src = (isx ? phi_in : phi_out) + static_cast<int64_t>(max(v, 0)) * D + c;
-                if constexpr (std::is_same<T, __nv_bfloat16>::value) {
-                    cp_async16(base + off, src, v >= 0 ? 16u : 0u);
-                } else {
-                    uint4 val = make_uint4(0, 0, 0, 0);
-                    if (v >= 0) val = ld_row8(src);
-                    *reinterpret_cast<uint4 *>(sm + off) = val;
-                }
-            }
-            if constexpr (std::is_same<T, __nv_bfloat16>::value) cp_async_wait_all();
-        }
-        // valid centers, and centers equal to a negative (exact check behind
-        // a bloom filter), as 128-bit masks
+        // valid centers, row nodes, and centers equal to a negative (exact
+        // check behind a bloom filter), as 128-bit masks
         if (tid < kTileRows) {
-            const int32_t v = node_s[tid];
+            const int32_t v = S.node[tid];
             const bool valid = v >= 0 && tid >= w && tid < w + a.Tc;
             bool hit = false;
-            if (valid && (bloom_s[(static_cast<uint32_t>(v) * 0x9E3779B1u) >> 27] >> (v & 31) & 1u)) {
+            if (valid && (S.bloom[(static_cast<uint32_t>(v) * 0x9E3779B1u) >> 27] >> (v & 31) & 1u)) {
                 uint32_t mw[4] = {0, 0, 0, 0};
 #pragma unroll
                 for (int wd = 0; wd < 4; ++wd)
-                    for (int b = 0; b < 32 && 32 * wd + b < Ns; ++b) mw[wd] |= (neg_s[32 * wd + b] == v ? 1u : 0u) << b;
+                    for (int b = 0; b < 32 && 32 * wd + b < Ns; ++b) mw[wd] |= (S.neg[32 * wd + b] == v ? 1u : 0u) << b;
                 hit = (mw[0] | mw[1] | mw[2] | mw[3]) != 0;
 #pragma unroll
-                for (int wd = 0; wd < 4; ++wd) negm_s[tid][wd] = mw[wd];
+                for (int wd = 0; wd < 4; ++wd) S.negm[tid][wd] = mw[wd];
             }
             const uint32_t vb = __ballot_sync(kFull, valid), hb = __ballot_sync(kFull, hit);
             const uint32_t nb = __ballot_sync(kFull, v >= 0);
             if (lane == 0) {
-                valid_s[warp] = vb;
-                hitm_s[warp] = hb;
-                nodem_s[warp] = nb;
+                S.valid[warp] = vb;
+                S.hitm[warp] = hb;
+                S.nodem[warp] = nb;
             }
         }
+    };
+
+    // X (phi_in of positions) and Y (phi_out of centers and negatives) of the
+    // tile in stage `sg` into the core-matrix layout, as bf16: asynchronous
+    // copies for bf16 tables (completed by cp_async_wait_all), converting
+    // loads for float tables.
+    auto gather = [&](int sg) {
+        const TileStage &S = st_s[sg];
+        const uint32_t xo = sg * sbytes, yo = xo + xbytes;
+        const int r8 = lane & 7, cq = lane >> 3;  // row within group, chunk within 4
+        constexpr int kUnitsPerGroup = D / 32;    // 4 chunks of 8 per unit
+        const int units = (kTileRows / 8 + NY / 8) * kUnitsPerGroup;
+#pragma unroll 4
+        for (int u = warp; u < units; u += kTileThreads / 32) {
+            const int gi = u / kUnitsPerGroup, c = ((u % kUnitsPerGroup) * 4 + cq) * 8;
+            const bool isx = gi < kTileRows / 8;
+            const int r = (isx ? gi : gi - kTileRows / 8) * 8 + r8;
+            int32_t v;
+            if (isx) v = S.node[r];
+            else if (r < kTileRows) v = (r >= w && r < w + a.Tc) ? S.node[r] : -1;  // centers only
+            else v = S.neg[r - kTileRows];
+            const uint32_t off = isx ? xo + core_offset(r, c, kTileRows) : yo + core_offset(r, c, NY);
+            const T *src = (isx ? phi_in : phi_out) + static_cast<int64_t>(max(v, 0)) * D + c;
+            if constexpr (kAsync) {
+                cp_async16(base + off, src, v >= 0 ? 16u : 0u);
+            } else {
+                uint4 val = make_uint4(0, 0, 0, 0);
+                if (v >= 0) val = ld_row8(src);
+                *reinterpret_cast<uint4 *>(sm + off) = val;
+            }
+        }
+    };
+
+    if (tid == 0) mbar_init(bar, 1);
+    if (warp == 0) tmem_alloc(smem_addr(&tmem_s), 512);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tm = tmem_s;
+    const uint32_t lane_base = tm + (static_cast<uint32_t>(quarter * 32) << 16);
+    uint32_t phase = 0;
+    double loss = 0.0;
+    bool failed = false;
+
+    int64_t t = blockIdx.x;
+    if (t < a.n_tiles) {
+        setup(0, t);
+        gather(0);
+        if constexpr (kAsync) cp_async_wait_all();
         fence_async_smem();
-        tc_fence_before();
         __syncthreads();
-        tc_fence_after();
+    }
+    for (int sg = 0; t < a.n_tiles; t += gridDim.x, sg ^= (stages - 1)) {
+        const TileStage &S = st_s[sg];
+        const uint32_t xs = base + sg * sbytes, ys = xs + xbytes, gs = base + goff;
+        const int64_t tn = t + gridDim.x;  // this CTA's next tile
         // ---- S = X Y^T ---------------------------------------------------------
+        tc_fence_after();
         if (tid == 0) {
 #pragma unroll
             for (int s = 0; s < D / 16; ++s)
                 mma_bf16(tm, smem_desc(xs + 2 * s * (kTileRows * 16), kTileRows * 16, 128),
-                         smem_desc(ys + 2 * s * (256 * 16), 256 * 16, 128), mma_idesc_bf16(128, NY, 0, 0), s > 0);
+                         smem_desc(ys + 2 * s * (NY * 16), NY * 16, 128), mma_idesc_bf16(128, NY, 0, 0), s > 0);
             mma_commit(bar);
+        }
+        // ---- meanwhile: the next tile's rows into the other stage --------------
+        if (stages == 2 && tn < a.n_tiles) {
+            setup(sg ^ 1, tn);
+            gather(sg ^ 1);
         }
         failed = !mbar_wait(bar, phase, kTileWaitLimit);
         phase ^= 1;
@@ -290,23 +308,23 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         if (__syncthreads_or(failed)) break;
         // ---- epilogue: gradient G (bf16).  Row q pairs with the centers
         //      p in [plo, phi] \ {q} whose node is >= 0 ----------------------------
-        const int32_t vq = node_s[q];
+        const int32_t vq = S.node[q];
         const float eta = static_cast<float>(
             static_cast<double>(a.lr0) *
             fmax(1e-4, 1.0 - static_cast<double>(a.clock_base + t * a.Tc) * a.inv_total));
-        int plo = max(max(q - w, w), static_cast<int>(lo_s[q]));
-        int phi = min(min(q + w, w + a.Tc - 1), static_cast<int>(hi_s[q]));
+        int plo = max(max(q - w, w), static_cast<int>(S.lo[q]));
+        int phi = min(min(q + w, w + a.Tc - 1), static_cast<int>(S.hi[q]));
         if (vq < 0) phi = plo - 1;
         uint32_t vm[4], hm[4], nm[4];
 #pragma unroll
         for (int wd = 0; wd < 4; ++wd) {
-            vm[wd] = valid_s[wd];
-            hm[wd] = hitm_s[wd];
-            nm[wd] = nodem_s[wd];
+            vm[wd] = S.valid[wd];
+            hm[wd] = S.hitm[wd];
+            nm[wd] = S.nodem[wd];
         }
         const bool q_in = q >= plo && q <= phi;
-        const int cnt = popc_range(vm, plo, phi) - (q_in ? static_cast<int>(valid_s[q >> 5] >> (q & 31) & 1u) : 0);
-        const bool any_hit = popc_range(hm, plo, phi) - (q_in ? static_cast<int>(hitm_s[q >> 5] >> (q & 31) & 1u) : 0) > 0;
+        const int cnt = popc_range(vm, plo, phi) - (q_in ? static_cast<int>(S.valid[q >> 5] >> (q & 31) & 1u) : 0);
+        const bool any_hit = popc_range(hm, plo, phi) - (q_in ? static_cast<int>(S.hitm[q >> 5] >> (q & 31) & 1u) : 0) > 0;
         float row_loss = 0.f;
         // positive band, columns 32c .. 32c+31: half 0 takes the warp's own
         // chunk, half 1 the other three (two band edges and a zero chunk).
@@ -319,7 +337,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
                 uint32_t r[32];
                 tmem_ld32(lane_base + 32 * c, r);
                 // pairs of row q among columns 32c .. 32c+31
-                uint32_t pm = valid_s[c];
+                uint32_t pm = S.valid[c];
                 const int a0 = plo - 32 * c, b0 = phi - 32 * c;
                 pm &= (a0 <= 0 ? 0xffffffffu : (a0 >= 32 ? 0u : (0xffffffffu << a0)));
                 pm &= (b0 >= 31 ? 0xffffffffu : (b0 < 0 ? 0u : (0xffffffffu >> (31 - b0))));
@@ -346,7 +364,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
             }
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                *reinterpret_cast<uint4 *>(sm + Lay::kG + core_offset(q, 32 * c + 8 * k, kTileRows)) =
+                *reinterpret_cast<uint4 *>(sm + goff + core_offset(q, 32 * c + 8 * k, kTileRows)) =
                     make_uint4(packed[4 * k], packed[4 * k + 1], packed[4 * k + 2], packed[4 * k + 3]);
         }
 #pragma unroll 1
@@ -367,7 +385,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
                     while (hb) {
                         const int p = 32 * wd + __ffs(hb) - 1;
                         hb &= hb - 1;
-                        const uint32_t mw = negm_s[p][c];
+                        const uint32_t mw = S.negm[p][c];
 #pragma unroll
                         for (int i = 0; i < 32; ++i) mk[i] -= static_cast<float>(mw >> i & 1u);
                     }
@@ -391,7 +409,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
             }
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                *reinterpret_cast<uint4 *>(sm + Lay::kG + core_offset(q, kTileRows + 32 * c + 8 * k, kTileRows)) =
+                *reinterpret_cast<uint4 *>(sm + goff + core_offset(q, kTileRows + 32 * c + 8 * k, kTileRows)) =
                     make_uint4(packed[4 * k], packed[4 * k + 1], packed[4 * k + 2], packed[4 * k + 3]);
         }
         loss += static_cast<double>(row_loss);
@@ -399,15 +417,16 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
-        // ---- dX = G Y, dY = G^T X -------------------------------------------
+        // ---- dX = G Y, dY = G^T X (second half: j in [NY - 128, NY)) --------
         if (tid == 0) {
             for (int s = 0; s < NY / 16; ++s)
                 mma_bf16(tm + 256, smem_desc(gs + 2 * s * (kTileRows * 16), kTileRows * 16, 128),
-                         smem_desc(ys + 2 * s * 128, 128, 256 * 16), mma_idesc_bf16(128, D, 0, 1), s > 0);
+                         smem_desc(ys + 2 * s * 128, 128, NY * 16), mma_idesc_bf16(128, D, 0, 1), s > 0);
             for (int h = 0; h < 2; ++h) {
+                const uint32_t g0 = gs + (h ? (NY - kTileRows) / 8 : 0) * (kTileRows * 16);
 #pragma unroll
                 for (int s = 0; s < kTileRows / 16; ++s)
-                    mma_bf16(tm + h * D, smem_desc(gs + h * 16 * (kTileRows * 16) + 2 * s * 128, 128, kTileRows * 16),
+                    mma_bf16(tm + h * D, smem_desc(g0 + 2 * s * 128, 128, kTileRows * 16),
                              smem_desc(xs + 2 * s * 128, 128, kTileRows * 16), mma_idesc_bf16(128, D, 1, 1), s > 0);
             }
             mma_commit(bar);
@@ -417,7 +436,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         tc_fence_after();
         if (__syncthreads_or(failed)) break;
         // ---- add the increments to the tables: half 0 adds dX of row q and dY
-        //      of negative q, half 1 dY of position q ----------------------------
+        //      of negative q - (256 - NY), half 1 dY of position q -------------
         {
             const u32x4 rw = philox(a.seed, static_cast<uint32_t>(t), static_cast<uint32_t>(q), a.round, kStreamSR);
             uint32_t sr0 = (half ? rw.z : rw.x) | 1u, sr1 = rw.y | 1u;
@@ -428,16 +447,17 @@ __global__ void __launch_bounds__(kTileThreads, 1)
             if (half == 0) {
                 first = vq >= 0 && cnt > 0;
             } else {
-                const bool vc = valid_s[q >> 5] >> (q & 31) & 1u;
-                const int clo = max(q - w, static_cast<int>(lo_s[q])), chi = min(q + w, static_cast<int>(hi_s[q]));
+                const bool vc = S.valid[q >> 5] >> (q & 31) & 1u;
+                const int clo = max(q - w, static_cast<int>(S.lo[q])), chi = min(q + w, static_cast<int>(S.hi[q]));
                 first = vc && popc_range(nm, clo, chi) > 1;
             }
-            const bool second = half == 0 && q < Ns;
+            const int jn = q - neg_lane0;  // negative held by this TMEM lane
+            const bool second = half == 0 && jn >= 0;
             T *p1 = (half == 0 ? phi_in : phi_out) + static_cast<int64_t>(max(vq, 0)) * D;
-            T *p2 = phi_out + static_cast<int64_t>(q < Ns ? neg_s[q] : 0) * D;
+            T *p2 = phi_out + static_cast<int64_t>(jn >= 0 ? S.neg[jn] : 0) * D;
             const uint32_t t1 = half == 0 ? lane_base + 256 : lane_base;  // dX or dY(positions)
-            const uint32_t s1 = half == 0 ? Lay::kX + 0 : Lay::kY + 0;
-            const int R1 = half == 0 ? kTileRows : 256;
+            const uint32_t s1 = half == 0 ? xs - base : ys - base;
+            const int R1 = half == 0 ? kTileRows : NY;
 #pragma unroll 1
             for (int c = 0; c < D / 32; ++c) {
                 uint32_t r1[32], r2[32];
@@ -456,7 +476,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
                     }
                     if (second) {
                         const uint4 snap =
-                            *reinterpret_cast<const uint4 *>(sm + Lay::kY + core_offset(kTileRows + q, col, 256));
+                            *reinterpret_cast<const uint4 *>(sm + (ys - base) + core_offset(kTileRows + jn, col, NY));
 #pragma unroll
                         for (int i = 0; i < 8; ++i) d8[i] = __uint_as_float(r2[8 * k + i]);
                         add8(p2 + col, d8, snap, xorshift32(sr1));
@@ -464,12 +484,20 @@ __global__ void __launch_bounds__(kTileThreads, 1)
                 }
             }
         }
-        // the next tile's gather reads what these reductions wrote
-        __threadfence();
+        // ---- the next tile: with one stage its rows are read only now, after
+        //      these reductions (tiles strictly in order) ------------------------
+        if (stages == 1 && tn < a.n_tiles) {
+            __threadfence();
+            __syncthreads();
+            setup(0, tn);
+            gather(0);
+        }
+        if constexpr (kAsync) cp_async_wait_all();
+        fence_async_smem();
         tc_fence_before();
         __syncthreads();
-        tc_fence_after();
     }
+    if constexpr (kAsync) cp_async_wait_all();  // none left in flight, also after a timeout
     if (failed && tid == 0) atomicExch(a.timeout, 1);
     long long fx = __double2ll_rn(loss * kLossScale);
     for (int o = 16; o; o >>= 1) fx += __shfl_xor_sync(kFull, fx, o);
@@ -481,9 +509,14 @@ __global__ void __launch_bounds__(kTileThreads, 1)
 }
 
 template <int D, class T>
-static felog_status launch_tile_dim(const TileArgs &a, int ctas, void *pi, void *po, cudaStream_t s) {
+static felog_status launch_tile_dim(TileArgs a, int ctas, void *pi, void *po, cudaStream_t s) {
     auto kern = k_sgns_tile<D, T>;
-    const int bytes = static_cast<int>(TileSmem<D>::kBytes);
+    const int NY = kTileRows + a.Ns;
+    // two stages (next tile gathered during this one) for bf16 tables when
+    // tiles may overlap and the buffers fit; one stage keeps tiles in order
+    a.prefetch = std::is_same<T, __nv_bfloat16>::value && ctas > 1 &&
+                 tile_smem_bytes(D, NY, 2) + sizeof(TileStage) * 2 + 1024 <= 227 * 1024;
+    const int bytes = static_cast<int>(tile_smem_bytes(D, NY, a.prefetch ? 2 : 1));
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return record_cuda_error(e, "felog_train (tile)");
     kern<<<ctas, kTileThreads, bytes, s>>>(a, static_cast<T *>(pi), static_cast<T *>(po));
