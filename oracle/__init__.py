@@ -66,8 +66,8 @@ def lib() -> ctypes.CDLL:
             "oracle_sgns_minibatch": (f64, [P, i64, i32, i32, P, i64, P, P, u64, u64, i32, i64,
                                             P, P, P]),
             "oracle_tile_negatives": (None, [P, P, i32, u64, u64, i32, i64, i32, P]),
-            "oracle_sgns_tile": (f64, [P, i64, i32, i32, P, i32, i32, P, P, u64, u64, i32, i64,
-                                       P, P, P]),
+            "oracle_sgns_tile": (f64, [P, i64, i32, i32, P, i32, i32, i32, P, P, u64, u64, i32,
+                                       i64, P, P, P]),
             "oracle_psi_subset": (None, [i64, i32, u64, i32, i32, P]),
             "oracle_psi_node": (f64, [P, P, P, i32, i32, u64, i32, i32]),
             "oracle_feedback": (i64, [P, P, i32, P, i32, P, u64, i32, P, P, P]),
@@ -197,9 +197,11 @@ def tile_negatives(thr, alias, n: int, S: int, seed: int, round_: int, t: int, N
 
 def sgns_tile(walks, n: int, dim: int, window: int, negatives: int, lr0: float, T_total: int,
               tile_centers: int, Ns: int, thr, alias, S: int, seed: int, round_: int,
-              clock_base: int, phi_in: np.ndarray, phi_out: np.ndarray, per_tile: bool = False):
+              clock_base: int, phi_in: np.ndarray, phi_out: np.ndarray, per_tile: bool = False,
+              normalize: bool = True):
     """Shared-negatives tile form of Eq. 2, tiles of `tile_centers` centers in
-    corpus order, Ns shared negatives per tile of weight negatives / Ns."""
+    corpus order, Ns shared negatives per tile of weight negatives / Ns;
+    normalize divides a node's summed tile increment by its rows in the tile."""
     w = _c(walks, np.int32)
     assert phi_in.dtype == np.float64 and phi_in.flags.c_contiguous
     assert phi_out.dtype == np.float64 and phi_out.flags.c_contiguous
@@ -207,7 +209,8 @@ def sgns_tile(walks, n: int, dim: int, window: int, negatives: int, lr0: float, 
     nt = (w.size + tile_centers - 1) // tile_centers
     tl = np.zeros(max(nt, 1), np.float64)
     loss = float(lib().oracle_sgns_tile(_p(w), w.shape[0], w.shape[1], n, ctypes.byref(tp),
-                                        tile_centers, Ns, _p(thr), _p(alias), S, seed, round_,
+                                        tile_centers, Ns, int(normalize), _p(thr), _p(alias), S,
+                                        seed, round_,
                                         clock_base, _p(phi_in), _p(phi_out), _p(tl)))
     return (loss, tl[:nt]) if per_tile else loss
 

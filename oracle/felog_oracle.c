@@ -434,14 +434,22 @@ void oracle_tile_negatives(const uint64_t *thr, const int32_t *alias, int32_t n,
 /*  - eta is the rate of the tile's first center position;                   */
 /*  - all scores of a tile read the tables as they stood when the tile       */
 /*    began and the summed increments are added when it ends (tiles run in  */
-/*    order).                                                               */
+/*    order);                                                               */
+/*  - normalize != 0: a node's summed increment is divided by the number of  */
+/*    the tile's rows that hold it in that table -- for phi_in the distinct */
+/*    context positions that take part in a pair, for phi_out the distinct  */
+/*    center positions that take part in a pair plus the negative slots    */
+/*    drawn as that node.  Without it, a node that a walk revisits every    */
+/*    other step (a hub between degree-1 neighbours) receives dozens of     */
+/*    pair gradients computed from one stale value in one step, and         */
+/*    training diverges on power-law graphs.                                */
 /* Per pair (x, c): loss -log sigma(f+) - (K/Ns) sum_j log sigma(-f_j),       */
 /* increments g+ = eta (1 - sigma(f+)), g_j = -eta (K/Ns) sigma(f_j) applied */
 /* as phi_in[x] += g phi_out[target], phi_out[target] += g phi_in[x].         */
 /* tile_loss (may be NULL) receives each tile's loss.                        */
 /* ------------------------------------------------------------------------ */
 double oracle_sgns_tile(const int32_t *walks, int64_t n_walks, int32_t L, int32_t n,
-                        const oracle_train_params *tp, int32_t T, int32_t Ns,
+                        const oracle_train_params *tp, int32_t T, int32_t Ns, int32_t normalize,
                         const uint64_t *thr, const int32_t *alias, uint64_t S, uint64_t seed,
                         int32_t round, int64_t clock_base, double *phi_in, double *phi_out,
                         double *tile_loss) {
@@ -455,6 +463,13 @@ double oracle_sgns_tile(const int32_t *walks, int64_t n_walks, int32_t L, int32_
     int32_t *list_out = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
     int32_t *neg = (int32_t *)malloc(sizeof(int32_t) * (size_t)Ns);
     const int64_t total = n_walks * L;
+    /* rows per node in the current tile, and the tile that last counted a */
+    /* position as a context / as a center                                 */
+    int32_t *rows_in = (int32_t *)calloc((size_t)n, sizeof(int32_t));
+    int32_t *rows_out = (int32_t *)calloc((size_t)n, sizeof(int32_t));
+    int64_t *ctx_tile = (int64_t *)malloc(sizeof(int64_t) * (size_t)(total > 0 ? total : 1));
+    int64_t *ctr_tile = (int64_t *)malloc(sizeof(int64_t) * (size_t)(total > 0 ? total : 1));
+    for (int64_t i = 0; i < total; ++i) ctx_tile[i] = ctr_tile[i] = -1;
     double loss = 0.0;
     int64_t t = 0;
     for (int64_t b0 = 0; b0 < total; b0 += T, ++t) {
@@ -474,6 +489,8 @@ double oracle_sgns_tile(const int32_t *walks, int64_t n_walks, int32_t L, int32_
                 int32_t pp = p + o;
                 if (pp < 0 || pp >= L || row[pp] < 0) continue;
                 int32_t x = row[pp];
+                if (ctx_tile[wi * L + pp] != t) { ctx_tile[wi * L + pp] = t; rows_in[x] += 1; }
+                if (ctr_tile[tok] != t) { ctr_tile[tok] = t; rows_out[c] += 1; }
                 const double *ix = phi_in + (int64_t)x * d;
                 double *dx = din + (int64_t)x * d;
                 if (!touched_in[x]) { touched_in[x] = 1; list_in[n_in++] = x; }
@@ -497,27 +514,34 @@ double oracle_sgns_tile(const int32_t *walks, int64_t n_walks, int32_t L, int32_
                 }
             }
         }
+        for (int32_t j = 0; j < Ns; ++j) rows_out[neg[j]] += 1;
         for (int32_t a = 0; a < n_in; ++a) {
             int64_t r = list_in[a];
+            double sc = normalize ? 1.0 / (double)rows_in[r] : 1.0;
             for (int32_t i = 0; i < d; ++i) {
-                phi_in[r * d + i] += din[r * d + i];
+                phi_in[r * d + i] += sc * din[r * d + i];
                 din[r * d + i] = 0.0;
             }
             touched_in[r] = 0;
+            rows_in[r] = 0;
         }
         for (int32_t a = 0; a < n_out; ++a) {
             int64_t r = list_out[a];
+            double sc = normalize ? 1.0 / (double)rows_out[r] : 1.0;
             for (int32_t i = 0; i < d; ++i) {
-                phi_out[r * d + i] += dout[r * d + i];
+                phi_out[r * d + i] += sc * dout[r * d + i];
                 dout[r * d + i] = 0.0;
             }
             touched_out[r] = 0;
         }
+        for (int32_t j = 0; j < Ns; ++j) rows_out[neg[j]] = 0;
+        for (int32_t a = 0; a < n_out; ++a) rows_out[list_out[a]] = 0;
         if (tile_loss) tile_loss[t] = tl;
         loss += tl;
     }
     free(din); free(dout); free(touched_in); free(touched_out);
     free(list_in); free(list_out); free(neg);
+    free(rows_in); free(rows_out); free(ctx_tile); free(ctr_tile);
     return loss;
 }
 

@@ -1,12 +1,15 @@
 """Pins for the oracle's shared-negatives tile form of Eq. 2.
 
 The tile form draws Ns negatives once per tile of T consecutive centers and
-gives each weight K / Ns.  It is pinned by: the loss at phi_out = 0 (every
-score 0, so the loss counts kept targets with their weights); equality with
-the per-pair minibatch form when the noise distribution is a point mass
-(then every draw of either form is the same node); finite differences of the
-tile loss (one tile updates by exactly -eta times its gradient); and the
-frequencies of the shared draws against the unigram^0.75 distribution.
+gives each weight K / Ns; a node's summed tile increment is divided by the
+node's rows in the tile.  It is pinned by: the loss at phi_out = 0 (every
+score 0, so the loss counts kept targets with their weights); without the
+averaging, equality with the per-pair minibatch form when the noise
+distribution is a point mass (then every draw of either form is the same
+node) and finite differences of the tile loss (one tile updates by exactly
+-eta times its gradient); the averaging against row counts taken here from
+the corpus; and the frequencies of the shared draws against the
+unigram^0.75 distribution.
 """
 import math
 
@@ -79,7 +82,7 @@ def test_tile_equals_minibatch_under_point_mass_noise(orc, T, Ns):
         a_in, a_out = pi0.copy(), po0.copy()
         b_in, b_out = pi0.copy(), po0.copy()
         lt, tl = orc.sgns_tile(W, g.n, d, w, K, 0.05, 5000, T, Ns, thr, alias, S, 3, 0, 7, a_in,
-                               a_out, per_tile=True)
+                               a_out, per_tile=True, normalize=False)
         lm, bl = orc.sgns_minibatch(W, g.n, d, w, K, 0.05, 5000, T, thr, alias, S, 3, 0, 7, b_in,
                                     b_out, per_batch=True)
         assert tl.shape == bl.shape
@@ -91,9 +94,9 @@ def test_tile_equals_minibatch_under_point_mass_noise(orc, T, Ns):
 
 
 def test_tile_update_is_minus_eta_gradient(orc):
-    """One tile: the update equals -eta times the gradient of the tile loss,
-    checked against central differences of the loss (lr0 = 0 evaluates the
-    loss without updating)."""
+    """One tile without averaging: the update equals -eta times the gradient
+    of the tile loss, checked against central differences of the loss
+    (lr0 = 0 evaluates the loss without updating)."""
     g = tiny_graph("triangle_tail")
     W = np.array([[0, 1, 2, 3, 2, 0], [3, 2, 1, 0, 2, 1]], np.int32)
     _, thr, alias, S = orc.noise_table(orc.counts(W, g.n))
@@ -106,10 +109,11 @@ def test_tile_update_is_minus_eta_gradient(orc):
 
     def loss_at(pi, po):
         return orc.sgns_tile(W, g.n, d, w, K, 0.0, 10 ** 9, T, Ns, thr, alias, S, seed, 0, 0,
-                             pi.copy(), po.copy())
+                             pi.copy(), po.copy(), normalize=False)
 
     a_in, a_out = pi0.copy(), po0.copy()
-    orc.sgns_tile(W, g.n, d, w, K, eta, 10 ** 9, T, Ns, thr, alias, S, seed, 0, 0, a_in, a_out)
+    orc.sgns_tile(W, g.n, d, w, K, eta, 10 ** 9, T, Ns, thr, alias, S, seed, 0, 0, a_in, a_out,
+                  normalize=False)
     grad_in = -(a_in - pi0) / eta
     grad_out = -(a_out - po0) / eta
     h = 1e-6
@@ -121,6 +125,52 @@ def test_tile_update_is_minus_eta_gradient(orc):
             fd_out = (loss_at(pi0, po0 + e) - loss_at(pi0, po0 - e)) / (2 * h)
             assert abs(fd_in - grad_in[v, i]) <= 1e-6 * max(1.0, abs(fd_in))
             assert abs(fd_out - grad_out[v, i]) <= 1e-6 * max(1.0, abs(fd_out))
+
+
+def _tile_rows(W, w, T, negs, t):
+    """Rows of tile t per node: distinct context positions in a pair (phi_in)
+    and distinct center positions in a pair plus negative slots (phi_out)."""
+    L = W.shape[1]
+    ctx, ctr = set(), set()
+    for wi, p, pp in _pairs(W, w):
+        if (wi * L + p) // T == t:
+            ctx.add((wi, pp))
+            ctr.add((wi, p))
+    r_in, r_out = {}, {}
+    for wi, pp in ctx:
+        r_in[W[wi, pp]] = r_in.get(W[wi, pp], 0) + 1
+    for wi, p in ctr:
+        r_out[W[wi, p]] = r_out.get(W[wi, p], 0) + 1
+    for v in negs:
+        r_out[int(v)] = r_out.get(int(v), 0) + 1
+    return r_in, r_out
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_tile_average_divides_by_rows_per_node(orc, seed):
+    """One tile: the averaged update of a node is the summed update divided by
+    the node's rows in the tile, counted here from the corpus and the draws.
+    Walks that revisit nodes make several counts exceed one."""
+    g = tiny_graph("star4")  # walks alternate between the hub 0 and a leaf
+    rng = np.random.default_rng(seed)
+    W = np.array([[0, 1, 0, 2, 0, 3, 0, 1], [2, 0, 3, 0, 1, 0, 2, 0]], np.int32)
+    _, thr, alias, S = orc.noise_table(orc.counts(W, g.n))
+    d, w, K, Ns = 4, 2, 3, 6
+    T = W.size
+    pi0 = rng.normal(scale=0.3, size=(g.n, d))
+    po0 = rng.normal(scale=0.3, size=(g.n, d))
+    res = {}
+    for norm in (False, True):
+        a_in, a_out = pi0.copy(), po0.copy()
+        orc.sgns_tile(W, g.n, d, w, K, 0.05, 10 ** 6, T, Ns, thr, alias, S, seed, 0, 0, a_in, a_out,
+                      normalize=norm)
+        res[norm] = (a_in - pi0, a_out - po0)
+    negs = orc.tile_negatives(thr, alias, g.n, S, seed, 0, 0, Ns)
+    r_in, r_out = _tile_rows(W, w, T, negs, 0)
+    assert max(r_in.values()) > 1 and max(r_out.values()) > 1
+    for v in range(g.n):
+        np.testing.assert_allclose(res[True][0][v], res[False][0][v] / r_in.get(v, 1), rtol=1e-12, atol=1e-15)
+        np.testing.assert_allclose(res[True][1][v], res[False][1][v] / r_out.get(v, 1), rtol=1e-12, atol=1e-15)
 
 
 def test_tile_negatives_follow_unigram_three_quarter(orc):
