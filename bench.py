@@ -529,14 +529,15 @@ def run_serve(fl, rate=20.0, duration=20.0, max_nodes=1 << 16, pool_size=48, bud
     return out
 
 
-TILE_NS = 64
+TILE_NS = 512
 
 
 def _tile_flops(n_tiles, dim, ns):
-    """Tensor-core FLOPs of the tile trainer: per tile S = X Y^T and
-    dX = G Y (128 x dim x (128 + Ns) each) and dY = G^T X (256 x dim x 128)."""
-    ny = 128 + ns
-    return n_tiles * 2 * 128 * dim * (2 * ny + 256)
+    """Tensor-core FLOPs of the tile trainer: per tile and per 128-column
+    block (positions, then Ns / 128 blocks of negatives) S_b = X Y_b^T,
+    dX += G_b Y_b and dY_b = G_b^T X, each 128 x 128 x dim."""
+    blocks = 1 + ns // 128
+    return n_tiles * blocks * 3 * 2 * 128 * 128 * dim
 
 
 def _tile_form(fl, dg, n_live, T, steps=3, warmup=2, scale=SCALE):

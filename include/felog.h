@@ -89,7 +89,9 @@ typedef enum {
  * negatives <= 7, full-warp form otherwise), 1 = full warp per pair,
  * 2 = two pairs per warp (half warp each; dim <= 128, negatives <= 7).
  * TILE mode (dim in {32, 64, 128}): tile_negatives = shared negatives per
- * tile (32, 64, 96 or 128; 0 selects 64); tile_ctas = concurrent tiles
+ * tile (128, 256, 384 or 512; 0 selects 512: each then stands for about 20
+ * per-pair draws, fewer shared negatives let hub rows take oversized stale
+ * steps and training can diverge); tile_ctas = concurrent tiles
  * (0 = min(SMs, max(1, n / 2048)), which bounds how many stale tile updates
  * meet on the rows of a small graph; 1 = tiles strictly in order, the
  * reproducible form). */

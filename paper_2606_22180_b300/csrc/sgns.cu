@@ -430,14 +430,17 @@ __global__ void k_init_tables(int32_t n, int32_t dim, uint64_t seed, T *__restri
 struct TrainWorkspace {
     unsigned long long *loss_acc;
     int32_t *timeout;  // set by a TILE launch whose tensor-core wait gave up
+    float *tile_scratch;  // TILE mode, tiles in order: a tile's staged dY rows
     MbState mb;
 };
+
+size_t tile_scratch_floats();
 
 felog_status launch_tile(const int32_t *walks, int64_t n_walks, int32_t L, int32_t n,
                          const felog_train_params *tp, const uint64_t *thr, const int32_t *alias,
                          const uint64_t *S, uint64_t seed, int32_t round, int64_t clock_base,
                          void *phi_in, void *phi_out, unsigned long long *loss_acc, int32_t *timeout,
-                         cudaStream_t s);
+                         float *scratch, cudaStream_t s);
 
 static bool minibatch_mode(const felog_train_params *tp) { return tp->mode == FELOG_SGNS_MINIBATCH; }
 
@@ -445,6 +448,7 @@ static TrainWorkspace carve_train(Carver &c, int32_t n, const felog_train_params
     TrainWorkspace w{};
     w.loss_acc = c.take<unsigned long long>(1);
     w.timeout = c.take<int32_t>(1);
+    if (tp->mode == FELOG_SGNS_TILE) w.tile_scratch = c.take<float>(tile_scratch_floats());
     if (minibatch_mode(tp)) {
         const size_t nn = n > 0 ? static_cast<size_t>(n) : 1;
         w.mb.acc_in = c.take<long long>(nn * tp->dim);
@@ -466,8 +470,8 @@ static bool params_ok(const felog_train_params *tp) {
         return false;
     if (tp->mode == FELOG_SGNS_TILE) {
         if (tp->dim > 128) return false;
-        if (tp->tile_negatives != 0 && (tp->tile_negatives < 32 || tp->tile_negatives > 128 ||
-                                        tp->tile_negatives % 32 != 0))
+        if (tp->tile_negatives != 0 && (tp->tile_negatives < 128 || tp->tile_negatives > 512 ||
+                                        tp->tile_negatives % 128 != 0))
             return false;
         if (tp->tile_ctas < 0) return false;
     }
@@ -586,7 +590,7 @@ extern "C" felog_status felog_train(const int32_t *walks, int64_t n_walks, int32
     }
     if (n_walks > 0 && tp->mode == FELOG_SGNS_TILE) {
         st = launch_tile(walks, n_walks, L, n, tp, thr, alias, S, seed, round, clock_base, phi_in, phi_out,
-                         w.loss_acc, w.timeout, s);
+                         w.loss_acc, w.timeout, w.tile_scratch, s);
         if (st) return st;
     } else if (n_walks > 0) {
         SgnsArgs a;

@@ -62,7 +62,7 @@ struct TileArgs {
     uint32_t round;
     unsigned long long *loss_acc;
     int32_t *timeout;
-    int32_t prefetch;  // gather the next tile while this one computes (2 stages)
+    float *scratch;  // in-order form: dY rows of a tile, added when the tile ends (else null)
 };
 
 // 8 floats -> 8 bf16 (round to nearest) packed in 4 words
@@ -87,6 +87,11 @@ __device__ __forceinline__ uint4 ld_row8(const __nv_bfloat16 *p) {
     asm volatile("ld.global.cg.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(p));
     return r;
 }
+
+// current packed bf16 values of p[0..8) (the rounding reference of add8);
+// float tables need none
+__device__ __forceinline__ uint4 ld_row8_raw(const __nv_bfloat16 *p) { return ld_row8(p); }
+__device__ __forceinline__ uint4 ld_row8_raw(const float *) { return make_uint4(0, 0, 0, 0); }
 
 // 16-byte asynchronous copy global -> shared (L2 only); src_bytes = 0
 // writes zeros without reading.
@@ -134,51 +139,90 @@ __device__ __forceinline__ void sigmoid_softplus(float s, float &sig, float &l1p
     l1p = __logf(1.f + e);
 }
 
-// Per-stage tile bookkeeping (shared memory).
+constexpr int kMaxNegBlocks = 4;                   // Ns <= 512
+constexpr int kMaxNs = 128 * kMaxNegBlocks;
+
+// Per-tile bookkeeping in shared memory (two, for the current and the next
+// tile).
 struct TileStage {
-    int32_t node[kTileRows];       // node of each row position (-1: none)
-    int16_t lo[kTileRows], hi[kTileRows];  // rows of the same walk as row q
-    int32_t neg[kTileRows];        // shared negatives (Ns used)
-    uint32_t negm[kTileRows][4];   // center p: bit j set where negative j equals it
-    uint32_t valid[4];             // bit p: row p is a center with a node
-    uint32_t hitm[4];              // bit p: that center equals a shared negative
-    uint32_t nodem[4];             // bit p: row p holds a node
-    uint32_t bloom[32];
+    int32_t node[kTileRows];                 // node of each row position (-1: none)
+    int16_t lo[kTileRows], hi[kTileRows];    // rows of the same walk as row q
+    int32_t neg[kMaxNs];                     // shared negatives
+    uint32_t negm[kTileRows][kMaxNs / 32];   // center p: bit j set where negative j equals it
+    uint32_t valid[4];                       // bit p: row p is a center with a node
+    uint32_t hitm[4];                        // bit p: that center equals a shared negative
+    uint32_t nodem[4];                       // bit p: row p holds a node
+    uint32_t bloom[128];                     // 4096-bit filter of the negatives
+    uint16_t rows_x[kTileRows];              // rows of node[q] among contexts in a pair (phi_in)
+    uint16_t rows_c[kTileRows];              // rows of node[p] among centers in a pair and negatives (phi_out)
+    uint16_t rows_n[kMaxNs];                 // the same count for negative j
 };
 
-// Dynamic shared memory: `stages` copies of [X (128 x d) | Y (128 + Ns rows
-// x d)], then G (128 x (128 + Ns)), all bf16 in the core-matrix layout.
-__host__ __device__ inline uint32_t tile_stage_bytes(int D, int NY) { return (kTileRows + NY) * D * 2; }
-__host__ __device__ inline uint32_t tile_smem_bytes(int D, int NY, int stages) {
-    const uint32_t b = stages * tile_stage_bytes(D, NY) + kTileRows * NY * 2;
-    return b > 122880 ? b : 122880;  // at least 120 KB: one CTA (and its 512 TMEM columns) per SM
+// Pairs of row q: centers p in [plo, phi] \ {q} with a node (phi < plo: none).
+__device__ __forceinline__ int row_pairs(const TileStage &S, int q, int w, int Tc, int &plo, int &phi) {
+    plo = max(max(q - w, w), static_cast<int>(S.lo[q]));
+    phi = min(min(q + w, w + Tc - 1), static_cast<int>(S.hi[q]));
+    if (S.node[q] < 0) phi = plo - 1;
+    uint32_t vm[4];
+#pragma unroll
+    for (int wd = 0; wd < 4; ++wd) vm[wd] = S.valid[wd];
+    const bool q_in = q >= plo && q <= phi;
+    return popc_range(vm, plo, phi) - (q_in ? static_cast<int>(S.valid[q >> 5] >> (q & 31) & 1u) : 0);
 }
+// Center p takes part in a pair: a valid center with another node of its walk within w.
+__device__ __forceinline__ bool center_used(const TileStage &S, int p, int w) {
+    if (!(S.valid[p >> 5] >> (p & 31) & 1u)) return false;
+    uint32_t nm[4];
+#pragma unroll
+    for (int wd = 0; wd < 4; ++wd) nm[wd] = S.nodem[wd];
+    return popc_range(nm, max(p - w, static_cast<int>(S.lo[p])), min(p + w, static_cast<int>(S.hi[p]))) > 1;
+}
+
+// Open-addressing table node -> (rows in phi_in, rows in phi_out), 1024
+// slots, in shared memory; a tile holds at most 128 + 128 + 512 distinct
+// nodes, so every probe sequence ends.
+constexpr uint32_t kRowHashSlots = 1024;
+__device__ __forceinline__ uint32_t row_hash_slot(uint32_t *keys, int32_t v, bool insert) {
+    uint32_t h = (static_cast<uint32_t>(v) * 0x9E3779B1u) >> 22;
+    for (uint32_t probe = 0; probe < kRowHashSlots; ++probe) {
+        const uint32_t k = insert ? atomicCAS(&keys[h], 0xffffffffu, static_cast<uint32_t>(v)) : keys[h];
+        if (k == static_cast<uint32_t>(v) || (insert && k == 0xffffffffu)) return h;
+        h = (h + 1) & (kRowHashSlots - 1);
+    }
+    return 0;  // not reached
+}
+
+// Dynamic shared memory: two X buffers, a ring of three Y blocks, one G;
+// each 128 x 128 (G) or 128 x d bf16 in the core-matrix layout.
+__host__ __device__ inline uint32_t tile_smem_bytes(int D) { return (2 + 3) * kTileRows * D * 2 + kTileRows * 128 * 2; }
 
 template <int D, class T>
 __global__ void __launch_bounds__(kTileThreads, 1)
     k_sgns_tile(TileArgs a, T *__restrict__ phi_in, T *__restrict__ phi_out) {
     constexpr bool kAsync = std::is_same<T, __nv_bfloat16>::value;
+    constexpr uint32_t kBuf = kTileRows * D * 2;  // one X or Y buffer
+    constexpr uint32_t kXo = 0, kYo = 2 * kBuf, kGo = 5 * kBuf;
     extern __shared__ __align__(1024) uint8_t sm[];
     __shared__ TileStage st_s[2];
-    __shared__ __align__(8) uint64_t bar_s;
+    __shared__ __align__(8) uint64_t bar_s[2];  // [0]: S ready, [1]: dX/dY ready
     __shared__ uint32_t tmem_s;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t base = smem_addr(sm);
-    const uint32_t bar = smem_addr(&bar_s);
-    const int w = a.window, Ns = a.Ns, NY = kTileRows + Ns;
-    const int stages = a.prefetch ? 2 : 1;
-    const uint32_t xbytes = kTileRows * D * 2, sbytes = tile_stage_bytes(D, NY);
-    const uint32_t goff = stages * sbytes;  // G
+    const uint32_t bar_S = smem_addr(&bar_s[0]), bar_D = smem_addr(&bar_s[1]);
+    const int w = a.window, Ns = a.Ns, P = Ns / 128, NB = P + 1;  // column blocks per tile
     const uint64_t nn = static_cast<uint64_t>(a.n), Ssum = *a.S;
     const float omega = static_cast<float>(a.K) / static_cast<float>(Ns);
+    const bool inorder = a.scratch != nullptr;  // tiles strictly in order, dY staged until the tile ends
     // epilogue roles: warps g and g + 4 share TMEM lanes 32g .. 32g + 31
     const int quarter = warp & 3, half = warp >> 2;
     const int q = quarter * 32 + lane;  // row of this thread in the epilogues
-    const int neg_lane0 = 256 - NY;     // dY lane of the first negative (second half of G^T X)
 
-    // Rows, shared negatives and masks of tile t into stage `sg`.
-    auto setup = [&](int sg, int64_t t) {
+    auto tile_of = [&](int64_t B) { return blockIdx.x + (B / NB) * static_cast<int64_t>(gridDim.x); };
+
+    // Rows, shared negatives, masks and row counts of tile t into stage `sg`;
+    // hash_off: a free 8 KB of dynamic shared memory (the Y slot filled next).
+    auto setup = [&](int sg, int64_t t, uint32_t hash_off) {
         TileStage &S = st_s[sg];
         const int64_t pos0 = t * a.Tc - w;  // corpus position of row 0
         if (tid < kTileRows) {
@@ -195,34 +239,34 @@ __global__ void __launch_bounds__(kTileThreads, 1)
             S.node[tid] = v;
             S.lo[tid] = static_cast<int16_t>(lo);
             S.hi[tid] = static_cast<int16_t>(hi);
-            if (tid < 32) S.bloom[tid] = 0;
+            S.bloom[tid] = 0;
         }
         __syncthreads();
-        if (tid >= kTileRows && tid < kTileRows + Ns) {
-            const int j = tid - kTileRows;
+        for (int j = tid; j < Ns; j += kTileThreads) {
             const u32x4 r = philox(a.seed, static_cast<uint32_t>(j), static_cast<uint32_t>(t), a.round, kStreamTile);
             const uint64_t b = mulhi64(lo64(r), nn);
             const uint64_t coin = mulhi64(hi64(r), Ssum);
             const uint64_t th = __ldg(reinterpret_cast<const unsigned long long *>(a.thr) + b);
             const int32_t v = coin < th ? static_cast<int32_t>(b) : __ldg(a.alias + b);
             S.neg[j] = v;
-            atomicOr(&S.bloom[(static_cast<uint32_t>(v) * 0x9E3779B1u) >> 27], 1u << (v & 31));
+            atomicOr(&S.bloom[(static_cast<uint32_t>(v) * 0x9E3779B1u) >> 25], 1u << (v & 31));
         }
         __syncthreads();
         // valid centers, row nodes, and centers equal to a negative (exact
-        // check behind a bloom filter), as 128-bit masks
+        // check behind the bloom filter), as 128-bit masks
         if (tid < kTileRows) {
             const int32_t v = S.node[tid];
             const bool valid = v >= 0 && tid >= w && tid < w + a.Tc;
             bool hit = false;
-            if (valid && (S.bloom[(static_cast<uint32_t>(v) * 0x9E3779B1u) >> 27] >> (v & 31) & 1u)) {
-                uint32_t mw[4] = {0, 0, 0, 0};
-#pragma unroll
-                for (int wd = 0; wd < 4; ++wd)
-                    for (int b = 0; b < 32 && 32 * wd + b < Ns; ++b) mw[wd] |= (S.neg[32 * wd + b] == v ? 1u : 0u) << b;
-                hit = (mw[0] | mw[1] | mw[2] | mw[3]) != 0;
-#pragma unroll
-                for (int wd = 0; wd < 4; ++wd) S.negm[tid][wd] = mw[wd];
+            if (valid && (S.bloom[(static_cast<uint32_t>(v) * 0x9E3779B1u) >> 25] >> (v & 31) & 1u)) {
+                uint32_t any = 0;
+                for (int wd = 0; wd < Ns / 32; ++wd) {
+                    uint32_t mw = 0;
+                    for (int b = 0; b < 32; ++b) mw |= (S.neg[32 * wd + b] == v ? 1u : 0u) << b;
+                    S.negm[tid][wd] = mw;
+                    any |= mw;
+                }
+                hit = any != 0;
             }
             const uint32_t vb = __ballot_sync(kFull, valid), hb = __ballot_sync(kFull, hit);
             const uint32_t nb = __ballot_sync(kFull, v >= 0);
@@ -232,270 +276,379 @@ __global__ void __launch_bounds__(kTileThreads, 1)
                 S.nodem[warp] = nb;
             }
         }
+        // rows per node: the averaging of a node's increments over its rows
+        uint32_t *hkey = reinterpret_cast<uint32_t *>(sm + hash_off);
+        uint32_t *hcnt = hkey + kRowHashSlots;  // rows in phi_in (low 16 bits), phi_out (high 16)
+        for (uint32_t e = tid; e < kRowHashSlots; e += kTileThreads) {
+            hkey[e] = 0xffffffffu;
+            hcnt[e] = 0;
+        }
+        __syncthreads();
+        bool ctx = false, ctr = false;
+        if (tid < kTileRows) {
+            int plo_, phi_;
+            ctx = row_pairs(S, tid, w, a.Tc, plo_, phi_) > 0;
+            ctr = center_used(S, tid, w);
+            if (ctx) atomicAdd(&hcnt[row_hash_slot(hkey, S.node[tid], true)], 1u);
+            if (ctr) atomicAdd(&hcnt[row_hash_slot(hkey, S.node[tid], true)], 1u << 16);
+        }
+        for (int j = tid; j < Ns; j += kTileThreads)
+            atomicAdd(&hcnt[row_hash_slot(hkey, S.neg[j], true)], 1u << 16);
+        __syncthreads();
+        if (tid < kTileRows) {
+            const uint32_t c = (ctx || ctr) ? hcnt[row_hash_slot(hkey, S.node[tid], false)] : 0u;
+            S.rows_x[tid] = ctx ? static_cast<uint16_t>(c & 0xffffu) : 1;
+            S.rows_c[tid] = ctr ? static_cast<uint16_t>(c >> 16) : 1;
+        }
+        for (int j = tid; j < Ns; j += kTileThreads)
+            S.rows_n[j] = static_cast<uint16_t>(hcnt[row_hash_slot(hkey, S.neg[j], false)] >> 16);
+        __syncthreads();  // before the gather reuses the table's memory
     };
 
-    // X (phi_in of positions) and Y (phi_out of centers and negatives) of the
-    // tile in stage `sg` into the core-matrix layout, as bf16: asynchronous
-    // copies for bf16 tables (completed by cp_async_wait_all), converting
-    // loads for float tables.
-    auto gather = [&](int sg) {
-        const TileStage &S = st_s[sg];
-        const uint32_t xo = sg * sbytes, yo = xo + xbytes;
+    // 128 rows into a buffer, as bf16 in the core-matrix layout: kind 0 =
+    // phi_in of the positions (X), 1 = phi_out of the centers (Y, block 0),
+    // 2 = phi_out of negatives 128 (b - 1) .. (Y, block b >= 1).  bf16
+    // tables: asynchronous copies (finished by cp.async waits); float
+    // tables: converting loads.
+    auto gather = [&](uint32_t off, const TileStage &S, int kind, int b) {
         const int r8 = lane & 7, cq = lane >> 3;  // row within group, chunk within 4
         constexpr int kUnitsPerGroup = D / 32;    // 4 chunks of 8 per unit
-        const int units = (kTileRows / 8 + NY / 8) * kUnitsPerGroup;
 #pragma unroll 4
-        for (int u = warp; u < units; u += kTileThreads / 32) {
-            const int gi = u / kUnitsPerGroup, c = ((u % kUnitsPerGroup) * 4 + cq) * 8;
-            const bool isx = gi < kTileRows / 8;
-            const int r = (isx ? gi : gi - kTileRows / 8) * 8 + r8;
+        for (int u = warp; u < 16 * kUnitsPerGroup; u += kTileThreads / 32) {
+            const int r = (u / kUnitsPerGroup) * 8 + r8, c = ((u % kUnitsPerGroup) * 4 + cq) * 8;
             int32_t v;
-            if (isx) v = S.node[r];
-            else if (r < kTileRows) v = (r >= w && r < w + a.Tc) ? S.node[r] : -1;  // centers only
-            else v = S.neg[r - kTileRows];
-            const uint32_t off = isx ? xo + core_offset(r, c, kTileRows) : yo + core_offset(r, c, NY);
-            const T *src = (isx ? phi_in : phi_out) + static_cast<int64_t>(max(v, 0)) * D + c;
+            if (kind == 0) v = S.node[r];
+            else if (kind == 1) v = (r >= w && r < w + a.Tc) ? S.node[r] : -1;  // centers only
+            else v = S.neg[128 * (b - 1) + r];
+            const T *src = (kind == 0 ? phi_in : phi_out) + static_cast<int64_t>(max(v, 0)) * D + c;
+            const uint32_t o = off + core_offset(r, c, kTileRows);
             if constexpr (kAsync) {
-                cp_async16(base + off, src, v >= 0 ? 16u : 0u);
+                cp_async16(base + o, src, v >= 0 ? 16u : 0u);
             } else {
                 uint4 val = make_uint4(0, 0, 0, 0);
                 if (v >= 0) val = ld_row8(src);
-                *reinterpret_cast<uint4 *>(sm + off) = val;
+                *reinterpret_cast<uint4 *>(sm + o) = val;
             }
         }
     };
+    // data of block B: stage, X buffer, Y ring slot
+    auto fetch_block = [&](int64_t B) {
+        const int64_t k = B / NB;
+        const int b = static_cast<int>(B % NB);
+        const TileStage &S = st_s[k & 1];
+        if (b == 0) gather(kXo + (k & 1) * kBuf, S, 0, 0);
+        gather(kYo + (B % 3) * kBuf, S, b == 0 ? 1 : 2, b);
+    };
+    auto issue_s = [&](int64_t B) {  // S_B = X Y_B^T into TMEM region B % 2
+        const uint32_t xs = base + kXo + ((B / NB) & 1) * kBuf, ys = base + kYo + (B % 3) * kBuf;
+#pragma unroll
+        for (int s = 0; s < D / 16; ++s)
+            mma_bf16(tmem_s + (B & 1) * 128, smem_desc(xs + 2 * s * 2048, 2048, 128), smem_desc(ys + 2 * s * 2048, 2048, 128),
+                     mma_idesc_bf16(128, 128, 0, 0), s > 0);
+    };
 
-    if (tid == 0) mbar_init(bar, 1);
+    if (tid == 0) {
+        mbar_init(bar_S, 1);
+        mbar_init(bar_D, 1);
+    }
     if (warp == 0) tmem_alloc(smem_addr(&tmem_s), 512);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tm = tmem_s;
-    const uint32_t lane_base = tm + (static_cast<uint32_t>(quarter * 32) << 16);
-    uint32_t phase = 0;
+    const uint32_t lane_off = static_cast<uint32_t>(quarter * 32) << 16;
+    const uint32_t tdx = tm + lane_off + 256;  // dX of this thread's row
+    uint32_t ph_S = 0, ph_D = 0;
     double loss = 0.0;
     bool failed = false;
+    const int64_t n_blocks = ((a.n_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x) * NB;  // this CTA's blocks
 
-    int64_t t = blockIdx.x;
-    if (t < a.n_tiles) {
-        setup(0, t);
-        gather(0);
+    // per-row state of the current tile (set by block 0)
+    int32_t vq = -1;
+    int plo = 0, phi = -1, cnt = 0;
+    bool any_hit = false;
+    uint32_t sr = 1;
+    float eta = 0.f;
+
+    if (n_blocks > 0) {
+        setup(0, tile_of(0), kYo);
+        fetch_block(0);
+        if (!inorder && n_blocks > 1) fetch_block(1);
         if constexpr (kAsync) cp_async_wait_all();
         fence_async_smem();
         __syncthreads();
-    }
-    for (int sg = 0; t < a.n_tiles; t += gridDim.x, sg ^= (stages - 1)) {
-        const TileStage &S = st_s[sg];
-        const uint32_t xs = base + sg * sbytes, ys = xs + xbytes, gs = base + goff;
-        const int64_t tn = t + gridDim.x;  // this CTA's next tile
-        // ---- S = X Y^T ---------------------------------------------------------
         tc_fence_after();
         if (tid == 0) {
-#pragma unroll
-            for (int s = 0; s < D / 16; ++s)
-                mma_bf16(tm, smem_desc(xs + 2 * s * (kTileRows * 16), kTileRows * 16, 128),
-                         smem_desc(ys + 2 * s * (NY * 16), NY * 16, 128), mma_idesc_bf16(128, NY, 0, 0), s > 0);
-            mma_commit(bar);
+            issue_s(0);
+            mma_commit(bar_S);
         }
-        // ---- meanwhile: the next tile's rows into the other stage --------------
-        if (stages == 2 && tn < a.n_tiles) {
-            setup(sg ^ 1, tn);
-            gather(sg ^ 1);
-        }
-        failed = !mbar_wait(bar, phase, kTileWaitLimit);
-        phase ^= 1;
+    }
+    for (int64_t B = 0; B < n_blocks; ++B) {
+        const int64_t k = B / NB, t = tile_of(B);
+        const int b = static_cast<int>(B % NB);
+        const TileStage &S = st_s[k & 1];
+        const uint32_t xo = kXo + (k & 1) * kBuf, yo = kYo + (B % 3) * kBuf;
+        const uint32_t treg = tm + lane_off + (B & 1) * 128;  // S_B, then dY_B
+        failed = !mbar_wait(bar_S, ph_S, kTileWaitLimit);
+        ph_S ^= 1;
         tc_fence_after();
         if (__syncthreads_or(failed)) break;
-        // ---- epilogue: gradient G (bf16).  Row q pairs with the centers
-        //      p in [plo, phi] \ {q} whose node is >= 0 ----------------------------
-        const int32_t vq = S.node[q];
-        const float eta = static_cast<float>(
-            static_cast<double>(a.lr0) *
-            fmax(1e-4, 1.0 - static_cast<double>(a.clock_base + t * a.Tc) * a.inv_total));
-        int plo = max(max(q - w, w), static_cast<int>(S.lo[q]));
-        int phi = min(min(q + w, w + a.Tc - 1), static_cast<int>(S.hi[q]));
-        if (vq < 0) phi = plo - 1;
-        uint32_t vm[4], hm[4], nm[4];
+        // ---- epilogue 1: G = gradient of block b's scores (bf16) --------------
+        if (b == 0) {
+            vq = S.node[q];
+            eta = static_cast<float>(static_cast<double>(a.lr0) *
+                                     fmax(1e-4, 1.0 - static_cast<double>(a.clock_base + t * a.Tc) * a.inv_total));
+            cnt = row_pairs(S, q, w, a.Tc, plo, phi);
+            uint32_t hm[4];
 #pragma unroll
-        for (int wd = 0; wd < 4; ++wd) {
-            vm[wd] = S.valid[wd];
-            hm[wd] = S.hitm[wd];
-            nm[wd] = S.nodem[wd];
+            for (int wd = 0; wd < 4; ++wd) hm[wd] = S.hitm[wd];
+            const bool q_in = q >= plo && q <= phi;
+            any_hit = popc_range(hm, plo, phi) - (q_in ? static_cast<int>(S.hitm[q >> 5] >> (q & 31) & 1u) : 0) > 0;
+            const u32x4 rw = philox(a.seed, static_cast<uint32_t>(t), static_cast<uint32_t>(q | (half << 8)), a.round, kStreamSR);
+            sr = rw.x | 1u;
         }
-        const bool q_in = q >= plo && q <= phi;
-        const int cnt = popc_range(vm, plo, phi) - (q_in ? static_cast<int>(S.valid[q >> 5] >> (q & 31) & 1u) : 0);
-        const bool any_hit = popc_range(hm, plo, phi) - (q_in ? static_cast<int>(S.hitm[q >> 5] >> (q & 31) & 1u) : 0) > 0;
         float row_loss = 0.f;
-        // positive band, columns 32c .. 32c+31: half 0 takes the warp's own
-        // chunk, half 1 the other three (two band edges and a zero chunk).
-        // Scores outside a row's pairs get coefficient 0 (no branches).
+        if (b == 0) {
+            // positive band, columns 32c .. 32c+31: half 0 takes the warp's own
+            // chunk, half 1 the other three (two band edges and a zero chunk).
+            // Scores outside a row's pairs get coefficient 0 (no branches).
 #pragma unroll 1
-        for (int c = 0; c < 4; ++c) {
-            if ((c == quarter) != (half == 0)) continue;  // warp-uniform
-            uint32_t packed[16];
-            if (c >= quarter - 1 && c <= quarter + 1) {
+            for (int c = 0; c < 4; ++c) {
+                if ((c == quarter) != (half == 0)) continue;  // warp-uniform
+                uint32_t packed[16];
+                if (c >= quarter - 1 && c <= quarter + 1) {
+                    uint32_t r[32];
+                    tmem_ld32(treg + 32 * c, r);
+                    uint32_t pm = S.valid[c];  // pairs of row q among columns 32c .. 32c+31
+                    const int a0 = plo - 32 * c, b0 = phi - 32 * c;
+                    pm &= (a0 <= 0 ? 0xffffffffu : (a0 >= 32 ? 0u : (0xffffffffu << a0)));
+                    pm &= (b0 >= 31 ? 0xffffffffu : (b0 < 0 ? 0u : (0xffffffffu >> (31 - b0))));
+                    if (q >= 32 * c && q < 32 * c + 32) pm &= ~(1u << (q - 32 * c));
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int i = 0; i < 32; i += 2) {
+                        float g2[2];
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const float on = static_cast<float>(pm >> (i + h) & 1u);
+                            const float s = __uint_as_float(r[i + h]);
+                            float sig, l1p;
+                            sigmoid_softplus(s, sig, l1p);
+                            g2[h] = on * eta * (1.f - sig);
+                            row_loss += on * (fmaxf(-s, 0.f) + l1p);  // -log sigma(s)
+                        }
+                        __nv_bfloat162 hv = __floats2bfloat162_rn(g2[0], g2[1]);
+                        packed[i / 2] = *reinterpret_cast<uint32_t *>(&hv);
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) packed[i] = 0;
+                }
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                    *reinterpret_cast<uint4 *>(sm + kGo + core_offset(q, 32 * c + 8 * kk, kTileRows)) =
+                        make_uint4(packed[4 * kk], packed[4 * kk + 1], packed[4 * kk + 2], packed[4 * kk + 3]);
+            }
+        } else {
+            // shared negatives 128 (b - 1) + 32c + i: half 0 chunks 0 and 2, half 1 chunks 1 and 3
+#pragma unroll 1
+            for (int c = half; c < 4; c += 2) {
                 uint32_t r[32];
-                tmem_ld32(lane_base + 32 * c, r);
-                // pairs of row q among columns 32c .. 32c+31
-                uint32_t pm = S.valid[c];
-                const int a0 = plo - 32 * c, b0 = phi - 32 * c;
-                pm &= (a0 <= 0 ? 0xffffffffu : (a0 >= 32 ? 0u : (0xffffffffu << a0)));
-                pm &= (b0 >= 31 ? 0xffffffffu : (b0 < 0 ? 0u : (0xffffffffu >> (31 - b0))));
-                if (q >= 32 * c && q < 32 * c + 32) pm &= ~(1u << (q - 32 * c));
+                tmem_ld32(treg + 32 * c, r);
+                float mk[32];  // pairs of row q that count this negative
+#pragma unroll
+                for (int i = 0; i < 32; ++i) mk[i] = static_cast<float>(cnt);
+                if (any_hit) {  // pairs whose center is this negative do not count
+                    const int word = 4 * (b - 1) + c;
+#pragma unroll
+                    for (int wd = 0; wd < 4; ++wd) {
+                        const int a0 = plo - 32 * wd, b0 = phi - 32 * wd;
+                        uint32_t hb = S.hitm[wd];
+                        hb &= (a0 <= 0 ? 0xffffffffu : (a0 >= 32 ? 0u : (0xffffffffu << a0)));
+                        hb &= (b0 >= 31 ? 0xffffffffu : (b0 < 0 ? 0u : (0xffffffffu >> (31 - b0))));
+                        if ((q >> 5) == wd) hb &= ~(1u << (q & 31));
+                        while (hb) {
+                            const int p = 32 * wd + __ffs(hb) - 1;
+                            hb &= hb - 1;
+                            const uint32_t mw = S.negm[p][word];
+#pragma unroll
+                            for (int i = 0; i < 32; ++i) mk[i] -= static_cast<float>(mw >> i & 1u);
+                        }
+                    }
+                }
                 tmem_wait_ld();
+                uint32_t packed[16];
 #pragma unroll
                 for (int i = 0; i < 32; i += 2) {
                     float g2[2];
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
-                        const float on = static_cast<float>(pm >> (i + h) & 1u);
                         const float s = __uint_as_float(r[i + h]);
                         float sig, l1p;
                         sigmoid_softplus(s, sig, l1p);
-                        g2[h] = on * eta * (1.f - sig);
-                        row_loss += on * (fmaxf(-s, 0.f) + l1p);  // -log sigma(s)
+                        g2[h] = -eta * omega * mk[i + h] * sig;
+                        row_loss += omega * mk[i + h] * (fmaxf(s, 0.f) + l1p);  // -log sigma(-s)
                     }
                     __nv_bfloat162 hv = __floats2bfloat162_rn(g2[0], g2[1]);
                     packed[i / 2] = *reinterpret_cast<uint32_t *>(&hv);
                 }
-            } else {
 #pragma unroll
-                for (int i = 0; i < 16; ++i) packed[i] = 0;
+                for (int kk = 0; kk < 4; ++kk)
+                    *reinterpret_cast<uint4 *>(sm + kGo + core_offset(q, 32 * c + 8 * kk, kTileRows)) =
+                        make_uint4(packed[4 * kk], packed[4 * kk + 1], packed[4 * kk + 2], packed[4 * kk + 3]);
             }
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                *reinterpret_cast<uint4 *>(sm + goff + core_offset(q, 32 * c + 8 * k, kTileRows)) =
-                    make_uint4(packed[4 * k], packed[4 * k + 1], packed[4 * k + 2], packed[4 * k + 3]);
-        }
-#pragma unroll 1
-        for (int c = half; c < Ns / 32; c += 2) {  // shared negatives, columns 128 + 32c ..
-            uint32_t r[32];
-            tmem_ld32(lane_base + kTileRows + 32 * c, r);
-            float mk[32];  // pair count of row q that counts negative 32c + i
-#pragma unroll
-            for (int i = 0; i < 32; ++i) mk[i] = static_cast<float>(cnt);
-            if (any_hit) {  // pairs whose center is this negative do not count
-#pragma unroll
-                for (int wd = 0; wd < 4; ++wd) {
-                    const int a0 = plo - 32 * wd, b0 = phi - 32 * wd;
-                    uint32_t hb = hm[wd];
-                    hb &= (a0 <= 0 ? 0xffffffffu : (a0 >= 32 ? 0u : (0xffffffffu << a0)));
-                    hb &= (b0 >= 31 ? 0xffffffffu : (b0 < 0 ? 0u : (0xffffffffu >> (31 - b0))));
-                    if ((q >> 5) == wd) hb &= ~(1u << (q & 31));
-                    while (hb) {
-                        const int p = 32 * wd + __ffs(hb) - 1;
-                        hb &= hb - 1;
-                        const uint32_t mw = S.negm[p][c];
-#pragma unroll
-                        for (int i = 0; i < 32; ++i) mk[i] -= static_cast<float>(mw >> i & 1u);
-                    }
-                }
-            }
-            tmem_wait_ld();
-            uint32_t packed[16];
-#pragma unroll
-            for (int i = 0; i < 32; i += 2) {
-                float g2[2];
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const float s = __uint_as_float(r[i + h]);
-                    float sig, l1p;
-                    sigmoid_softplus(s, sig, l1p);
-                    g2[h] = -eta * omega * mk[i + h] * sig;
-                    row_loss += omega * mk[i + h] * (fmaxf(s, 0.f) + l1p);  // -log sigma(-s)
-                }
-                __nv_bfloat162 hv = __floats2bfloat162_rn(g2[0], g2[1]);
-                packed[i / 2] = *reinterpret_cast<uint32_t *>(&hv);
-            }
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                *reinterpret_cast<uint4 *>(sm + goff + core_offset(q, kTileRows + 32 * c + 8 * k, kTileRows)) =
-                    make_uint4(packed[4 * k], packed[4 * k + 1], packed[4 * k + 2], packed[4 * k + 3]);
         }
         loss += static_cast<double>(row_loss);
-        fence_async_smem();
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        // ---- dX = G Y, dY = G^T X (second half: j in [NY - 128, NY)) --------
-        if (tid == 0) {
-            for (int s = 0; s < NY / 16; ++s)
-                mma_bf16(tm + 256, smem_desc(gs + 2 * s * (kTileRows * 16), kTileRows * 16, 128),
-                         smem_desc(ys + 2 * s * 128, 128, NY * 16), mma_idesc_bf16(128, D, 0, 1), s > 0);
-            for (int h = 0; h < 2; ++h) {
-                const uint32_t g0 = gs + (h ? (NY - kTileRows) / 8 : 0) * (kTileRows * 16);
-#pragma unroll
-                for (int s = 0; s < kTileRows / 16; ++s)
-                    mma_bf16(tm + h * D, smem_desc(g0 + 2 * s * 128, 128, kTileRows * 16),
-                             smem_desc(xs + 2 * s * 128, 128, kTileRows * 16), mma_idesc_bf16(128, D, 1, 1), s > 0);
-            }
-            mma_commit(bar);
-        }
-        failed = !mbar_wait(bar, phase, kTileWaitLimit);
-        phase ^= 1;
-        tc_fence_after();
-        if (__syncthreads_or(failed)) break;
-        // ---- add the increments to the tables: half 0 adds dX of row q and dY
-        //      of negative q - (256 - NY), half 1 dY of position q -------------
-        {
-            const u32x4 rw = philox(a.seed, static_cast<uint32_t>(t), static_cast<uint32_t>(q), a.round, kStreamSR);
-            uint32_t sr0 = (half ? rw.z : rw.x) | 1u, sr1 = rw.y | 1u;
-            // position q is a center of some pair iff it is a valid center with
-            // another node of its walk within w; a negative row is always added
-            // (a zero increment leaves a table unchanged)
-            bool first;
-            if (half == 0) {
-                first = vq >= 0 && cnt > 0;
-            } else {
-                const bool vc = S.valid[q >> 5] >> (q & 31) & 1u;
-                const int clo = max(q - w, static_cast<int>(S.lo[q])), chi = min(q + w, static_cast<int>(S.hi[q]));
-                first = vc && popc_range(nm, clo, chi) > 1;
-            }
-            const int jn = q - neg_lane0;  // negative held by this TMEM lane
-            const bool second = half == 0 && jn >= 0;
-            T *p1 = (half == 0 ? phi_in : phi_out) + static_cast<int64_t>(max(vq, 0)) * D;
-            T *p2 = phi_out + static_cast<int64_t>(jn >= 0 ? S.neg[jn] : 0) * D;
-            const uint32_t t1 = half == 0 ? lane_base + 256 : lane_base;  // dX or dY(positions)
-            const uint32_t s1 = half == 0 ? xs - base : ys - base;
-            const int R1 = half == 0 ? kTileRows : NY;
-#pragma unroll 1
-            for (int c = 0; c < D / 32; ++c) {
-                uint32_t r1[32], r2[32];
-                tmem_ld32(t1 + 32 * c, r1);
-                if (half == 0) tmem_ld32(lane_base + D + 32 * c, r2);
-                tmem_wait_ld();
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const int col = 32 * c + 8 * k;
-                    float d8[8];
-                    if (first) {
-                        const uint4 snap = *reinterpret_cast<const uint4 *>(sm + s1 + core_offset(q, col, R1));
-#pragma unroll
-                        for (int i = 0; i < 8; ++i) d8[i] = __uint_as_float(r1[8 * k + i]);
-                        add8(p1 + col, d8, snap, xorshift32(sr0));
-                    }
-                    if (second) {
-                        const uint4 snap =
-                            *reinterpret_cast<const uint4 *>(sm + (ys - base) + core_offset(kTileRows + jn, col, NY));
-#pragma unroll
-                        for (int i = 0; i < 8; ++i) d8[i] = __uint_as_float(r2[8 * k + i]);
-                        add8(p2 + col, d8, snap, xorshift32(sr1));
-                    }
-                }
-            }
-        }
-        // ---- the next tile: with one stage its rows are read only now, after
-        //      these reductions (tiles strictly in order) ------------------------
-        if (stages == 1 && tn < a.n_tiles) {
-            __threadfence();
-            __syncthreads();
-            setup(0, tn);
-            gather(0);
-        }
+        // the next block's rows must have landed before its S is issued
         if constexpr (kAsync) cp_async_wait_all();
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
+        tc_fence_after();
+        // ---- dX (+)= G Y_b; dY_b = G^T X; then S of the next block -----------
+        const bool has_next = B + 1 < n_blocks;
+        const bool next_is_new_tile = (B + 1) % NB == 0;
+        if (tid == 0) {
+            const uint32_t gs = base + kGo, xs = base + xo, ys = base + yo;  // G, X, Y_b
+#pragma unroll
+            for (int s = 0; s < 8; ++s)
+                mma_bf16(tm + 256, smem_desc(gs + 2 * s * 2048, 2048, 128), smem_desc(ys + 2 * s * 128, 128, 2048),
+                         mma_idesc_bf16(128, D, 0, 1), b > 0 || s > 0);
+#pragma unroll
+            for (int s = 0; s < 8; ++s)
+                mma_bf16(tm + (B & 1) * 128, smem_desc(gs + 2 * s * 128, 128, 2048), smem_desc(xs + 2 * s * 128, 128, 2048),
+                         mma_idesc_bf16(128, D, 1, 1), s > 0);
+            mma_commit(bar_D);
+            if (has_next && !inorder) {  // its rows landed before the barrier above
+                issue_s(B + 1);
+                mma_commit(bar_S);
+            }
+        }
+        // ---- meanwhile: rows of block B + 2 (a new tile's setup first) -------
+        if (!inorder && B + 2 < n_blocks) {
+            if ((B + 2) % NB == 0) setup(((B + 2) / NB) & 1, tile_of(B + 2), kYo + ((B + 2) % 3) * kBuf);
+            fetch_block(B + 2);
+        } else if (inorder && has_next && !next_is_new_tile) {
+            fetch_block(B + 1);  // in order: the next block of this tile; its S is issued after epilogue 2
+        }
+        failed = !mbar_wait(bar_D, ph_D, kTileWaitLimit);
+        ph_D ^= 1;
+        tc_fence_after();
+        if (__syncthreads_or(failed)) break;
+        // ---- epilogue 2: add dY_b (and dX at the tile's last block) ------------
+        {
+            const int c0 = half == 0 ? 0 : (D / 32 + 1) / 2, c1 = half == 0 ? (D / 32 + 1) / 2 : D / 32;
+            bool use;
+            T *prow;
+            float scale;  // 1 / rows of this node in phi_out in this tile
+            if (b == 0) {  // center q: used iff it takes part in a pair
+                use = center_used(S, q, w);
+                prow = phi_out + static_cast<int64_t>(max(S.node[q], 0)) * D;
+                scale = 1.f / static_cast<float>(S.rows_c[q]);
+            } else {  // a negative row is always added (a zero increment changes nothing)
+                use = true;
+                prow = phi_out + static_cast<int64_t>(S.neg[128 * (b - 1) + q]) * D;
+                scale = 1.f / static_cast<float>(S.rows_n[128 * (b - 1) + q]);
+            }
+            float *scr = inorder ? a.scratch + (static_cast<int64_t>(b) * kTileRows + q) * D : nullptr;
+#pragma unroll 1
+            for (int c = c0; c < c1; ++c) {
+                uint32_t r[32];
+                tmem_ld32(treg + 32 * c, r);
+                tmem_wait_ld();
+                if (!use) continue;
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    const int col = 32 * c + 8 * kk;
+                    float d8[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) d8[i] = scale * __uint_as_float(r[8 * kk + i]);
+                    if (inorder) {
+                        *reinterpret_cast<float4 *>(scr + col) = make_float4(d8[0], d8[1], d8[2], d8[3]);
+                        *reinterpret_cast<float4 *>(scr + col + 4) = make_float4(d8[4], d8[5], d8[6], d8[7]);
+                    } else {
+                        const uint4 snap = *reinterpret_cast<const uint4 *>(sm + yo + core_offset(q, col, kTileRows));
+                        add8(prow + col, d8, snap, xorshift32(sr));
+                    }
+                }
+            }
+            if (inorder && !use) {
+                for (int c = c0; c < c1; ++c)
+                    for (int col = 32 * c; col < 32 * c + 32; col += 4)
+                        *reinterpret_cast<float4 *>(scr + col) = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            if (b == NB - 1) {  // dX of row q
+                const bool ux = vq >= 0 && cnt > 0;
+                T *px = phi_in + static_cast<int64_t>(max(vq, 0)) * D;
+                const float sx = 1.f / static_cast<float>(S.rows_x[q]);
+#pragma unroll 1
+                for (int c = c0; c < c1; ++c) {
+                    uint32_t r[32];
+                    tmem_ld32(tdx + 32 * c, r);
+                    tmem_wait_ld();
+                    if (!ux) continue;
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const int col = 32 * c + 8 * kk;
+                        float d8[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) d8[i] = sx * __uint_as_float(r[8 * kk + i]);
+                        const uint4 snap = *reinterpret_cast<const uint4 *>(sm + xo + core_offset(q, col, kTileRows));
+                        add8(px + col, d8, snap, xorshift32(sr));
+                    }
+                }
+            }
+        }
+        // ---- in order: at the tile's end add the staged dY rows, then read
+        //      the next tile (which sees every update of this one) -------------
+        if (inorder && b == NB - 1) {
+            __syncthreads();
+            for (int e = tid; e < NB * kTileRows * (D / 8); e += kTileThreads) {
+                const int bb = e / (kTileRows * (D / 8)), row = (e / (D / 8)) % kTileRows, col = (e % (D / 8)) * 8;
+                int32_t v;
+                if (bb == 0) v = (row >= w && row < w + a.Tc) ? S.node[row] : -1;
+                else v = S.neg[128 * (bb - 1) + row];
+                if (v < 0) continue;
+                const float *src = a.scratch + (static_cast<int64_t>(bb) * kTileRows + row) * D + col;
+                float d8[8];
+                bool nz = false;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    d8[i] = src[i];
+                    nz |= d8[i] != 0.f;
+                }
+                if (!nz) continue;
+                T *p = phi_out + static_cast<int64_t>(v) * D + col;
+                add8(p, d8, ld_row8_raw(p), xorshift32(sr));
+            }
+            __threadfence();
+            __syncthreads();
+            if (has_next) {
+                setup((k + 1) & 1, tile_of(B + 1), kYo + ((B + 1) % 3) * kBuf);
+                fetch_block(B + 1);
+                if constexpr (kAsync) cp_async_wait_all();
+                fence_async_smem();
+                tc_fence_before();
+                __syncthreads();
+                tc_fence_after();
+                if (tid == 0) {
+                    issue_s(B + 1);
+                    mma_commit(bar_S);
+                }
+            }
+        } else if (inorder && has_next) {
+            // the next block of this tile was fetched above; issue its S now
+            if constexpr (kAsync) cp_async_wait_all();
+            fence_async_smem();
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+            if (tid == 0) {
+                issue_s(B + 1);
+                mma_commit(bar_S);
+            }
+        }
+        tc_fence_before();
     }
     if constexpr (kAsync) cp_async_wait_all();  // none left in flight, also after a timeout
     if (failed && tid == 0) atomicExch(a.timeout, 1);
@@ -511,12 +664,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
 template <int D, class T>
 static felog_status launch_tile_dim(TileArgs a, int ctas, void *pi, void *po, cudaStream_t s) {
     auto kern = k_sgns_tile<D, T>;
-    const int NY = kTileRows + a.Ns;
-    // two stages (next tile gathered during this one) for bf16 tables when
-    // tiles may overlap and the buffers fit; one stage keeps tiles in order
-    a.prefetch = std::is_same<T, __nv_bfloat16>::value && ctas > 1 &&
-                 tile_smem_bytes(D, NY, 2) + sizeof(TileStage) * 2 + 1024 <= 227 * 1024;
-    const int bytes = static_cast<int>(tile_smem_bytes(D, NY, a.prefetch ? 2 : 1));
+    const int bytes = static_cast<int>(std::max<uint32_t>(tile_smem_bytes(D), 122880));
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return record_cuda_error(e, "felog_train (tile)");
     kern<<<ctas, kTileThreads, bytes, s>>>(a, static_cast<T *>(pi), static_cast<T *>(po));
@@ -530,14 +678,18 @@ static felog_status launch_tile_dim(TileArgs a, int ctas, void *pi, void *po, cu
 // does); at most n / kTileRowsPerCta tiles run at once.
 constexpr int64_t kTileRowsPerCta = 2048;
 
+// Floats of the in-order form's staging buffer (dY of one tile's blocks).
+size_t tile_scratch_floats() { return static_cast<size_t>(kMaxNegBlocks + 1) * kTileRows * 128; }
+
 // Launches the tile trainer over walks[n_walks][L]; called by felog_train
 // after argument checks.  tile_ctas <= 0: min(SMs, max(1, n / 2048)) tiles
-// at once; 1 runs the tiles in order (the reproducible form).
+// at once; 1 runs the tiles in order (the reproducible form, which stages
+// each tile's dY rows in `scratch`, tile_scratch_floats() floats).
 felog_status launch_tile(const int32_t *walks, int64_t n_walks, int32_t L, int32_t n,
                          const felog_train_params *tp, const uint64_t *thr, const int32_t *alias,
                          const uint64_t *S, uint64_t seed, int32_t round, int64_t clock_base,
                          void *phi_in, void *phi_out, unsigned long long *loss_acc, int32_t *timeout,
-                         cudaStream_t s) {
+                         float *scratch, cudaStream_t s) {
     TileArgs a;
     a.walks = walks;
     a.total = n_walks * L;
@@ -545,7 +697,7 @@ felog_status launch_tile(const int32_t *walks, int64_t n_walks, int32_t L, int32
     a.n = n;
     a.window = tp->window;
     a.K = tp->negatives;
-    a.Ns = tp->tile_negatives > 0 ? tp->tile_negatives : 64;
+    a.Ns = tp->tile_negatives > 0 ? tp->tile_negatives : kMaxNs;
     a.Tc = kTileRows - 2 * tp->window;
     a.n_tiles = (a.total + a.Tc - 1) / a.Tc;
     a.lr0 = tp->lr0;
@@ -564,6 +716,7 @@ felog_status launch_tile(const int32_t *walks, int64_t n_walks, int32_t L, int32
                    ? std::min(tp->tile_ctas, sm_count())
                    : static_cast<int>(std::min<int64_t>(sm_count(), std::max<int64_t>(1, n / kTileRowsPerCta)));
     ctas = static_cast<int>(std::min<int64_t>(ctas, a.n_tiles));
+    a.scratch = ctas == 1 ? scratch : nullptr;  // one CTA: tiles strictly in order
     const bool f32 = tp->precision == FELOG_FP32;
     switch (tp->dim) {
         case 32: return f32 ? launch_tile_dim<32, float>(a, ctas, phi_in, phi_out, s)

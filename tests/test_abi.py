@@ -49,9 +49,9 @@ def test_host_side_argument_checks(lib):
     assert lib.felog_train_workspace_bytes(1, 40, 10, ctypes.byref(bad)) == 0
     good = felog._TrainParams(64, 5, 5, 0.025, 1, 0, 1, 0, 0, 0)
     assert lib.felog_train_workspace_bytes(1, 40, 10, ctypes.byref(good)) > 0
-    # TILE mode: dim <= 128, tile_negatives a multiple of 32 in [32, 128] (0 = 64)
-    for dim, ns, ok in [(128, 0, True), (64, 128, True), (32, 32, True), (256, 0, False),
-                        (128, 48, False), (128, 160, False), (128, 16, False)]:
+    # TILE mode: dim <= 128, tile_negatives a multiple of 128 in [128, 512] (0 = 512)
+    for dim, ns, ok in [(128, 0, True), (64, 128, True), (32, 512, True), (128, 384, True),
+                        (256, 0, False), (128, 64, False), (128, 640, False), (128, 200, False)]:
         tp = felog.train_params(dim, 5, 5, 0.025, 1, felog.FELOG_SGNS_TILE, 1, 0, tile_negatives=ns)
         assert (lib.felog_train_workspace_bytes(1, 40, 10, ctypes.byref(tp)) > 0) == ok, (dim, ns)
     wp = felog._WalkParams(0, 1)  # zero-length walks rejected

@@ -72,16 +72,18 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-@pytest.mark.parametrize("dim,window,Ns,prec,pad", [(128, 10, 64, 0, False), (64, 5, 128, 1, True),
-                                                    (32, 16, 32, 0, True), (128, 3, 96, 1, False)])
-def test_tile_loss_matches_oracle_at_fixed_tables(fl, orc, sbm, dim, window, Ns, prec, pad):
+@pytest.mark.parametrize("dim,window,Ns,prec,pad,ctas", [(128, 10, 512, 0, False, 8), (64, 5, 128, 1, True, 0),
+                                                         (32, 16, 256, 0, True, 8), (128, 3, 384, 1, False, 4),
+                                                         (64, 10, 512, 1, True, 1)])
+def test_tile_loss_matches_oracle_at_fixed_tables(fl, orc, sbm, dim, window, Ns, prec, pad, ctas):
+    """Both the in-order form (one CTA) and the pipelined form (several)."""
     g = sbm
     L, K = 40, 5
-    W, thr, alias, S = _corpus(orc, g, L, SEED, 1, n_starts=300, pad=pad)
+    W, thr, alias, S = _corpus(orc, g, L, SEED, 1, n_starts=120, pad=pad)
     ri, ro = _tables(g.n, dim, 3)
     pi, po = _to_dev(fl, ri, prec), _to_dev(fl, ro, prec)
     tp = fl.train_params(dim, window, K, 0.0, 10 ** 9, fl.FELOG_SGNS_TILE, 1, prec,
-                         tile_negatives=Ns, tile_ctas=0)
+                         tile_negatives=Ns, tile_ctas=ctas)
     lg = _train(fl, W, thr, alias, S, g.n, tp, SEED, 1, 0, pi, po)
     lo = orc.sgns_tile(W, g.n, dim, window, K, 0.0, 10 ** 9, 128 - 2 * window, Ns, thr, alias, S,
                        SEED, 1, 0, ri, ro)
@@ -91,13 +93,13 @@ def test_tile_loss_matches_oracle_at_fixed_tables(fl, orc, sbm, dim, window, Ns,
     assert np.array_equal(po.double().cpu().numpy(), ro)
 
 
-@pytest.mark.parametrize("dim,window,Ns", [(128, 10, 64), (64, 5, 128), (32, 8, 32)])
+@pytest.mark.parametrize("dim,window,Ns", [(128, 10, 512), (64, 5, 128), (32, 8, 256)])
 def test_tile_serial_fp32_tracks_oracle(fl, orc, sbm, dim, window, Ns):
     """Tiles one at a time (tile_ctas = 1) is the oracle's order: the loss
     and the table increments agree up to the bf16 gradient operand."""
     g = sbm
     L, K = 40, 5
-    W, thr, alias, S = _corpus(orc, g, L, SEED, 0, n_starts=200, pad=True)
+    W, thr, alias, S = _corpus(orc, g, L, SEED, 0, n_starts=100, pad=True)
     ri0, ro0 = _tables(g.n, dim, 4)
     ri, ro = ri0.copy(), ro0.copy()
     pi, po = _to_dev(fl, ri0, 0), _to_dev(fl, ro0, 0)
@@ -121,8 +123,8 @@ def test_tile_serial_bf16_tracks_oracle(fl, orc, sbm):
     0.4 % of a value, per update; some 20 updates per element in this
     round), so they are held to 1.5 % in norm."""
     g = sbm
-    dim, window, K, Ns = 128, 10, 5, 64
-    W, thr, alias, S = _corpus(orc, g, 40, SEED, 2, n_starts=200)
+    dim, window, K, Ns = 128, 10, 5, 512
+    W, thr, alias, S = _corpus(orc, g, 40, SEED, 2, n_starts=100)
     ri0, ro0 = _tables(g.n, dim, 5)
     ri, ro = ri0.copy(), ro0.copy()
     pi, po = _to_dev(fl, ri0, 1), _to_dev(fl, ro0, 1)
@@ -146,8 +148,8 @@ def test_tile_parallel_round_close_to_serial(fl, orc):
     quality of this form is judged by link AUC); here the round must stay
     stable: loss within 10 % of the oracle's, increments of the same size."""
     g = inputs.rmat(16, 16, seed=3)
-    dim, window, K, Ns = 64, 10, 5, 64
-    W, thr, alias, S = _corpus(orc, g, 80, SEED, 0, n_starts=1000)
+    dim, window, K, Ns = 64, 10, 5, 512
+    W, thr, alias, S = _corpus(orc, g, 80, SEED, 0, n_starts=300)
     ri0, ro0 = _tables(g.n, dim, 6, scale=0.05)
     ri, ro = ri0.copy(), ro0.copy()
     pi, po = _to_dev(fl, ri0, 0), _to_dev(fl, ro0, 0)
