@@ -131,7 +131,15 @@ def _peaks():
         return 6400.0, "fallback"
 
 
-def _profile_traffic(kernel_src):
+def _kernel_source_hash(paths):
+    h = hashlib.sha256()
+    for p in paths:
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _profile_traffic(kernel_srcs):
     """DRAM bytes per launch of the SGNS kernel from the committed ncu
     summary, or None when the kernel source changed since the capture."""
     path = os.path.join(ROOT, "profiles", "sgns_hogwild_rmat20_fp32.md")
@@ -139,13 +147,13 @@ def _profile_traffic(kernel_src):
         txt = open(path).read()
     except OSError:
         return None
-    src_hash = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    src_hash = _kernel_source_hash(kernel_srcs)
     vals = {}
     for line in txt.splitlines():
         if ":" in line and line.strip().startswith("- "):
             k, v = line.strip()[2:].split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
-    if vals.get("sgns.cu sha256[:16]") != src_hash:
+    if vals.get("sgns.cu + sgns_core.cuh sha256[:16]") != src_hash:
         return None
     try:
         return float(vals["dram_bytes_per_full_launch"])
@@ -334,7 +342,8 @@ def run_native(args):
     alg_bytes = row * (4 * n_live * WPR * L + 2 * NEG * pairs)
     achieved = alg_bytes / (phase["train"] / 1e3) / 1e9
     peak, peak_kind = _peaks()
-    traffic = _profile_traffic(os.path.join(ROOT, "paper_2606_22180_b300", "csrc", "sgns.cu"))
+    csrc = os.path.join(ROOT, "paper_2606_22180_b300", "csrc")
+    traffic = _profile_traffic([os.path.join(csrc, "sgns.cu"), os.path.join(csrc, "sgns_core.cuh")])
     if args.precision != "fp32" or args.scale != SCALE:
         traffic = None  # the committed capture is of the fp32 launch at scale 20
 
