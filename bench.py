@@ -150,8 +150,8 @@ def _profile_traffic(kernel_srcs):
     src_hash = _kernel_source_hash(kernel_srcs)
     vals = {}
     for line in txt.splitlines():
-        if ":" in line and line.strip().startswith("- "):
-            k, v = line.strip()[2:].split(":", 1)
+        if ": " in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(": ", 1)
             vals[k.strip()] = v.strip().strip("`")
     if vals.get("sgns.cu + sgns_core.cuh sha256[:16]") != src_hash:
         return None
