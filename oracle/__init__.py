@@ -68,6 +68,9 @@ def lib() -> ctypes.CDLL:
             "oracle_tile_negatives": (None, [P, P, i32, u64, u64, i32, i64, i32, P]),
             "oracle_sgns_tile": (f64, [P, i64, i32, i32, P, i32, i32, i32, P, P, u64, u64, i32,
                                        i64, P, P, P]),
+            "oracle_fabc_select": (i32, [P, i32, i32, i32, P, P]),
+            "oracle_fabc_encode": (i64, [P, i64, i32, P, i32, P]),
+            "oracle_fabc_decode": (None, [P, i64, i32, i32, P]),
             "oracle_psi_subset": (None, [i64, i32, u64, i32, i32, P]),
             "oracle_psi_node": (f64, [P, P, P, i32, i32, u64, i32, i32]),
             "oracle_feedback": (i64, [P, P, i32, P, i32, P, u64, i32, P, P, P]),
@@ -275,3 +278,30 @@ def link_scores(phi: np.ndarray, pairs) -> np.ndarray:
 
 def link_auc(phi: np.ndarray, pos_pairs, neg_pairs) -> float:
     return auc_pairs(link_scores(phi, pos_pairs), link_scores(phi, neg_pairs))
+
+
+def fabc_select(counts, L: int, k_max: int):
+    """FaBC top-k (Section 5.2.2, Eq. 7, Eq. 8): (ids, F_k)."""
+    cnt = _c(counts, np.uint32)
+    ids = np.zeros(max(k_max, 1), np.int32)
+    F = ctypes.c_double(0.0)
+    k = lib().oracle_fabc_select(_p(cnt), cnt.size, L, k_max, _p(ids), ctypes.byref(F))
+    return ids[:k].copy(), F.value
+
+
+def fabc_encode(walks, ids) -> np.ndarray:
+    """FaBC encoding of walks[N][L] with the selected ids (bytes)."""
+    w = _c(walks, np.int32)
+    sel = _c(ids, np.int32)
+    N, L = w.shape
+    k = sel.size
+    out = np.zeros(4 * N * k + N * k * ((L + 7) // 8) + 4 * N * L, np.uint8)
+    size = lib().oracle_fabc_encode(_p(w), N, L, _p(sel) if k else None, k, _p(out))
+    return out[:size].copy()
+
+
+def fabc_decode(buf, N: int, L: int, k: int) -> np.ndarray:
+    b = _c(buf, np.uint8)
+    w = np.zeros((N, L), np.int32)
+    lib().oracle_fabc_decode(_p(b), N, L, k, _p(w))
+    return w

@@ -741,3 +741,91 @@ void oracle_link_scores(const double *phi, int32_t d, const int32_t *pairs, int6
     for (int64_t a = 0; a < m; ++a)
         scores[a] = dot(phi + (int64_t)pairs[2 * a] * d, phi + (int64_t)pairs[2 * a + 1] * d, d);
 }
+
+/* ------------------------------------------------------------------------ */
+/* FaBC, frequency-aware bitmap compression of walk sequences (Section      */
+/* 5.2.2).  Selection (Eq. 7, Eq. 8): nodes ordered by frequency p (count / */
+/* total, ties to the smaller id); with c = 1/L + 1/32 and                  */
+/* g(k) = 1 - F_k + k c, k grows from 0 while p(k+1) >= c + 0.1 g(k)         */
+/* (reading: stop at the first node that fails, k <= k_max).  Returns k;     */
+/* ids[0..k) receive the nodes and *F the covered fraction F_k.             */
+/* ------------------------------------------------------------------------ */
+int32_t oracle_fabc_select(const uint32_t *counts, int32_t n, int32_t L, int32_t k_max,
+                           int32_t *ids, double *F) {
+    uint64_t total = 0;
+    for (int32_t v = 0; v < n; ++v) total += counts[v];
+    const double c = 1.0 / (double)L + 1.0 / 32.0;
+    double Fk = 0.0, g = 1.0;
+    int32_t k = 0;
+    while (k < k_max && total > 0) {
+        /* the (k+1)-th most frequent node: largest count, smallest id, not yet taken */
+        int32_t best = -1;
+        for (int32_t v = 0; v < n; ++v) {
+            int taken = 0;
+            for (int32_t j = 0; j < k; ++j) taken |= ids[j] == v;
+            if (taken) continue;
+            if (best < 0 || counts[v] > counts[best]) best = v;
+        }
+        if (best < 0) break;
+        const double p = (double)counts[best] / (double)total;
+        if (!(p >= c + 0.1 * g)) break;
+        ids[k] = best;
+        k += 1;
+        Fk += p;
+        g = 1.0 - Fk + (double)k * c;
+    }
+    if (F) *F = Fk;
+    return k;
+}
+
+/* Encoded layout for N sequences of L ids, B = ceil(L / 8) bytes per bitmap: */
+/*   N*k int32   the k selected ids, stored with every sequence (Eq. 7 counts */
+/*               4Nk bytes for them)                                          */
+/*   N*k*B bytes bitmap (s, j) at (s*k + j)*B: bit i (byte i/8, bit i%8) set  */
+/*               iff walks[s][i] == ids[j]                                    */
+/*   int32 tail  ids of the positions no bitmap covers, in sequence order    */
+/* Returns the encoded size in bytes; out must hold 4Nk + NkB + 4NL bytes.    */
+int64_t oracle_fabc_encode(const int32_t *walks, int64_t N, int32_t L, const int32_t *ids,
+                           int32_t k, uint8_t *out) {
+    const int64_t B = (L + 7) / 8;
+    uint8_t *idreg = out, *bm = out + 4 * N * k, *tail = bm + N * k * B;
+    int64_t t = 0;
+    for (int64_t s = 0; s < N; ++s) {
+        for (int32_t j = 0; j < k; ++j) memcpy(idreg + 4 * (s * k + j), &ids[j], 4);
+        for (int32_t j = 0; j < k; ++j) memset(bm + (s * k + j) * B, 0, (size_t)B);
+        for (int32_t i = 0; i < L; ++i) {
+            int32_t v = walks[s * L + i];
+            int covered = 0;
+            for (int32_t j = 0; j < k; ++j) {
+                if (v == ids[j]) {
+                    bm[(s * k + j) * B + i / 8] |= (uint8_t)(1u << (i % 8));
+                    covered = 1;
+                }
+            }
+            if (!covered) memcpy(tail + 4 * t++, &v, 4);
+        }
+    }
+    return 4 * N * k + N * k * B + 4 * t;
+}
+
+/* Inverse of oracle_fabc_encode: a position covered by bitmap j takes the */
+/* sequence's j-th id, the others take the tail ids in order.               */
+void oracle_fabc_decode(const uint8_t *in, int64_t N, int32_t L, int32_t k, int32_t *walks) {
+    const int64_t B = (L + 7) / 8;
+    const uint8_t *idreg = in, *bm = in + 4 * N * k, *tail = bm + N * k * B;
+    int64_t t = 0;
+    for (int64_t s = 0; s < N; ++s) {
+        for (int32_t i = 0; i < L; ++i) {
+            int32_t v = 0;
+            int found = 0;
+            for (int32_t j = 0; j < k && !found; ++j) {
+                if (bm[(s * k + j) * B + i / 8] >> (i % 8) & 1u) {
+                    memcpy(&v, idreg + 4 * (s * k + j), 4);
+                    found = 1;
+                }
+            }
+            if (!found) memcpy(&v, tail + 4 * t++, 4);
+            walks[s * L + i] = v;
+        }
+    }
+}
