@@ -270,6 +270,49 @@ felog_status felog_embed(const felog_csr *g, const felog_walk_params *wp,
                          void *stream);
 
 /* ------------------------------------------------------------------------
+ * FaBC (Section 5.2.2, Eq. 7, Eq. 8): frequency-aware bitmap compression of
+ * a walk corpus, to persist it or move it off the GPU.
+ *
+ * Selection: nodes ordered by frequency p = count / total (ties to the
+ * smaller id); with c = 1/L + 1/32 and g(k) = 1 - F_k + k c (Eq. 7), k grows
+ * from 0 while p(k+1) >= c + 0.1 g(k) (Eq. 8; the first node that fails
+ * stops it) and k < k_max <= felog_fabc_max_k() = 32.
+ *
+ * Encoded layout for n_seq sequences of L ids, B = ceil(L / 8):
+ *   n_seq*k int32      the k selected ids, stored with every sequence
+ *   n_seq*k*B bytes    bitmap (s, j) at byte (s*k + j)*B: bit i (byte i/8,
+ *                      bit i%8) is set iff walks[s][i] == ids[j]
+ *   int32 tail         the ids of the positions no bitmap covers, sequence
+ *                      by sequence in position order (little-endian, not
+ *                      padded: it starts 4*n_seq*k + n_seq*k*B bytes in)
+ * Its size is 4*n_seq*k + n_seq*k*B + 4*tail bytes, which for L a multiple
+ * of 8 is g(k) * 4*n_seq*L with F_k the covered fraction of positions.
+ * Any int32 value round-trips, -1 padding included.
+ * ------------------------------------------------------------------------ */
+int32_t felog_fabc_max_k(void);
+/* Device workspace for n_seq sequences (selection needs felog_fabc_workspace_bytes(0)). */
+size_t felog_fabc_workspace_bytes(int64_t n_seq);
+/* Capacity an encode output needs: 4*n_seq*k + n_seq*k*B + 4*n_seq*L. */
+size_t felog_fabc_max_bytes(int64_t n_seq, int32_t L, int32_t k);
+/* counts: device uint32[n] (corpus frequencies, e.g. from felog_walk); ids:
+ * host int32[k_max]; *k and *F (host; F may be NULL) receive k and F_k.
+ * Synchronises `stream` to read the candidates. */
+felog_status felog_fabc_select(const uint32_t *counts, int32_t n, int32_t L, int32_t k_max,
+                               int32_t *ids, int32_t *k, double *F, void *workspace,
+                               size_t workspace_bytes, void *stream);
+/* walks: device int32[n_seq][L]; ids: device int32[k] (distinct); out:
+ * device bytes, 4-byte aligned, out_bytes >= felog_fabc_max_bytes; *tail
+ * (device int64) receives the number of tail ids. */
+felog_status felog_fabc_encode(const int32_t *walks, int64_t n_seq, int32_t L, const int32_t *ids,
+                               int32_t k, uint8_t *out, size_t out_bytes, int64_t *tail,
+                               void *workspace, size_t workspace_bytes, void *stream);
+/* in: device encoded bytes (4-byte aligned), in_bytes of them: reads stay
+ * below in_bytes, and a tail position past it (a damaged buffer) decodes as
+ * -1; walks: device int32[n_seq][L]. */
+felog_status felog_fabc_decode(const uint8_t *in, size_t in_bytes, int64_t n_seq, int32_t L, int32_t k,
+                               int32_t *walks, void *workspace, size_t workspace_bytes, void *stream);
+
+/* ------------------------------------------------------------------------
  * Batching form: many independent embedding jobs (Algorithm 1 each) trained
  * together.  One round of every unfinished job runs as one fixed sequence
  * of launches with no host synchronisation, each job at its own round index,

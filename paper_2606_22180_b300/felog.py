@@ -30,6 +30,8 @@ SYMBOLS = [
     "felog_train_workspace_bytes", "felog_train",
     "felog_feedback",
     "felog_embed_workspace_bytes", "felog_embed",
+    "felog_fabc_max_k", "felog_fabc_workspace_bytes", "felog_fabc_max_bytes", "felog_fabc_select",
+    "felog_fabc_encode", "felog_fabc_decode",
     "felog_batch_create", "felog_batch_destroy", "felog_batch_device_bytes", "felog_batch_reset",
     "felog_batch_step", "felog_batch_run", "felog_batch_read", "felog_batch_job_buffers",
     "felog_batch_autotune",
@@ -108,6 +110,12 @@ def load() -> ctypes.CDLL:
         "felog_feedback": (st, [P, P, i32, i32, P, u64, i32, P, P, P, P, P]),
         "felog_embed_workspace_bytes": (sz, [i32, P, P]),
         "felog_embed": (st, [P, P, P, P, u64, P, P, P, P, P, sz, P]),
+        "felog_fabc_max_k": (i32, []),
+        "felog_fabc_workspace_bytes": (sz, [i64]),
+        "felog_fabc_max_bytes": (sz, [i64, i32, i32]),
+        "felog_fabc_select": (st, [P, i32, i32, i32, P, P, P, P, sz, P]),
+        "felog_fabc_encode": (st, [P, i64, i32, P, i32, P, sz, P, P, sz, P]),
+        "felog_fabc_decode": (st, [P, sz, i64, i32, i32, P, P, sz, P]),
         "felog_batch_create": (st, [P, i32, P, P, P, P]),
         "felog_batch_destroy": (st, [P]),
         "felog_batch_device_bytes": (sz, [P]),
@@ -301,6 +309,55 @@ def felog_train(walks: torch.Tensor, n: int, tp: _TrainParams, thr: torch.Tensor
                            _ptr(S), seed, round_, clock_base, _ptr(phi_in), _ptr(phi_out), _ptr(loss),
                            _ptr(workspace), workspace.numel(), _stream()), "felog_train")
     return loss
+
+
+def felog_fabc_select(counts: torch.Tensor, L: int, k_max: int = 32):
+    """FaBC top-k (Eq. 8) from device corpus counts; returns (ids list, F_k)."""
+    _require_cuda(counts)
+    lib = load()
+    ws = _workspace(lib.felog_fabc_workspace_bytes(0), counts.device)
+    ids = (ctypes.c_int32 * max(k_max, 1))()
+    k = ctypes.c_int32(0)
+    F = ctypes.c_double(0.0)
+    _check(lib.felog_fabc_select(_ptr(counts), counts.numel(), L, k_max, ids, ctypes.byref(k), ctypes.byref(F),
+                                 _ptr(ws), ws.numel(), _stream()), "felog_fabc_select")
+    return [ids[i] for i in range(k.value)], F.value
+
+
+def felog_fabc_encode(walks: torch.Tensor, ids: torch.Tensor, workspace: torch.Tensor | None = None):
+    """FaBC encoding of walks [n_seq, L] (device int32) with device ids [k];
+    returns (device uint8 buffer of capacity max_bytes, device int64 tail count)."""
+    _require_cuda(walks, ids, workspace)
+    lib = load()
+    n_seq, L = walks.shape
+    k = ids.numel()
+    out = torch.empty(lib.felog_fabc_max_bytes(n_seq, L, k), dtype=torch.uint8, device=walks.device)
+    tail = torch.empty(1, dtype=torch.int64, device=walks.device)
+    need = lib.felog_fabc_workspace_bytes(n_seq)
+    if workspace is None or workspace.numel() < need:
+        workspace = _workspace(need, walks.device)
+    _check(lib.felog_fabc_encode(_ptr(walks), n_seq, L, _ptr(ids) if k else None, k, _ptr(out), out.numel(),
+                                 _ptr(tail), _ptr(workspace), workspace.numel(), _stream()), "felog_fabc_encode")
+    return out, tail
+
+
+def fabc_encoded_bytes(n_seq: int, L: int, k: int, tail: int) -> int:
+    return 4 * n_seq * k + n_seq * k * ((L + 7) // 8) + 4 * tail
+
+
+def felog_fabc_decode(buf: torch.Tensor, n_seq: int, L: int, k: int, walks: torch.Tensor | None = None,
+                      workspace: torch.Tensor | None = None) -> torch.Tensor:
+    """Inverse of felog_fabc_encode; returns device int32 walks [n_seq, L]."""
+    _require_cuda(buf, walks, workspace)
+    lib = load()
+    if walks is None:
+        walks = torch.empty((n_seq, L), dtype=torch.int32, device=buf.device)
+    need = lib.felog_fabc_workspace_bytes(n_seq)
+    if workspace is None or workspace.numel() < need:
+        workspace = _workspace(need, buf.device)
+    _check(lib.felog_fabc_decode(_ptr(buf), buf.numel(), n_seq, L, k, _ptr(walks), _ptr(workspace),
+                                 workspace.numel(), _stream()), "felog_fabc_decode")
+    return walks
 
 
 def felog_feedback(g: DeviceGraph, phi_in: torch.Tensor, precision: int, fp: _FeedbackParams,
