@@ -416,6 +416,8 @@ def run_native(args):
             "chosen": "feedback mu=0.65 + bf16-SR tables, same graph and split",
         }
     if not args.no_forms and rank == 0:
+        na = int(runner.n_active_h.item())
+        result["fabc"] = _fabc_form(fl, runner.walks[: na * WPR * L].view(-1, L), runner.counts)
         del runner
         torch.cuda.empty_cache()
         result["tile_form"] = _tile_form(fl, dg, n_live, T)
@@ -539,6 +541,45 @@ def run_serve(fl, rate=20.0, duration=20.0, max_nodes=1 << 16, pool_size=48, bud
 
 
 TILE_NS = 512
+
+
+def _fabc_form(fl, walks, counts, reps=5):
+    """FaBC (Section 5.2.2) on the last round's corpus: the Eq. 8 selection
+    and, for it and for a forced top-2, the encoded size against the raw
+    4 N L bytes (Eq. 7) and the encode / decode rates (CUDA events; bytes =
+    the walks read plus the encoded bytes written, or the reverse)."""
+    import torch
+
+    N, Lw = walks.shape
+    ids, F = fl.felog_fabc_select(counts, Lw, 32)
+    peak, _ = _peaks()
+    out = {"workload": f"one plain round of the round workload: {N} walks x {Lw}",
+           "eq8": {"k": len(ids), "F_k": F, "g_k": 1 - F + len(ids) / Lw + len(ids) / 32}}
+    top2 = torch.topk(counts.long(), 2).indices.tolist()
+    for name, sel in (("eq8", ids), ("top2", top2)):
+        ids_d = torch.tensor(sel, dtype=torch.int32, device=walks.device)
+        k = len(sel)
+        buf, tail = fl.felog_fabc_encode(walks, ids_d)
+        size = fl.fabc_encoded_bytes(N, Lw, k, int(tail.item()))
+        back = fl.felog_fabc_decode(buf[:size], N, Lw, k)
+        ok = bool(torch.equal(back, walks))
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record()
+        for _ in range(reps):
+            fl.felog_fabc_encode(walks, ids_d)
+        ev[1].record()
+        for _ in range(reps):
+            fl.felog_fabc_decode(buf[:size], N, Lw, k, walks=back)
+        ev[2].record()
+        torch.cuda.synchronize()
+        t_enc = ev[0].elapsed_time(ev[1]) / reps / 1e3
+        t_dec = ev[1].elapsed_time(ev[2]) / reps / 1e3
+        raw = 4 * N * Lw
+        out[name] = {"k": k, "ratio": size / raw, "round_trip_exact": ok,
+                     "encode_ms": t_enc * 1e3, "decode_ms": t_dec * 1e3,
+                     "encode_gbs": (raw + size) / t_enc / 1e9, "decode_gbs": (raw + size) / t_dec / 1e9,
+                     "encode_frac_hbm": (raw + size) / t_enc / 1e9 / peak}
+    return out
 
 
 def _tile_flops(n_tiles, dim, ns):
