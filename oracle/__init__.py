@@ -57,6 +57,7 @@ def lib() -> ctypes.CDLL:
             "oracle_philox": (None, [u64, P, P]),
             "oracle_walk": (ctypes.c_int, [P, P, i32, P, i32, i32, i32, u64, i32, P]),
             "oracle_counts": (None, [P, i64, i32, P]),
+            "oracle_walk_node2vec": (ctypes.c_int, [P, P, i32, P, i32, i32, i32, f64, f64, u64, i32, P]),
             "oracle_noise_table": (ctypes.c_int, [P, i32, P, P, P, P]),
             "oracle_draw_negative": (i32, [P, P, i32, u64, u64, i32, i64, i32, i32, i32]),
             "oracle_init_tables": (None, [i32, i32, u64, P, P]),
@@ -109,6 +110,18 @@ def walk(offsets, cols, starts, L: int, wpr: int, seed: int, round_: int) -> np.
                            seed, round_, _p(out))
     if rc:
         raise ValueError(f"oracle_walk failed ({rc})")
+    return out
+
+
+def walk_node2vec(offsets, cols, starts, L: int, wpr: int, p: float, q: float, seed: int,
+                  round_: int) -> np.ndarray:
+    """node2vec second-order walks (return parameter p, in-out parameter q)."""
+    off, col, st = _c(offsets, np.int32), _c(cols, np.int32), _c(starts, np.int32)
+    out = np.empty((wpr * st.shape[0], L), np.int32)
+    rc = lib().oracle_walk_node2vec(_p(off), _p(col), off.shape[0] - 1, _p(st), st.shape[0], L, wpr,
+                                    p, q, seed, round_, _p(out))
+    if rc:
+        raise ValueError(f"oracle_walk_node2vec failed ({rc})")
     return out
 
 

@@ -31,6 +31,7 @@
 #define STREAM_NEG 2u
 #define STREAM_INIT 3u
 #define STREAM_TILE 7u
+#define STREAM_N2V 8u
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10 (SC 2011): ten rounds of two 32x32->64 multiplies; the key  */
@@ -101,6 +102,63 @@ int oracle_walk(const int32_t *offsets, const int32_t *cols, int32_t n, const in
                 philox4(seed, (uint32_t)t, (uint32_t)s, (uint32_t)(round * wpr + j), STREAM_WALK, w);
                 uint64_t idx = mulhi64(lo_word64(w), (uint64_t)deg);
                 v = cols[offsets[v] + (int64_t)idx];
+                row[t] = v;
+            }
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* node2vec second-order walks (a Sample variant the paper names, Section   */
+/* 5.4; the rule is node2vec's, Grover and Leskovec, KDD 2016): having come */
+/* from t to v, the next node x, a neighbour of v, has unnormalised weight  */
+/* 1/p if x == t, 1 if x is a neighbour of t, 1/q otherwise.                */
+/* Reading (sampling procedure): step 1 is uniform; later steps use         */
+/* rejection -- attempt a draws Philox(x0 = t | a << 16, x1 = s,            */
+/* x2 = r*wpr + j, stream 8), proposes neighbour floor(u64 * deg / 2^64)    */
+/* and accepts iff (hi64 >> 11) * 2^-53 < alpha(x) / alpha_max in binary64, */
+/* alpha_max = max(1/p, 1, 1/q); after 64 rejected attempts the last        */
+/* proposal is taken.  Rows, padding and start handling as in oracle_walk.  */
+/* ------------------------------------------------------------------------ */
+static int is_neighbour(const int32_t *offsets, const int32_t *cols, int32_t t, int32_t x) {
+    for (int32_t e = offsets[t]; e < offsets[t + 1]; ++e)
+        if (cols[e] == x) return 1;
+    return 0;
+}
+
+int oracle_walk_node2vec(const int32_t *offsets, const int32_t *cols, int32_t n, const int32_t *starts,
+                         int32_t n_starts, int32_t L, int32_t wpr, double p, double q, uint64_t seed,
+                         int32_t round, int32_t *walks) {
+    if (L < 1 || L > 65535 || wpr < 1 || n_starts < 0 || !(p > 0.0) || !(q > 0.0)) return 1;
+    const double ap = 1.0 / p, aq = 1.0 / q;
+    const double amax = ap > 1.0 ? (ap > aq ? ap : aq) : (1.0 > aq ? 1.0 : aq);
+    for (int32_t j = 0; j < wpr; ++j) {
+        for (int32_t i = 0; i < n_starts; ++i) {
+            int32_t *row = walks + ((int64_t)j * n_starts + i) * L;
+            int32_t s = starts[i];
+            if (s < 0 || s >= n) return 2;
+            int32_t prev = -1, v = s;
+            row[0] = s;
+            for (int32_t t = 1; t < L; ++t) {
+                int64_t deg = (int64_t)offsets[v + 1] - offsets[v];
+                if (deg == 0) {
+                    for (int32_t r = t; r < L; ++r) row[r] = -1;
+                    break;
+                }
+                int32_t x = -1;
+                for (uint32_t a = 0; a < 64; ++a) {
+                    uint32_t w[4];
+                    philox4(seed, (uint32_t)t | (a << 16), (uint32_t)s, (uint32_t)(round * wpr + j),
+                            STREAM_N2V, w);
+                    x = cols[offsets[v] + (int64_t)mulhi64(lo_word64(w), (uint64_t)deg)];
+                    if (prev < 0) break; /* first step: uniform */
+                    double alpha = x == prev ? ap : (is_neighbour(offsets, cols, prev, x) ? 1.0 : aq);
+                    double u = (double)(hi_word64(w) >> 11) * 0x1p-53;
+                    if (u < alpha / amax) break;
+                }
+                prev = v;
+                v = x;
                 row[t] = v;
             }
         }
