@@ -418,6 +418,7 @@ def run_native(args):
     if not args.no_forms and rank == 0:
         na = int(runner.n_active_h.item())
         result["fabc"] = _fabc_form(fl, runner.walks[: na * WPR * L].view(-1, L), runner.counts)
+        result["node2vec"] = _node2vec_form(fl, dg, runner.starts[:na], runner.walks, runner.counts)
         del runner
         torch.cuda.empty_cache()
         result["tile_form"] = _tile_form(fl, dg, n_live, T)
@@ -541,6 +542,27 @@ def run_serve(fl, rate=20.0, duration=20.0, max_nodes=1 << 16, pool_size=48, bud
 
 
 TILE_NS = 512
+
+
+def _node2vec_form(fl, dg, starts, walks, counts, reps=3, p=0.5, q=2.0):
+    """node2vec walks (Sample variant) over the same starts as a round: walk
+    steps per second (CUDA events), next to the uniform walk kernel's."""
+    import torch
+
+    n = starts.numel()
+    out = walks[: n * WPR * L].view(-1, L)
+    fl.felog_walk_node2vec(dg, starts, n, L, WPR, p, q, SEED, 0, counts=counts, out=out)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    for r in range(reps):
+        counts.zero_()
+        fl.felog_walk_node2vec(dg, starts, n, L, WPR, p, q, SEED, r + 1, counts=counts, out=out)
+    ev[1].record()
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1]) / reps
+    steps = n * WPR * (L - 1)
+    return {"workload": f"{n} starts x {WPR} walks x {L} nodes on the round graph, p={p}, q={q}",
+            "ms_per_launch": ms, "walk_steps_per_s": steps / (ms / 1e3)}
 
 
 def _fabc_form(fl, walks, counts, reps=5):

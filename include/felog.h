@@ -183,6 +183,20 @@ felog_status felog_walk(const felog_csr *g, const int32_t *starts, int32_t n_sta
                         const felog_walk_params *wp, uint64_t seed, int32_t round,
                         int32_t *walks, uint32_t *counts, void *stream);
 
+/* node2vec second-order walks, a Sample variant (Section 5.4; the rule is
+ * node2vec's, Grover and Leskovec, KDD 2016): having come from t to v, the
+ * next node x has weight 1/p if x == t, 1 if x is a neighbour of t, 1/q
+ * otherwise.  Step 1 is uniform.  Later steps use rejection: attempt a
+ * draws Philox(x0 = t | a << 16, x1 = s, x2 = r*wpr + j, stream 8),
+ * proposes neighbour floor(u64 * deg / 2^64) and accepts iff
+ * (hi64 >> 11) * 2^-53 < alpha(x) / max(1/p, 1, 1/q) in binary64.  After
+ * 64 rejected attempts it takes the last proposal.  Rows, padding and
+ * counts as felog_walk; L <= 65535; p, q > 0 finite.  The CSR rows must be
+ * sorted (a binary search decides "neighbour of t"). */
+felog_status felog_walk_node2vec(const felog_csr *g, const int32_t *starts, int32_t n_starts,
+                                 const felog_walk_params *wp, double p, double q, uint64_t seed,
+                                 int32_t round, int32_t *walks, uint32_t *counts, void *stream);
+
 /* Corpus histogram: counts[v] += occurrences of v in tokens[n_tokens]
  * (entries < 0 are skipped).  counts must be zeroed by the caller. */
 felog_status felog_count(const int32_t *tokens, int64_t n_tokens, int32_t n, uint32_t *counts,

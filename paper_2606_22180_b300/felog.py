@@ -30,6 +30,7 @@ SYMBOLS = [
     "felog_train_workspace_bytes", "felog_train",
     "felog_feedback",
     "felog_embed_workspace_bytes", "felog_embed",
+    "felog_walk_node2vec",
     "felog_fabc_max_k", "felog_fabc_workspace_bytes", "felog_fabc_max_bytes", "felog_fabc_select",
     "felog_fabc_encode", "felog_fabc_decode",
     "felog_batch_create", "felog_batch_destroy", "felog_batch_device_bytes", "felog_batch_reset",
@@ -102,6 +103,7 @@ def load() -> ctypes.CDLL:
         "felog_compact_active_noalloc": (st, [P, i32, P, P, P]),
         "felog_walk": (st, [P, P, i32, P, u64, i32, P, P, P]),
         "felog_count": (st, [P, i64, i32, P, P]),
+        "felog_walk_node2vec": (st, [P, P, i32, P, f64, f64, u64, i32, P, P, P]),
         "felog_noise_workspace_bytes": (sz, [i32]),
         "felog_noise_table": (st, [P, i32, P, P, P, P, sz, P]),
         "felog_init_tables": (st, [i32, i32, i32, u64, P, P, P]),
@@ -243,6 +245,21 @@ def felog_walk(g: DeviceGraph, starts: torch.Tensor, n_starts: int, length: int,
     csr = g._c()
     _check(lib.felog_walk(ctypes.byref(csr), _ptr(starts), n_starts, ctypes.byref(wp), seed, round_,
                           _ptr(out), _ptr(counts), _stream()), "felog_walk")
+    return out
+
+
+def felog_walk_node2vec(g: DeviceGraph, starts: torch.Tensor, n_starts: int, length: int,
+                        walks_per_round: int, p: float, q: float, seed: int, round_: int,
+                        counts: torch.Tensor | None = None, out: torch.Tensor | None = None) -> torch.Tensor:
+    """node2vec walks (return parameter p, in-out parameter q); int32 [n_starts * wpr, length]."""
+    _require_cuda(starts, counts, out)
+    lib = load()
+    if out is None:
+        out = torch.empty((n_starts * walks_per_round, length), dtype=torch.int32, device=starts.device)
+    wp = _WalkParams(length, walks_per_round)
+    csr = g._c()
+    _check(lib.felog_walk_node2vec(ctypes.byref(csr), _ptr(starts), n_starts, ctypes.byref(wp), p, q, seed,
+                                   round_, _ptr(out), _ptr(counts), _stream()), "felog_walk_node2vec")
     return out
 
 
