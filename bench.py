@@ -52,10 +52,11 @@ def _args():
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     p.add_argument("--form", type=int, default=0, choices=[0, 1, 2],
                    help="Hogwild kernel form: 0 automatic, 1 full warp per pair, 2 half warp per pair")
-    p.add_argument("--mode", default="round", choices=["round", "tile", "batch", "serve"],
+    p.add_argument("--mode", default="round", choices=["round", "tile", "batch", "serve", "mu"],
                    help="round: one round of Algorithm 1 on R-MAT 20 (default); tile: rounds with the "
                         "shared-negatives tile trainer; batch: the 512-graph "
-                        "batching form; serve: the request loop with Poisson arrivals")
+                        "batching form; serve: the request loop with Poisson arrivals; mu: the "
+                        "feedback-threshold sweep on homophilic / heterophilic / R-MAT graphs")
     p.add_argument("--jobs", type=int, default=512, help="batch mode: number of graphs")
     p.add_argument("--rate", type=float, default=20.0, help="serve mode: arrivals per second")
     p.add_argument("--duration", type=float, default=20.0, help="serve mode: seconds of arrivals")
@@ -544,6 +545,64 @@ def run_serve(fl, rate=20.0, duration=20.0, max_nodes=1 << 16, pool_size=48, bud
 TILE_NS = 512
 
 
+MU_GRID = (0.5, 0.6, 0.65, 0.7, 0.8, 0.9)
+
+
+def run_mu_sweep(fl, evaluate, seed=5):
+    """Feedback threshold mu (Eq. 5) on synthetic graphs of three kinds:
+    homophilic planted partition (20 communities, p_in / p_out = 20),
+    heterophilic planted partition (2 communities, p_in / p_out = 1/20: most
+    edges cross, close to bipartite) and R-MAT scale 16.  Edges: 10 % test,
+    then 10 % of the rest validation.  For each mu (and feedback off, and
+    mu = 0.65 with reactivation) one run of Algorithm 1: trained tokens, wall
+    time, validation and test AUC.  The validation-calibrated mu is the one
+    with the fewest tokens whose validation AUC is within 0.005 of feedback
+    off; its test AUC and token saving are reported."""
+    import torch
+
+    from paper_2606_22180_b300 import inputs
+
+    graphs = {
+        "sbm_homophilic": inputs.sbm_degree(20000, 20, 16, seed, ratio=20.0),
+        "sbm_heterophilic": inputs.sbm_degree(20000, 2, 16, seed, ratio=0.05),
+        "rmat16": inputs.rmat(16, 16, seed=seed),
+    }
+    Lm, R = 40, 10
+    out = {"workload": f"L={Lm}, {R} rounds, w=5, K=5, d=64 fp32 Hogwild; 10 % test, 10 % validation edges",
+           "graphs": {}}
+    for name, g in graphs.items():
+        test = inputs.link_split(g, 0.1, seed)
+        val = inputs.link_split(test.train, 0.1, seed + 1)
+        dg = fl.DeviceGraph.from_host(val.train)
+        n_live = int((val.train.degrees() > 0).sum())
+        T = R * n_live * Lm
+        runs = {}
+        settings = [("off", False, 0.65, False)] + [(f"mu={m}", True, m, False) for m in MU_GRID] + \
+                   [("mu=0.65 reactivate", True, 0.65, True)]
+        for label, enabled, mu, react in settings:
+            tp = fl.train_params(64, 5, 5, LR0, T, fl.FELOG_SGNS_HOGWILD, 4096, fl.FELOG_FP32)
+            fp = fl.feedback_params(enabled, mu, KS, R, react)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            pi, _, st = fl.felog_embed(dg, Lm, 1, tp, fp, seed)
+            torch.cuda.synchronize()
+            runs[label] = {"tokens": int(sum(x["tokens"] for x in st)), "rounds": len(st),
+                           "seconds": time.perf_counter() - t0,
+                           "active_per_round": [x["n_active"] for x in st],
+                           "auc_val": evaluate.link_auc(pi, val.pos, val.neg),
+                           "auc_test": evaluate.link_auc(pi, test.pos, test.neg)}
+            del pi
+        base = runs["off"]
+        ok = [k for k in runs if k.startswith("mu=") and runs[k]["auc_val"] >= base["auc_val"] - 0.005]
+        pick = min(ok, key=lambda k: runs[k]["tokens"]) if ok else "off"
+        out["graphs"][name] = {
+            "nodes": g.n, "runs": runs, "calibrated": pick,
+            "calibrated_auc_test_delta": runs[pick]["auc_test"] - base["auc_test"],
+            "calibrated_token_fraction": runs[pick]["tokens"] / base["tokens"],
+        }
+    return out
+
+
 def _node2vec_form(fl, dg, starts, walks, counts, reps=3, p=0.5, q=2.0):
     """node2vec walks (Sample variant) over the same starts as a round: walk
     steps per second (CUDA events), next to the uniform walk kernel's."""
@@ -777,7 +836,7 @@ def run_reference(args):
 
 
 def run_form(args):
-    """--mode tile / batch / serve: one JSON line for that form."""
+    """--mode tile / batch / serve / mu: one JSON line for that form."""
     import torch
 
     from paper_2606_22180_b300 import build, felog as fl
@@ -785,7 +844,15 @@ def run_form(args):
     build.build()
     fl.load()
     torch.cuda.set_device(0)
-    if args.mode == "tile":
+    if args.mode == "mu":
+        from paper_2606_22180_b300 import evaluate
+
+        r = run_mu_sweep(fl, evaluate)
+        line = {"metric": "trained tokens and link AUC per feedback threshold mu", "value": None,
+                "unit": "tokens", "n_gpus": 1, "higher_is_better": False, "dtype": "f32",
+                "data": "synthetic (seeded SBM and R-MAT graphs)", "config": {"workload": r["workload"]},
+                "mu_sweep": r}
+    elif args.mode == "tile":
         split = _workload(args.scale)
         dg = fl.DeviceGraph.from_host(split.train)
         n_live = int((split.train.degrees() > 0).sum())
