@@ -671,15 +671,31 @@ def _tile_flops(n_tiles, dim, ns):
     return n_tiles * blocks * 3 * 2 * 128 * 128 * dim
 
 
-def _tile_form(fl, dg, n_live, T, steps=3, warmup=2, scale=SCALE):
+def _tile_form(fl, dg, n_live, T, steps=3, warmup=2, scale=SCALE, full=True):
     """The shared-negatives tile trainer (TILE mode, bf16 tables) on the same
     graph: plain rounds timed with CUDA events per phase; its tensor FLOP/s
     against the measured bf16 peak and its gathered/added row bytes against
-    HBM bandwidth."""
+    HBM bandwidth.  The automatic concurrency cap is the quality-preserving
+    setting; `full` adds the same measurement with one tile per SM (the
+    kernel's speed; lower AUC)."""
+    out = _tile_rounds(fl, dg, T, steps, warmup, scale, 0)
+    if full:
+        full_ctas = _sm_count()
+        out["one_tile_per_sm"] = _tile_rounds(fl, dg, T, steps, warmup, scale, full_ctas)
+    return out
+
+
+def _sm_count():
+    import torch
+
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+
+
+def _tile_rounds(fl, dg, T, steps, warmup, scale, ctas):
     import torch
 
     tp = fl.train_params(DIM, WINDOW, NEG, LR0, T, fl.FELOG_SGNS_TILE, 1, fl.FELOG_BF16_SR,
-                         tile_negatives=TILE_NS)
+                         tile_negatives=TILE_NS, tile_ctas=ctas)
     runner = RoundRunner(fl, dg, tp, fl.feedback_params(False, MU, KS, ROUNDS, False), SEED)
     runner.reset()
     for w in range(warmup):
@@ -712,6 +728,7 @@ def _tile_form(fl, dg, n_live, T, steps=3, warmup=2, scale=SCALE):
     gbs = alg_bytes / (train_ms / 1e3) / 1e9
     out = {
         "workload": f"{_workload_name(scale, 'bf16')}, TILE mode, Ns={TILE_NS} shared negatives per tile of {tc} centers",
+        "concurrent_tiles": ctas if ctas else f"automatic: min(SMs, n / 28000) = {min(_sm_count(), max(1, dg.n // 28000))}",
         "tokens_per_round": tok_round,
         "round_tokens_per_s": tokens / sec,
         "train_ms": train_ms,
@@ -743,6 +760,9 @@ def _quality(fl, evaluate, dg, split, n_live):
         "tile": (fl.train_params(DIM, WINDOW, NEG, LR0, T, fl.FELOG_SGNS_TILE, 1, fl.FELOG_BF16_SR,
                                  tile_negatives=TILE_NS),
                  fl.feedback_params(False, MU, KS, ROUNDS, False)),
+        "tile_one_per_sm": (fl.train_params(DIM, WINDOW, NEG, LR0, T, fl.FELOG_SGNS_TILE, 1, fl.FELOG_BF16_SR,
+                                            tile_negatives=TILE_NS, tile_ctas=_sm_count()),
+                            fl.feedback_params(False, MU, KS, ROUNDS, False)),
     }
     for name, (tp, fp) in forms.items():
         torch.cuda.synchronize()

@@ -92,9 +92,9 @@ typedef enum {
  * tile (128, 256, 384 or 512; 0 selects 512: each then stands for about 20
  * per-pair draws, fewer shared negatives let hub rows take oversized stale
  * steps and training can diverge); tile_ctas = concurrent tiles
- * (0 = min(SMs, max(1, n / 2048)), which bounds how many stale tile updates
- * meet on the rows of a small graph; 1 = tiles strictly in order, the
- * reproducible form). */
+ * (0 = min(SMs, max(1, n / 28000)), which bounds how many stale tile
+ * updates meet on shared rows: more tiles at once train faster and reach a
+ * lower link AUC; 1 = tiles strictly in order, the reproducible form). */
 typedef struct {
     int32_t dim;
     int32_t window;

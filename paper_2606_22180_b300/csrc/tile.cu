@@ -671,18 +671,20 @@ static felog_status launch_tile_dim(TileArgs a, int ctas, void *pi, void *po, cu
     return check_launch("felog_train (tile)");
 }
 
-// Rows per concurrent tile under the automatic cap: a tile adds its summed
-// increments to ~300 rows at once, computed from values gathered when it
-// began, so too many tiles in flight on a small graph pile stale steps onto
-// the same rows and training diverges (1,000 nodes with one tile per SM
-// does); at most n / kTileRowsPerCta tiles run at once.
-constexpr int64_t kTileRowsPerCta = 2048;
+// Rows per concurrent tile under the automatic cap.  A tile adds its summed
+// increments to ~750 rows at once, computed from values gathered when it
+// began.  With many tiles in flight, those stale steps pile up on shared
+// rows (hubs above all).  On 1,000 nodes with one tile per SM training
+// diverged; on R-MAT 20 (2^20 nodes, 10 rounds) link AUC fell from 0.832 (8
+// tiles) through 0.809 (37) to 0.709 (148).  At most n / kTileRowsPerCta
+// tiles run at once: 37 on 2^20 nodes, one on graphs below 56,000 nodes.
+constexpr int64_t kTileRowsPerCta = 28000;
 
 // Floats of the in-order form's staging buffer (dY of one tile's blocks).
 size_t tile_scratch_floats() { return static_cast<size_t>(kMaxNegBlocks + 1) * kTileRows * 128; }
 
 // Launches the tile trainer over walks[n_walks][L]; called by felog_train
-// after argument checks.  tile_ctas <= 0: min(SMs, max(1, n / 2048)) tiles
+// after argument checks.  tile_ctas <= 0: min(SMs, max(1, n / 28000)) tiles
 // at once; 1 runs the tiles in order (the reproducible form, which stages
 // each tile's dY rows in `scratch`, tile_scratch_floats() floats).
 felog_status launch_tile(const int32_t *walks, int64_t n_walks, int32_t L, int32_t n,

@@ -143,10 +143,10 @@ def test_tile_serial_bf16_tracks_oracle(fl, orc, sbm):
 
 
 def test_tile_parallel_round_close_to_serial(fl, orc):
-    """Many tiles at once (R-MAT 16: the automatic cap allows 32) race on
-    shared rows, so the trajectory departs from the in-order oracle (the
-    quality of this form is judged by link AUC); here the round must stay
-    stable: loss within 10 % of the oracle's, increments of the same size."""
+    """Many tiles at once (32 on R-MAT 16) race on shared rows, so the
+    trajectory departs from the in-order oracle (the quality of this form is
+    judged by link AUC); here the round must stay stable: loss within 10 %
+    of the oracle's, increments of the same size."""
     g = inputs.rmat(16, 16, seed=3)
     dim, window, K, Ns = 64, 10, 5, 512
     W, thr, alias, S = _corpus(orc, g, 80, SEED, 0, n_starts=300)
@@ -155,7 +155,7 @@ def test_tile_parallel_round_close_to_serial(fl, orc):
     pi, po = _to_dev(fl, ri0, 0), _to_dev(fl, ro0, 0)
     T = 5 * W.size
     tp = fl.train_params(dim, window, K, 0.025, T, fl.FELOG_SGNS_TILE, 1, fl.FELOG_FP32,
-                         tile_negatives=Ns, tile_ctas=0)
+                         tile_negatives=Ns, tile_ctas=32)
     lg = _train(fl, W, thr, alias, S, g.n, tp, SEED, 0, 0, pi, po)
     lo = orc.sgns_tile(W, g.n, dim, window, K, 0.025, T, 128 - 2 * window, Ns, thr, alias, S, SEED,
                        0, 0, ri, ro)
