@@ -86,3 +86,33 @@ def test_bf16_round_trip_is_exact_for_representable_values(fl):
         tp = fl.train_params(64, 3, 3, 0.0, 10 ** 6, mode, 512, fl.FELOG_BF16_SR)
         fl.felog_train(W, g.n, tp, thr, alias, S, 5, 0, 0, pi, po)
         assert torch.equal(pi, a) and torch.equal(po, b)
+
+
+@pytest.mark.slow
+def test_bf16_matches_fp32_on_rmat22(fl):
+    """The precision workload at full size: R-MAT scale 22 (4.2 M nodes),
+    d = 128, L = 80, window 10, 5 negatives, 10 % of edges held out.  The
+    binary64 oracle does not fit at this size, so bf16 tables with
+    stochastic rounding are held against fp32 tables trained the same way
+    (Hogwild, 3 rounds): link AUC within 0.005, round losses within 1 %,
+    and every table value finite."""
+    from paper_2606_22180_b300 import evaluate
+
+    split = inputs.link_split(inputs.workload_rmat(22, 2), 0.1, 2)
+    dg = fl.DeviceGraph.from_host(split.train)
+    n_live = int((split.train.degrees() > 0).sum())
+    R = 3
+    fp = fl.feedback_params(False, 0.65, 8, R, False)
+    res = {}
+    for name, prec in [("fp32", fl.FELOG_FP32), ("bf16", fl.FELOG_BF16_SR)]:
+        tp = fl.train_params(128, 10, 5, 0.025, R * n_live * 80, fl.FELOG_SGNS_HOGWILD, 4096, prec)
+        pi, po, st = fl.felog_embed(dg, 80, 1, tp, fp, 2)
+        assert torch.isfinite(pi.float()).all() and torch.isfinite(po.float()).all()
+        res[name] = (evaluate.link_auc(pi, split.pos, split.neg), [s["loss"] for s in st])
+        del pi, po
+    gap = res["bf16"][0] - res["fp32"][0]
+    rel = [abs(b - a) / a for a, b in zip(res["fp32"][1], res["bf16"][1])]
+    print(f"R-MAT 22: AUC fp32 {res['fp32'][0]:.4f} bf16 {res['bf16'][0]:.4f} gap {gap:+.4f}; "
+          f"round loss rel diff {['%.2e' % r for r in rel]}")
+    assert abs(gap) <= 0.005
+    assert max(rel) < 0.01
