@@ -65,7 +65,9 @@ __global__ void k_fabc_argmax(const uint32_t *__restrict__ counts, int32_t n, in
 }
 
 // ---------------------------------------------------------------------------
-// tail lengths and their exclusive scan
+// per-sequence work, shared by the staged kernels (a tile of whole sequences
+// copied to shared memory first) and the unstaged ones (long sequences,
+// read straight from global memory)
 // ---------------------------------------------------------------------------
 // coverage of 32 positions of a sequence by the k ids held in lanes 0..k-1
 __device__ __forceinline__ uint32_t covered_ids(int32_t v, bool in, int32_t my_id, int k, int lane, uint32_t *per_id) {
@@ -79,45 +81,322 @@ __device__ __forceinline__ uint32_t covered_ids(int32_t v, bool in, int32_t my_i
     return any;
 }
 
+// number of positions of row[0..L) that no id covers (the whole warp)
+__device__ __forceinline__ int64_t tail_len_seq(const int32_t *row, int32_t L, int k, int32_t my_id, int lane) {
+    int64_t t = 0;
+    for (int c = 0; c < L; c += 32) {
+        const bool in = c + lane < L;
+        const int32_t v = in ? row[c + lane] : 0;
+        uint32_t mine = 0;
+        const uint32_t cov = covered_ids(v, in, my_id, k, lane, &mine);
+        t += __popc(__ballot_sync(kFull, in) & ~cov);
+    }
+    return t;
+}
+
+__device__ __forceinline__ void put32(uint8_t *p, int64_t i, int32_t v, bool aligned) {
+    if (aligned) {
+        reinterpret_cast<int32_t *>(p)[i] = v;
+    } else {
+        const uint32_t u = static_cast<uint32_t>(v);
+        for (int b = 0; b < 4; ++b) p[4 * i + b] = static_cast<uint8_t>(u >> (8 * b));
+    }
+}
+__device__ __forceinline__ int32_t get32(const uint8_t *p, int64_t i, bool aligned) {
+    if (aligned) return reinterpret_cast<const int32_t *>(p)[i];
+    uint32_t u = 0;
+    for (int b = 0; b < 4; ++b) u |= static_cast<uint32_t>(p[4 * i + b]) << (8 * b);
+    return static_cast<int32_t>(u);
+}
+
+// encodes sequence s from row[0..L) with its first tail entry at index t
+__device__ __forceinline__ void encode_seq(const int32_t *row, int64_t s, int32_t L, int B, int k, int32_t my_id,
+                                           int lane, int64_t t, int32_t *idreg, uint8_t *bm, uint8_t *tail,
+                                           bool aligned) {
+    if (lane < k) idreg[s * k + lane] = my_id;
+    for (int c = 0; c < L; c += 32) {
+        const bool in = c + lane < L;
+        const int32_t v = in ? row[c + lane] : 0;
+        uint32_t mine = 0;  // lane j: the bits of id j in these 32 positions
+        const uint32_t cov = covered_ids(v, in, my_id, k, lane, &mine);
+        // lane j < k writes bytes c/8 .. c/8 + 3 of bitmap j (those below B)
+        if (lane < k)
+            for (int b = 0; b < 4 && c / 8 + b < B; ++b)
+                bm[(s * k + lane) * B + c / 8 + b] = static_cast<uint8_t>(mine >> (8 * b));
+        const uint32_t keep = __ballot_sync(kFull, in) & ~cov;
+        if (keep >> lane & 1u) put32(tail, t + __popc(keep & ((1u << lane) - 1u)), v, aligned);
+        t += __popc(keep);
+    }
+}
+
+// decodes one sequence: bms = its k*B bitmap bytes, tail entry t of the
+// sequence at tailp + 4t (entries at or past cap decode as -1)
+__device__ __forceinline__ void decode_seq(const uint8_t *bms, int32_t my_id, int32_t L, int B, int k, int lane,
+                                           int64_t t, const uint8_t *tailp, int64_t cap, bool aligned,
+                                           int32_t *out) {
+    for (int c = 0; c < L; c += 32) {
+        const int i = c + lane;
+        int found = -1;
+        for (int j = 0; j < k && i < L; ++j)
+            if (found < 0 && ((bms[j * B + (i >> 3)] >> (i & 7)) & 1u)) found = j;
+        int32_t v = 0;
+        for (int j = 0; j < k; ++j) {  // every lane joins the shuffles
+            const int32_t idj = __shfl_sync(kFull, my_id, j);
+            if (found == j) v = idj;
+        }
+        const uint32_t fromtail = __ballot_sync(kFull, i < L && found < 0);
+        if (fromtail >> lane & 1u) {
+            const int64_t ti = t + __popc(fromtail & ((1u << lane) - 1u));
+            v = ti < cap ? get32(tailp, ti, aligned) : -1;
+        }
+        if (i < L) out[i] = v;
+        t += __popc(fromtail);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// staging: a block copies its tile to shared memory with independent loads
+// issued back to back (4 per thread in flight), then works from there
+// ---------------------------------------------------------------------------
+constexpr int kStageBytes = 24576;  // shared memory per block
+constexpr int kStageMaxSeq = 64;    // sequences per tile
+constexpr int kStageUnroll = 4;
+
+// n int32 from global src to shared dst (16-byte aligned); 16-byte vectors
+// when src is 16-byte aligned
+__device__ __forceinline__ void stage_words(int32_t *dst, const int32_t *__restrict__ src, int n) {
+    if ((reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
+        const int n4 = n >> 2;
+        const int4 *s4 = reinterpret_cast<const int4 *>(src);
+        int4 *d4 = reinterpret_cast<int4 *>(dst);
+        for (int base = threadIdx.x; base < n4; base += kStageUnroll * blockDim.x) {
+            int4 r[kStageUnroll];
+#pragma unroll
+            for (int u = 0; u < kStageUnroll; ++u) {
+                const int i = base + u * static_cast<int>(blockDim.x);
+                if (i < n4) r[u] = __ldg(s4 + i);
+            }
+#pragma unroll
+            for (int u = 0; u < kStageUnroll; ++u) {
+                const int i = base + u * static_cast<int>(blockDim.x);
+                if (i < n4) d4[i] = r[u];
+            }
+        }
+        for (int i = 4 * n4 + static_cast<int>(threadIdx.x); i < n; i += blockDim.x) dst[i] = __ldg(src + i);
+    } else {
+        for (int base = threadIdx.x; base < n; base += kStageUnroll * blockDim.x) {
+            int32_t r[kStageUnroll];
+#pragma unroll
+            for (int u = 0; u < kStageUnroll; ++u) {
+                const int i = base + u * static_cast<int>(blockDim.x);
+                if (i < n) r[u] = __ldg(src + i);
+            }
+#pragma unroll
+            for (int u = 0; u < kStageUnroll; ++u) {
+                const int i = base + u * static_cast<int>(blockDim.x);
+                if (i < n) dst[i] = r[u];
+            }
+        }
+    }
+}
+
+// n bytes from global src (any alignment) to shared dst (4-byte aligned,
+// n + 4 bytes of room): the bytes land at dst + o, o = src mod 4, so that
+// the aligned middle moves as 4-byte words; returns o
+__device__ __forceinline__ int stage_bytes(uint8_t *dst, const uint8_t *__restrict__ src, int n) {
+    const int o = static_cast<int>(reinterpret_cast<uintptr_t>(src) & 3u);
+    const int head = min(n, (4 - o) & 3);
+    if (static_cast<int>(threadIdx.x) < head) dst[o + threadIdx.x] = src[threadIdx.x];
+    const int nw = (n - head) >> 2;
+    const uint32_t *sw = reinterpret_cast<const uint32_t *>(src + head);
+    uint32_t *dw = reinterpret_cast<uint32_t *>(dst + o + head);
+    for (int base = threadIdx.x; base < nw; base += kStageUnroll * blockDim.x) {
+        uint32_t r[kStageUnroll];
+#pragma unroll
+        for (int u = 0; u < kStageUnroll; ++u) {
+            const int i = base + u * static_cast<int>(blockDim.x);
+            if (i < nw) r[u] = __ldg(sw + i);
+        }
+#pragma unroll
+        for (int u = 0; u < kStageUnroll; ++u) {
+            const int i = base + u * static_cast<int>(blockDim.x);
+            if (i < nw) dw[i] = r[u];
+        }
+    }
+    const int done = head + 4 * nw;
+    if (static_cast<int>(threadIdx.x) < n - done) dst[o + done + threadIdx.x] = src[done + threadIdx.x];
+    return o;
+}
+
+__host__ __device__ constexpr int align16(int x) { return (x + 15) & ~15; }
+
+// encode tiles: TS sequences, a multiple of 4 so that every tile starts on a
+// 16-byte boundary of the walks; 0 = sequences too long to stage
+static int encode_tile_seqs(int32_t L) {
+    const int64_t ts = std::min<int64_t>(kStageMaxSeq, (kStageBytes - kStageMaxSeq * 8) / (4 * static_cast<int64_t>(L)));
+    return static_cast<int>(ts) & ~3;
+}
+static int encode_stage_bytes(int ts, int32_t L) { return align16(ts * 8) + align16(4 * ts * L); }
+
+// decode tiles stage per sequence: its offset, k ids, k*B bitmap bytes and
+// at most L tail entries
+static int decode_stage_bytes(int ts, int32_t L, int32_t k) {
+    const int B = (L + 7) / 8;
+    return align16(ts * 8) + align16(4 * ts * k + 4) + align16(ts * k * B + 4) + align16(4 * ts * L + 4);
+}
+static int decode_tile_seqs(int32_t L, int32_t k) {
+    int ts = kStageMaxSeq;
+    while (ts > 0 && decode_stage_bytes(ts, L, k) > kStageBytes) --ts;
+    return ts;
+}
+
+// ---------------------------------------------------------------------------
+// encode.  COUNT: the tail length of every sequence into len; else the
+// encoding, the tail of sequence s starting at off[s] (s*L when k = 0, when
+// block 0 also writes the tail total n_seq*L).  The tail starts 4Nk + NkB
+// bytes into the buffer, a multiple of 4 only when NkB is; otherwise its
+// entries move byte by byte (the layout has no padding: its size is exactly
+// Eq. 7's count).
+// ---------------------------------------------------------------------------
+template <bool COUNT>
 __global__ void __launch_bounds__(kFabcThreads)
-    k_fabc_tail_len(const int32_t *__restrict__ walks, int64_t n_seq, int32_t L, const int32_t *__restrict__ ids,
-                    int32_t k, int64_t *__restrict__ len) {
-    const int lane = threadIdx.x & 31;
+    k_fabc_encode_st(const int32_t *__restrict__ walks, int64_t n_seq, int32_t L, int32_t ts,
+                     const int32_t *__restrict__ ids, int32_t k, const int64_t *__restrict__ off,
+                     int64_t *__restrict__ len, uint8_t *__restrict__ out, int64_t *__restrict__ total) {
+    extern __shared__ int4 fabc_smem[];
+    int64_t *soff = reinterpret_cast<int64_t *>(fabc_smem);
+    int32_t *tile = reinterpret_cast<int32_t *>(reinterpret_cast<uint8_t *>(fabc_smem) + align16(ts * 8));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int B = (L + 7) / 8;
     const int32_t my_id = lane < k ? ids[lane] : 0;
+    int32_t *idreg = reinterpret_cast<int32_t *>(out);
+    uint8_t *bm = out + 4 * n_seq * k, *tail = bm + n_seq * k * B;
+    const bool aligned = ((n_seq * k * B) & 3) == 0;
+    if (!COUNT && k == 0 && blockIdx.x == 0 && threadIdx.x == 0) *total = n_seq * L;
+    const int64_t n_tiles = (n_seq + ts - 1) / ts;
+    for (int64_t ti = blockIdx.x; ti < n_tiles; ti += gridDim.x) {
+        const int64_t s0 = ti * ts;
+        const int ns = static_cast<int>(n_seq - s0 < ts ? n_seq - s0 : ts);
+        if (!COUNT && static_cast<int>(threadIdx.x) < ns) soff[threadIdx.x] = k ? off[s0 + threadIdx.x] : (s0 + threadIdx.x) * L;
+        stage_words(tile, walks + s0 * L, ns * L);
+        __syncthreads();
+        for (int si = warp; si < ns; si += kFabcWarps) {
+            const int32_t *row = tile + si * L;
+            if (COUNT) {
+                const int64_t t = tail_len_seq(row, L, k, my_id, lane);
+                if (lane == 0) len[s0 + si] = t;
+            } else {
+                encode_seq(row, s0 + si, L, B, k, my_id, lane, soff[si], idreg, bm, tail, aligned);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// the same, one warp per sequence straight from global memory (long L)
+template <bool COUNT>
+__global__ void __launch_bounds__(kFabcThreads)
+    k_fabc_encode_g(const int32_t *__restrict__ walks, int64_t n_seq, int32_t L, const int32_t *__restrict__ ids,
+                    int32_t k, const int64_t *__restrict__ off, int64_t *__restrict__ len, uint8_t *__restrict__ out,
+                    int64_t *__restrict__ total) {
+    const int lane = threadIdx.x & 31;
+    const int B = (L + 7) / 8;
+    const int32_t my_id = lane < k ? ids[lane] : 0;
+    int32_t *idreg = reinterpret_cast<int32_t *>(out);
+    uint8_t *bm = out + 4 * n_seq * k, *tail = bm + n_seq * k * B;
+    const bool aligned = ((n_seq * k * B) & 3) == 0;
+    if (!COUNT && k == 0 && blockIdx.x == 0 && threadIdx.x == 0) *total = n_seq * L;
     const int64_t warps = static_cast<int64_t>(gridDim.x) * kFabcWarps;
     for (int64_t s = static_cast<int64_t>(blockIdx.x) * kFabcWarps + (threadIdx.x >> 5); s < n_seq; s += warps) {
         const int32_t *row = walks + s * L;
-        int64_t t = 0;
-        for (int c = 0; c < L; c += 32) {
-            const bool in = c + lane < L;
-            const int32_t v = in ? row[c + lane] : 0;
-            uint32_t mine = 0;
-            const uint32_t cov = covered_ids(v, in, my_id, k, lane, &mine);
-            const uint32_t valid = __ballot_sync(kFull, in);
-            t += __popc(valid & ~cov);
+        if (COUNT) {
+            const int64_t t = tail_len_seq(row, L, k, my_id, lane);
+            if (lane == 0) len[s] = t;
+        } else {
+            encode_seq(row, s, L, B, k, my_id, lane, k ? off[s] : s * L, idreg, bm, tail, aligned);
         }
-        if (lane == 0) len[s] = t;
     }
 }
 
+// ---------------------------------------------------------------------------
+// decode.  Tail lengths first, one thread per sequence: L minus the set bits
+// of the OR of its k bitmaps (bits at or past L ignored).
+// ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kFabcThreads)
     k_fabc_tail_len_dec(const uint8_t *__restrict__ bm, int64_t n_seq, int32_t L, int32_t k, int64_t *__restrict__ len) {
-    const int lane = threadIdx.x & 31;
     const int B = (L + 7) / 8;
-    const int64_t warps = static_cast<int64_t>(gridDim.x) * kFabcWarps;
-    for (int64_t s = static_cast<int64_t>(blockIdx.x) * kFabcWarps + (threadIdx.x >> 5); s < n_seq; s += warps) {
-        int64_t t = 0;
-        for (int c = 0; c < L; c += 32) {
-            const int i = c + lane;
-            bool cov = false;
-            for (int j = 0; j < k && i < L; ++j) cov |= (bm[(s * k + j) * B + (i >> 3)] >> (i & 7)) & 1u;
-            t += __popc(__ballot_sync(kFull, i < L && !cov));
+    const int last_bits = L - 8 * (B - 1);
+    const uint32_t last_mask = (1u << last_bits) - 1u;
+    for (int64_t s = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; s < n_seq;
+         s += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const uint8_t *b = bm + s * k * B;
+        int32_t cov = 0;
+        for (int i = 0; i < B; ++i) {
+            uint32_t x = 0;
+            for (int j = 0; j < k; ++j) x |= __ldg(b + j * B + i);
+            if (i == B - 1) x &= last_mask;
+            cov += __popc(x);
         }
-        if (lane == 0) len[s] = t;
+        len[s] = L - cov;
     }
 }
 
-// exclusive scan of len[n] into off[n] (in place allowed), total into *total
+// staged: per tile, the offsets, ids, bitmaps and the tile's stretch of the
+// tail [off[s0], off[s0 + ns]) go to shared memory (tail entries at or past
+// cap, the end of the buffer, decode as -1)
+__global__ void __launch_bounds__(kFabcThreads)
+    k_fabc_decode_st(const uint8_t *__restrict__ in, int64_t n_seq, int32_t L, int32_t k, int32_t ts,
+                     const int64_t *__restrict__ off, const int64_t *__restrict__ total, int64_t cap,
+                     int32_t *__restrict__ walks) {
+    extern __shared__ int4 fabc_smem[];
+    const int B = (L + 7) / 8;
+    uint8_t *base = reinterpret_cast<uint8_t *>(fabc_smem);
+    int64_t *soff = reinterpret_cast<int64_t *>(base);
+    uint8_t *sids = base + align16(ts * 8);
+    uint8_t *sbm = sids + align16(4 * ts * k + 4);
+    uint8_t *stl = sbm + align16(ts * k * B + 4);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint8_t *bm = in + 4 * n_seq * k, *tail = bm + n_seq * k * B;
+    const int64_t n_tiles = (n_seq + ts - 1) / ts;
+    for (int64_t ti = blockIdx.x; ti < n_tiles; ti += gridDim.x) {
+        const int64_t s0 = ti * ts;
+        const int ns = static_cast<int>(n_seq - s0 < ts ? n_seq - s0 : ts);
+        const int64_t t0 = k ? off[s0] : s0 * L;
+        const int64_t t1 = k ? (s0 + ns < n_seq ? off[s0 + ns] : *total) : (s0 + ns) * L;
+        const int64_t hi = t1 < cap ? t1 : cap, lo = t0 < hi ? t0 : hi;
+        if (static_cast<int>(threadIdx.x) < ns) soff[threadIdx.x] = (k ? off[s0 + threadIdx.x] : (s0 + threadIdx.x) * L) - t0;
+        const int oid = stage_bytes(sids, in + 4 * s0 * k, 4 * ns * k);
+        const int obm = stage_bytes(sbm, bm + s0 * k * B, ns * k * B);
+        const int otl = stage_bytes(stl, tail + 4 * lo, static_cast<int>(4 * (hi - lo)));
+        __syncthreads();
+        for (int si = warp; si < ns; si += kFabcWarps) {
+            const int32_t my_id = lane < k ? get32(sids + oid, static_cast<int64_t>(si) * k + lane, oid == 0) : 0;
+            decode_seq(sbm + obm + si * k * B, my_id, L, B, k, lane, soff[si], stl + otl, hi - t0, otl == 0,
+                       walks + (s0 + si) * L);
+        }
+        __syncthreads();
+    }
+}
+
+// unstaged, one warp per sequence (long L)
+__global__ void __launch_bounds__(kFabcThreads)
+    k_fabc_decode_g(const uint8_t *__restrict__ in, int64_t n_seq, int32_t L, int32_t k,
+                    const int64_t *__restrict__ off, int64_t cap, int32_t *__restrict__ walks) {
+    const int lane = threadIdx.x & 31;
+    const int B = (L + 7) / 8;
+    const int32_t *idreg = reinterpret_cast<const int32_t *>(in);
+    const uint8_t *bm = in + 4 * n_seq * k, *tail = bm + n_seq * k * B;
+    const bool aligned = ((n_seq * k * B) & 3) == 0;
+    const int64_t warps = static_cast<int64_t>(gridDim.x) * kFabcWarps;
+    for (int64_t s = static_cast<int64_t>(blockIdx.x) * kFabcWarps + (threadIdx.x >> 5); s < n_seq; s += warps) {
+        const int32_t my_id = lane < k ? idreg[s * k + lane] : 0;
+        decode_seq(bm + s * k * B, my_id, L, B, k, lane, k ? off[s] : s * L, tail, cap, aligned, walks + s * L);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// exclusive scan of len[n] into itself, the total into *total
+// ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kFabcThreads)
     k_scan_tiles(const int64_t *__restrict__ len, int64_t n, int64_t *__restrict__ tile_sum) {
     __shared__ int64_t part[kFabcWarps];
@@ -137,20 +416,32 @@ __global__ void __launch_bounds__(kFabcThreads)
     }
 }
 
-__global__ void k_scan_top(int64_t *__restrict__ tile_sum, int64_t tiles, int64_t *__restrict__ total) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    int64_t run = 0;
-    for (int64_t t = 0; t < tiles; ++t) {
-        const int64_t x = tile_sum[t];
-        tile_sum[t] = run;
-        run += x;
+__device__ __forceinline__ int64_t warp_inclusive_scan(int64_t x, int lane) {
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
     }
-    *total = run;
+    return x;
+}
+
+// one warp: the tile sums into their exclusive prefix, 32 at a time
+__global__ void k_scan_top(int64_t *__restrict__ tile_sum, int64_t tiles, int64_t *__restrict__ total) {
+    const int lane = threadIdx.x;
+    int64_t run = 0;
+    for (int64_t b = 0; b < tiles; b += 32) {
+        const int64_t i = b + lane;
+        const int64_t x = i < tiles ? tile_sum[i] : 0;
+        const int64_t inc = warp_inclusive_scan(x, lane);
+        if (i < tiles) tile_sum[i] = run + inc - x;
+        run += __shfl_sync(kFull, inc, 31);
+    }
+    if (lane == 0) *total = run;
 }
 
 __global__ void __launch_bounds__(kFabcThreads)
     k_scan_apply(int64_t *__restrict__ len, int64_t n, const int64_t *__restrict__ tile_off) {
-    __shared__ int64_t part[kFabcThreads];
+    __shared__ int64_t wsum[kFabcWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // each thread owns kScanItems consecutive items of the tile
     const int64_t base = static_cast<int64_t>(blockIdx.x) * kScanTile + static_cast<int64_t>(threadIdx.x) * kScanItems;
     int64_t v[kScanItems];
@@ -159,103 +450,14 @@ __global__ void __launch_bounds__(kFabcThreads)
         v[k] = base + k < n ? len[base + k] : 0;
         s += v[k];
     }
-    part[threadIdx.x] = s;
+    const int64_t inc = warp_inclusive_scan(s, lane);
+    if (lane == 31) wsum[warp] = inc;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        int64_t run = tile_off[blockIdx.x];
-        for (int i = 0; i < kFabcThreads; ++i) {
-            const int64_t x = part[i];
-            part[i] = run;
-            run += x;
-        }
-    }
-    __syncthreads();
-    int64_t run = part[threadIdx.x];
+    int64_t run = tile_off[blockIdx.x] + inc - s;
+    for (int w = 0; w < warp; ++w) run += wsum[w];
     for (int k = 0; k < kScanItems; ++k) {
         if (base + k < n) len[base + k] = run;
         run += v[k];
-    }
-}
-
-// ---------------------------------------------------------------------------
-// encode / decode.  The tail starts 4Nk + NkB bytes into the buffer, which is
-// a multiple of 4 only when NkB is; otherwise its entries are moved byte by
-// byte (the layout has no padding, so its size is exactly Eq. 7's count).
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void put32(uint8_t *p, int64_t i, int32_t v, bool aligned) {
-    if (aligned) {
-        reinterpret_cast<int32_t *>(p)[i] = v;
-    } else {
-        const uint32_t u = static_cast<uint32_t>(v);
-        for (int b = 0; b < 4; ++b) p[4 * i + b] = static_cast<uint8_t>(u >> (8 * b));
-    }
-}
-__device__ __forceinline__ int32_t get32(const uint8_t *p, int64_t i, bool aligned) {
-    if (aligned) return reinterpret_cast<const int32_t *>(p)[i];
-    uint32_t u = 0;
-    for (int b = 0; b < 4; ++b) u |= static_cast<uint32_t>(p[4 * i + b]) << (8 * b);
-    return static_cast<int32_t>(u);
-}
-__global__ void __launch_bounds__(kFabcThreads)
-    k_fabc_encode(const int32_t *__restrict__ walks, int64_t n_seq, int32_t L, const int32_t *__restrict__ ids,
-                  int32_t k, const int64_t *__restrict__ off, uint8_t *__restrict__ out) {
-    const int lane = threadIdx.x & 31;
-    const int B = (L + 7) / 8;
-    const int32_t my_id = lane < k ? ids[lane] : 0;
-    int32_t *idreg = reinterpret_cast<int32_t *>(out);
-    uint8_t *bm = out + 4 * n_seq * k, *tail = bm + n_seq * k * B;
-    const bool aligned = ((n_seq * k * B) & 3) == 0;
-    const int64_t warps = static_cast<int64_t>(gridDim.x) * kFabcWarps;
-    for (int64_t s = static_cast<int64_t>(blockIdx.x) * kFabcWarps + (threadIdx.x >> 5); s < n_seq; s += warps) {
-        const int32_t *row = walks + s * L;
-        if (lane < k) idreg[s * k + lane] = my_id;
-        int64_t t = off[s];
-        for (int c = 0; c < L; c += 32) {
-            const bool in = c + lane < L;
-            const int32_t v = in ? row[c + lane] : 0;
-            uint32_t mine = 0;  // lane j: the bits of id j in these 32 positions
-            const uint32_t cov = covered_ids(v, in, my_id, k, lane, &mine);
-            // lane j < k writes bytes c/8 .. c/8 + 3 of bitmap j (those below B)
-            if (lane < k)
-                for (int b = 0; b < 4 && c / 8 + b < B; ++b) bm[(s * k + lane) * B + c / 8 + b] = static_cast<uint8_t>(mine >> (8 * b));
-            const uint32_t keep = __ballot_sync(kFull, in) & ~cov;
-            if (keep >> lane & 1u) put32(tail, t + __popc(keep & ((1u << lane) - 1u)), v, aligned);
-            t += __popc(keep);
-        }
-    }
-}
-
-__global__ void __launch_bounds__(kFabcThreads)
-    k_fabc_decode(const uint8_t *__restrict__ in, int64_t n_seq, int32_t L, int32_t k, const int64_t *__restrict__ off,
-                  int64_t tail_cap, int32_t *__restrict__ walks) {
-    const int lane = threadIdx.x & 31;
-    const int B = (L + 7) / 8;
-    const int32_t *idreg = reinterpret_cast<const int32_t *>(in);
-    const uint8_t *bm = in + 4 * n_seq * k, *tail = bm + n_seq * k * B;
-    const bool aligned = ((n_seq * k * B) & 3) == 0;
-    const int64_t warps = static_cast<int64_t>(gridDim.x) * kFabcWarps;
-    for (int64_t s = static_cast<int64_t>(blockIdx.x) * kFabcWarps + (threadIdx.x >> 5); s < n_seq; s += warps) {
-        int32_t my_id = 0;
-        if (lane < k) my_id = idreg[s * k + lane];
-        int64_t t = off[s];
-        for (int c = 0; c < L; c += 32) {
-            const int i = c + lane;
-            int found = -1;
-            for (int j = 0; j < k && i < L; ++j)
-                if (found < 0 && ((bm[(s * k + j) * B + (i >> 3)] >> (i & 7)) & 1u)) found = j;
-            int32_t v = 0;
-            for (int j = 0; j < k; ++j) {  // every lane joins the shuffles
-                const int32_t idj = __shfl_sync(kFull, my_id, j);
-                if (found == j) v = idj;
-            }
-            const uint32_t fromtail = __ballot_sync(kFull, i < L && found < 0);
-            if (fromtail >> lane & 1u) {
-                const int64_t ti = t + __popc(fromtail & ((1u << lane) - 1u));
-                v = ti < tail_cap ? get32(tail, ti, aligned) : -1;  // past the buffer: -1
-            }
-            if (i < L) walks[s * L + i] = v;
-            t += __popc(fromtail);
-        }
     }
 }
 
@@ -277,6 +479,9 @@ static FabcWorkspace carve_fabc(Carver &c, int64_t n_seq) {
 
 static int seq_grid(int64_t n_seq) {
     return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((n_seq + kFabcWarps - 1) / kFabcWarps, sm_count() * 8)));
+}
+static int tile_grid(int64_t n_seq, int ts) {
+    return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((n_seq + ts - 1) / ts, sm_count() * 8)));
 }
 
 static felog_status scan_offsets(FabcWorkspace &w, int64_t n_seq, int64_t *total, cudaStream_t s) {
@@ -354,17 +559,31 @@ extern "C" felog_status felog_fabc_encode(const int32_t *walks, int64_t n_seq, i
                                           size_t workspace_bytes, void *stream) {
     if (n_seq < 0 || L < 1 || k < 0 || k > kFabcMaxK || !tail) return FELOG_ERR_INVALID_ARG;
     if (n_seq > 0 && (!walks || !out || (k > 0 && !ids))) return FELOG_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(out) & 3u) || (reinterpret_cast<uintptr_t>(walks) & 3u)) return FELOG_ERR_INVALID_ARG;
     if (out_bytes < felog_fabc_max_bytes(n_seq, L, k)) return FELOG_ERR_INVALID_ARG;
     if (!workspace || workspace_bytes < felog_fabc_workspace_bytes(n_seq)) return FELOG_ERR_WORKSPACE;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     Carver c(workspace, workspace_bytes);
     FabcWorkspace w = carve_fabc(c, n_seq);
     if (n_seq == 0) return record_cuda_error(cudaMemsetAsync(tail, 0, sizeof(int64_t), s), "fabc");
-    const int grid = seq_grid(n_seq);
-    k_fabc_tail_len<<<grid, kFabcThreads, 0, s>>>(walks, n_seq, L, ids, k, w.off);
-    felog_status st = scan_offsets(w, n_seq, tail, s);
-    if (st) return st;
-    k_fabc_encode<<<grid, kFabcThreads, 0, s>>>(walks, n_seq, L, ids, k, w.off, out);
+    const int ts = encode_tile_seqs(L);
+    const int smem = ts ? encode_stage_bytes(ts, L) : 0;
+    if (k > 0) {  // tail lengths and their offsets; with k = 0 the tail of s starts at s*L
+        if (ts)
+            k_fabc_encode_st<true><<<tile_grid(n_seq, ts), kFabcThreads, smem, s>>>(walks, n_seq, L, ts, ids, k,
+                                                                                  nullptr, w.off, out, tail);
+        else
+            k_fabc_encode_g<true><<<seq_grid(n_seq), kFabcThreads, 0, s>>>(walks, n_seq, L, ids, k, nullptr, w.off,
+                                                                           out, tail);
+        felog_status st = scan_offsets(w, n_seq, tail, s);
+        if (st) return st;
+    }
+    if (ts)
+        k_fabc_encode_st<false><<<tile_grid(n_seq, ts), kFabcThreads, smem, s>>>(walks, n_seq, L, ts, ids, k, w.off,
+                                                                               nullptr, out, tail);
+    else
+        k_fabc_encode_g<false><<<seq_grid(n_seq), kFabcThreads, 0, s>>>(walks, n_seq, L, ids, k, w.off, nullptr, out,
+                                                                        tail);
     return check_launch("felog_fabc_encode");
 }
 
@@ -374,16 +593,25 @@ extern "C" felog_status felog_fabc_decode(const uint8_t *in, size_t in_bytes, in
     const int64_t head = 4 * n_seq * k + n_seq * k * ((L + 7) / 8);
     if (static_cast<int64_t>(in_bytes) < head) return FELOG_ERR_INVALID_ARG;
     if (n_seq > 0 && (!in || !walks)) return FELOG_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(in) & 3u) || (reinterpret_cast<uintptr_t>(walks) & 3u)) return FELOG_ERR_INVALID_ARG;
     if (!workspace || workspace_bytes < felog_fabc_workspace_bytes(n_seq)) return FELOG_ERR_WORKSPACE;
     if (n_seq == 0) return FELOG_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     Carver c(workspace, workspace_bytes);
     FabcWorkspace w = carve_fabc(c, n_seq);
-    const int grid = seq_grid(n_seq);
-    k_fabc_tail_len_dec<<<grid, kFabcThreads, 0, s>>>(in + 4 * n_seq * k, n_seq, L, k, w.off);
-    felog_status st = scan_offsets(w, n_seq, reinterpret_cast<int64_t *>(w.total), s);
-    if (st) return st;
-    k_fabc_decode<<<grid, kFabcThreads, 0, s>>>(in, n_seq, L, k, w.off, (static_cast<int64_t>(in_bytes) - head) / 4,
-                                                 walks);
+    int64_t *total = reinterpret_cast<int64_t *>(w.total);
+    if (k > 0) {
+        const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((n_seq + kFabcThreads - 1) / kFabcThreads, sm_count() * 8)));
+        k_fabc_tail_len_dec<<<grid, kFabcThreads, 0, s>>>(in + 4 * n_seq * k, n_seq, L, k, w.off);
+        felog_status st = scan_offsets(w, n_seq, total, s);
+        if (st) return st;
+    }
+    const int64_t cap = (static_cast<int64_t>(in_bytes) - head) / 4;
+    const int ts = decode_tile_seqs(L, k);
+    if (ts)
+        k_fabc_decode_st<<<tile_grid(n_seq, ts), kFabcThreads, decode_stage_bytes(ts, L, k), s>>>(
+            in, n_seq, L, k, ts, w.off, total, cap, walks);
+    else
+        k_fabc_decode_g<<<seq_grid(n_seq), kFabcThreads, 0, s>>>(in, n_seq, L, k, w.off, cap, walks);
     return check_launch("felog_fabc_decode");
 }

@@ -8,7 +8,8 @@
 // j, stream 8), proposes neighbour floor(u64 * deg / 2^64) and accepts iff
 // (hi64 >> 11) * 2^-53 < alpha(x) / alpha_max (binary64), after 64 rejected
 // attempts the last proposal.  "x is a neighbour of t" is a binary search
-// in t's sorted CSR row.  Rows, -1 padding and counts as in felog_walk.
+// in t's sorted CSR row, made only when it decides the attempt.  Rows, -1
+// padding and counts as in felog_walk.
 #include <algorithm>
 
 #include "common.cuh"
@@ -38,11 +39,37 @@ struct N2vThresholds {
     double back, near, far;  // alpha / alpha_max for x == t, x ~ t, otherwise
 };
 
+constexpr int kN2vGroup = 8;  // steps buffered per walker before they are stored
+
+// the buffered steps t0 .. t0 + n - 1 of one walker to its row: 32 bytes in
+// two 16-byte stores when whole and aligned, else one by one
+__device__ __forceinline__ void n2v_flush(int32_t *__restrict__ dst, const int32_t *__restrict__ buf, int n) {
+    if (n == kN2vGroup && (reinterpret_cast<uintptr_t>(dst) & 15u) == 0) {
+        reinterpret_cast<int4 *>(dst)[0] = make_int4(buf[0], buf[kN2vThreads], buf[2 * kN2vThreads], buf[3 * kN2vThreads]);
+        reinterpret_cast<int4 *>(dst)[1] =
+            make_int4(buf[4 * kN2vThreads], buf[5 * kN2vThreads], buf[6 * kN2vThreads], buf[7 * kN2vThreads]);
+    } else {
+        for (int i = 0; i < n; ++i) dst[i] = buf[i * kN2vThreads];
+    }
+}
+
+// Each walker buffers its steps in shared memory and stores them 8 at a time,
+// so that a row's 32-byte sectors are written whole: one at a time, the
+// stores of 600k walkers interleaved with random reads of the graph were
+// evicted from L2 half-written and cost several DRAM writes each.  The
+// acceptance test only searches t's row when the draw u falls between the
+// two thresholds that x != t can have (below both: accept; at or above
+// both: reject), which takes the same decision the full test would.
 template <bool COUNT>
 __global__ void __launch_bounds__(kN2vThreads)
     k_walk_n2v(const int32_t *__restrict__ offsets, const int32_t *__restrict__ cols,
                const int32_t *__restrict__ starts, int32_t n_starts, int32_t L, int32_t wpr, N2vThresholds th,
                uint64_t seed, uint32_t round, int32_t *__restrict__ walks, uint32_t *__restrict__ counts) {
+    __shared__ int32_t stage[kN2vGroup * kN2vThreads];
+    int32_t *buf = stage + threadIdx.x;  // step t0 + i at buf[i * kN2vThreads]
+    const double lo_thr = th.near < th.far ? th.near : th.far;
+    const double hi_thr = th.near < th.far ? th.far : th.near;
+    const bool near_wins = th.near > th.far;  // between the thresholds, accept iff x ~ t does
     const int64_t total = static_cast<int64_t>(n_starts) * wpr;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int64_t w = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; w < total; w += stride) {
@@ -51,9 +78,9 @@ __global__ void __launch_bounds__(kN2vThreads)
         const int32_t s = __ldg(starts + i);
         const uint32_t x2 = round * static_cast<uint32_t>(wpr) + static_cast<uint32_t>(j);
         int32_t *row = walks + w * L;
-        row[0] = s;
+        buf[0] = s;
         if (COUNT) atomicAdd(counts + s, 1u);
-        int32_t prev = -1, v = s;
+        int32_t prev = -1, v = s, plo = 0, phi = 0;  // plo, phi: prev's row
         bool alive = true;
         for (int32_t t = 1; t < L; ++t) {
             int32_t nxt = -1;
@@ -63,24 +90,32 @@ __global__ void __launch_bounds__(kN2vThreads)
                 if (deg == 0) {
                     alive = false;
                 } else {
-                    const int32_t plo = prev >= 0 ? __ldg(offsets + prev) : 0;
-                    const int32_t phi = prev >= 0 ? __ldg(offsets + prev + 1) : 0;
                     for (uint32_t a = 0; a < kN2vAttempts; ++a) {
                         const u32x4 r = philox(seed, static_cast<uint32_t>(t) | (a << 16), static_cast<uint32_t>(s),
                                                x2, kStreamN2v);
                         nxt = __ldg(cols + lo + static_cast<int64_t>(mulhi64(lo64(r), static_cast<uint64_t>(deg))));
                         if (prev < 0) break;  // first step: uniform
-                        const double thr = nxt == prev ? th.back : (in_row(cols, plo, phi, nxt) ? th.near : th.far);
                         const double u = static_cast<double>(hi64(r) >> 11) * 0x1p-53;
-                        if (u < thr) break;
+                        if (nxt == prev) {
+                            if (u < th.back) break;
+                        } else if (u < lo_thr) {
+                            break;
+                        } else if (u < hi_thr && in_row(cols, plo, phi, nxt) == near_wins) {
+                            break;
+                        }
                     }
                     prev = v;
+                    plo = lo;
+                    phi = hi;
                     v = nxt;
                     if (COUNT) atomicAdd(counts + nxt, 1u);
                 }
             }
-            row[t] = nxt;
+            buf[(t % kN2vGroup) * kN2vThreads] = nxt;
+            if (t % kN2vGroup == kN2vGroup - 1) n2v_flush(row + t - (kN2vGroup - 1), buf, kN2vGroup);
         }
+        const int32_t rest = L % kN2vGroup;  // steps still buffered
+        if (rest) n2v_flush(row + L - rest, buf, rest);
     }
 }
 

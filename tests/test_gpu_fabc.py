@@ -73,6 +73,73 @@ def test_encode_bytes_match_oracle_and_decode_inverts(fl, orc, N, L, k, pad):
     assert np.array_equal(back2.cpu().numpy(), W)
 
 
+@pytest.mark.parametrize("N,L,k", [(9, 3000, 2), (5, 7000, 3), (131, 100, 4), (70, 81, 0), (200, 1504, 1),
+                                   (3, 1505, 2)])
+def test_tile_shapes_and_long_sequences(fl, orc, N, L, k):
+    """Tiles of 64 sequences with a ragged last one, tile sizes other than 64
+    (L = 100, 1504), and sequences too long to stage (L = 1505 and 3000 for
+    encode, 7000 for both) against the oracle's bytes."""
+    rng = np.random.default_rng(N + L + k)
+    W = rng.integers(0, 16, size=(N, L)).astype(np.int32)
+    W[::4, L // 3:] = -1
+    ids = np.arange(k, dtype=np.int32) * 2
+    ref = orc.fabc_encode(W, ids)
+    buf, tail = fl.felog_fabc_encode(_dev(W), _dev(ids))
+    size = fl.fabc_encoded_bytes(N, L, k, int(tail.item()))
+    assert size == ref.size and np.array_equal(buf[:size].cpu().numpy(), ref)
+    assert np.array_equal(fl.felog_fabc_decode(_dev(ref), N, L, k).cpu().numpy(), W)
+
+
+@pytest.mark.parametrize("shift", [1, 2, 3])
+def test_walks_off_16_byte_boundary(fl, orc, shift):
+    """Walks starting 4, 8 or 12 bytes past a 16-byte boundary (the staging
+    falls back from 16-byte to 4-byte loads) encode and decode the same."""
+    N, L, k = 150, 80, 2
+    rng = np.random.default_rng(shift)
+    W = rng.integers(0, 8, size=(N, L)).astype(np.int32)
+    ids = np.array([1, 5], np.int32)
+    big = torch.zeros(N * L + 4, dtype=torch.int32, device="cuda")
+    view = big[shift:shift + N * L].view(N, L)
+    view.copy_(_dev(W))
+    ref = orc.fabc_encode(W, ids)
+    buf, tail = fl.felog_fabc_encode(view, _dev(ids))
+    size = fl.fabc_encoded_bytes(N, L, k, int(tail.item()))
+    assert np.array_equal(buf[:size].cpu().numpy(), ref)
+    out = big[shift:shift + N * L].view(N, L)
+    out.zero_()
+    fl.felog_fabc_decode(buf[:size].clone(), N, L, k, walks=out)
+    assert np.array_equal(out.cpu().numpy(), W)
+
+
+def test_unaligned_buffers_are_refused(fl):
+    """The encoded buffer must start on a 4-byte boundary (documented)."""
+    W = torch.zeros((4, 80), dtype=torch.int32, device="cuda")
+    ids = torch.tensor([0], dtype=torch.int32, device="cuda")
+    buf, tail = fl.felog_fabc_encode(W, ids)
+    size = fl.fabc_encoded_bytes(4, 80, 1, int(tail.item()))
+    raw = torch.zeros(size + 4, dtype=torch.uint8, device="cuda")
+    raw[1:1 + size] = buf[:size]
+    with pytest.raises(fl.FelogError):
+        fl.felog_fabc_decode(raw[1:1 + size], 4, 80, 1)
+    assert torch.equal(fl.felog_fabc_decode(raw[1:1 + size].clone(), 4, 80, 1), W)
+
+
+def test_damaged_tail_decodes_as_minus_one(fl, orc):
+    """A buffer cut short inside the tail: the ids past the end come back
+    as -1 and nothing past in_bytes is read."""
+    N, L, k = 100, 40, 1
+    rng = np.random.default_rng(9)
+    W = rng.integers(0, 6, size=(N, L)).astype(np.int32)
+    ids = np.array([0], np.int32)
+    ref = orc.fabc_encode(W, ids)
+    cut = ref.size - 4 * 37
+    back = fl.felog_fabc_decode(_dev(ref[:cut]), N, L, k).cpu().numpy()
+    want = W.copy()
+    tail_pos = np.argwhere(W.ravel() != 0).ravel()  # tail positions in order
+    want.ravel()[tail_pos[-37:]] = -1
+    assert np.array_equal(back, want)
+
+
 def test_empty_and_degenerate(fl):
     W = torch.zeros((0, 80), dtype=torch.int32, device="cuda")
     ids = torch.tensor([1, 2], dtype=torch.int32, device="cuda")

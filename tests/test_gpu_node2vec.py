@@ -37,6 +37,21 @@ def test_node2vec_bit_exact(fl, orc, graph, L, wpr, p, q, rnd):
     assert np.array_equal(counts.cpu().numpy().astype(np.int64), orc.counts(ref, g.n).astype(np.int64))
 
 
+@pytest.mark.parametrize("shift,L", [(1, 80), (2, 21), (0, 9)])
+def test_node2vec_rows_off_16_byte_boundary(fl, orc, shift, L):
+    """Rows that do not start on 16-byte boundaries (the 8-step groups are
+    then stored one id at a time) and lengths that leave a partial group."""
+    g = inputs.rmat(12, 16, seed=3)
+    starts = np.arange(g.n, dtype=np.int32)
+    ref = orc.walk_node2vec(g.offsets, g.cols, starts, L, 1, 0.5, 2.0, 6, 1)
+    dg = fl.DeviceGraph.from_host(g)
+    big = torch.full((g.n * L + 4,), 7, dtype=torch.int32, device="cuda")
+    out = big[shift:shift + g.n * L].view(g.n, L)
+    fl.felog_walk_node2vec(dg, _dev(starts), starts.size, L, 1, 0.5, 2.0, 6, 1, out=out)
+    assert np.array_equal(out.cpu().numpy(), ref)
+    assert int(big[:shift].ne(7).sum()) == 0 and int(big[shift + g.n * L:].ne(7).sum()) == 0
+
+
 @pytest.mark.slow
 def test_node2vec_rmat20_sampled(fl, orc):
     """Full-size graph, all non-isolated starts on the GPU; 2,000 sampled
