@@ -637,20 +637,21 @@ def _fabc_form(fl, walks, counts, reps=5):
     out = {"workload": f"one plain round of the round workload: {N} walks x {Lw}",
            "eq8": {"k": len(ids), "F_k": F, "g_k": 1 - F + len(ids) / Lw + len(ids) / 32}}
     top2 = torch.topk(counts.long(), 2).indices.tolist()
+    ws = fl.fabc_workspace(N, walks.device)
     for name, sel in (("eq8", ids), ("top2", top2)):
         ids_d = torch.tensor(sel, dtype=torch.int32, device=walks.device)
         k = len(sel)
-        buf, tail = fl.felog_fabc_encode(walks, ids_d)
+        buf, tail = fl.felog_fabc_encode(walks, ids_d, workspace=ws)
         size = fl.fabc_encoded_bytes(N, Lw, k, int(tail.item()))
-        back = fl.felog_fabc_decode(buf[:size], N, Lw, k)
+        back = fl.felog_fabc_decode(buf[:size], N, Lw, k, workspace=ws)
         ok = bool(torch.equal(back, walks))
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         ev[0].record()
-        for _ in range(reps):
-            fl.felog_fabc_encode(walks, ids_d)
+        for _ in range(reps):  # output, tail count and workspace reused, as a caller streaming rounds would
+            fl.felog_fabc_encode(walks, ids_d, workspace=ws, out=buf, tail=tail)
         ev[1].record()
         for _ in range(reps):
-            fl.felog_fabc_decode(buf[:size], N, Lw, k, walks=back)
+            fl.felog_fabc_decode(buf[:size], N, Lw, k, walks=back, workspace=ws)
         ev[2].record()
         torch.cuda.synchronize()
         t_enc = ev[0].elapsed_time(ev[1]) / reps / 1e3

@@ -11,10 +11,14 @@
 //   N*k int32    the selected ids, stored with every sequence
 //   N*k*B bytes  bitmap (s, j) at (s*k + j)*B, bit i = walks[s][i] == ids[j]
 //   int32 tail   the ids no bitmap covers, in sequence and position order
-// Encode and decode work one warp per sequence: the bitmaps are ballots over
-// 32 positions at a time, and the tail positions are ranked within the
-// sequence by ballot prefix counts; a scan of the per-sequence tail lengths
-// gives each sequence's place in the tail.
+// For k >= 1, encode and decode work one warp per sequence: the bitmaps are
+// ballots over 32 positions at a time, and the tail positions are ranked
+// within the sequence by ballot prefix counts; a scan of the per-sequence
+// tail lengths gives each sequence's place in the tail.  A block first copies
+// a tile of up to 64 whole sequences (their walks, or their ids, bitmaps and
+// stretch of tail) to shared memory with independent coalesced loads; only
+// sequences too long for 24 KB are read in place.  For k = 0 the encoding is
+// the walks verbatim and both directions are one streaming copy.
 #include <algorithm>
 
 #include "common.cuh"
@@ -251,9 +255,8 @@ static int decode_tile_seqs(int32_t L, int32_t k) {
 }
 
 // ---------------------------------------------------------------------------
-// encode.  COUNT: the tail length of every sequence into len; else the
-// encoding, the tail of sequence s starting at off[s] (s*L when k = 0, when
-// block 0 also writes the tail total n_seq*L).  The tail starts 4Nk + NkB
+// encode, k >= 1.  COUNT: the tail length of every sequence into len; else
+// the encoding, the tail of sequence s starting at off[s].  The tail starts 4Nk + NkB
 // bytes into the buffer, a multiple of 4 only when NkB is; otherwise its
 // entries move byte by byte (the layout has no padding: its size is exactly
 // Eq. 7's count).
@@ -262,7 +265,7 @@ template <bool COUNT>
 __global__ void __launch_bounds__(kFabcThreads)
     k_fabc_encode_st(const int32_t *__restrict__ walks, int64_t n_seq, int32_t L, int32_t ts,
                      const int32_t *__restrict__ ids, int32_t k, const int64_t *__restrict__ off,
-                     int64_t *__restrict__ len, uint8_t *__restrict__ out, int64_t *__restrict__ total) {
+                     int64_t *__restrict__ len, uint8_t *__restrict__ out) {
     extern __shared__ int4 fabc_smem[];
     int64_t *soff = reinterpret_cast<int64_t *>(fabc_smem);
     int32_t *tile = reinterpret_cast<int32_t *>(reinterpret_cast<uint8_t *>(fabc_smem) + align16(ts * 8));
@@ -272,12 +275,11 @@ __global__ void __launch_bounds__(kFabcThreads)
     int32_t *idreg = reinterpret_cast<int32_t *>(out);
     uint8_t *bm = out + 4 * n_seq * k, *tail = bm + n_seq * k * B;
     const bool aligned = ((n_seq * k * B) & 3) == 0;
-    if (!COUNT && k == 0 && blockIdx.x == 0 && threadIdx.x == 0) *total = n_seq * L;
     const int64_t n_tiles = (n_seq + ts - 1) / ts;
     for (int64_t ti = blockIdx.x; ti < n_tiles; ti += gridDim.x) {
         const int64_t s0 = ti * ts;
         const int ns = static_cast<int>(n_seq - s0 < ts ? n_seq - s0 : ts);
-        if (!COUNT && static_cast<int>(threadIdx.x) < ns) soff[threadIdx.x] = k ? off[s0 + threadIdx.x] : (s0 + threadIdx.x) * L;
+        if (!COUNT && static_cast<int>(threadIdx.x) < ns) soff[threadIdx.x] = off[s0 + threadIdx.x];
         stage_words(tile, walks + s0 * L, ns * L);
         __syncthreads();
         for (int si = warp; si < ns; si += kFabcWarps) {
@@ -297,15 +299,13 @@ __global__ void __launch_bounds__(kFabcThreads)
 template <bool COUNT>
 __global__ void __launch_bounds__(kFabcThreads)
     k_fabc_encode_g(const int32_t *__restrict__ walks, int64_t n_seq, int32_t L, const int32_t *__restrict__ ids,
-                    int32_t k, const int64_t *__restrict__ off, int64_t *__restrict__ len, uint8_t *__restrict__ out,
-                    int64_t *__restrict__ total) {
+                    int32_t k, const int64_t *__restrict__ off, int64_t *__restrict__ len, uint8_t *__restrict__ out) {
     const int lane = threadIdx.x & 31;
     const int B = (L + 7) / 8;
     const int32_t my_id = lane < k ? ids[lane] : 0;
     int32_t *idreg = reinterpret_cast<int32_t *>(out);
     uint8_t *bm = out + 4 * n_seq * k, *tail = bm + n_seq * k * B;
     const bool aligned = ((n_seq * k * B) & 3) == 0;
-    if (!COUNT && k == 0 && blockIdx.x == 0 && threadIdx.x == 0) *total = n_seq * L;
     const int64_t warps = static_cast<int64_t>(gridDim.x) * kFabcWarps;
     for (int64_t s = static_cast<int64_t>(blockIdx.x) * kFabcWarps + (threadIdx.x >> 5); s < n_seq; s += warps) {
         const int32_t *row = walks + s * L;
@@ -313,13 +313,13 @@ __global__ void __launch_bounds__(kFabcThreads)
             const int64_t t = tail_len_seq(row, L, k, my_id, lane);
             if (lane == 0) len[s] = t;
         } else {
-            encode_seq(row, s, L, B, k, my_id, lane, k ? off[s] : s * L, idreg, bm, tail, aligned);
+            encode_seq(row, s, L, B, k, my_id, lane, off[s], idreg, bm, tail, aligned);
         }
     }
 }
 
 // ---------------------------------------------------------------------------
-// decode.  Tail lengths first, one thread per sequence: L minus the set bits
+// decode, k >= 1.  Tail lengths first, one thread per sequence: L minus the set bits
 // of the OR of its k bitmaps (bits at or past L ignored).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kFabcThreads)
@@ -361,10 +361,10 @@ __global__ void __launch_bounds__(kFabcThreads)
     for (int64_t ti = blockIdx.x; ti < n_tiles; ti += gridDim.x) {
         const int64_t s0 = ti * ts;
         const int ns = static_cast<int>(n_seq - s0 < ts ? n_seq - s0 : ts);
-        const int64_t t0 = k ? off[s0] : s0 * L;
-        const int64_t t1 = k ? (s0 + ns < n_seq ? off[s0 + ns] : *total) : (s0 + ns) * L;
+        const int64_t t0 = off[s0];
+        const int64_t t1 = s0 + ns < n_seq ? off[s0 + ns] : *total;
         const int64_t hi = t1 < cap ? t1 : cap, lo = t0 < hi ? t0 : hi;
-        if (static_cast<int>(threadIdx.x) < ns) soff[threadIdx.x] = (k ? off[s0 + threadIdx.x] : (s0 + threadIdx.x) * L) - t0;
+        if (static_cast<int>(threadIdx.x) < ns) soff[threadIdx.x] = off[s0 + threadIdx.x] - t0;
         const int oid = stage_bytes(sids, in + 4 * s0 * k, 4 * ns * k);
         const int obm = stage_bytes(sbm, bm + s0 * k * B, ns * k * B);
         const int otl = stage_bytes(stl, tail + 4 * lo, static_cast<int>(4 * (hi - lo)));
@@ -390,8 +390,42 @@ __global__ void __launch_bounds__(kFabcThreads)
     const int64_t warps = static_cast<int64_t>(gridDim.x) * kFabcWarps;
     for (int64_t s = static_cast<int64_t>(blockIdx.x) * kFabcWarps + (threadIdx.x >> 5); s < n_seq; s += warps) {
         const int32_t my_id = lane < k ? idreg[s * k + lane] : 0;
-        decode_seq(bm + s * k * B, my_id, L, B, k, lane, k ? off[s] : s * L, tail, cap, aligned, walks + s * L);
+        decode_seq(bm + s * k * B, my_id, L, B, k, lane, off[s], tail, cap, aligned, walks + s * L);
     }
+}
+
+// ---------------------------------------------------------------------------
+// k = 0: the encoding is the walks themselves (no ids, no bitmaps, every
+// position in the tail), so encode and decode are a copy: dst[i] = src[i]
+// for i < n_src, -1 up to n (a tail cut short); block 0 writes *total = n.
+// ---------------------------------------------------------------------------
+constexpr int kCopyUnroll = 4;
+
+__global__ void __launch_bounds__(kFabcThreads)
+    k_fabc_copy(const int32_t *__restrict__ src, int64_t n_src, int64_t n, int32_t *__restrict__ dst,
+                int64_t *__restrict__ total) {
+    if (total && blockIdx.x == 0 && threadIdx.x == 0) *total = n;
+    const int64_t m = n_src < n ? n_src : n;
+    const int64_t tid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t nthreads = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    int64_t done = 0;
+    if (((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15u) == 0) {
+        const int64_t m4 = m >> 2;
+        const int4 *s4 = reinterpret_cast<const int4 *>(src);
+        int4 *d4 = reinterpret_cast<int4 *>(dst);
+        for (int64_t base = tid; base < m4; base += kCopyUnroll * nthreads) {
+            int4 r[kCopyUnroll];
+#pragma unroll
+            for (int u = 0; u < kCopyUnroll; ++u)
+                if (base + u * nthreads < m4) r[u] = __ldcs(s4 + base + u * nthreads);
+#pragma unroll
+            for (int u = 0; u < kCopyUnroll; ++u)
+                if (base + u * nthreads < m4) __stcs(d4 + base + u * nthreads, r[u]);
+        }
+        done = 4 * m4;
+    }
+    for (int64_t i = done + tid; i < m; i += nthreads) dst[i] = src[i];
+    for (int64_t i = m + tid; i < n; i += nthreads) dst[i] = -1;
 }
 
 // ---------------------------------------------------------------------------
@@ -480,6 +514,9 @@ static FabcWorkspace carve_fabc(Carver &c, int64_t n_seq) {
 static int seq_grid(int64_t n_seq) {
     return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((n_seq + kFabcWarps - 1) / kFabcWarps, sm_count() * 8)));
 }
+static int copy_grid(int64_t n) {
+    return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((n / 4 + kFabcThreads - 1) / kFabcThreads, sm_count() * 8)));
+}
 static int tile_grid(int64_t n_seq, int ts) {
     return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((n_seq + ts - 1) / ts, sm_count() * 8)));
 }
@@ -566,24 +603,26 @@ extern "C" felog_status felog_fabc_encode(const int32_t *walks, int64_t n_seq, i
     Carver c(workspace, workspace_bytes);
     FabcWorkspace w = carve_fabc(c, n_seq);
     if (n_seq == 0) return record_cuda_error(cudaMemsetAsync(tail, 0, sizeof(int64_t), s), "fabc");
+    if (k == 0) {
+        k_fabc_copy<<<copy_grid(n_seq * L), kFabcThreads, 0, s>>>(walks, n_seq * L, n_seq * L,
+                                                                  reinterpret_cast<int32_t *>(out), tail);
+        return check_launch("felog_fabc_encode");
+    }
     const int ts = encode_tile_seqs(L);
     const int smem = ts ? encode_stage_bytes(ts, L) : 0;
-    if (k > 0) {  // tail lengths and their offsets; with k = 0 the tail of s starts at s*L
-        if (ts)
-            k_fabc_encode_st<true><<<tile_grid(n_seq, ts), kFabcThreads, smem, s>>>(walks, n_seq, L, ts, ids, k,
-                                                                                  nullptr, w.off, out, tail);
-        else
-            k_fabc_encode_g<true><<<seq_grid(n_seq), kFabcThreads, 0, s>>>(walks, n_seq, L, ids, k, nullptr, w.off,
-                                                                           out, tail);
-        felog_status st = scan_offsets(w, n_seq, tail, s);
-        if (st) return st;
-    }
+    // tail lengths, then their offsets
+    if (ts)
+        k_fabc_encode_st<true><<<tile_grid(n_seq, ts), kFabcThreads, smem, s>>>(walks, n_seq, L, ts, ids, k, nullptr,
+                                                                              w.off, out);
+    else
+        k_fabc_encode_g<true><<<seq_grid(n_seq), kFabcThreads, 0, s>>>(walks, n_seq, L, ids, k, nullptr, w.off, out);
+    felog_status st = scan_offsets(w, n_seq, tail, s);
+    if (st) return st;
     if (ts)
         k_fabc_encode_st<false><<<tile_grid(n_seq, ts), kFabcThreads, smem, s>>>(walks, n_seq, L, ts, ids, k, w.off,
-                                                                               nullptr, out, tail);
+                                                                               nullptr, out);
     else
-        k_fabc_encode_g<false><<<seq_grid(n_seq), kFabcThreads, 0, s>>>(walks, n_seq, L, ids, k, w.off, nullptr, out,
-                                                                        tail);
+        k_fabc_encode_g<false><<<seq_grid(n_seq), kFabcThreads, 0, s>>>(walks, n_seq, L, ids, k, w.off, nullptr, out);
     return check_launch("felog_fabc_encode");
 }
 
@@ -600,13 +639,16 @@ extern "C" felog_status felog_fabc_decode(const uint8_t *in, size_t in_bytes, in
     Carver c(workspace, workspace_bytes);
     FabcWorkspace w = carve_fabc(c, n_seq);
     int64_t *total = reinterpret_cast<int64_t *>(w.total);
-    if (k > 0) {
-        const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((n_seq + kFabcThreads - 1) / kFabcThreads, sm_count() * 8)));
-        k_fabc_tail_len_dec<<<grid, kFabcThreads, 0, s>>>(in + 4 * n_seq * k, n_seq, L, k, w.off);
-        felog_status st = scan_offsets(w, n_seq, total, s);
-        if (st) return st;
-    }
     const int64_t cap = (static_cast<int64_t>(in_bytes) - head) / 4;
+    if (k == 0) {
+        k_fabc_copy<<<copy_grid(n_seq * L), kFabcThreads, 0, s>>>(reinterpret_cast<const int32_t *>(in), cap,
+                                                                  n_seq * L, walks, nullptr);
+        return check_launch("felog_fabc_decode");
+    }
+    const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((n_seq + kFabcThreads - 1) / kFabcThreads, sm_count() * 8)));
+    k_fabc_tail_len_dec<<<grid, kFabcThreads, 0, s>>>(in + 4 * n_seq * k, n_seq, L, k, w.off);
+    felog_status st = scan_offsets(w, n_seq, total, s);
+    if (st) return st;
     const int ts = decode_tile_seqs(L, k);
     if (ts)
         k_fabc_decode_st<<<tile_grid(n_seq, ts), kFabcThreads, decode_stage_bytes(ts, L, k), s>>>(

@@ -341,15 +341,20 @@ def felog_fabc_select(counts: torch.Tensor, L: int, k_max: int = 32):
     return [ids[i] for i in range(k.value)], F.value
 
 
-def felog_fabc_encode(walks: torch.Tensor, ids: torch.Tensor, workspace: torch.Tensor | None = None):
+def felog_fabc_encode(walks: torch.Tensor, ids: torch.Tensor, workspace: torch.Tensor | None = None,
+                      out: torch.Tensor | None = None, tail: torch.Tensor | None = None):
     """FaBC encoding of walks [n_seq, L] (device int32) with device ids [k];
-    returns (device uint8 buffer of capacity max_bytes, device int64 tail count)."""
-    _require_cuda(walks, ids, workspace)
+    returns (device uint8 buffer of capacity max_bytes, device int64 tail count).
+    `out` and `tail` may be passed in to be reused."""
+    _require_cuda(walks, ids, workspace, out, tail)
     lib = load()
     n_seq, L = walks.shape
     k = ids.numel()
-    out = torch.empty(lib.felog_fabc_max_bytes(n_seq, L, k), dtype=torch.uint8, device=walks.device)
-    tail = torch.empty(1, dtype=torch.int64, device=walks.device)
+    cap = lib.felog_fabc_max_bytes(n_seq, L, k)
+    if out is None:
+        out = torch.empty(cap, dtype=torch.uint8, device=walks.device)
+    if tail is None:
+        tail = torch.empty(1, dtype=torch.int64, device=walks.device)
     need = lib.felog_fabc_workspace_bytes(n_seq)
     if workspace is None or workspace.numel() < need:
         workspace = _workspace(need, walks.device)
@@ -360,6 +365,11 @@ def felog_fabc_encode(walks: torch.Tensor, ids: torch.Tensor, workspace: torch.T
 
 def fabc_encoded_bytes(n_seq: int, L: int, k: int, tail: int) -> int:
     return 4 * n_seq * k + n_seq * k * ((L + 7) // 8) + 4 * tail
+
+
+def fabc_workspace(n_seq: int, device="cuda") -> torch.Tensor:
+    """A device workspace for encoding or decoding n_seq sequences, to reuse across calls."""
+    return _workspace(load().felog_fabc_workspace_bytes(n_seq), device)
 
 
 def felog_fabc_decode(buf: torch.Tensor, n_seq: int, L: int, k: int, walks: torch.Tensor | None = None,
