@@ -113,11 +113,10 @@ __device__ __forceinline__ int32_t get32(const uint8_t *p, int64_t i, bool align
     return static_cast<int32_t>(u);
 }
 
-// encodes sequence s from row[0..L) with its first tail entry at index t
-__device__ __forceinline__ void encode_seq(const int32_t *row, int64_t s, int32_t L, int B, int k, int32_t my_id,
-                                           int lane, int64_t t, int32_t *idreg, uint8_t *bm, uint8_t *tail,
-                                           bool aligned) {
-    if (lane < k) idreg[s * k + lane] = my_id;
+// encodes one sequence from row[0..L): its k bitmaps into bms[0..k*B), its
+// tail from index t on
+__device__ __forceinline__ void encode_seq(const int32_t *row, int32_t L, int B, int k, int32_t my_id, int lane,
+                                           int64_t t, uint8_t *bms, uint8_t *tail, bool aligned) {
     for (int c = 0; c < L; c += 32) {
         const bool in = c + lane < L;
         const int32_t v = in ? row[c + lane] : 0;
@@ -126,7 +125,7 @@ __device__ __forceinline__ void encode_seq(const int32_t *row, int64_t s, int32_
         // lane j < k writes bytes c/8 .. c/8 + 3 of bitmap j (those below B)
         if (lane < k)
             for (int b = 0; b < 4 && c / 8 + b < B; ++b)
-                bm[(s * k + lane) * B + c / 8 + b] = static_cast<uint8_t>(mine >> (8 * b));
+                bms[lane * B + c / 8 + b] = static_cast<uint8_t>(mine >> (8 * b));
         const uint32_t keep = __ballot_sync(kFull, in) & ~cov;
         if (keep >> lane & 1u) put32(tail, t + __popc(keep & ((1u << lane) - 1u)), v, aligned);
         t += __popc(keep);
@@ -236,11 +235,17 @@ __host__ __device__ constexpr int align16(int x) { return (x + 15) & ~15; }
 
 // encode tiles: TS sequences, a multiple of 4 so that every tile starts on a
 // 16-byte boundary of the walks; 0 = sequences too long to stage
-static int encode_tile_seqs(int32_t L) {
-    const int64_t ts = std::min<int64_t>(kStageMaxSeq, (kStageBytes - kStageMaxSeq * 8) / (4 * static_cast<int64_t>(L)));
-    return static_cast<int>(ts) & ~3;
+// with their offsets and, while encoding, their bitmaps (written out whole
+// afterwards)
+static int encode_stage_bytes(int ts, int32_t L, int32_t k) {
+    return align16(ts * 8) + align16(4 * ts * L) + align16(ts * k * ((L + 7) / 8));
 }
-static int encode_stage_bytes(int ts, int32_t L) { return align16(ts * 8) + align16(4 * ts * L); }
+static int encode_tile_seqs(int32_t L, int32_t k) {
+    if (L > kStageBytes / 16) return 0;
+    int ts = kStageMaxSeq;
+    while (ts > 0 && encode_stage_bytes(ts, L, k) > kStageBytes) ts -= 4;
+    return ts;
+}
 
 // decode tiles stage per sequence: its offset, k ids, k*B bitmap bytes and
 // at most L tail entries
@@ -267,10 +272,11 @@ __global__ void __launch_bounds__(kFabcThreads)
                      const int32_t *__restrict__ ids, int32_t k, const int64_t *__restrict__ off,
                      int64_t *__restrict__ len, uint8_t *__restrict__ out) {
     extern __shared__ int4 fabc_smem[];
+    const int B = (L + 7) / 8;
     int64_t *soff = reinterpret_cast<int64_t *>(fabc_smem);
     int32_t *tile = reinterpret_cast<int32_t *>(reinterpret_cast<uint8_t *>(fabc_smem) + align16(ts * 8));
+    uint8_t *sbm = reinterpret_cast<uint8_t *>(tile) + align16(4 * ts * L);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int B = (L + 7) / 8;
     const int32_t my_id = lane < k ? ids[lane] : 0;
     int32_t *idreg = reinterpret_cast<int32_t *>(out);
     uint8_t *bm = out + 4 * n_seq * k, *tail = bm + n_seq * k * B;
@@ -288,10 +294,18 @@ __global__ void __launch_bounds__(kFabcThreads)
                 const int64_t t = tail_len_seq(row, L, k, my_id, lane);
                 if (lane == 0) len[s0 + si] = t;
             } else {
-                encode_seq(row, s0 + si, L, B, k, my_id, lane, soff[si], idreg, bm, tail, aligned);
+                encode_seq(row, L, B, k, my_id, lane, soff[si], sbm + si * k * B, tail, aligned);
             }
         }
         __syncthreads();
+        if (!COUNT) {  // the tile's ids and bitmaps, contiguous in the output (4-byte aligned: ts % 4 == 0)
+            for (int i = threadIdx.x; i < ns * k; i += blockDim.x) idreg[s0 * k + i] = __ldg(ids + i % k);
+            const int nb = ns * k * B, nw = nb >> 2;
+            uint32_t *dw = reinterpret_cast<uint32_t *>(bm + s0 * k * B);
+            const uint32_t *sw = reinterpret_cast<const uint32_t *>(sbm);
+            for (int i = threadIdx.x; i < nw; i += blockDim.x) dw[i] = sw[i];
+            if (static_cast<int>(threadIdx.x) < nb - 4 * nw) bm[s0 * k * B + 4 * nw + threadIdx.x] = sbm[4 * nw + threadIdx.x];
+        }
     }
 }
 
@@ -313,7 +327,8 @@ __global__ void __launch_bounds__(kFabcThreads)
             const int64_t t = tail_len_seq(row, L, k, my_id, lane);
             if (lane == 0) len[s] = t;
         } else {
-            encode_seq(row, s, L, B, k, my_id, lane, off[s], idreg, bm, tail, aligned);
+            if (lane < k) idreg[s * k + lane] = my_id;
+            encode_seq(row, L, B, k, my_id, lane, off[s], bm + s * k * B, tail, aligned);
         }
     }
 }
@@ -608,8 +623,8 @@ extern "C" felog_status felog_fabc_encode(const int32_t *walks, int64_t n_seq, i
                                                                   reinterpret_cast<int32_t *>(out), tail);
         return check_launch("felog_fabc_encode");
     }
-    const int ts = encode_tile_seqs(L);
-    const int smem = ts ? encode_stage_bytes(ts, L) : 0;
+    const int ts = encode_tile_seqs(L, k);
+    const int smem = ts ? encode_stage_bytes(ts, L, k) : 0;
     // tail lengths, then their offsets
     if (ts)
         k_fabc_encode_st<true><<<tile_grid(n_seq, ts), kFabcThreads, smem, s>>>(walks, n_seq, L, ts, ids, k, nullptr,
