@@ -191,9 +191,8 @@ felog_status felog_walk(const felog_csr *g, const int32_t *starts, int32_t n_sta
  * proposes neighbour floor(u64 * deg / 2^64) and accepts iff
  * (hi64 >> 11) * 2^-53 < alpha(x) / max(1/p, 1, 1/q) in binary64.  After
  * 64 rejected attempts it takes the last proposal.  Rows, padding and
- * counts as felog_walk; L <= 65535; p, q > 0 finite.  The CSR must be
- * sorted and symmetric, as felog_csr states: "x is a neighbour of t" is a
- * binary search for x in t's row or for t in x's, whichever is shorter. */
+ * counts as felog_walk; L <= 65535; p, q > 0 finite.  The CSR rows must be
+ * sorted (a binary search decides "neighbour of t"). */
 felog_status felog_walk_node2vec(const felog_csr *g, const int32_t *starts, int32_t n_starts,
                                  const felog_walk_params *wp, double p, double q, uint64_t seed,
                                  int32_t round, int32_t *walks, uint32_t *counts, void *stream);

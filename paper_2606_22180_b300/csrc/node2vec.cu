@@ -8,8 +8,8 @@
 // neighbour floor(u64 * deg / 2^64) and accepts iff (hi64 >> 11) * 2^-53 <
 // alpha(x) / alpha_max (binary64, evaluated in an exactly equivalent integer
 // form); after 64 rejected attempts the last proposal is taken.  "x is a
-// neighbour of t" is a binary search in the shorter of the two sorted CSR
-// rows, made only when it decides the attempt.  A group of lanes per walker tries consecutive
+// neighbour of t" is a binary search in t's sorted CSR row, made only when
+// it decides the attempt.  A group of lanes per walker tries consecutive
 // attempts side by side.  Rows, -1 padding and counts as in felog_walk.
 #include <algorithm>
 #include <cmath>
@@ -57,10 +57,8 @@ static_assert(kN2vAttempts % kN2vLanes == 0 && 32 % kN2vLanes == 0, "attempt rou
 // attempt the one-at-a-time loop would stop at (after 64 rejections, the
 // 64th proposal).  A non-return proposal is accepted outright below both of
 // its possible thresholds and rejected at or above both; only in between,
-// and only for lanes ahead of the group's first outright acceptance, is
-// "x ~ t" looked up, by a binary search in the shorter of x's and t's rows
-// (the CSR is symmetric).  Every lane reads its proposal's row bounds, which
-// size that search and, for the chosen one, are the next step's row.  The lanes of a walker keep its state in step; the first
+// and only for lanes ahead of the group's first outright acceptance, is t's
+// row searched.  The lanes of a walker keep its state in step; the first
 // lane counts and buffers 8 steps in shared memory, which the group then
 // stores as whole 32-byte sectors (one id per step per walker, interleaved
 // with random reads of the graph, left sectors half-written in L2 and cost
@@ -97,29 +95,27 @@ __global__ void __launch_bounds__(kN2vThreads, kN2vBlocksPerSm)
             buf[0] = s;
             if (COUNT) atomicAdd(counts + s, 1u);
         }
-        int32_t lo = 0, hi = 0;  // v's row
-        if (valid) {
-            lo = __ldg(offsets + s);
-            hi = __ldg(offsets + s + 1);
-        }
         int32_t prev = -1, v = s, plo = 0, phi = 0;  // plo, phi: prev's row
         bool alive = valid;
         for (int32_t t = 1; t < L; ++t) {
-            if (hi == lo) alive = false;
+            int32_t lo = 0, hi = 0;
+            if (alive) {
+                lo = __ldg(offsets + v);
+                hi = __ldg(offsets + v + 1);
+                if (hi == lo) alive = false;
+            }
             const uint64_t deg = static_cast<uint64_t>(static_cast<int64_t>(hi) - lo);
-            int32_t nxt = -1, nlo = 0, nhi = 0;
+            int32_t nxt = -1;
             bool done = !alive;
             for (int k = 0; k < kN2vRounds; ++k) {
                 if (__ballot_sync(kFull, !done) == 0) break;
-                int32_t prop = -1, xlo = 0, xhi = 0;  // the proposal and its row
-                int state = 0;  // 0 reject, 1 accept, 2 decided by whether x ~ t
+                int32_t prop = -1;
+                int state = 0;  // 0 reject, 1 accept, 2 decided by t's row
                 if (!done) {
                     const uint32_t a = static_cast<uint32_t>(k * kN2vLanes + rank);
                     const u32x4 r = philox(seed, static_cast<uint32_t>(t) | (a << 16), static_cast<uint32_t>(s), x2,
                                            kStreamN2v);
                     prop = __ldg(cols + lo + static_cast<int64_t>(mulhi64(lo64(r), deg)));
-                    xlo = __ldg(offsets + prop);
-                    xhi = __ldg(offsets + prop + 1);
                     if (prev < 0) {
                         state = a == 0;  // first step: uniform, the first proposal
                     } else {
@@ -131,20 +127,12 @@ __global__ void __launch_bounds__(kN2vThreads, kN2vBlocksPerSm)
                 }
                 const uint32_t quick = __ballot_sync(kFull, state == 1) & gmask;
                 const uint32_t ahead = quick ? (quick & (~quick + 1u)) - 1u : ~0u;  // lanes before it
-                if (state == 2 && ((ahead >> lane) & 1u)) {  // symmetric rows: search the shorter one
-                    const bool nb = xhi - xlo < phi - plo ? in_row(cols, xlo, xhi, prev) : in_row(cols, plo, phi, prop);
-                    state = nb == near_wins;
-                } else if (state == 2) {
-                    state = 0;  // an earlier attempt of the round accepts
-                }
+                if (state == 2) state = ((ahead >> lane) & 1u) && in_row(cols, plo, phi, prop) == near_wins;
                 const uint32_t acc = __ballot_sync(kFull, state == 1) & gmask;
                 const int src = acc ? __ffs(acc) - 1 : gbase + kN2vLanes - 1;
                 const int32_t pick = __shfl_sync(kFull, prop, src);
-                const int32_t pick_lo = __shfl_sync(kFull, xlo, src), pick_hi = __shfl_sync(kFull, xhi, src);
                 if (!done && (acc || k == kN2vRounds - 1)) {
                     nxt = pick;
-                    nlo = pick_lo;
-                    nhi = pick_hi;
                     done = true;
                 }
             }
@@ -153,8 +141,6 @@ __global__ void __launch_bounds__(kN2vThreads, kN2vBlocksPerSm)
                 plo = lo;
                 phi = hi;
                 v = nxt;
-                lo = nlo;
-                hi = nhi;
                 if (COUNT && rank == 0) atomicAdd(counts + nxt, 1u);
             }
             if (valid && rank == 0) buf[t % kN2vGroup] = nxt;
