@@ -165,44 +165,6 @@ constexpr int kStageBytes = 24576;  // shared memory per block
 constexpr int kStageMaxSeq = 64;    // sequences per tile
 constexpr int kStageUnroll = 4;
 
-// n int32 from global src to shared dst (16-byte aligned); 16-byte vectors
-// when src is 16-byte aligned
-__device__ __forceinline__ void stage_words(int32_t *dst, const int32_t *__restrict__ src, int n) {
-    if ((reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
-        const int n4 = n >> 2;
-        const int4 *s4 = reinterpret_cast<const int4 *>(src);
-        int4 *d4 = reinterpret_cast<int4 *>(dst);
-        for (int base = threadIdx.x; base < n4; base += kStageUnroll * blockDim.x) {
-            int4 r[kStageUnroll];
-#pragma unroll
-            for (int u = 0; u < kStageUnroll; ++u) {
-                const int i = base + u * static_cast<int>(blockDim.x);
-                if (i < n4) r[u] = __ldg(s4 + i);
-            }
-#pragma unroll
-            for (int u = 0; u < kStageUnroll; ++u) {
-                const int i = base + u * static_cast<int>(blockDim.x);
-                if (i < n4) d4[i] = r[u];
-            }
-        }
-        for (int i = 4 * n4 + static_cast<int>(threadIdx.x); i < n; i += blockDim.x) dst[i] = __ldg(src + i);
-    } else {
-        for (int base = threadIdx.x; base < n; base += kStageUnroll * blockDim.x) {
-            int32_t r[kStageUnroll];
-#pragma unroll
-            for (int u = 0; u < kStageUnroll; ++u) {
-                const int i = base + u * static_cast<int>(blockDim.x);
-                if (i < n) r[u] = __ldg(src + i);
-            }
-#pragma unroll
-            for (int u = 0; u < kStageUnroll; ++u) {
-                const int i = base + u * static_cast<int>(blockDim.x);
-                if (i < n) dst[i] = r[u];
-            }
-        }
-    }
-}
-
 // n bytes from global src (any alignment) to shared dst (4-byte aligned,
 // n + 4 bytes of room): the bytes land at dst + o, o = src mod 4, so that
 // the aligned middle moves as 4-byte words; returns o
@@ -231,19 +193,44 @@ __device__ __forceinline__ int stage_bytes(uint8_t *dst, const uint8_t *__restri
     return o;
 }
 
+// asynchronous global -> shared copies (cp.async), waited on per commit group
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 __host__ __device__ constexpr int align16(int x) { return (x + 15) & ~15; }
 
 // encode tiles: TS sequences, a multiple of 4 so that every tile starts on a
-// 16-byte boundary of the walks; 0 = sequences too long to stage
-// with their offsets and, while encoding, their bitmaps (written out whole
-// afterwards)
+// 16-byte boundary of the walks; 0 = sequences too long to stage.  Two
+// buffers of offsets and walks (the next tile arrives while this one is
+// encoded) and the tile's bitmaps, written out whole afterwards.
+constexpr int kEncodeStageBytes = 40960;
+static_assert(kEncodeStageBytes <= 48 * 1024, "dynamic shared memory above 48 KB needs an opt-in");
+static int encode_buffer_bytes(int ts, int32_t L) { return align16(ts * 8) + align16(4 * ts * L); }
 static int encode_stage_bytes(int ts, int32_t L, int32_t k) {
-    return align16(ts * 8) + align16(4 * ts * L) + align16(ts * k * ((L + 7) / 8));
+    return 2 * encode_buffer_bytes(ts, L) + align16(ts * k * ((L + 7) / 8));
 }
 static int encode_tile_seqs(int32_t L, int32_t k) {
-    if (L > kStageBytes / 16) return 0;
+    if (L > kEncodeStageBytes / 32) return 0;
     int ts = kStageMaxSeq;
-    while (ts > 0 && encode_stage_bytes(ts, L, k) > kStageBytes) ts -= 4;
+    while (ts > 0 && encode_stage_bytes(ts, L, k) > kEncodeStageBytes) ts -= 4;
     return ts;
 }
 
@@ -273,21 +260,46 @@ __global__ void __launch_bounds__(kFabcThreads)
                      int64_t *__restrict__ len, uint8_t *__restrict__ out) {
     extern __shared__ int4 fabc_smem[];
     const int B = (L + 7) / 8;
-    int64_t *soff = reinterpret_cast<int64_t *>(fabc_smem);
-    int32_t *tile = reinterpret_cast<int32_t *>(reinterpret_cast<uint8_t *>(fabc_smem) + align16(ts * 8));
-    uint8_t *sbm = reinterpret_cast<uint8_t *>(tile) + align16(4 * ts * L);
+    const int buf_bytes = align16(ts * 8) + align16(4 * ts * L);
+    uint8_t *sbm = reinterpret_cast<uint8_t *>(fabc_smem) + 2 * buf_bytes;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int32_t my_id = lane < k ? ids[lane] : 0;
     int32_t *idreg = reinterpret_cast<int32_t *>(out);
     uint8_t *bm = out + 4 * n_seq * k, *tail = bm + n_seq * k * B;
     const bool aligned = ((n_seq * k * B) & 3) == 0;
+    const bool vec = (reinterpret_cast<uintptr_t>(walks) & 15u) == 0;  // then every tile start is (ts % 4 == 0)
     const int64_t n_tiles = (n_seq + ts - 1) / ts;
-    for (int64_t ti = blockIdx.x; ti < n_tiles; ti += gridDim.x) {
+    // copies tile ti into buffer b: its offsets (encode) and walks
+    auto issue = [&](int64_t ti, int b) {
+        uint8_t *base = reinterpret_cast<uint8_t *>(fabc_smem) + b * buf_bytes;
+        int64_t *so = reinterpret_cast<int64_t *>(base);
+        int32_t *tl = reinterpret_cast<int32_t *>(base + align16(ts * 8));
         const int64_t s0 = ti * ts;
         const int ns = static_cast<int>(n_seq - s0 < ts ? n_seq - s0 : ts);
-        if (!COUNT && static_cast<int>(threadIdx.x) < ns) soff[threadIdx.x] = off[s0 + threadIdx.x];
-        stage_words(tile, walks + s0 * L, ns * L);
-        __syncthreads();
+        const int n = ns * L;
+        const int32_t *src = walks + s0 * L;
+        int i0 = 0;
+        if (vec) {
+            const int n4 = n >> 2;
+            for (int i = threadIdx.x; i < n4; i += blockDim.x) cp_async16(tl + 4 * i, src + 4 * i);
+            i0 = 4 * n4;
+        }
+        for (int i = i0 + static_cast<int>(threadIdx.x); i < n; i += blockDim.x) cp_async4(tl + i, src + i);
+        if (!COUNT && static_cast<int>(threadIdx.x) < ns) cp_async8(so + threadIdx.x, off + s0 + threadIdx.x);
+    };
+    int64_t ti = blockIdx.x;
+    if (ti < n_tiles) issue(ti, 0);
+    cp_async_commit();
+    for (int b = 0; ti < n_tiles; ti += gridDim.x, b ^= 1) {
+        if (ti + gridDim.x < n_tiles) issue(ti + gridDim.x, b ^ 1);
+        cp_async_commit();
+        cp_async_wait<1>();  // this thread's copies of tile ti
+        __syncthreads();     // and everyone's
+        uint8_t *base = reinterpret_cast<uint8_t *>(fabc_smem) + b * buf_bytes;
+        const int64_t *soff = reinterpret_cast<const int64_t *>(base);
+        const int32_t *tile = reinterpret_cast<const int32_t *>(base + align16(ts * 8));
+        const int64_t s0 = ti * ts;
+        const int ns = static_cast<int>(n_seq - s0 < ts ? n_seq - s0 : ts);
         for (int si = warp; si < ns; si += kFabcWarps) {
             const int32_t *row = tile + si * L;
             if (COUNT) {
@@ -307,6 +319,7 @@ __global__ void __launch_bounds__(kFabcThreads)
             if (static_cast<int>(threadIdx.x) < nb - 4 * nw) bm[s0 * k * B + 4 * nw + threadIdx.x] = sbm[4 * nw + threadIdx.x];
         }
     }
+    cp_async_wait<0>();
 }
 
 // the same, one warp per sequence straight from global memory (long L)
@@ -535,6 +548,15 @@ static int copy_grid(int64_t n) {
 static int tile_grid(int64_t n_seq, int ts) {
     return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((n_seq + ts - 1) / ts, sm_count() * 8)));
 }
+// one wave of resident blocks of a persistent kernel (each block walks its
+// tiles in a pipeline, so blocks beyond one wave would only wait)
+template <class Kernel>
+static int resident_grid(Kernel kernel, int smem, int64_t n_tiles) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kFabcThreads, smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(n_tiles, static_cast<int64_t>(sm_count()) * per_sm)));
+}
 
 static felog_status scan_offsets(FabcWorkspace &w, int64_t n_seq, int64_t *total, cudaStream_t s) {
     const int64_t tiles = (n_seq + kScanTile - 1) / kScanTile;
@@ -626,16 +648,17 @@ extern "C" felog_status felog_fabc_encode(const int32_t *walks, int64_t n_seq, i
     const int ts = encode_tile_seqs(L, k);
     const int smem = ts ? encode_stage_bytes(ts, L, k) : 0;
     // tail lengths, then their offsets
+    const int64_t n_tiles = ts ? (n_seq + ts - 1) / ts : 0;
     if (ts)
-        k_fabc_encode_st<true><<<tile_grid(n_seq, ts), kFabcThreads, smem, s>>>(walks, n_seq, L, ts, ids, k, nullptr,
-                                                                              w.off, out);
+        k_fabc_encode_st<true><<<resident_grid(k_fabc_encode_st<true>, smem, n_tiles), kFabcThreads, smem, s>>>(
+            walks, n_seq, L, ts, ids, k, nullptr, w.off, out);
     else
         k_fabc_encode_g<true><<<seq_grid(n_seq), kFabcThreads, 0, s>>>(walks, n_seq, L, ids, k, nullptr, w.off, out);
     felog_status st = scan_offsets(w, n_seq, tail, s);
     if (st) return st;
     if (ts)
-        k_fabc_encode_st<false><<<tile_grid(n_seq, ts), kFabcThreads, smem, s>>>(walks, n_seq, L, ts, ids, k, w.off,
-                                                                               nullptr, out);
+        k_fabc_encode_st<false><<<resident_grid(k_fabc_encode_st<false>, smem, n_tiles), kFabcThreads, smem, s>>>(
+            walks, n_seq, L, ts, ids, k, w.off, nullptr, out);
     else
         k_fabc_encode_g<false><<<seq_grid(n_seq), kFabcThreads, 0, s>>>(walks, n_seq, L, ids, k, w.off, nullptr, out);
     return check_launch("felog_fabc_encode");
