@@ -73,27 +73,64 @@ __global__ void k_fabc_argmax(const uint32_t *__restrict__ counts, int32_t n, in
 // copied to shared memory first) and the unstaged ones (long sequences,
 // read straight from global memory)
 // ---------------------------------------------------------------------------
-// coverage of 32 positions of a sequence by the k ids held in lanes 0..k-1
-__device__ __forceinline__ uint32_t covered_ids(int32_t v, bool in, int32_t my_id, int k, int lane, uint32_t *per_id) {
+// The selected ids as the warp holds them.  K > 0: k == K and every lane
+// keeps all K ids in registers (the loops over ids unroll); K == 0: any
+// k <= 32, id j in lane j, fetched by shuffle.
+template <int K>
+struct IdSet {
+    int32_t r[K > 0 ? K : 1];
+    int32_t mine;
+    int k;
+};
+template <int K>
+__device__ __forceinline__ IdSet<K> load_ids(const int32_t *__restrict__ ids, int k, int lane) {
+    IdSet<K> s;
+    s.k = k;
+    s.mine = K == 0 && lane < k ? __ldg(ids + lane) : 0;
+#pragma unroll
+    for (int j = 0; j < (K > 0 ? K : 1); ++j) s.r[j] = K > 0 ? __ldg(ids + j) : 0;
+    return s;
+}
+
+// coverage of 32 positions by the ids: the OR of the per-id ballots, and
+// in lane j the ballot of id j
+template <int K>
+__device__ __forceinline__ uint32_t covered_ids(int32_t v, bool in, const IdSet<K> &ids, int lane, uint32_t *per_id) {
     uint32_t any = 0;
-    for (int j = 0; j < k; ++j) {
-        const int32_t idj = __shfl_sync(kFull, my_id, j);
-        const uint32_t m = __ballot_sync(kFull, in && v == idj);
-        if (lane == j) *per_id = m;
-        any |= m;
+    if constexpr (K > 0) {
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const uint32_t m = __ballot_sync(kFull, in && v == ids.r[j]);
+            if (lane == j) *per_id = m;
+            any |= m;
+        }
+    } else {
+        for (int j = 0; j < ids.k; ++j) {
+            const uint32_t m = __ballot_sync(kFull, in && v == __shfl_sync(kFull, ids.mine, j));
+            if (lane == j) *per_id = m;
+            any |= m;
+        }
     }
     return any;
 }
 
 // number of positions of row[0..L) that no id covers (the whole warp)
-__device__ __forceinline__ int64_t tail_len_seq(const int32_t *row, int32_t L, int k, int32_t my_id, int lane) {
-    int64_t t = 0;
+template <int K>
+__device__ __forceinline__ int64_t tail_len_seq(const int32_t *row, int32_t L, const IdSet<K> &ids, int lane) {
+    int t = 0;
     for (int c = 0; c < L; c += 32) {
         const bool in = c + lane < L;
         const int32_t v = in ? row[c + lane] : 0;
-        uint32_t mine = 0;
-        const uint32_t cov = covered_ids(v, in, my_id, k, lane, &mine);
-        t += __popc(__ballot_sync(kFull, in) & ~cov);
+        if constexpr (K > 0) {
+            bool cov = false;
+#pragma unroll
+            for (int j = 0; j < K; ++j) cov |= v == ids.r[j];
+            t += __popc(__ballot_sync(kFull, in && !cov));
+        } else {
+            uint32_t mine = 0;
+            const uint32_t cov = covered_ids<K>(v, in, ids, lane, &mine);
+            t += __popc(__ballot_sync(kFull, in) & ~cov);
+        }
     }
     return t;
 }
@@ -115,13 +152,15 @@ __device__ __forceinline__ int32_t get32(const uint8_t *p, int64_t i, bool align
 
 // encodes one sequence from row[0..L): its k bitmaps into bms[0..k*B), its
 // tail from index t on
-__device__ __forceinline__ void encode_seq(const int32_t *row, int32_t L, int B, int k, int32_t my_id, int lane,
+template <int K>
+__device__ __forceinline__ void encode_seq(const int32_t *row, int32_t L, int B, const IdSet<K> &ids, int lane,
                                            int64_t t, uint8_t *bms, uint8_t *tail, bool aligned) {
+    const int k = K > 0 ? K : ids.k;
     for (int c = 0; c < L; c += 32) {
         const bool in = c + lane < L;
         const int32_t v = in ? row[c + lane] : 0;
         uint32_t mine = 0;  // lane j: the bits of id j in these 32 positions
-        const uint32_t cov = covered_ids(v, in, my_id, k, lane, &mine);
+        const uint32_t cov = covered_ids<K>(v, in, ids, lane, &mine);
         // lane j < k writes bytes c/8 .. c/8 + 3 of bitmap j (those below B)
         if (lane < k)
             for (int b = 0; b < 4 && c / 8 + b < B; ++b)
@@ -132,21 +171,28 @@ __device__ __forceinline__ void encode_seq(const int32_t *row, int32_t L, int B,
     }
 }
 
-// decodes one sequence: bms = its k*B bitmap bytes, tail entry t of the
-// sequence at tailp + 4t (entries at or past cap decode as -1)
+// decodes one sequence: bms = its k*B bitmap bytes, id j in lane j, tail
+// entry t of the sequence at tailp + 4t (entries at or past cap decode as -1)
+template <int K>
 __device__ __forceinline__ void decode_seq(const uint8_t *bms, int32_t my_id, int32_t L, int B, int k, int lane,
                                            int64_t t, const uint8_t *tailp, int64_t cap, bool aligned,
                                            int32_t *out) {
     for (int c = 0; c < L; c += 32) {
         const int i = c + lane;
-        int found = -1;
-        for (int j = 0; j < k && i < L; ++j)
-            if (found < 0 && ((bms[j * B + (i >> 3)] >> (i & 7)) & 1u)) found = j;
-        int32_t v = 0;
-        for (int j = 0; j < k; ++j) {  // every lane joins the shuffles
-            const int32_t idj = __shfl_sync(kFull, my_id, j);
-            if (found == j) v = idj;
+        int found = -1;  // the first id whose bit is set
+        if (i < L) {
+            const uint8_t *by = bms + (i >> 3);
+            const int sh = i & 7;
+            if constexpr (K > 0) {
+#pragma unroll
+                for (int j = K - 1; j >= 0; --j)
+                    if ((by[j * B] >> sh) & 1u) found = j;
+            } else {
+                for (int j = k - 1; j >= 0; --j)
+                    if ((by[j * B] >> sh) & 1u) found = j;
+            }
         }
+        int32_t v = __shfl_sync(kFull, my_id, found < 0 ? 0 : found);
         const uint32_t fromtail = __ballot_sync(kFull, i < L && found < 0);
         if (fromtail >> lane & 1u) {
             const int64_t ti = t + __popc(fromtail & ((1u << lane) - 1u));
@@ -251,9 +297,9 @@ static int decode_tile_seqs(int32_t L, int32_t k) {
 // the encoding, the tail of sequence s starting at off[s].  The tail starts 4Nk + NkB
 // bytes into the buffer, a multiple of 4 only when NkB is; otherwise its
 // entries move byte by byte (the layout has no padding: its size is exactly
-// Eq. 7's count).
+// Eq. 7's count).  K > 0: compiled for k == K (see IdSet).
 // ---------------------------------------------------------------------------
-template <bool COUNT>
+template <bool COUNT, int K>
 __global__ void __launch_bounds__(kFabcThreads)
     k_fabc_encode_st(const int32_t *__restrict__ walks, int64_t n_seq, int32_t L, int32_t ts,
                      const int32_t *__restrict__ ids, int32_t k, const int64_t *__restrict__ off,
@@ -263,7 +309,7 @@ __global__ void __launch_bounds__(kFabcThreads)
     const int buf_bytes = align16(ts * 8) + align16(4 * ts * L);
     uint8_t *sbm = reinterpret_cast<uint8_t *>(fabc_smem) + 2 * buf_bytes;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int32_t my_id = lane < k ? ids[lane] : 0;
+    const IdSet<K> idset = load_ids<K>(ids, k, lane);
     int32_t *idreg = reinterpret_cast<int32_t *>(out);
     uint8_t *bm = out + 4 * n_seq * k, *tail = bm + n_seq * k * B;
     const bool aligned = ((n_seq * k * B) & 3) == 0;
@@ -303,10 +349,10 @@ __global__ void __launch_bounds__(kFabcThreads)
         for (int si = warp; si < ns; si += kFabcWarps) {
             const int32_t *row = tile + si * L;
             if (COUNT) {
-                const int64_t t = tail_len_seq(row, L, k, my_id, lane);
+                const int64_t t = tail_len_seq<K>(row, L, idset, lane);
                 if (lane == 0) len[s0 + si] = t;
             } else {
-                encode_seq(row, L, B, k, my_id, lane, soff[si], sbm + si * k * B, tail, aligned);
+                encode_seq<K>(row, L, B, idset, lane, soff[si], sbm + si * k * B, tail, aligned);
             }
         }
         __syncthreads();
@@ -329,7 +375,7 @@ __global__ void __launch_bounds__(kFabcThreads)
                     int32_t k, const int64_t *__restrict__ off, int64_t *__restrict__ len, uint8_t *__restrict__ out) {
     const int lane = threadIdx.x & 31;
     const int B = (L + 7) / 8;
-    const int32_t my_id = lane < k ? ids[lane] : 0;
+    const IdSet<0> idset = load_ids<0>(ids, k, lane);
     int32_t *idreg = reinterpret_cast<int32_t *>(out);
     uint8_t *bm = out + 4 * n_seq * k, *tail = bm + n_seq * k * B;
     const bool aligned = ((n_seq * k * B) & 3) == 0;
@@ -337,11 +383,11 @@ __global__ void __launch_bounds__(kFabcThreads)
     for (int64_t s = static_cast<int64_t>(blockIdx.x) * kFabcWarps + (threadIdx.x >> 5); s < n_seq; s += warps) {
         const int32_t *row = walks + s * L;
         if (COUNT) {
-            const int64_t t = tail_len_seq(row, L, k, my_id, lane);
+            const int64_t t = tail_len_seq<0>(row, L, idset, lane);
             if (lane == 0) len[s] = t;
         } else {
-            if (lane < k) idreg[s * k + lane] = my_id;
-            encode_seq(row, L, B, k, my_id, lane, off[s], bm + s * k * B, tail, aligned);
+            if (lane < k) idreg[s * k + lane] = idset.mine;
+            encode_seq<0>(row, L, B, idset, lane, off[s], bm + s * k * B, tail, aligned);
         }
     }
 }
@@ -371,7 +417,8 @@ __global__ void __launch_bounds__(kFabcThreads)
 
 // staged: per tile, the offsets, ids, bitmaps and the tile's stretch of the
 // tail [off[s0], off[s0 + ns]) go to shared memory (tail entries at or past
-// cap, the end of the buffer, decode as -1)
+// cap, the end of the buffer, decode as -1).  K > 0: compiled for k == K.
+template <int K>
 __global__ void __launch_bounds__(kFabcThreads)
     k_fabc_decode_st(const uint8_t *__restrict__ in, int64_t n_seq, int32_t L, int32_t k, int32_t ts,
                      const int64_t *__restrict__ off, const int64_t *__restrict__ total, int64_t cap,
@@ -399,8 +446,8 @@ __global__ void __launch_bounds__(kFabcThreads)
         __syncthreads();
         for (int si = warp; si < ns; si += kFabcWarps) {
             const int32_t my_id = lane < k ? get32(sids + oid, static_cast<int64_t>(si) * k + lane, oid == 0) : 0;
-            decode_seq(sbm + obm + si * k * B, my_id, L, B, k, lane, soff[si], stl + otl, hi - t0, otl == 0,
-                       walks + (s0 + si) * L);
+            decode_seq<K>(sbm + obm + si * k * B, my_id, L, B, k, lane, soff[si], stl + otl, hi - t0, otl == 0,
+                          walks + (s0 + si) * L);
         }
         __syncthreads();
     }
@@ -418,7 +465,7 @@ __global__ void __launch_bounds__(kFabcThreads)
     const int64_t warps = static_cast<int64_t>(gridDim.x) * kFabcWarps;
     for (int64_t s = static_cast<int64_t>(blockIdx.x) * kFabcWarps + (threadIdx.x >> 5); s < n_seq; s += warps) {
         const int32_t my_id = lane < k ? idreg[s * k + lane] : 0;
-        decode_seq(bm + s * k * B, my_id, L, B, k, lane, off[s], tail, cap, aligned, walks + s * L);
+        decode_seq<0>(bm + s * k * B, my_id, L, B, k, lane, off[s], tail, cap, aligned, walks + s * L);
     }
 }
 
@@ -558,6 +605,40 @@ static int resident_grid(Kernel kernel, int smem, int64_t n_tiles) {
     return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(n_tiles, static_cast<int64_t>(sm_count()) * per_sm)));
 }
 
+// the staged kernels compiled for k = 1..4, the generic loop above that
+template <bool COUNT, int K>
+static void launch_encode_k(int k, int64_t n_tiles, int smem, cudaStream_t s, const int32_t *walks, int64_t n_seq,
+                            int32_t L, int ts, const int32_t *ids, int64_t *off, uint8_t *out) {
+    k_fabc_encode_st<COUNT, K><<<resident_grid(k_fabc_encode_st<COUNT, K>, smem, n_tiles), kFabcThreads, smem, s>>>(
+        walks, n_seq, L, ts, ids, k, COUNT ? nullptr : off, COUNT ? off : nullptr, out);
+}
+template <bool COUNT>
+static void launch_encode_st(int k, int64_t n_tiles, int smem, cudaStream_t s, const int32_t *walks, int64_t n_seq,
+                             int32_t L, int ts, const int32_t *ids, int64_t *off, uint8_t *out) {
+    switch (k) {
+    case 1: launch_encode_k<COUNT, 1>(k, n_tiles, smem, s, walks, n_seq, L, ts, ids, off, out); break;
+    case 2: launch_encode_k<COUNT, 2>(k, n_tiles, smem, s, walks, n_seq, L, ts, ids, off, out); break;
+    case 3: launch_encode_k<COUNT, 3>(k, n_tiles, smem, s, walks, n_seq, L, ts, ids, off, out); break;
+    case 4: launch_encode_k<COUNT, 4>(k, n_tiles, smem, s, walks, n_seq, L, ts, ids, off, out); break;
+    default: launch_encode_k<COUNT, 0>(k, n_tiles, smem, s, walks, n_seq, L, ts, ids, off, out); break;
+    }
+}
+template <int K>
+static void launch_decode_k(int grid, int smem, cudaStream_t s, const uint8_t *in, int64_t n_seq, int32_t L, int32_t k,
+                            int ts, const int64_t *off, const int64_t *total, int64_t cap, int32_t *walks) {
+    k_fabc_decode_st<K><<<grid, kFabcThreads, smem, s>>>(in, n_seq, L, k, ts, off, total, cap, walks);
+}
+static void launch_decode_st(int grid, int smem, cudaStream_t s, const uint8_t *in, int64_t n_seq, int32_t L,
+                             int32_t k, int ts, const int64_t *off, const int64_t *total, int64_t cap, int32_t *walks) {
+    switch (k) {
+    case 1: launch_decode_k<1>(grid, smem, s, in, n_seq, L, k, ts, off, total, cap, walks); break;
+    case 2: launch_decode_k<2>(grid, smem, s, in, n_seq, L, k, ts, off, total, cap, walks); break;
+    case 3: launch_decode_k<3>(grid, smem, s, in, n_seq, L, k, ts, off, total, cap, walks); break;
+    case 4: launch_decode_k<4>(grid, smem, s, in, n_seq, L, k, ts, off, total, cap, walks); break;
+    default: launch_decode_k<0>(grid, smem, s, in, n_seq, L, k, ts, off, total, cap, walks); break;
+    }
+}
+
 static felog_status scan_offsets(FabcWorkspace &w, int64_t n_seq, int64_t *total, cudaStream_t s) {
     const int64_t tiles = (n_seq + kScanTile - 1) / kScanTile;
     k_scan_tiles<<<static_cast<int>(tiles), kFabcThreads, 0, s>>>(w.off, n_seq, w.tile);
@@ -650,15 +731,13 @@ extern "C" felog_status felog_fabc_encode(const int32_t *walks, int64_t n_seq, i
     // tail lengths, then their offsets
     const int64_t n_tiles = ts ? (n_seq + ts - 1) / ts : 0;
     if (ts)
-        k_fabc_encode_st<true><<<resident_grid(k_fabc_encode_st<true>, smem, n_tiles), kFabcThreads, smem, s>>>(
-            walks, n_seq, L, ts, ids, k, nullptr, w.off, out);
+        launch_encode_st<true>(k, n_tiles, smem, s, walks, n_seq, L, ts, ids, w.off, out);
     else
         k_fabc_encode_g<true><<<seq_grid(n_seq), kFabcThreads, 0, s>>>(walks, n_seq, L, ids, k, nullptr, w.off, out);
     felog_status st = scan_offsets(w, n_seq, tail, s);
     if (st) return st;
     if (ts)
-        k_fabc_encode_st<false><<<resident_grid(k_fabc_encode_st<false>, smem, n_tiles), kFabcThreads, smem, s>>>(
-            walks, n_seq, L, ts, ids, k, w.off, nullptr, out);
+        launch_encode_st<false>(k, n_tiles, smem, s, walks, n_seq, L, ts, ids, w.off, out);
     else
         k_fabc_encode_g<false><<<seq_grid(n_seq), kFabcThreads, 0, s>>>(walks, n_seq, L, ids, k, w.off, nullptr, out);
     return check_launch("felog_fabc_encode");
@@ -689,8 +768,8 @@ extern "C" felog_status felog_fabc_decode(const uint8_t *in, size_t in_bytes, in
     if (st) return st;
     const int ts = decode_tile_seqs(L, k);
     if (ts)
-        k_fabc_decode_st<<<tile_grid(n_seq, ts), kFabcThreads, decode_stage_bytes(ts, L, k), s>>>(
-            in, n_seq, L, k, ts, w.off, total, cap, walks);
+        launch_decode_st(tile_grid(n_seq, ts), decode_stage_bytes(ts, L, k), s, in, n_seq, L, k, ts, w.off, total, cap,
+                         walks);
     else
         k_fabc_decode_g<<<seq_grid(n_seq), kFabcThreads, 0, s>>>(in, n_seq, L, k, w.off, cap, walks);
     return check_launch("felog_fabc_decode");
