@@ -106,7 +106,8 @@ __device__ __forceinline__ uint32_t covered_ids(int32_t v, bool in, const IdSet<
         }
     } else {
         for (int j = 0; j < ids.k; ++j) {
-            const uint32_t m = __ballot_sync(kFull, in && v == __shfl_sync(kFull, ids.mine, j));
+            const int32_t idj = __shfl_sync(kFull, ids.mine, j);  // every lane, before any short-circuit
+            const uint32_t m = __ballot_sync(kFull, in && v == idj);
             if (lane == j) *per_id = m;
             any |= m;
         }
