@@ -143,6 +143,22 @@ def test_damaged_tail_decodes_as_minus_one(fl, orc, k):
     assert np.array_equal(back, want)
 
 
+def test_encode_into_reused_buffers(fl, orc):
+    """A caller's output, tail count and workspace reused across encodes of
+    different corpora give each corpus's own bytes."""
+    rng = np.random.default_rng(4)
+    N, L = 200, 80
+    ws = fl.fabc_workspace(N)
+    ids = np.array([3, 7], np.int32)
+    out = tail = None
+    for trial in range(3):
+        W = rng.integers(0, 12, size=(N, L)).astype(np.int32)
+        ref = orc.fabc_encode(W, ids)
+        out, tail = fl.felog_fabc_encode(_dev(W), _dev(ids), workspace=ws, out=out, tail=tail)
+        size = fl.fabc_encoded_bytes(N, L, 2, int(tail.item()))
+        assert np.array_equal(out[:size].cpu().numpy(), ref), trial
+
+
 def test_empty_and_degenerate(fl):
     W = torch.zeros((0, 80), dtype=torch.int32, device="cuda")
     ids = torch.tensor([1, 2], dtype=torch.int32, device="cuda")
