@@ -62,8 +62,7 @@ static_assert(kN2vAttempts % kN2vLanes == 0 && 32 % kN2vLanes == 0, "attempt rou
 // lane counts and buffers 8 steps in shared memory, which the group then
 // stores as whole 32-byte sectors (one id per step per walker, interleaved
 // with random reads of the graph, left sectors half-written in L2 and cost
-// several DRAM writes each), marked evict-first so that the streaming output
-// displaces as little of the graph from L2 as it can.
+// several DRAM writes each).
 template <bool COUNT>
 __global__ void __launch_bounds__(kN2vThreads, kN2vBlocksPerSm)
     k_walk_n2v(const int32_t *__restrict__ offsets, const int32_t *__restrict__ cols,
@@ -148,14 +147,14 @@ __global__ void __launch_bounds__(kN2vThreads, kN2vBlocksPerSm)
             if (t % kN2vGroup == kN2vGroup - 1) {
                 __syncwarp();
                 if (valid)
-                    for (int i = rank; i < kN2vGroup; i += kN2vLanes) __stcs(row + t - (kN2vGroup - 1) + i, buf[i]);
+                    for (int i = rank; i < kN2vGroup; i += kN2vLanes) row[t - (kN2vGroup - 1) + i] = buf[i];
                 __syncwarp();
             }
         }
         const int32_t rest = L % kN2vGroup;  // steps still buffered
         __syncwarp();
         if (valid)
-            for (int i = rank; i < rest; i += kN2vLanes) __stcs(row + L - rest + i, buf[i]);
+            for (int i = rank; i < rest; i += kN2vLanes) row[L - rest + i] = buf[i];
         __syncwarp();
     }
 }
