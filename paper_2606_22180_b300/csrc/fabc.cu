@@ -205,8 +205,9 @@ __device__ __forceinline__ void decode_seq(const uint8_t *bms, int32_t my_id, in
 }
 
 // ---------------------------------------------------------------------------
-// staging: a block copies its tile to shared memory with independent loads
-// issued back to back (4 per thread in flight), then works from there
+// staging: a block copies its tile to shared memory and works from there.
+// Decode moves bytes with independent word loads issued back to back (4 per
+// thread in flight); encode uses cp.async, two tiles deep.
 // ---------------------------------------------------------------------------
 constexpr int kStageBytes = 24576;  // shared memory per block
 constexpr int kStageMaxSeq = 64;    // sequences per tile
