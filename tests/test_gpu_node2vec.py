@@ -52,6 +52,20 @@ def test_node2vec_rows_off_16_byte_boundary(fl, orc, shift, L):
     assert int(big[:shift].ne(7).sum()) == 0 and int(big[shift + g.n * L:].ne(7).sum()) == 0
 
 
+@pytest.mark.parametrize("p,q", [(1e6, 2e6), (1e-6, 3e5)])
+def test_node2vec_attempt_cap_bit_exact(fl, orc, p, q):
+    """Acceptance ratios near 1e-6: most steps exhaust the 64 attempts and
+    take the 64th proposal (the last lane of the last round on the GPU)."""
+    g = inputs.rmat(10, 8, seed=2)
+    starts = np.arange(g.n, dtype=np.int32)
+    ref = orc.walk_node2vec(g.offsets, g.cols, starts, 24, 2, p, q, 3, 5)
+    dg = fl.DeviceGraph.from_host(g)
+    counts = torch.zeros(g.n, dtype=torch.int32, device="cuda")
+    out = fl.felog_walk_node2vec(dg, _dev(starts), starts.size, 24, 2, p, q, 3, 5, counts=counts)
+    assert np.array_equal(out.cpu().numpy(), ref)
+    assert np.array_equal(counts.cpu().numpy().astype(np.int64), orc.counts(ref, g.n).astype(np.int64))
+
+
 @pytest.mark.slow
 def test_node2vec_rmat20_sampled(fl, orc):
     """Full-size graph, all non-isolated starts on the GPU; 2,000 sampled

@@ -5,8 +5,10 @@ Pinned by: the second-order transition law, checked by chi-square on every
 (previous, current) pair of small graphs against weights written from the
 definition (1/p back to the previous node, 1 to its neighbours, 1/q
 further out); the p = q = 1 case, where every step is uniform; every step
-an edge; a dead end padded with -1; and a degree-1 node, where the only
-move is back even when returning is unlikely.
+an edge; a dead end padded with -1; a degree-1 node, where the only move
+is back even when returning is unlikely; and the 64-attempt cap, which
+with acceptance ratios near 1e-6 makes the step the 64th proposal,
+uniform, instead of the rule's 2:1.
 """
 import numpy as np
 import pytest
@@ -76,3 +78,27 @@ def test_dead_end_and_forced_return(orc):
     # 0 has one neighbour: every step from 0 or 2 must go back to 1
     assert list(W[1]) == [0, 1, W[1, 2], 1, W[1, 4], 1]
     assert set(W[1, [2, 4]]) <= {0, 2}
+
+
+def test_attempt_cap_takes_the_64th_proposal(orc):
+    """Path 0-1-2 with p = 1e6, q = 2e6: at node 1 every proposal is accepted
+    with probability 1e-6 (back) or 5e-7 (further out), so nearly every step
+    exhausts the 64 attempts and takes the last proposal, uniform over {0, 2}.
+    The uncapped rule would give 2:1 towards the previous node."""
+    from paper_2606_22180_b300.inputs import csr_from_edges
+
+    e = np.array([(0, 1), (1, 2)], np.int64)
+    g = csr_from_edges(3, e[:, 0], e[:, 1])
+    W = orc.walk_node2vec(g.offsets, g.cols, np.array([0], np.int32), 40, 2000, 1e6, 2e6, 17, 0)
+    back = fwd = 0
+    for row in W:
+        for i in range(2, row.size):
+            if row[i - 1] == 1:
+                if row[i] == row[i - 2]:
+                    back += 1
+                else:
+                    fwd += 1
+    n = back + fwd
+    assert n > 30000
+    assert stats.chisquare([back, fwd], [n / 2, n / 2]).pvalue > 1e-4
+    assert stats.chisquare([back, fwd], [2 * n / 3, n / 3]).pvalue < 1e-12
