@@ -52,7 +52,9 @@ def test_select_hand_profile(fl, orc):
 
 @pytest.mark.parametrize("N,L,k,pad", [(1, 80, 1, False), (333, 80, 2, True), (257, 40, 3, True),
                                        (100, 13, 1, True), (64, 33, 5, False), (77, 80, 0, True),
-                                       (50, 1, 2, False), (300, 100, 32, True)])
+                                       (50, 1, 2, False), (300, 100, 32, True),
+                                       # tails off a 4-byte boundary (N k ceil(L/8) not a multiple of 4)
+                                       (101, 13, 1, True), (99, 24, 2, True), (65, 33, 5, True)])
 def test_encode_bytes_match_oracle_and_decode_inverts(fl, orc, N, L, k, pad):
     rng = np.random.default_rng(N * 7 + L + k)
     p = np.array([0.25, 0.2, 0.1] + [0.45 / 61] * 61)
