@@ -316,13 +316,15 @@ felog_status felog_fabc_select(const uint32_t *counts, int32_t n, int32_t L, int
                                size_t workspace_bytes, void *stream);
 /* walks: device int32[n_seq][L]; ids: device int32[k] (distinct); out:
  * device bytes, 4-byte aligned, out_bytes >= felog_fabc_max_bytes; *tail
- * (device int64) receives the number of tail ids. */
+ * (device int64) receives the number of tail ids.  A misaligned out or
+ * walks returns FELOG_ERR_INVALID_ARG.  With k = 0 the encoding is the walks
+ * verbatim. */
 felog_status felog_fabc_encode(const int32_t *walks, int64_t n_seq, int32_t L, const int32_t *ids,
                                int32_t k, uint8_t *out, size_t out_bytes, int64_t *tail,
                                void *workspace, size_t workspace_bytes, void *stream);
-/* in: device encoded bytes (4-byte aligned), in_bytes of them: reads stay
- * below in_bytes, and a tail position past it (a damaged buffer) decodes as
- * -1; walks: device int32[n_seq][L]. */
+/* in: device encoded bytes (4-byte aligned, else FELOG_ERR_INVALID_ARG),
+ * in_bytes of them: reads stay below in_bytes, and a tail position past it
+ * (a damaged buffer) decodes as -1; walks: device int32[n_seq][L]. */
 felog_status felog_fabc_decode(const uint8_t *in, size_t in_bytes, int64_t n_seq, int32_t L, int32_t k,
                                int32_t *walks, void *workspace, size_t workspace_bytes, void *stream);
 
