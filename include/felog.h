@@ -160,7 +160,9 @@ felog_status felog_compact_active(const uint8_t *active, int32_t n, int32_t *sta
  *     returns FELOG_ERR_INVALID_ARG and launches nothing.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *     before any stream capture.  The address is kept for later calls, which
+ *     assumes the device's primary context lives as long as the process: after
+ *     a cudaDeviceReset the kept address is stale.
  *   - All calls share the one array: calls that can overlap on the GPU (on
  *     different streams, or from different threads) race and must be
  *     serialised by the caller.  Every slot a call reads is written earlier
@@ -242,8 +244,10 @@ felog_status felog_init_tables(int32_t n, int32_t dim, int32_t precision, uint64
  * increments are added at its end; products run in bf16 on the tensor
  * cores with f32 accumulation.  *loss (device double) receives the summed
  * pair loss -log sigma(s+) - sum log sigma(-s_k) (TILE: negatives weighted
- * by K / Ns); it is NaN if a TILE launch gave up waiting for the tensor
- * cores (the launch then stops early).
+ * by K / Ns).  A TILE call waits for its launch (outside stream capture)
+ * and returns FELOG_ERR_TIMEOUT if a wait for the tensor cores ran out; the
+ * launch then stopped early, *loss is NaN and the tables are undefined.
+ * During stream capture the NaN loss is the only report.
  * Workspace: felog_train_workspace_bytes(...). */
 size_t felog_train_workspace_bytes(int64_t n_walks, int32_t L, int32_t n,
                                    const felog_train_params *tp);

@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "felog_oracle.c")
 _LIB = os.path.join(_HERE, "_felog_oracle.so")
 
-STREAM_WALK, STREAM_PSI, STREAM_NEG, STREAM_INIT = 0, 1, 2, 3
+STREAM_WALK, STREAM_PSI, STREAM_NEG, STREAM_INIT, STREAM_SR = 0, 1, 2, 3, 4
 
 
 def build(force: bool = False) -> str:
@@ -61,6 +61,10 @@ def lib() -> ctypes.CDLL:
             "oracle_noise_table": (ctypes.c_int, [P, i32, P, P, P, P]),
             "oracle_draw_negative": (i32, [P, P, i32, u64, u64, i32, i64, i32, i32, i32]),
             "oracle_init_tables": (None, [i32, i32, u64, P, P]),
+            "oracle_sr_bf16": (ctypes.c_uint32, [ctypes.c_uint32, ctypes.c_uint32]),
+            "oracle_sr_bf16_keyed": (ctypes.c_uint32, [ctypes.c_uint32, u64, ctypes.c_uint32,
+                                                       ctypes.c_uint32, ctypes.c_uint32]),
+            "oracle_sr_bf16_row": (None, [P, i64, u64, ctypes.c_uint32, ctypes.c_uint32, P]),
             "oracle_learning_rate": (f64, [f64, i64, i64]),
             "oracle_pair_update": (f64, [P, P, i32, i32, f64, P]),
             "oracle_sgns_serial": (f64, [P, i64, i32, i32, P, P, P, u64, u64, i32, i64, P, P]),
@@ -160,6 +164,27 @@ def init_tables(n: int, d: int, seed: int):
     phi_out = np.empty((n, d), np.float64)
     lib().oracle_init_tables(n, d, seed, _p(phi_in), _p(phi_out))
     return phi_in, phi_out
+
+
+def sr_bf16(xbits: int, r16: int) -> int:
+    """Stochastic rounding of the binary32 pattern xbits to bfloat16 with the
+    16 random bits r16; returns the bf16 pattern."""
+    return int(lib().oracle_sr_bf16(xbits & 0xffffffff, r16 & 0xffff))
+
+
+def sr_bf16_keyed(xbits: int, seed: int, element: int, row: int, counter: int) -> int:
+    """Stochastic rounding with bits from the rounding stream (stream 4) keyed
+    by (element / 4, row, counter)."""
+    return int(lib().oracle_sr_bf16_keyed(xbits & 0xffffffff, seed, element, row, counter))
+
+
+def sr_bf16_row(xbits, seed: int, row: int, counter: int) -> np.ndarray:
+    """Stochastic rounding of a row of binary32 patterns (uint32 array);
+    element i takes its bits from key (i / 4, row, counter).  Returns uint16."""
+    x = _c(xbits, np.uint32)
+    out = np.empty(x.shape[0], np.uint16)
+    lib().oracle_sr_bf16_row(_p(x), x.shape[0], seed, row, counter, _p(out))
+    return out
 
 
 def learning_rate(lr0: float, t: int, T: int) -> float:

@@ -30,6 +30,7 @@
 #define STREAM_PSI 1u
 #define STREAM_NEG 2u
 #define STREAM_INIT 3u
+#define STREAM_SR 4u
 #define STREAM_TILE 7u
 #define STREAM_N2V 8u
 
@@ -277,6 +278,45 @@ void oracle_init_tables(int32_t n, int32_t d, uint64_t seed, double *phi_in, dou
             phi_out[(int64_t)v * d + i] = 0.0;
         }
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Stochastic rounding of a binary32 value to bfloat16 (precision form:      */
+/* bf16 tables with float arithmetic and stochastic rounding on every        */
+/* store).  Definition: a bfloat16 is the upper half of a binary32 pattern;  */
+/* x lies between its truncation RD = x & 0xffff0000 and the next pattern    */
+/* away from zero, at the fraction f = (x & 0xffff) / 2^16 of the way.  SR   */
+/* returns the farther one with probability f: a uniform 16-bit r is added   */
+/* to the lower half and the sum is truncated, which carries into the upper  */
+/* half for exactly the f * 2^16 values r >= 2^16 - (x & 0xffff).  Carries   */
+/* run through the exponent, so the rounding crosses binades and reaches     */
+/* infinity from the largest finite values, as rounding away from zero      */
+/* does.  Reading: infinities are returned unchanged; any NaN returns the    */
+/* canonical quiet NaN 0x7fc0 (truncating could turn a NaN whose payload is  */
+/* in the lower half into an infinity).  Returns the bf16 bit pattern.       */
+/* ------------------------------------------------------------------------ */
+uint32_t oracle_sr_bf16(uint32_t xbits, uint32_t r16) {
+    uint32_t exponent = (xbits >> 23) & 0xffu, mantissa = xbits & 0x7fffffu;
+    if (exponent == 0xffu) return mantissa ? 0x7fc0u : (xbits >> 16);
+    return (uint32_t)(((uint64_t)xbits + (r16 & 0xffffu)) >> 16) & 0xffffu;
+}
+
+/* The keyed form: r16 is the low half of word (element % 4) of             */
+/* Philox(seed; x0 = element / 4, x1 = row, x2 = counter, stream 4), the     */
+/* rounding stream keyed by element, row and a per-row update counter.       */
+uint32_t oracle_sr_bf16_keyed(uint32_t xbits, uint64_t seed, uint32_t element, uint32_t row,
+                              uint32_t counter) {
+    uint32_t w[4];
+    philox4(seed, element / 4u, row, counter, STREAM_SR, w);
+    return oracle_sr_bf16(xbits, w[element % 4u] & 0xffffu);
+}
+
+/* A row store with stochastic rounding: out[i] = SR(x[i]) with the bits of  */
+/* element i of the rounding stream keyed (i / 4, row, counter).             */
+void oracle_sr_bf16_row(const uint32_t *x, int64_t m, uint64_t seed, uint32_t row, uint32_t counter,
+                        uint16_t *out) {
+    for (int64_t i = 0; i < m; ++i)
+        out[i] = (uint16_t)oracle_sr_bf16_keyed(x[i], seed, (uint32_t)i, row, counter);
 }
 
 /* linear learning-rate decay on the global token clock (reading: word2vec) */

@@ -614,7 +614,20 @@ extern "C" felog_status felog_train(const int32_t *walks, int64_t n_walks, int32
         if (st) return st;
     }
     k_loss_finish<<<1, 1, 0, s>>>(w.loss_acc, w.timeout, loss);
-    return check_launch("felog_train");
+    st = check_launch("felog_train");
+    if (st || n_walks == 0 || tp->mode != FELOG_SGNS_TILE) return st;
+    // TILE: a launch that gave up waiting for the tensor cores is a failed
+    // call.  Outside stream capture the call waits for the launch and reads
+    // the flag; during capture the NaN loss is the only report.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    st = record_cuda_error(cudaStreamIsCapturing(s, &cap), "felog_train (tile)");
+    if (st || cap != cudaStreamCaptureStatusNone) return st;
+    int32_t timed_out = 0;
+    st = record_cuda_error(cudaMemcpyAsync(&timed_out, w.timeout, sizeof timed_out, cudaMemcpyDeviceToHost, s),
+                           "felog_train (tile)");
+    if (!st) st = record_cuda_error(cudaStreamSynchronize(s), "felog_train (tile)");
+    if (!st && timed_out) st = FELOG_ERR_TIMEOUT;
+    return st;
 }
 
 extern "C" felog_status felog_init_tables(int32_t n, int32_t dim, int32_t precision, uint64_t seed,

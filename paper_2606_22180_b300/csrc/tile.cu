@@ -204,12 +204,12 @@ __global__ void __launch_bounds__(kTileThreads, 1)
     constexpr uint32_t kXo = 0, kYo = 2 * kBuf, kGo = 5 * kBuf;
     extern __shared__ __align__(1024) uint8_t sm[];
     __shared__ TileStage st_s[2];
-    __shared__ __align__(8) uint64_t bar_s[2];  // [0]: S ready, [1]: dX/dY ready
+    __shared__ __align__(8) uint64_t bar_s[3];  // [0]: S ready, [1]: dX/dY ready, [2]: drain after a timeout
     __shared__ uint32_t tmem_s;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t base = smem_addr(sm);
-    const uint32_t bar_S = smem_addr(&bar_s[0]), bar_D = smem_addr(&bar_s[1]);
+    const uint32_t bar_S = smem_addr(&bar_s[0]), bar_D = smem_addr(&bar_s[1]), bar_Z = smem_addr(&bar_s[2]);
     const int w = a.window, Ns = a.Ns, P = Ns / 128, NB = P + 1;  // column blocks per tile
     const uint64_t nn = static_cast<uint64_t>(a.n), Ssum = *a.S;
     const float omega = static_cast<float>(a.K) / static_cast<float>(Ns);
@@ -350,6 +350,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
     if (tid == 0) {
         mbar_init(bar_S, 1);
         mbar_init(bar_D, 1);
+        mbar_init(bar_Z, 1);
     }
     if (warp == 0) tmem_alloc(smem_addr(&tmem_s), 512);
     tc_fence_before();
@@ -651,7 +652,18 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         tc_fence_before();
     }
     if constexpr (kAsync) cp_async_wait_all();  // none left in flight, also after a timeout
-    if (failed && tid == 0) atomicExch(a.timeout, 1);
+    // After a timeout the tables are in an undefined state and the launch has
+    // failed (the host reports FELOG_ERR_TIMEOUT).  MMAs committed before the
+    // failed wait may still run: one more commit by the issuing thread tracks
+    // all of them, and a bounded wait on it lets them finish before the
+    // tensor memory they write is freed.
+    if (__syncthreads_or(failed)) {
+        if (tid == 0) {
+            atomicExch(a.timeout, 1);
+            mma_commit(bar_Z);
+        }
+        mbar_wait(bar_Z, 0, kTileWaitLimit);
+    }
     long long fx = __double2ll_rn(loss * kLossScale);
     for (int o = 16; o; o >>= 1) fx += __shfl_xor_sync(kFull, fx, o);
     if (lane == 0 && fx != 0) atomicAdd(a.loss_acc, static_cast<unsigned long long>(fx));
