@@ -44,7 +44,7 @@ extern "C" {
 typedef enum {
     FELOG_OK = 0,
     FELOG_ERR_INVALID_ARG = 1, /* a size, pointer or parameter is out of range */
-    FELOG_ERR_BAD_CSR = 2,     /* CSR fails host-side validation */
+    FELOG_ERR_BAD_CSR = 2,     /* CSR fails validation (host shape checks or felog_validate_csr) */
     FELOG_ERR_WORKSPACE = 3,   /* workspace missing or smaller than required */
     FELOG_ERR_CUDA = 4,        /* CUDA launch / runtime error */
     FELOG_ERR_UNSUPPORTED = 5, /* a parameter combination with no kernel */
@@ -137,6 +137,27 @@ typedef struct {
 const char *felog_status_string(felog_status s);
 /* Text of the last CUDA error seen by a call on this host thread. */
 const char *felog_last_cuda_error(void);
+
+/* Device-side check of a caller's CSR (the shape felog_csr documents) and,
+ * optionally, of a start list.  status (device int32) is cleared and then
+ * receives the OR of the FELOG_CSR_* bits of every problem found (0: valid).
+ * Columns are only read where a row's offsets are in range, so a malformed
+ * graph is reported without any out-of-range read.  Symmetry is not checked.
+ * Asynchronous: read *status after the stream reaches it.  felog_embed and
+ * felog_batch_create run this check themselves and return FELOG_ERR_BAD_CSR
+ * before any kernel reads the graph; the single-step calls (felog_walk,
+ * felog_feedback, ...) trust the graph but guard every index they derive
+ * from it, so a malformed graph cannot make them read out of range. */
+enum {
+    FELOG_CSR_ENDS = 1,         /* offsets[0] != 0, offsets[n] != nnz, or a row outside [0, nnz] */
+    FELOG_CSR_DECREASING = 2,   /* offsets[v+1] < offsets[v] */
+    FELOG_CSR_COL_RANGE = 4,    /* a column outside [0, n) */
+    FELOG_CSR_ORDER = 8,        /* a row not strictly ascending (unsorted or duplicate) */
+    FELOG_CSR_SELF_LOOP = 16,   /* a column equal to its row */
+    FELOG_CSR_START_RANGE = 32  /* a start outside [0, n) */
+};
+felog_status felog_validate_csr(const felog_csr *g, const int32_t *starts, int32_t n_starts, int32_t *status,
+                                void *stream);
 
 /* Stable compaction of the active set (Algorithm 1's V_a): starts[] receives
  * the indices v with active[v] != 0 in ascending order, *n_active (device

@@ -35,6 +35,8 @@
 namespace felog {
 
 bool csr_shape_ok(const felog_csr *g);
+felog_status validate_csr_async(const felog_csr *g, const int32_t *starts, int32_t n_starts, int32_t *status,
+                                cudaStream_t s);
 
 // largest j with prefix[j] <= x (x < prefix[n_jobs])
 __device__ __forceinline__ int find_job(const int64_t *__restrict__ prefix, int n_jobs, int64_t x) {
@@ -209,7 +211,8 @@ __global__ void k_b_walk(BArgs a) {
         const int32_t i = static_cast<int32_t>(o - static_cast<int64_t>(rep) * st.n_active);
         const int32_t s = jb.starts[i];
         const uint32_t x2 = static_cast<uint32_t>(st.round) * static_cast<uint32_t>(a.wpr) + static_cast<uint32_t>(rep);
-        walk_fill_row<true, VEC>(jb.offsets, jb.cols, s, a.L, jb.seed, x2, jb.walks + o * a.L, jb.counts);
+        walk_fill_row<true, VEC>(jb.offsets, jb.cols, jb.n, jb.nnz, s, a.L, jb.seed, x2, jb.walks + o * a.L,
+                                 jb.counts);
     }
 }
 
@@ -413,12 +416,12 @@ __global__ void __launch_bounds__(kBThreads) k_b_feedback(BArgs a) {
         if (st.done) continue;
         const BJob &jb = a.jobs[j];
         const int32_t v = static_cast<int32_t>(x - a.node_prefix[j]);
-        const int32_t lo = jb.offsets[v];
-        const int64_t deg = static_cast<int64_t>(jb.offsets[v + 1]) - lo;
+        const int32_t lo = jb.offsets[v], hi = jb.offsets[v + 1];
+        const int64_t deg = lo >= 0 && hi <= jb.nnz ? static_cast<int64_t>(hi) - lo : 0;
         const bool evaluate = deg > 0 && (a.reactivate || jb.active[st.cur][v]);
         double psi = 0.0;
         if (evaluate)
-            psi = psi_node<T>(jb.cols, static_cast<const T *>(jb.phi_in), jb.dim, a.ks, jb.seed,
+            psi = psi_node<T>(jb.cols, static_cast<const T *>(jb.phi_in), jb.n, jb.dim, a.ks, jb.seed,
                               static_cast<uint32_t>(st.round), v, lo, deg, sub_s[wib], sorted_s[wib]);
         const uint8_t next = a.enabled ? (evaluate && psi < a.mu) : (deg > 0);
         if (lane == 0) {
@@ -813,6 +816,22 @@ extern "C" felog_status felog_batch_create(const felog_job *jobs, int32_t n_jobs
         if ((st = check_job(jobs[i].graph.n, jobs[i].graph.nnz, jobs[i].dim))) return st;
         if (jobs[i].graph.n > 0 && (!jobs[i].phi_in || !jobs[i].phi_out)) return FELOG_ERR_INVALID_ARG;
     }
+    // every job's graph is checked on the device before any kernel gathers through it
+    {
+        int32_t *status = nullptr;
+        st = record_cuda_error(cudaMalloc(&status, sizeof(int32_t) * n_jobs), "felog_batch_create");
+        if (st) return st;
+        for (int32_t i = 0; i < n_jobs && !st; ++i)
+            st = validate_csr_async(&jobs[i].graph, nullptr, 0, status + i, nullptr);
+        std::vector<int32_t> host(n_jobs, 0);
+        if (!st)
+            st = record_cuda_error(cudaMemcpy(host.data(), status, sizeof(int32_t) * n_jobs, cudaMemcpyDeviceToHost),
+                                   "felog_batch_create");
+        cudaFree(status);
+        if (st) return st;
+        for (int32_t i = 0; i < n_jobs; ++i)
+            if (host[i]) return FELOG_ERR_BAD_CSR;
+    }
     felog_batch *b = new (std::nothrow) felog_batch();
     if (!b) return FELOG_ERR_INVALID_ARG;
     b->n_jobs = n_jobs;
@@ -842,6 +861,7 @@ extern "C" felog_status felog_batch_create(const felog_job *jobs, int32_t n_jobs
         jb = BJob{};
         jb.offsets = j.graph.offsets;
         jb.cols = j.graph.cols;
+        jb.nnz = j.graph.nnz;
         jb.n = j.graph.n;
         jb.dim = j.dim;
         jb.seed = j.seed;

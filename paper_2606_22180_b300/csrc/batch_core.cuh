@@ -16,6 +16,7 @@ constexpr int kBTileItems = kBTile / kBThreads;  // 16 per thread
 
 struct BJob {
     const int32_t *offsets, *cols;
+    int64_t nnz;
     int32_t n, dim;
     uint64_t seed;
     void *phi_in, *phi_out;

@@ -28,12 +28,15 @@ __global__ void k_active_init(const int32_t *__restrict__ offsets, int32_t n, ui
 
 int sm_count();
 bool csr_shape_ok(const felog_csr *g);
+felog_status validate_csr_async(const felog_csr *g, const int32_t *starts, int32_t n_starts, int32_t *status,
+                                cudaStream_t s);
 
 struct EmbedWorkspace {
     uint8_t *active[2];
     int32_t *starts;
     int32_t *n_active;
     int32_t *n_next;
+    int32_t *csr_status;
     unsigned long long *n_live;
     int32_t *walks;
     uint32_t *counts;
@@ -67,6 +70,7 @@ static EmbedWorkspace carve_embed(Carver &c, int32_t n, const felog_walk_params 
     w.starts = c.take<int32_t>(nn);
     w.n_active = c.take<int32_t>(1);
     w.n_next = c.take<int32_t>(1);
+    w.csr_status = c.take<int32_t>(1);
     w.n_live = c.take<unsigned long long>(1);
     w.walks = c.take<int32_t>(nn * wp->walks_per_round * wp->length);
     w.counts = c.take<uint32_t>(nn);
@@ -136,7 +140,15 @@ extern "C" felog_status felog_embed(const felog_csr *g, const felog_walk_params 
     EmbedWorkspace w = carve_embed(c, g->n, wp, tp_in);
     const int32_t n = g->n, L = wp->length, wpr = wp->walks_per_round;
 
-    felog_status st = felog_init_tables(n, tp_in->dim, tp_in->precision, seed, phi_in, phi_out, stream);
+    // the graph is checked on the device before any kernel gathers through it
+    int32_t csr_status = 0;
+    felog_status st = validate_csr_async(g, nullptr, 0, w.csr_status, s);
+    if (!st) st = record_cuda_error(cudaMemcpyAsync(&csr_status, w.csr_status, sizeof csr_status,
+                                                    cudaMemcpyDeviceToHost, s), "embed");
+    if (!st) st = record_cuda_error(cudaStreamSynchronize(s), "embed");
+    if (st) return st;
+    if (csr_status) return FELOG_ERR_BAD_CSR;
+    st = felog_init_tables(n, tp_in->dim, tp_in->precision, seed, phi_in, phi_out, stream);
     if (st) return st;
     st = record_cuda_error(cudaMemsetAsync(w.n_live, 0, sizeof(unsigned long long), s), "embed");
     if (st) return st;

@@ -27,7 +27,7 @@ constexpr int kPsiWarps = kPsiThreads / 32;
 
 template <class T>
 __global__ void __launch_bounds__(kPsiThreads)
-    k_feedback(const int32_t *__restrict__ offsets, const int32_t *__restrict__ cols, int32_t n,
+    k_feedback(const int32_t *__restrict__ offsets, const int32_t *__restrict__ cols, int32_t n, int64_t nnz,
                const T *__restrict__ phi, int32_t dim, int32_t enabled, double mu, int32_t ks,
                int32_t reactivate, uint64_t seed, uint32_t round, const uint8_t *__restrict__ active_in,
                uint8_t *__restrict__ active_out, double *__restrict__ psi_out,
@@ -40,11 +40,12 @@ __global__ void __launch_bounds__(kPsiThreads)
     int32_t count = 0;
     const int64_t warps = static_cast<int64_t>(gridDim.x) * kPsiWarps;
     for (int64_t v = static_cast<int64_t>(blockIdx.x) * kPsiWarps + wib; v < n; v += warps) {
-        const int32_t lo = offsets[v];
-        const int64_t deg = static_cast<int64_t>(offsets[v + 1]) - lo;
+        const int32_t lo = offsets[v], hi = offsets[v + 1];
+        // a row outside [0, nnz] (a malformed graph) is treated as isolated
+        const int64_t deg = lo >= 0 && hi <= nnz ? static_cast<int64_t>(hi) - lo : 0;
         const bool evaluate = deg > 0 && (reactivate || active_in[v]);
         double psi = __longlong_as_double(0x7ff8000000000000LL);  // quiet NaN
-        if (evaluate) psi = psi_node<T>(cols, phi, dim, ks, seed, round, v, lo, deg, sub, sorted);
+        if (evaluate) psi = psi_node<T>(cols, phi, n, dim, ks, seed, round, v, lo, deg, sub, sorted);
         uint8_t next;
         if (!enabled) next = deg > 0;
         else next = evaluate && psi < mu;
@@ -77,11 +78,11 @@ extern "C" felog_status felog_feedback(const felog_csr *g, const void *phi_in, i
     const int grid = std::min(ceil_div(g->n, kPsiWarps), sm_count() * 16);
     if (precision == FELOG_FP32)
         k_feedback<float><<<grid, kPsiThreads, 0, s>>>(
-            g->offsets, g->cols, g->n, static_cast<const float *>(phi_in), dim, fp->enabled, fp->mu,
+            g->offsets, g->cols, g->n, g->nnz, static_cast<const float *>(phi_in), dim, fp->enabled, fp->mu,
             fp->ks, fp->reactivate, seed, static_cast<uint32_t>(round), active_in, active_out, psi, n_next);
     else
         k_feedback<__nv_bfloat16><<<grid, kPsiThreads, 0, s>>>(
-            g->offsets, g->cols, g->n, static_cast<const __nv_bfloat16 *>(phi_in), dim, fp->enabled,
+            g->offsets, g->cols, g->n, g->nnz, static_cast<const __nv_bfloat16 *>(phi_in), dim, fp->enabled,
             fp->mu, fp->ks, fp->reactivate, seed, static_cast<uint32_t>(round), active_in, active_out,
             psi, n_next);
     return check_launch("felog_feedback");

@@ -65,7 +65,7 @@ static_assert(kN2vAttempts % kN2vLanes == 0 && 32 % kN2vLanes == 0, "attempt rou
 // several DRAM writes each).
 template <bool COUNT>
 __global__ void __launch_bounds__(kN2vThreads, kN2vBlocksPerSm)
-    k_walk_n2v(const int32_t *__restrict__ offsets, const int32_t *__restrict__ cols,
+    k_walk_n2v(const int32_t *__restrict__ offsets, const int32_t *__restrict__ cols, int32_t n, int64_t nnz,
                const int32_t *__restrict__ starts, int32_t n_starts, int32_t L, int32_t wpr, N2vThresholds th,
                uint64_t seed, uint32_t round, int32_t *__restrict__ walks, uint32_t *__restrict__ counts) {
     __shared__ int32_t stage[kN2vThreads / kN2vLanes][kN2vGroup];
@@ -89,20 +89,25 @@ __global__ void __launch_bounds__(kN2vThreads, kN2vBlocksPerSm)
             const int32_t j = static_cast<int32_t>(w / n_starts);
             s = __ldg(starts + (w - static_cast<int64_t>(j) * n_starts));
             x2 = round * static_cast<uint32_t>(wpr) + static_cast<uint32_t>(j);
+            if (s < 0 || s >= n) s = -1;  // a start outside the graph: a row of -1
         }
         int32_t *row = walks + (valid ? w : 0) * L;
         if (valid && rank == 0) {
             buf[0] = s;
-            if (COUNT) atomicAdd(counts + s, 1u);
+            if (COUNT && s >= 0) atomicAdd(counts + s, 1u);
         }
         int32_t prev = -1, v = s, plo = 0, phi = 0;  // plo, phi: prev's row
-        bool alive = valid;
+        bool alive = valid && s >= 0;
         for (int32_t t = 1; t < L; ++t) {
             int32_t lo = 0, hi = 0;
             if (alive) {
                 lo = __ldg(offsets + v);
                 hi = __ldg(offsets + v + 1);
-                if (hi == lo) alive = false;
+                // a row outside [0, nnz] ends the walk like a node without neighbours
+                if (hi <= lo || lo < 0 || hi > nnz) {
+                    alive = false;
+                    lo = hi = 0;
+                }
             }
             const uint64_t deg = static_cast<uint64_t>(static_cast<int64_t>(hi) - lo);
             int32_t nxt = -1;
@@ -135,6 +140,10 @@ __global__ void __launch_bounds__(kN2vThreads, kN2vBlocksPerSm)
                     nxt = pick;
                     done = true;
                 }
+            }
+            if (alive && (nxt < 0 || nxt >= n)) {  // a column outside the graph ends the walk
+                nxt = -1;
+                alive = false;
             }
             if (alive) {
                 prev = v;
@@ -182,11 +191,11 @@ extern "C" felog_status felog_walk_node2vec(const felog_csr *g, const int32_t *s
     const int64_t per_block = kN2vThreads / kN2vLanes;
     const int blocks = static_cast<int>(std::min<int64_t>(ceil_div(total, per_block), static_cast<int64_t>(sm_count()) * kN2vBlocksPerSm));
     if (counts)
-        k_walk_n2v<true><<<blocks, kN2vThreads, 0, s>>>(g->offsets, g->cols, starts, n_starts, wp->length,
+        k_walk_n2v<true><<<blocks, kN2vThreads, 0, s>>>(g->offsets, g->cols, g->n, g->nnz, starts, n_starts, wp->length,
                                                         wp->walks_per_round, th, seed, static_cast<uint32_t>(round),
                                                         walks, counts);
     else
-        k_walk_n2v<false><<<blocks, kN2vThreads, 0, s>>>(g->offsets, g->cols, starts, n_starts, wp->length,
+        k_walk_n2v<false><<<blocks, kN2vThreads, 0, s>>>(g->offsets, g->cols, g->n, g->nnz, starts, n_starts, wp->length,
                                                          wp->walks_per_round, th, seed, static_cast<uint32_t>(round),
                                                          walks, counts);
     return check_launch("felog_walk_node2vec");

@@ -113,6 +113,7 @@ felog_status upload_job(felog_server *sv, Resident &r) {
     jb = BJob{};
     jb.offsets = offsets;
     jb.cols = cols;
+    jb.nnz = q.nnz;
     jb.n = q.n;
     jb.dim = q.dim;
     jb.seed = q.seed;

@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(kSgnsThreads, 3)
     const int64_t warps = static_cast<int64_t>(gridDim.x) * kWarps;
     for (int64_t wi = static_cast<int64_t>(blockIdx.x) * kWarps + wib; wi < a.n_walks; wi += warps) {
         const int32_t *row = a.walks + wi * L;
-        for (int p = lane; p < L; p += 32) wk[p] = row[p];
+        for (int p = lane; p < L; p += 32) wk[p] = walk_id(row[p], n);
         __syncwarp();
         for (int p = 0; p < L; ++p) {
             const int32_t c = wk[p];
@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(kSgnsThreads)
     const int64_t wi = tok / L;
     const int p = static_cast<int>(tok - wi * L);
     const int32_t *row = a.walks + wi * L;
-    const int32_t c = row[p];
+    const int32_t c = walk_id(row[p], n);
     if (c < 0) return;
     for (int idx = lane; idx < 2 * W * K; idx += 32) {
         const int q = idx / K, k = idx - q * K;
@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(kSgnsThreads)
         if (o == 0) continue;
         const int pp = p + o;
         if (pp < 0 || pp >= L) continue;
-        const int32_t x = row[pp];
+        const int32_t x = walk_id(row[pp], n);
         if (x < 0) continue;
         any = true;
         const int q = o < 0 ? o + W : o + W - 1;

@@ -172,7 +172,14 @@ __device__ __forceinline__ int32_t draw_negative(const uint64_t *__restrict__ th
     const uint64_t coin = mulhi64(hi64(r), S);
     const uint64_t t = __ldg(reinterpret_cast<const unsigned long long *>(thr) + b);
     const int32_t a = __ldg(alias + b);
-    return coin < t ? static_cast<int32_t>(b) : a;
+    // b < n always; an alias outside [0, n) (a damaged table) falls back to b
+    return coin < t || static_cast<uint64_t>(static_cast<uint32_t>(a)) >= n ? static_cast<int32_t>(b) : a;
+}
+
+// A walk entry as the trainers read it: ids outside [0, n) count as padding,
+// so a damaged corpus cannot index the tables out of range.
+__device__ __forceinline__ int32_t walk_id(int32_t x, uint64_t n) {
+    return static_cast<uint64_t>(static_cast<uint32_t>(x)) < n ? x : -1;
 }
 
 // ----------------------------------------------------------------------------
@@ -475,7 +482,7 @@ __device__ __forceinline__ long long hw_train_walk(const TrainView<T> &a, const 
     const bool loss_lane = (hl & 1) == 0;
     long long loss_fx = 0;
 
-    for (int p = lane; p < L; p += 32) wk[p] = row[p];
+    for (int p = lane; p < L; p += 32) wk[p] = walk_id(row[p], n);
     __syncwarp();
     for (int p = 0; p < L; ++p) {
         const int32_t c = wk[p];

@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
             int32_t v = -1;
             int lo = 1, hi = 0;
             if (pos >= 0 && pos < a.total) {
-                v = __ldg(a.walks + pos);
+                v = walk_id(__ldg(a.walks + pos), static_cast<uint64_t>(a.n));
                 const int64_t wstart = pos - pos % a.L;  // first position of this walk
                 const int64_t wend = (wstart + a.L < a.total ? wstart + a.L : a.total) - 1;  // last position
                 lo = wstart > pos0 ? static_cast<int>(wstart - pos0) : 0;

@@ -6,6 +6,7 @@
 // step is two dependent gathers (offsets[v], offsets[v+1] then cols[...]),
 // the latency chain that bounds the kernel; the Philox block of the step is
 // computed while the previous gather is in flight.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -211,7 +212,7 @@ constexpr int kWalkThreads = 256;
 // aligned, output buffered 4 steps at a time and stored as one int4.
 template <bool COUNT, bool VEC>
 __global__ void __launch_bounds__(kWalkThreads)
-    k_walk(const int32_t *__restrict__ offsets, const int32_t *__restrict__ cols,
+    k_walk(const int32_t *__restrict__ offsets, const int32_t *__restrict__ cols, int32_t n, int64_t nnz,
            const int32_t *__restrict__ starts, int32_t n_starts, int32_t L, int32_t wpr,
            uint64_t seed, uint32_t round, int32_t *__restrict__ walks,
            uint32_t *__restrict__ counts) {
@@ -223,7 +224,7 @@ __global__ void __launch_bounds__(kWalkThreads)
         const int32_t i = static_cast<int32_t>(w - static_cast<int64_t>(j) * n_starts);
         const int32_t s = __ldg(starts + i);
         const uint32_t x2 = round * static_cast<uint32_t>(wpr) + static_cast<uint32_t>(j);
-        walk_fill_row<COUNT, VEC>(offsets, cols, s, L, seed, x2, walks + w * L, counts);
+        walk_fill_row<COUNT, VEC>(offsets, cols, n, nnz, s, L, seed, x2, walks + w * L, counts);
     }
 }
 
@@ -253,7 +254,68 @@ bool csr_shape_ok(const felog_csr *g) {
            (g->nnz == 0 || g->cols);
 }
 
+// ---------------------------------------------------------------------------
+// Device-side validation of a CSR (and optionally a start list).  One warp
+// per row: lane 0 checks the row's offsets, the lanes stride its columns.
+// Columns are read only where 0 <= offsets[v] <= offsets[v+1] <= nnz, so a
+// malformed graph is reported without any out-of-range read.  Problems are
+// OR-ed into *status as FELOG_CSR_* bits.
+// ---------------------------------------------------------------------------
+constexpr int kValidateThreads = 256;
+
+__global__ void __launch_bounds__(kValidateThreads)
+    k_validate_csr(const int32_t *__restrict__ offsets, const int32_t *__restrict__ cols, int32_t n, int64_t nnz,
+                   const int32_t *__restrict__ starts, int32_t n_starts, int32_t *__restrict__ status) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t warps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    int32_t bad = 0;
+    if (warp == 0 && lane == 0 && (offsets[0] != 0 || offsets[n] != nnz)) bad |= FELOG_CSR_ENDS;
+    for (int64_t v = warp; v < n; v += warps) {
+        const int32_t lo = offsets[v], hi = offsets[v + 1];
+        if (hi < lo) {
+            bad |= FELOG_CSR_DECREASING;
+            continue;
+        }
+        if (lo < 0 || hi > nnz) {
+            bad |= FELOG_CSR_ENDS;
+            continue;
+        }
+        for (int64_t e = lo + lane; e < hi; e += 32) {
+            const int32_t c = cols[e];
+            if (c < 0 || c >= n) bad |= FELOG_CSR_COL_RANGE;
+            if (c == v) bad |= FELOG_CSR_SELF_LOOP;
+            if (e + 1 < hi && cols[e + 1] <= c) bad |= FELOG_CSR_ORDER;
+        }
+    }
+    const int64_t tid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    for (int64_t i = tid; i < n_starts; i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int32_t s = starts[i];
+        if (s < 0 || s >= n) bad |= FELOG_CSR_START_RANGE;
+    }
+    const unsigned any = __reduce_or_sync(kFull, static_cast<unsigned>(bad));
+    if (lane == 0 && any) atomicOr(status, static_cast<int32_t>(any));
+}
+
+felog_status validate_csr_async(const felog_csr *g, const int32_t *starts, int32_t n_starts, int32_t *status,
+                                cudaStream_t s) {
+    felog_status st = record_cuda_error(cudaMemsetAsync(status, 0, sizeof(int32_t), s), "felog_validate_csr");
+    if (st) return st;
+    const int64_t warps = std::max<int64_t>(g->n, (n_starts + 31) / 32);
+    const int blocks = static_cast<int>(std::max<int64_t>(
+        1, std::min<int64_t>(ceil_div(warps, kValidateThreads / 32), static_cast<int64_t>(sm_count()) * 16)));
+    k_validate_csr<<<blocks, kValidateThreads, 0, s>>>(g->offsets, g->cols, g->n, g->nnz, starts, n_starts, status);
+    return check_launch("felog_validate_csr");
+}
+
 }  // namespace felog
+
+extern "C" felog_status felog_validate_csr(const felog_csr *g, const int32_t *starts, int32_t n_starts,
+                                           int32_t *status, void *stream) {
+    if (!csr_shape_ok(g)) return FELOG_ERR_BAD_CSR;
+    if (!status || n_starts < 0 || (n_starts > 0 && !starts)) return FELOG_ERR_INVALID_ARG;
+    return validate_csr_async(g, starts, n_starts, status, static_cast<cudaStream_t>(stream));
+}
 
 extern "C" felog_status felog_walk(const felog_csr *g, const int32_t *starts, int32_t n_starts,
                                    const felog_walk_params *wp, uint64_t seed, int32_t round,
@@ -271,7 +333,7 @@ extern "C" felog_status felog_walk(const felog_csr *g, const int32_t *starts, in
         std::min<int64_t>(ceil_div(total, kWalkThreads), static_cast<int64_t>(sm_count()) * 8));
     const bool vec = (L % 4 == 0) && (reinterpret_cast<uintptr_t>(walks) % 16 == 0);
 #define FELOG_WALK_LAUNCH(C, V)                                                                   \
-    k_walk<C, V><<<blocks, kWalkThreads, 0, s>>>(g->offsets, g->cols, starts, n_starts, L,        \
+    k_walk<C, V><<<blocks, kWalkThreads, 0, s>>>(g->offsets, g->cols, g->n, g->nnz, starts, n_starts, L, \
                                                  wp->walks_per_round, seed,                        \
                                                  static_cast<uint32_t>(round), walks, counts)
     if (counts) {

@@ -11,14 +11,19 @@ namespace felog {
 // neighbour floor(u64 * deg / 2^64).  A node without neighbours ends the walk
 // and the rest of the row is -1.  COUNT adds every written node to counts[];
 // VEC stores 4 steps at a time (L % 4 == 0, row 16-byte aligned).
+// Guards (a graph of n nodes and nnz columns): a start outside [0, n) gives a
+// row of -1; a row whose offsets leave [0, nnz] ends the walk like a node
+// without neighbours; a column outside [0, n) ends it before it is written.
+// On a well-formed graph none of them changes a walk.
 template <bool COUNT, bool VEC>
 __device__ __forceinline__ void walk_fill_row(const int32_t *__restrict__ offsets,
-                                              const int32_t *__restrict__ cols, int32_t s, int32_t L,
-                                              uint64_t seed, uint32_t x2, int32_t *__restrict__ row,
-                                              uint32_t *__restrict__ counts) {
+                                              const int32_t *__restrict__ cols, int32_t n, int64_t nnz,
+                                              int32_t s, int32_t L, uint64_t seed, uint32_t x2,
+                                              int32_t *__restrict__ row, uint32_t *__restrict__ counts) {
     int32_t v = s;
-    bool alive = true;
-    if (COUNT) atomicAdd(counts + s, 1u);
+    bool alive = s >= 0 && s < n;
+    if (!alive) s = -1;
+    if (COUNT && alive) atomicAdd(counts + s, 1u);
     if (VEC) {
         int4 buf;
         buf.x = s;
@@ -31,15 +36,20 @@ __device__ __forceinline__ void walk_fill_row(const int32_t *__restrict__ offset
                 if (alive) {
                     const int32_t lo = __ldg(offsets + v), hi = __ldg(offsets + v + 1);
                     const int64_t deg = static_cast<int64_t>(hi) - lo;
-                    if (deg == 0) {
+                    if (deg <= 0 || lo < 0 || hi > nnz) {
                         alive = false;
                     } else {
                         const u32x4 r = philox(seed, static_cast<uint32_t>(t),
                                                static_cast<uint32_t>(s), x2, kStreamWalk);
                         const uint64_t idx = mulhi64(lo64(r), static_cast<uint64_t>(deg));
                         nxt = __ldg(cols + lo + static_cast<int64_t>(idx));
-                        v = nxt;
-                        if (COUNT) atomicAdd(counts + nxt, 1u);
+                        if (nxt < 0 || nxt >= n) {
+                            nxt = -1;
+                            alive = false;
+                        } else {
+                            v = nxt;
+                            if (COUNT) atomicAdd(counts + nxt, 1u);
+                        }
                     }
                 }
                 if (u == 0) buf.x = nxt;
@@ -56,15 +66,20 @@ __device__ __forceinline__ void walk_fill_row(const int32_t *__restrict__ offset
             if (alive) {
                 const int32_t lo = __ldg(offsets + v), hi = __ldg(offsets + v + 1);
                 const int64_t deg = static_cast<int64_t>(hi) - lo;
-                if (deg == 0) {
+                if (deg <= 0 || lo < 0 || hi > nnz) {
                     alive = false;
                 } else {
                     const u32x4 r = philox(seed, static_cast<uint32_t>(t),
                                            static_cast<uint32_t>(s), x2, kStreamWalk);
                     const uint64_t idx = mulhi64(lo64(r), static_cast<uint64_t>(deg));
                     nxt = __ldg(cols + lo + static_cast<int64_t>(idx));
-                    v = nxt;
-                    if (COUNT) atomicAdd(counts + nxt, 1u);
+                    if (nxt < 0 || nxt >= n) {
+                        nxt = -1;
+                        alive = false;
+                    } else {
+                        v = nxt;
+                        if (COUNT) atomicAdd(counts + nxt, 1u);
+                    }
                 }
             }
             row[t] = nxt;

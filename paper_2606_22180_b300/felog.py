@@ -22,6 +22,7 @@ FELOG_FP32, FELOG_BF16_SR = 0, 1
 # exported symbols (the boundary); tests check each one is present
 SYMBOLS = [
     "felog_status_string", "felog_last_cuda_error",
+    "felog_validate_csr",
     "felog_compact_workspace_bytes", "felog_compact_active",
     "felog_compact_active_noalloc_max_n", "felog_compact_active_noalloc",
     "felog_walk", "felog_count",
@@ -97,6 +98,7 @@ def load() -> ctypes.CDLL:
     sig = {
         "felog_status_string": (ctypes.c_char_p, [st]),
         "felog_last_cuda_error": (ctypes.c_char_p, []),
+        "felog_validate_csr": (st, [P, P, i32, P, P]),
         "felog_compact_workspace_bytes": (sz, [i32]),
         "felog_compact_active": (st, [P, i32, P, P, P, sz, P]),
         "felog_compact_active_noalloc_max_n": (i32, []),
@@ -209,6 +211,24 @@ def table_dtype(precision: int) -> torch.dtype:
 # ---------------------------------------------------------------------------
 # One wrapper per C entry point, with the same name.
 # ---------------------------------------------------------------------------
+
+CSR_ENDS, CSR_DECREASING, CSR_COL_RANGE, CSR_ORDER, CSR_SELF_LOOP, CSR_START_RANGE = 1, 2, 4, 8, 16, 32
+
+
+def felog_validate_csr(g: DeviceGraph, starts: torch.Tensor | None = None,
+                       status: torch.Tensor | None = None) -> torch.Tensor:
+    """Device-side check of the graph (and of a start list); returns the
+    device int32 status word (0: valid, else an OR of the CSR_* bits)."""
+    _require_cuda(starts, status)
+    lib = load()
+    if status is None:
+        status = torch.empty(1, dtype=torch.int32, device=g.offsets.device)
+    csr = g._c()
+    n_starts = 0 if starts is None else starts.numel()
+    _check(lib.felog_validate_csr(ctypes.byref(csr), _ptr(starts), n_starts, _ptr(status), _stream()),
+           "felog_validate_csr")
+    return status
+
 
 def felog_compact_active(active: torch.Tensor):
     """Ascending indices of the nonzero flags; returns (starts[n], n_active device int32[1])."""
