@@ -20,12 +20,34 @@ __device__ __forceinline__ double butterfly(double s) {
     return s;
 }
 
+// Reduce-scatter of 16 per-lane partial sums over the warp: each total is
+// formed from the same pairs of partials as butterfly() (xor distance 16,
+// 8, 4, 2, 1), so it is bit-identical to the butterfly's; afterwards lanes
+// 2t and 2t + 1 hold total t.
+__device__ __forceinline__ double reduce_scatter16_f64(double (&v)[16], int lane) {
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        const int dist = 16 >> s;
+        const int half = 8 >> s;
+        const bool upper = (lane & dist) != 0;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const double send = upper ? v[i] : v[i + half];
+            const double keep = upper ? v[i + half] : v[i];
+            v[i] = __dadd_rn(keep, __shfl_xor_sync(kFull, send, dist));
+        }
+    }
+    return __dadd_rn(v[0], __shfl_xor_sync(kFull, v[0], 1));
+}
+
 // Psi of node v (deg > 0) on a warp; sub / sorted are this warp's kMaxKs-int
-// shared buffers.  Every lane returns the same value.
+// shared buffers.  Every lane returns the same value.  A neighbour id outside
+// [0, n) (a malformed graph) counts as a zero row, so nothing is read out of
+// range; on a well-formed graph it never occurs.
 template <class T>
 __device__ __forceinline__ double psi_node(const int32_t *__restrict__ cols, const T *__restrict__ phi,
-                                           int32_t dim, int32_t ks, uint64_t seed, uint32_t round, int64_t v,
-                                           int32_t lo, int64_t deg, int32_t *sub, int32_t *sorted) {
+                                           int64_t n, int32_t dim, int32_t ks, uint64_t seed, uint32_t round,
+                                           int64_t v, int32_t lo, int64_t deg, int32_t *sub, int32_t *sorted) {
     const int lane = threadIdx.x & 31;
     int32_t m;
     if (deg <= ks) {
@@ -58,7 +80,9 @@ __device__ __forceinline__ double psi_node(const int32_t *__restrict__ cols, con
         }
     }
     __syncwarp();
-    // elements l, l+32, ... of phi[v] (dim <= 256, so at most 8 per lane)
+    // elements l, l+32, ... of phi[v] (dim <= 256, so at most 8 per lane).
+    // Products of two float values are exact in binary64, so fma(x, y, s)
+    // rounds exactly as s + x * y does: one FP64 instruction per term.
     const T *pv = phi + v * dim;
     const int per_lane = dim >> 5;
     double xv[8];
@@ -67,43 +91,51 @@ __device__ __forceinline__ double psi_node(const int32_t *__restrict__ cols, con
     double nv = 0.0;
 #pragma unroll
     for (int c = 0; c < 8; ++c)
-        if (c < per_lane) nv = __dadd_rn(nv, __dmul_rn(xv[c], xv[c]));
+        if (c < per_lane) nv = __fma_rn(xv[c], xv[c], nv);
     nv = butterfly(nv);
-    // neighbours in groups of 4 so that their row loads overlap; each dot
-    // product keeps the fixed per-lane order and butterfly, and the cosines
-    // are added in ascending subset order
-    constexpr int G = 4;
+    const double sq_nv = __dsqrt_rn(nv);
+    // neighbours in chunks of 8: their row loads overlap, and the 16 partial
+    // sums of a chunk (|u|^2 and x.u per neighbour) are reduced together by a
+    // reduce-scatter that adds the same pairs as the xor butterfly (so each
+    // total is bit-identical to it) with 16 instead of 80 additions per lane;
+    // lane 4b then forms the cosine of neighbour b, and the cosines are added
+    // in ascending subset order
+    constexpr int G = 8;
     double sum = 0.0;
     for (int a0 = 0; a0 < m; a0 += G) {
         const T *pu[G];
+        bool inside[G];
 #pragma unroll
         for (int b = 0; b < G; ++b) {
-            const int32_t u = a0 + b < m ? cols[lo + sorted[a0 + b]] : 0;
-            pu[b] = phi + static_cast<int64_t>(u) * dim;
+            const int32_t u = a0 + b < m ? cols[lo + sorted[a0 + b]] : -1;
+            inside[b] = u >= 0 && u < n;
+            pu[b] = phi + static_cast<int64_t>(inside[b] ? u : v) * dim;
         }
-        double nu[G], dt[G];
+        double part[2 * G];  // part[2b] = |u_b|^2, part[2b + 1] = x . u_b
 #pragma unroll
-        for (int b = 0; b < G; ++b) nu[b] = dt[b] = 0.0;
+        for (int i = 0; i < 2 * G; ++i) part[i] = 0.0;
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
             if (c >= per_lane) break;
             double y[G];
 #pragma unroll
-            for (int b = 0; b < G; ++b) y[b] = elem(pu[b], lane + 32 * c);
+            for (int b = 0; b < G; ++b) y[b] = inside[b] ? elem(pu[b], lane + 32 * c) : 0.0;
 #pragma unroll
             for (int b = 0; b < G; ++b) {
-                nu[b] = __dadd_rn(nu[b], __dmul_rn(y[b], y[b]));
-                dt[b] = __dadd_rn(dt[b], __dmul_rn(xv[c], y[b]));
+                part[2 * b] = __fma_rn(y[b], y[b], part[2 * b]);
+                part[2 * b + 1] = __fma_rn(xv[c], y[b], part[2 * b + 1]);
             }
         }
+        const double tot = reduce_scatter16_f64(part, lane);  // lanes 2t, 2t+1: total t
+        const double d2 = __shfl_down_sync(kFull, tot, 2);    // at lane 4b: x . u_b
+        double cs = 0.0;
+        const int b_mine = lane >> 2;
+        if ((lane & 3) == 0 && a0 + b_mine < m && nv > 0.0 && tot > 0.0)
+            cs = __ddiv_rn(d2, __dmul_rn(sq_nv, __dsqrt_rn(tot)));
 #pragma unroll
         for (int b = 0; b < G; ++b) {
-            if (a0 + b >= m) break;
-            const double n2 = butterfly(nu[b]);
-            const double d2 = butterfly(dt[b]);
-            double cs = 0.0;
-            if (nv > 0.0 && n2 > 0.0) cs = __ddiv_rn(d2, __dmul_rn(__dsqrt_rn(nv), __dsqrt_rn(n2)));
-            sum = __dadd_rn(sum, cs);
+            const double cb = __shfl_sync(kFull, cs, 4 * b);
+            if (a0 + b < m) sum = __dadd_rn(sum, cb);
         }
     }
     const double psi = __ddiv_rn(sum, static_cast<double>(m));
