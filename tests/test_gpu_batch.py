@@ -87,8 +87,9 @@ def test_batch_init_matches_solo_and_graph_capture(fl):
 
 
 def test_batch_hogwild_quality_equals_solo(fl):
-    """Each job's link-prediction AUC in the batch is within 0.005 of the
-    same job trained alone (mean over jobs)."""
+    """Each job's link-prediction AUC in the batch is within 0.01 of the same
+    job trained alone (mean over 3 seeds per job; every job is checked, and
+    the mean over jobs is within 0.005)."""
     from paper_2606_22180_b300 import evaluate
 
     gs, splits = [], []
@@ -99,21 +100,24 @@ def test_batch_hogwild_quality_equals_solo(fl):
         splits.append(sp)
     dgs = [fl.DeviceGraph.from_host(g) for g in gs]
     dims = [64] * 6
-    seeds = [5 + i for i in range(6)]
     tp = fl.train_params(64, W, K, 0.025, 0, fl.FELOG_SGNS_HOGWILD, 4096, fl.FELOG_FP32)
     fp = fl.feedback_params(False, 0.65, 8, 10, False)
-    b = fl.Batch(dgs, dims, seeds, L, 1, tp, fp)
-    b.run(use_graph=False)
-    b.read()
-    diffs = []
-    for j in range(6):
-        solo, _, _ = fl.felog_embed(dgs[j], L, 1, tp, fp, seeds[j])
-        a_b = evaluate.link_auc(b.phi_in[j], splits[j].pos, splits[j].neg)
-        a_s = evaluate.link_auc(solo, splits[j].pos, splits[j].neg)
-        diffs.append(a_b - a_s)
-    print("batch - solo AUC per job:", np.round(diffs, 4))
-    assert abs(np.mean(diffs)) <= 0.005
-    b.close()
+    diffs = np.zeros((3, 6))
+    for rep in range(3):
+        seeds = [5 + i + 100 * rep for i in range(6)]
+        b = fl.Batch(dgs, dims, seeds, L, 1, tp, fp)
+        b.run(use_graph=False)
+        b.read()
+        for j in range(6):
+            solo, _, _ = fl.felog_embed(dgs[j], L, 1, tp, fp, seeds[j])
+            a_b = evaluate.link_auc(b.phi_in[j], splits[j].pos, splits[j].neg)
+            a_s = evaluate.link_auc(solo, splits[j].pos, splits[j].neg)
+            diffs[rep, j] = a_b - a_s
+        b.close()
+    per_job = diffs.mean(0)
+    print("batch - solo AUC per job (mean of 3 seeds):", np.round(per_job, 4), "spread", np.round(diffs.std(0), 4))
+    assert np.all(np.abs(per_job) <= 0.01), per_job
+    assert abs(per_job.mean()) <= 0.005
 
 
 def test_batch_autotune_and_cache(fl, tmp_path):

@@ -38,37 +38,46 @@ def _params(fl):
 
 
 def test_served_results_equal_solo_and_overlap(fl):
+    """Six graphs, each served twice (two seeds, 12 requests): the second
+    half of the requests arrives while the first are on the GPU.  Every job
+    trains the same tokens as alone, and each graph's link AUC (mean of its
+    two seeds) is within 0.01 of the same jobs trained alone; the mean over
+    graphs is within 0.005."""
     from paper_2606_22180_b300 import evaluate
 
     splits = _jobs(6)
     tp, fp = _params(fl)
     sv = fl.Server(4 << 30, L, 1, tp, fp)
+    reqs = [(i, 50 + i + 100 * rep) for rep in range(2) for i in range(6)]
     ids = []
-    for i in range(3):
-        ids.append(sv.submit(splits[i].train, 64, 50 + i))
+    for i, seed in reqs[:6]:
+        ids.append(sv.submit(splits[i].train, 64, seed))
     # the next requests arrive while the first ones are on the GPU
     t0 = time.time()
     while sv.poll(ids[0])["state"] == fl.JOB_QUEUED and time.time() - t0 < 30:
         time.sleep(0.001)
-    for i in range(3, 6):
-        ids.append(sv.submit(splits[i].train, 64, 50 + i))
+    for i, seed in reqs[6:]:
+        ids.append(sv.submit(splits[i].train, 64, seed))
     res = [sv.wait(r, 300) for r in ids]
     st = sv.stats()
     embs = [sv.fetch(r) for r in ids]
     sv.close()
     assert all(r["state"] == fl.JOB_DONE for r in res)
-    assert st["completed"] == 6 and st["peak_resident_jobs"] >= 2
+    assert st["completed"] == 12 and st["peak_resident_jobs"] >= 2
     # some job was admitted while an earlier one was still running
     assert any(res[j]["t_admit"] < res[i]["t_done"] and res[j]["t_submit"] > res[i]["t_admit"]
-               for i in range(6) for j in range(6) if i != j)
-    diffs = []
-    for i, sp in enumerate(splits):
+               for i in range(12) for j in range(12) if i != j)
+    diffs = np.zeros((2, 6))
+    for k, (i, seed) in enumerate(reqs):
+        sp = splits[i]
         dg = fl.DeviceGraph.from_host(sp.train)
-        solo, _, sst = fl.felog_embed(dg, L, 1, tp, fp, 50 + i)
-        assert res[i]["rounds"] == len(sst) and res[i]["tokens"] == sum(s["tokens"] for s in sst)
-        diffs.append(evaluate.link_auc(embs[i], sp.pos, sp.neg) - evaluate.link_auc(solo, sp.pos, sp.neg))
-    print("served - solo AUC per job:", np.round(diffs, 4))
-    assert abs(np.mean(diffs)) <= 0.005
+        solo, _, sst = fl.felog_embed(dg, L, 1, tp, fp, seed)
+        assert res[k]["rounds"] == len(sst) and res[k]["tokens"] == sum(s["tokens"] for s in sst)
+        diffs[k // 6, i] = evaluate.link_auc(embs[k], sp.pos, sp.neg) - evaluate.link_auc(solo, sp.pos, sp.neg)
+    per_graph = diffs.mean(0)
+    print("served - solo AUC per graph (mean of 2 seeds):", np.round(per_graph, 4))
+    assert np.all(np.abs(per_graph) <= 0.01), per_graph
+    assert abs(per_graph.mean()) <= 0.005
 
 
 def test_budget_admission_and_rejection(fl):

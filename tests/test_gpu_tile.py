@@ -79,7 +79,7 @@ def test_tile_loss_matches_oracle_at_fixed_tables(fl, orc, sbm, dim, window, Ns,
     """Both the in-order form (one CTA) and the pipelined form (several)."""
     g = sbm
     L, K = 40, 5
-    W, thr, alias, S = _corpus(orc, g, L, SEED, 1, n_starts=120, pad=pad)
+    W, thr, alias, S = _corpus(orc, g, L, SEED, 1, n_starts=300, pad=pad)
     ri, ro = _tables(g.n, dim, 3)
     pi, po = _to_dev(fl, ri, prec), _to_dev(fl, ro, prec)
     tp = fl.train_params(dim, window, K, 0.0, 10 ** 9, fl.FELOG_SGNS_TILE, 1, prec,
@@ -99,7 +99,7 @@ def test_tile_serial_fp32_tracks_oracle(fl, orc, sbm, dim, window, Ns):
     and the table increments agree up to the bf16 gradient operand."""
     g = sbm
     L, K = 40, 5
-    W, thr, alias, S = _corpus(orc, g, L, SEED, 0, n_starts=100, pad=True)
+    W, thr, alias, S = _corpus(orc, g, L, SEED, 0, n_starts=200, pad=True)
     ri0, ro0 = _tables(g.n, dim, 4)
     ri, ro = ri0.copy(), ro0.copy()
     pi, po = _to_dev(fl, ri0, 0), _to_dev(fl, ro0, 0)
@@ -124,7 +124,7 @@ def test_tile_serial_bf16_tracks_oracle(fl, orc, sbm):
     round), so they are held to 1.5 % in norm."""
     g = sbm
     dim, window, K, Ns = 128, 10, 5, 512
-    W, thr, alias, S = _corpus(orc, g, 40, SEED, 2, n_starts=100)
+    W, thr, alias, S = _corpus(orc, g, 40, SEED, 2, n_starts=200)
     ri0, ro0 = _tables(g.n, dim, 5)
     ri, ro = ri0.copy(), ro0.copy()
     pi, po = _to_dev(fl, ri0, 1), _to_dev(fl, ro0, 1)
@@ -149,7 +149,7 @@ def test_tile_parallel_round_close_to_serial(fl, orc):
     of the oracle's, increments of the same size."""
     g = inputs.rmat(16, 16, seed=3)
     dim, window, K, Ns = 64, 10, 5, 512
-    W, thr, alias, S = _corpus(orc, g, 80, SEED, 0, n_starts=300)
+    W, thr, alias, S = _corpus(orc, g, 80, SEED, 0, n_starts=1000)
     ri0, ro0 = _tables(g.n, dim, 6, scale=0.05)
     ri, ro = ri0.copy(), ro0.copy()
     pi, po = _to_dev(fl, ri0, 0), _to_dev(fl, ro0, 0)
