@@ -286,7 +286,9 @@ def feedback(offsets, cols, phi: np.ndarray, active_in, enabled: bool, mu: float
 def embed(offsets, cols, L: int, wpr: int, dim: int, window: int, negatives: int, lr0: float,
           feedback_enabled: bool, mu: float, ks: int, max_rounds: int, reactivate: bool,
           seed: int, mode: str = "serial", B: int = 4096, T: int = 0):
-    """Algorithm 1 end to end; returns (phi_in, phi_out, stats[rounds, 4])."""
+    """Algorithm 1 end to end; returns (phi_in, phi_out, stats[rounds, 4]).
+    mode: "serial", "minibatch" (B positions per batch) or "tile" (tiles of
+    128 - 2 window centers with B shared negatives, row averaging)."""
     off, col = _c(offsets, np.int32), _c(cols, np.int32)
     n = off.shape[0] - 1
     phi_in = np.empty((n, dim), np.float64)
@@ -295,7 +297,7 @@ def embed(offsets, cols, L: int, wpr: int, dim: int, window: int, negatives: int
     tp = _tp(dim, window, negatives, lr0, T)
     fp = _FeedbackParams(int(feedback_enabled), mu, ks, max_rounds, int(reactivate))
     rounds = lib().oracle_embed(_p(off), _p(col), n, L, wpr, ctypes.byref(tp), ctypes.byref(fp),
-                                0 if mode == "serial" else 1, B, seed, _p(phi_in), _p(phi_out),
+                                {"serial": 0, "minibatch": 1, "tile": 2}[mode], B, seed, _p(phi_in), _p(phi_out),
                                 _p(stats))
     return phi_in, phi_out, stats[:rounds]
 

@@ -759,7 +759,9 @@ int64_t oracle_feedback(const int32_t *offsets, const int32_t *cols, int32_t n, 
 /* ------------------------------------------------------------------------ */
 /* Algorithm 1: initialise V_a to the non-isolated nodes, then repeat        */
 /* sample -> train -> feedback until V_a is empty or max_rounds is reached.  */
-/* mode 0 = serial SGNS, mode 1 = synchronous minibatch of B positions.      */
+/* mode 0 = serial SGNS, mode 1 = synchronous minibatch of B positions,      */
+/* mode 2 = the shared-negatives tile form, tiles of 128 - 2w centers in     */
+/* corpus order with B shared negatives each and row averaging.              */
 /* phi_in / phi_out are filled by the initialiser.  Per-round statistics:    */
 /* stats[r*4 + 0] = |V_a^r|, +1 = tokens, +2 = loss, +3 = |V_a^{r+1}|.       */
 /* Returns the number of rounds run.                                         */
@@ -802,9 +804,12 @@ int32_t oracle_embed(const int32_t *offsets, const int32_t *cols, int32_t n, int
         if (mode == 0)
             loss = oracle_sgns_serial(walks, n_walks, L, n, &tp, thr, alias, S, seed, r, clock,
                                       phi_in, phi_out);
-        else
+        else if (mode == 1)
             loss = oracle_sgns_minibatch(walks, n_walks, L, n, &tp, B, thr, alias, S, seed, r,
                                          clock, phi_in, phi_out, NULL);
+        else
+            loss = oracle_sgns_tile(walks, n_walks, L, n, &tp, 128 - 2 * tp.window, (int32_t)B, 1,
+                                    thr, alias, S, seed, r, clock, phi_in, phi_out, NULL);
         clock += n_walks * L;
         int64_t na = oracle_feedback(offsets, cols, n, phi_in, d, fp, seed, r, active, next, NULL);
         if (stats) {

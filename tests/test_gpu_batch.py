@@ -87,9 +87,8 @@ def test_batch_init_matches_solo_and_graph_capture(fl):
 
 
 def test_batch_hogwild_quality_equals_solo(fl):
-    """Each job's link-prediction AUC in the batch is within 0.01 of the same
-    job trained alone (mean over 3 seeds per job; every job is checked, and
-    the mean over jobs is within 0.005)."""
+    """Each job's link-prediction AUC in the batch is within 0.005 of the same
+    job trained alone (mean over 3 seeds per job; every job is checked)."""
     from paper_2606_22180_b300 import evaluate
 
     gs, splits = [], []
@@ -116,8 +115,7 @@ def test_batch_hogwild_quality_equals_solo(fl):
         b.close()
     per_job = diffs.mean(0)
     print("batch - solo AUC per job (mean of 3 seeds):", np.round(per_job, 4), "spread", np.round(diffs.std(0), 4))
-    assert np.all(np.abs(per_job) <= 0.01), per_job
-    assert abs(per_job.mean()) <= 0.005
+    assert np.all(np.abs(per_job) <= 0.005), per_job
 
 
 def test_batch_autotune_and_cache(fl, tmp_path):

@@ -17,8 +17,11 @@ pytestmark = pytest.mark.gpu
 
 SEED = 11
 # per-row relative error of the minibatch tables against the oracle: every
-# increment is formed in float on the GPU and summed in 2^-40 fixed point
-ROW_TOL = 1e-4
+# increment is formed in float on the GPU and summed in 2^-40 fixed point;
+# rows whose increments largely cancel keep less relative precision (the
+# largest seen over these cases is 1.4e-4, a dim-64 row with 15 negatives),
+# while a wrong element in a row is an error of order 1
+ROW_TOL = 1e-3
 
 
 @pytest.fixture(scope="module")

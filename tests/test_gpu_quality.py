@@ -8,6 +8,7 @@ from paper_2606_22180_b300 import inputs
 pytestmark = pytest.mark.gpu
 
 L, DIM, W, K, R = 40, 64, 5, 5, 10
+TILE_R, TILE_NS = 3, 128
 
 
 @pytest.fixture(scope="module")
@@ -32,13 +33,21 @@ def runs(fl, orc):
         dg = fl.DeviceGraph.from_host(tr)
         fp = fl.feedback_params(False, 0.65, 8, R, False)
         out = {"oracle": a_or}
-        for name, prec in [("hogwild", fl.FELOG_FP32), ("bf16", fl.FELOG_BF16_SR)]:
-            tp = fl.train_params(DIM, W, K, 0.025, 0, fl.FELOG_SGNS_HOGWILD, 4096, prec)
+        for name, prec, form in [("hogwild", fl.FELOG_FP32, 0), ("bf16", fl.FELOG_BF16_SR, 0),
+                                 ("staged", fl.FELOG_FP32, 3), ("staged_bf16", fl.FELOG_BF16_SR, 3)]:
+            tp = fl.train_params(DIM, W, K, 0.025, 0, fl.FELOG_SGNS_HOGWILD, 4096, prec, hogwild_form=form)
             pi, _, _ = fl.felog_embed(dg, L, 1, tp, fp, seed)
             out[name] = evaluate.link_auc(pi, sp.pos, sp.neg)
-        tp = fl.train_params(DIM, W, K, 0.025, 0, fl.FELOG_SGNS_TILE, 1, fl.FELOG_BF16_SR)
-        pi, _, _ = fl.felog_embed(dg, L, 1, tp, fp, seed)
+        # tile form: 3 rounds, 128 shared negatives on both sides (the serial
+        # binary64 tile oracle is the slow one: about 20 s per seed here)
+        fp3 = fl.feedback_params(False, 0.65, 8, TILE_R, False)
+        T3 = TILE_R * int((tr.degrees() > 0).sum()) * L
+        tp = fl.train_params(DIM, W, K, 0.025, T3, fl.FELOG_SGNS_TILE, 1, fl.FELOG_BF16_SR, tile_negatives=TILE_NS)
+        pi, _, _ = fl.felog_embed(dg, L, 1, tp, fp3, seed)
         out["tile"] = evaluate.link_auc(pi, sp.pos, sp.neg)
+        rt, _, _ = orc.embed(tr.offsets, tr.cols, L, 1, DIM, W, K, 0.025, False, 0.65, 8, TILE_R, False, seed,
+                             mode="tile", B=TILE_NS, T=T3)
+        out["oracle_tile"] = orc.link_auc(rt, sp.pos, sp.neg)
         res.append(out)
     return res
 
@@ -55,10 +64,21 @@ def test_bf16_auc_within_tolerance_of_serial_oracle(runs):
     assert abs(d.mean()) <= 0.005
 
 
-def test_tile_auc_close_to_serial_oracle(runs):
+@pytest.mark.parametrize("form", ["staged", "staged_bf16"])
+def test_staged_hogwild_auc_within_tolerance_of_serial_oracle(runs, form):
+    """The staged form (window phi_in increments summed in shared memory and
+    added when a position leaves the window) keeps the per-pair estimator."""
+    d = np.array([r[form] - r["oracle"] for r in runs])
+    print(f"{form} - oracle AUC per seed:", d.round(4))
+    assert abs(d.mean()) <= 0.005
+
+
+def test_tile_auc_within_tolerance_of_serial_tile_oracle(runs):
     """The shared-negatives tile form changes the estimator (Ns draws per
-    tile of weight K/Ns instead of K per pair), so it is held to a looser
-    bound than the per-pair forms."""
-    d = np.array([r["tile"] - r["oracle"] for r in runs])
-    print("tile (bf16) - oracle AUC per seed:", d.round(4))
-    assert d.mean() >= -0.02
+    tile of weight K/Ns instead of K per pair), so it is held to the oracle of
+    that estimator run serially (tiles in order, binary64): on this graph
+    the GPU runs its tiles in order too.  Against the per-pair oracle it is
+    only reported."""
+    d = np.array([r["tile"] - r["oracle_tile"] for r in runs])
+    print("tile (bf16, 3 rounds) - serial tile oracle AUC per seed:", d.round(4))
+    assert abs(d.mean()) <= 0.005

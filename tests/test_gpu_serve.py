@@ -41,8 +41,7 @@ def test_served_results_equal_solo_and_overlap(fl):
     """Six graphs, each served twice (two seeds, 12 requests): the second
     half of the requests arrives while the first are on the GPU.  Every job
     trains the same tokens as alone, and each graph's link AUC (mean of its
-    two seeds) is within 0.01 of the same jobs trained alone; the mean over
-    graphs is within 0.005."""
+    two seeds) is within 0.005 of the same jobs trained alone."""
     from paper_2606_22180_b300 import evaluate
 
     splits = _jobs(6)
@@ -76,8 +75,7 @@ def test_served_results_equal_solo_and_overlap(fl):
         diffs[k // 6, i] = evaluate.link_auc(embs[k], sp.pos, sp.neg) - evaluate.link_auc(solo, sp.pos, sp.neg)
     per_graph = diffs.mean(0)
     print("served - solo AUC per graph (mean of 2 seeds):", np.round(per_graph, 4))
-    assert np.all(np.abs(per_graph) <= 0.01), per_graph
-    assert abs(per_graph.mean()) <= 0.005
+    assert np.all(np.abs(per_graph) <= 0.005), per_graph
 
 
 def test_budget_admission_and_rejection(fl):
