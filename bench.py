@@ -50,8 +50,9 @@ def _args():
     p.add_argument("--scale", type=int, default=SCALE, help="R-MAT scale (20 = the benchmark workload)")
     p.add_argument("--no-quality", action="store_true", help="skip the full-run AUC comparison")
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
-    p.add_argument("--form", type=int, default=0, choices=[0, 1, 2],
-                   help="Hogwild kernel form: 0 automatic, 1 full warp per pair, 2 half warp per pair")
+    p.add_argument("--form", type=int, default=0, choices=[0, 1, 2, 3],
+                   help="Hogwild kernel form: 0 automatic, 1 full warp per pair, 2 half warp per pair, "
+                        "3 half warp with the window's phi_in increments staged in shared memory")
     p.add_argument("--mode", default="round", choices=["round", "tile", "batch", "serve", "mu"],
                    help="round: one round of Algorithm 1 on R-MAT 20 (default); tile: rounds with the "
                         "shared-negatives tile trainer; batch: the 512-graph "

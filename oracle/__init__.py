@@ -23,13 +23,26 @@ _LIB = os.path.join(_HERE, "_felog_oracle.so")
 STREAM_WALK, STREAM_PSI, STREAM_NEG, STREAM_INIT, STREAM_SR = 0, 1, 2, 3, 4
 
 
+_BASE_SRC = os.path.join(_HERE, "felog_cpu_baseline.c")
+_BASE_LIB = os.path.join(_HERE, "_felog_cpu_baseline.so")
+_FLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+
+
+def _stale(lib_path: str, srcs) -> bool:
+    return not os.path.exists(lib_path) or any(os.path.getmtime(lib_path) < os.path.getmtime(s) for s in srcs)
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (binary64, no contraction, no fast-math)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    """Compile the oracle with gcc (binary64, no contraction, no fast-math),
+    and the all-cores timed baseline (the oracle's routines under OpenMP)."""
+    if force or _stale(_LIB, [_SRC]):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc"] + _FLAGS + ["-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
+    if force or _stale(_BASE_LIB, [_SRC, _BASE_SRC]):
+        tmp = _BASE_LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc"] + _FLAGS + ["-fopenmp", "-o", tmp, _SRC, _BASE_SRC, "-lm"])
+        os.replace(tmp, _BASE_LIB)
     return _LIB
 
 
@@ -345,3 +358,66 @@ def fabc_decode(buf, N: int, L: int, k: int) -> np.ndarray:
     w = np.zeros((N, L), np.int32)
     lib().oracle_fabc_decode(_p(b), N, L, k, _p(w))
     return w
+
+
+# ---------------------------------------------------------------------------
+# the timed CPU baseline: the oracle's routines on every host core
+# ---------------------------------------------------------------------------
+_base = None
+
+
+def baseline_lib() -> ctypes.CDLL:
+    global _base
+    if _base is None:
+        build()
+        _base = ctypes.CDLL(_BASE_LIB)
+        P = ctypes.c_void_p
+        i32, i64, u64, f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+        sig = {
+            "baseline_threads": (ctypes.c_int, []),
+            "baseline_walk": (ctypes.c_int, [P, P, i32, P, i32, i32, u64, i32, P]),
+            "baseline_sgns_hogwild": (f64, [P, i64, i32, i32, P, P, P, u64, u64, i32, i64, P, P]),
+            "baseline_psi": (None, [P, P, P, i32, i32, u64, i32, P, i64, P]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(_base, name)
+            fn.restype = res
+            fn.argtypes = args
+    return _base
+
+
+def baseline_threads() -> int:
+    return int(baseline_lib().baseline_threads())
+
+
+def baseline_walk(offsets, cols, starts, L: int, seed: int, round_: int) -> np.ndarray:
+    """oracle.walk with one walk per start, the starts split over all cores
+    (bit-identical to the single call)."""
+    off, col, st = _c(offsets, np.int32), _c(cols, np.int32), _c(starts, np.int32)
+    out = np.empty((st.shape[0], L), np.int32)
+    rc = baseline_lib().baseline_walk(_p(off), _p(col), off.shape[0] - 1, _p(st), st.shape[0], L, seed,
+                                      round_, _p(out))
+    if rc:
+        raise ValueError("start out of range")
+    return out
+
+
+def baseline_sgns_hogwild(walks, n: int, dim: int, window: int, negatives: int, lr0: float, T: int,
+                          thr, alias, S: int, seed: int, round_: int, clock_base: int,
+                          phi_in: np.ndarray, phi_out: np.ndarray) -> float:
+    """Binary64 Hogwild SGNS: chunks of walks through the serial oracle on
+    all cores, sharing the tables without locks."""
+    w = _c(walks, np.int32)
+    tp = _tp(dim, window, negatives, lr0, T)
+    return float(baseline_lib().baseline_sgns_hogwild(_p(w), w.shape[0], w.shape[1], n, ctypes.byref(tp),
+                                                      _p(thr), _p(alias), S, seed, round_, clock_base,
+                                                      _p(phi_in), _p(phi_out)))
+
+
+def baseline_psi(offsets, cols, phi: np.ndarray, ks: int, seed: int, round_: int, nodes) -> np.ndarray:
+    """Psi of the listed nodes on all cores (bit-identical to oracle.psi_node)."""
+    off, col, nd = _c(offsets, np.int32), _c(cols, np.int32), _c(nodes, np.int32)
+    out = np.empty(nd.shape[0], np.float64)
+    baseline_lib().baseline_psi(_p(off), _p(col), _p(phi), phi.shape[1], ks, seed, round_, _p(nd), nd.shape[0],
+                                _p(out))
+    return out

@@ -381,15 +381,17 @@ typedef struct {
 /* position, window offsets -w..-1, 1..w.  eta is taken from the global      */
 /* token clock  clock_base + walk*L + pos.  Returns the summed loss.         */
 /* ------------------------------------------------------------------------ */
-double oracle_sgns_serial(const int32_t *walks, int64_t n_walks, int32_t L, int32_t n,
-                          const oracle_train_params *tp, const uint64_t *thr,
-                          const int32_t *alias, uint64_t S, uint64_t seed, int32_t round,
-                          int64_t clock_base, double *phi_in, double *phi_out) {
+/* Walks [w0, w1) of the round's corpus, in order, with their indices in the */
+/* whole corpus (which key the negatives and the token clock).               */
+double oracle_sgns_serial_range(const int32_t *walks, int64_t w0, int64_t w1, int32_t L, int32_t n,
+                                const oracle_train_params *tp, const uint64_t *thr,
+                                const int32_t *alias, uint64_t S, uint64_t seed, int32_t round,
+                                int64_t clock_base, double *phi_in, double *phi_out) {
     const int32_t d = tp->dim, w = tp->window, K = tp->negatives;
     double *scratch = (double *)malloc(sizeof(double) * (size_t)d);
     double **targets = (double **)malloc(sizeof(double *) * (size_t)(K + 1));
     double loss = 0.0;
-    for (int64_t wi = 0; wi < n_walks; ++wi) {
+    for (int64_t wi = w0; wi < w1; ++wi) {
         const int32_t *row = walks + wi * L;
         for (int32_t p = 0; p < L; ++p) {
             int32_t c = row[p];
@@ -414,6 +416,14 @@ double oracle_sgns_serial(const int32_t *walks, int64_t n_walks, int32_t L, int3
     free(scratch);
     free(targets);
     return loss;
+}
+
+double oracle_sgns_serial(const int32_t *walks, int64_t n_walks, int32_t L, int32_t n,
+                          const oracle_train_params *tp, const uint64_t *thr,
+                          const int32_t *alias, uint64_t S, uint64_t seed, int32_t round,
+                          int64_t clock_base, double *phi_in, double *phi_out) {
+    return oracle_sgns_serial_range(walks, 0, n_walks, L, n, tp, thr, alias, S, seed, round, clock_base,
+                                    phi_in, phi_out);
 }
 
 /* ------------------------------------------------------------------------ */

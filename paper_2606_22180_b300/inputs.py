@@ -260,22 +260,40 @@ def rmat_nodes(n: int, degree: float, seed: int, a=0.57, b=0.19, c=0.19) -> CSR:
     return csr_from_edges(n, s[ok], t[ok])
 
 
+def _mix_one(spec):
+    kind, n, k, deg, gseed = spec
+    if kind == "sbm":
+        return sbm_degree(n, k, deg, seed=gseed)
+    return rmat_nodes(n, deg, seed=gseed)
+
+
 def graph_mix(count: int, seed: int, n_lo: int, n_hi: int, deg_lo: float = 8.0, deg_hi: float = 32.0,
-              dims=(64, 128)):
+              dims=(64, 128), workers: int = 1):
     """A mix of jobs for the batching and serving forms: half planted
     partitions (4..32 communities), half R-MAT; node counts log-uniform in
     [n_lo, n_hi], average degree uniform in [deg_lo, deg_hi], embedding
-    dimension drawn from dims.  Returns a list of (CSR, dim)."""
+    dimension drawn from dims.  Returns a list of (CSR, dim).  Every graph's
+    parameters and seed are drawn first, in order, so the graphs do not
+    depend on `workers` (> 1: generated in that many spawned processes)."""
     rng = np.random.Generator(np.random.PCG64(seed))
-    out = []
+    specs, out_dims = [], []
     for i in range(count):
         n = int(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi))))
         deg = float(rng.uniform(deg_lo, deg_hi))
         dim = int(dims[int(rng.integers(0, len(dims)))])
         if i % 2 == 0:
             k = int(rng.integers(4, 33))
-            g = sbm_degree(n, k, deg, seed=int(rng.integers(1 << 31)))
+            specs.append(("sbm", n, k, deg, int(rng.integers(1 << 31))))
         else:
-            g = rmat_nodes(n, deg, seed=int(rng.integers(1 << 31)))
-        out.append((g, dim))
-    return out
+            specs.append(("rmat", n, 0, deg, int(rng.integers(1 << 31))))
+        out_dims.append(dim)
+    if workers > 1 and count > 1:
+        import concurrent.futures
+        import multiprocessing
+
+        ctx = multiprocessing.get_context("spawn")
+        with concurrent.futures.ProcessPoolExecutor(max_workers=workers, mp_context=ctx) as ex:
+            graphs = list(ex.map(_mix_one, specs, chunksize=4))
+    else:
+        graphs = [_mix_one(sp) for sp in specs]
+    return list(zip(graphs, out_dims))
