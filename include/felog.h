@@ -85,9 +85,14 @@ typedef enum {
  * hogwild_rows_per_warp (HOGWILD mode, <= 0 selects 16): at most
  * n / hogwild_rows_per_warp walks are trained concurrently, which bounds the
  * staleness of lock-free updates on small graphs; hogwild_form selects the
- * HOGWILD kernel: 0 = automatic (half-warp form where dim <= 128 and
- * negatives <= 7, full-warp form otherwise), 1 = full warp per pair,
- * 2 = two pairs per warp (half warp each; dim <= 128, negatives <= 7).
+ * HOGWILD kernel: 1 = full warp per pair, 2 = two pairs per warp (half warp
+ * each; dim <= 128, negatives <= 7), 3 = form 2 with each walk window's
+ * phi_in increments summed in shared memory (window <= 15): a warp reads a
+ * context row plus its own pending increments of that node, and a window
+ * position's summed increment reaches memory when the position leaves the
+ * window (other warps see it then); 0 = automatic: form 3 for float tables,
+ * form 2 for bf16 tables (where dim <= 128 and negatives <= 7, window <= 15
+ * for form 3), form 1 otherwise.
  * TILE mode (dim in {32, 64, 128}): tile_negatives = shared negatives per
  * tile (128, 256, 384 or 512; 0 selects 512: each then stands for about 20
  * per-pair draws, fewer shared negatives let hub rows take oversized stale

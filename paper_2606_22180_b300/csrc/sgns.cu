@@ -181,20 +181,35 @@ __global__ void __launch_bounds__(kSgnsThreads, 3)
 }
 
 
-template <int D, class T, int KFIX>
+// Shared memory words per warp of the half-warp trainer: walk and negative
+// ids (rounded up to 16 bytes), then with STAGE the staged phi_in increments.
+inline int hw_words_per_warp(int L, int window, int K, int dim, bool stage) {
+    const int ids = (L + 2 * window * K + 3) & ~3;
+    return ids + (stage ? static_cast<int>(stage_floats(window, dim)) : 0);
+}
+
+template <int D, class T, int KFIX, bool STAGE>
 __global__ void __launch_bounds__(kSgnsThreads, 2)
     k_sgns_hogwild_hw(SgnsArgs a, T *__restrict__ phi_in, T *__restrict__ phi_out) {
-    extern __shared__ int32_t smem[];
+    extern __shared__ __align__(16) int32_t smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int K = KFIX > 0 ? KFIX : a.K;
-    int32_t *wk = smem + wib * (a.L + 2 * a.window * K);
+    const int ids = (a.L + 2 * a.window * K + 3) & ~3;
+    const int R = 2 * a.window + 1;
+    int32_t *wk = smem + wib * (ids + (STAGE ? R * D : 0));
     int32_t *negs = wk + a.L;
+    float *delta = nullptr;
+    if constexpr (STAGE) {
+        delta = reinterpret_cast<float *>(wk + ids);
+        for (int i = lane; i < R * D; i += 32) delta[i] = 0.f;
+        __syncwarp();
+    }
     TrainView<T> v{phi_in, phi_out, a.thr, a.alias, static_cast<uint64_t>(a.n), *a.S, a.seed, a.round,
                    a.lr0, a.inv_T, a.clock_base, a.window, a.K, a.L};
     long long loss_fx = 0;
     const int64_t warps = static_cast<int64_t>(gridDim.x) * kWarps;
     for (int64_t wi = static_cast<int64_t>(blockIdx.x) * kWarps + wib; wi < a.n_walks; wi += warps)
-        loss_fx += hw_train_walk<D, T, KFIX>(v, a.walks + wi * a.L, wi, wk, negs);
+        loss_fx += hw_train_walk<D, T, KFIX, STAGE>(v, a.walks + wi * a.L, wi, wk, negs, delta);
     for (int o = 16; o; o >>= 1) loss_fx += __shfl_xor_sync(kFull, loss_fx, o);
     if (lane == 0 && loss_fx != 0) atomicAdd(a.loss_acc, static_cast<unsigned long long>(loss_fx));
 }
@@ -477,8 +492,9 @@ static bool params_ok(const felog_train_params *tp) {
     }
     if (tp->precision != FELOG_FP32 && tp->precision != FELOG_BF16_SR) return false;
     if (tp->mode == FELOG_SGNS_MINIBATCH && tp->minibatch < 1) return false;
-    if (tp->hogwild_form < 0 || tp->hogwild_form > 2) return false;
-    if (tp->hogwild_form == 2 && (tp->dim > 128 || tp->negatives > 7)) return false;
+    if (tp->hogwild_form < 0 || tp->hogwild_form > 3) return false;
+    if (tp->hogwild_form >= 2 && (tp->dim > 128 || tp->negatives > 7)) return false;
+    if (tp->hogwild_form == 3 && tp->window > kStageMaxWindow) return false;
     if (!(tp->lr0 >= 0.f) || tp->lr_total_tokens <= 0) return false;
     return true;
 }
@@ -489,11 +505,21 @@ static felog_status launch_train(const SgnsArgs &a, const felog_train_params *tp
     T *pin = static_cast<T *>(phi_in);
     T *pout = static_cast<T *>(phi_out);
     if (!minibatch_mode(tp)) {
-        const size_t smem = sizeof(int32_t) * kWarps * (a.L + 2 * a.window * a.K);
-        if (smem > 200 * 1024) return FELOG_ERR_UNSUPPORTED;  // walk too long to stage per warp
-        // half-warp form for dim <= 128 and K + 1 <= 8, full-warp form otherwise
+        // half-warp form for dim <= 128 and K + 1 <= 8, full-warp form otherwise;
+        // form 3 stages the window's phi_in increments (window <= 15), which the
+        // automatic choice takes for float tables (measured on R-MAT 20: 559 vs
+        // 613 ms per round) but not for bf16 ones (513 vs 475 ms: that kernel is
+        // bound by instruction issue, and staging adds more than it saves)
         const bool half_warp = D <= 128 && MAXT == 8 && tp->hogwild_form != 1;
-        auto kern = half_warp ? k_sgns_hogwild_hw<(D <= 128 ? D : 128), T, KFIX> : k_sgns_hogwild<D, T, MAXT, KFIX>;
+        const bool stage = half_warp && (tp->hogwild_form == 3 ||
+                                         (tp->hogwild_form == 0 && std::is_same<T, float>::value &&
+                                          a.window <= kStageMaxWindow));
+        constexpr int DH = D <= 128 ? D : 128;
+        const size_t smem = half_warp ? sizeof(int32_t) * kWarps * hw_words_per_warp(a.L, a.window, a.K, DH, stage)
+                                      : sizeof(int32_t) * kWarps * (a.L + 2 * a.window * a.K);
+        if (smem > 200 * 1024) return FELOG_ERR_UNSUPPORTED;  // walk too long to stage per warp
+        auto kern = stage ? k_sgns_hogwild_hw<DH, T, KFIX, true>
+                          : (half_warp ? k_sgns_hogwild_hw<DH, T, KFIX, false> : k_sgns_hogwild<D, T, MAXT, KFIX>);
         if (smem > 48 * 1024)
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
         int per_sm = 0;

@@ -460,13 +460,68 @@ struct TrainView {
     int W, K, L;
 };
 
+// Staged phi_in increments (STAGE): a warp keeps, for each of the 2W + 1
+// positions of its current window, the summed increment of that position's
+// phi_in row in shared memory (fp32, `delta`: (2W + 1) rows of D floats, slot
+// = position mod (2W + 1)).  A pair reads phi_in[x] from memory plus every
+// pending increment this warp holds for node x (all window positions whose
+// node is x), so the warp sees all of its own updates as before; the pair's
+// increment is added to the slot of its context position; when a position
+// leaves the window its summed increment is added to memory once (fp32:
+// vector reduction; bf16: stochastically rounded against the row read at
+// that moment).  Other warps see a position's phi_in updates when it leaves
+// the window instead of after each pair.  Layout of a slot row: lane l of a
+// half owns floats [l * EPL, (l + 1) * EPL) for EPL <= 4, and for EPL = 8
+// the two 4-float chunks at l * 4 and 64 + l * 4 (conflict-free 16-byte
+// accesses by the 16 lanes).
+template <int EPL>
+__device__ __forceinline__ float *delta_chunk(float *slot_row, int hl, int c) {
+    return EPL == 8 ? slot_row + c * 64 + hl * 4 : slot_row + hl * EPL;
+}
+
+template <int EPL>
+__device__ __forceinline__ void delta_load(float *slot_row, int hl, float (&d)[EPL]) {
+    if constexpr (EPL == 8) {
+        const float4 a = *reinterpret_cast<const float4 *>(delta_chunk<EPL>(slot_row, hl, 0));
+        const float4 b = *reinterpret_cast<const float4 *>(delta_chunk<EPL>(slot_row, hl, 1));
+        d[0] = a.x; d[1] = a.y; d[2] = a.z; d[3] = a.w;
+        d[4] = b.x; d[5] = b.y; d[6] = b.z; d[7] = b.w;
+    } else if constexpr (EPL == 4) {
+        const float4 a = *reinterpret_cast<const float4 *>(slot_row + hl * 4);
+        d[0] = a.x; d[1] = a.y; d[2] = a.z; d[3] = a.w;
+    } else {
+        const float2 a = *reinterpret_cast<const float2 *>(slot_row + hl * 2);
+        d[0] = a.x; d[1] = a.y;
+    }
+}
+
+template <int EPL>
+__device__ __forceinline__ void delta_store(float *slot_row, int hl, const float (&d)[EPL]) {
+    if constexpr (EPL == 8) {
+        *reinterpret_cast<float4 *>(delta_chunk<EPL>(slot_row, hl, 0)) = make_float4(d[0], d[1], d[2], d[3]);
+        *reinterpret_cast<float4 *>(delta_chunk<EPL>(slot_row, hl, 1)) = make_float4(d[4], d[5], d[6], d[7]);
+    } else if constexpr (EPL == 4) {
+        *reinterpret_cast<float4 *>(slot_row + hl * 4) = make_float4(d[0], d[1], d[2], d[3]);
+    } else {
+        *reinterpret_cast<float2 *>(slot_row + hl * 2) = make_float2(d[0], d[1]);
+    }
+}
+
+// Largest window (2W + 1 positions, one per lane) the staged form handles.
+constexpr int kStageMaxWindow = 15;
+
+// Floats of staged increments per warp.
+inline size_t stage_floats(int window, int dim) { return static_cast<size_t>(2 * window + 1) * dim; }
+
 // Trains all pairs of one walk (row: L node ids local to the graph; wi: the
 // walk's index in the graph's round, which keys its negatives and its
 // token clock).  wk (L ints) and negs (2 W K ints) are this warp's shared
-// memory.  Returns this lane's loss in 2^-24 units.
-template <int D, class T, int KFIX>
+// memory, and with STAGE delta ((2W + 1) * D floats, all zero on entry and
+// on return).  Returns this lane's loss in 2^-24 units.
+template <int D, class T, int KFIX, bool STAGE = false>
 __device__ __forceinline__ long long hw_train_walk(const TrainView<T> &a, const int32_t *__restrict__ row,
-                                                   int64_t wi, int32_t *wk, int32_t *negs) {
+                                                   int64_t wi, int32_t *wk, int32_t *negs,
+                                                   float *delta = nullptr) {
     constexpr int EPL = D / 16;
     constexpr int MAXT = 8;
     constexpr bool kBf16 = !std::is_same<T, float>::value;
@@ -481,10 +536,47 @@ __device__ __forceinline__ long long hw_train_walk(const TrainView<T> &a, const 
     const int my_t = hl >> 1;
     const bool loss_lane = (hl & 1) == 0;
     long long loss_fx = 0;
+    const int R = 2 * W + 1;
+    int sbase = W + 1;  // slot of position p - W, i.e. (p - W) mod R, at p = 0
+
+    // adds the staged increment of position q (slot sq) to memory and clears
+    // the slot; half 0 of the warp does it
+    auto flush = [&](int q, int sq, uint32_t rw) {
+        const int32_t y = wk[q];
+        if (h == 0 && y >= 0) {
+            float *srow = delta + sq * D;
+            float d[EPL];
+            delta_load<EPL>(srow, hl, d);
+            const float zero[EPL] = {};
+            delta_store<EPL>(srow, hl, zero);
+            T *grow = phi_in + static_cast<int64_t>(y) * D;
+            if constexpr (kBf16) {
+                uint32_t raw[EPL / 2];
+                load_raw<EPL>(grow + hl * EPL, raw);
+                add_delta_raw<EPL>(grow + hl * EPL, raw, d, rw);
+            } else {
+                hw_add<EPL>(reinterpret_cast<float *>(grow), hl, d);
+            }
+        }
+    };
 
     for (int p = lane; p < L; p += 32) wk[p] = walk_id(row[p], n);
     __syncwarp();
     for (int p = 0; p < L; ++p) {
+        uint32_t srs = 0;
+        if constexpr (kBf16)
+            srs = philox(a.seed, static_cast<uint32_t>(lane), static_cast<uint32_t>(wi),
+                         (a.round << 16) | static_cast<uint32_t>(p), kStreamSR).x | 1u;
+        if constexpr (STAGE) {
+            // position p - W - 1 leaves the window (its slot is the one before sbase)
+            if (p > 0) sbase = sbase + 1 == R ? 0 : sbase + 1;
+            const int q = p - W - 1;
+            if (q >= 0) {
+                srs = srs * 1664525u + 1013904223u;
+                flush(q, sbase == 0 ? R - 1 : sbase - 1, srs);
+                __syncwarp();
+            }
+        }
         const int32_t c = wk[p];
         if (c < 0) continue;
         for (int idx = lane; idx < 2 * W * K; idx += 32) {
@@ -508,13 +600,15 @@ __device__ __forceinline__ long long hw_train_walk(const TrainView<T> &a, const 
 #pragma unroll
         for (int e = 0; e < EPL; ++e) doc[e] = 0.f;
         float closs = 0.f;
-        uint32_t srs = 0;
-        if constexpr (kBf16)
-            srs = philox(a.seed, static_cast<uint32_t>(lane), static_cast<uint32_t>(wi),
-                         (a.round << 16) | static_cast<uint32_t>(p), kStreamSR).x | 1u;
         // window offsets o in [lo, hi] \ {0}; lo <= 0 <= hi
         const int lo = max(-W, -p), hi = min(W, L - 1 - p);
         const int npairs = hi - lo;
+        // STAGE: lane i stands for window position p - W + i (i < R)
+        int32_t win_id = -1;
+        if constexpr (STAGE) {
+            const int pos = p - W + lane;
+            if (lane < R && pos >= 0 && pos < L) win_id = wk[pos];
+        }
         for (int j0 = 0; j0 < npairs; j0 += 2) {
             const int j = j0 + h;
             int o = lo + j;
@@ -571,6 +665,26 @@ __device__ __forceinline__ long long hw_train_walk(const TrainView<T> &a, const 
                         for (int e = 0; e < EPL; ++e) nr[t][e] = 0.f;
                     }
                 }
+            }
+            if constexpr (STAGE) {
+                // add this warp's pending increments of node x (every window
+                // position holding x, its own position included)
+                const int32_t x0 = __shfl_sync(kFull, x, 0), x1 = __shfl_sync(kFull, x, 16);
+                const uint32_t m0 = __ballot_sync(kFull, win_id >= 0 && win_id == x0);
+                const uint32_t m1 = __ballot_sync(kFull, win_id >= 0 && win_id == x1);
+                uint32_t mine = valid ? (h ? m1 : m0) : 0u;
+                while (__any_sync(kFull, mine != 0)) {
+                    if (mine) {
+                        const int b = __ffs(mine) - 1;
+                        mine &= mine - 1;
+                        const int sl = sbase + b >= R ? sbase + b - R : sbase + b;
+                        float d[EPL];
+                        delta_load<EPL>(delta + sl * D, hl, d);
+#pragma unroll
+                        for (int e = 0; e < EPL; ++e) ix[e] += d[e];
+                    }
+                }
+                __syncwarp();
             }
 #pragma unroll
             for (int e = 0; e < EPL; ++e) nr[0][e] = oc[e];
@@ -642,7 +756,18 @@ __device__ __forceinline__ long long hw_train_walk(const TrainView<T> &a, const 
                 doc[e] += u.x + v0;
                 doc[e + 1] += u.y + v1;
             }
-            if (valid) {
+            if constexpr (STAGE) {
+                if (valid) {  // the context position's slot takes the increment
+                    const int i = o + W;
+                    float *srow = delta + (sbase + i >= R ? sbase + i - R : sbase + i) * D;
+                    float d[EPL];
+                    delta_load<EPL>(srow, hl, d);
+#pragma unroll
+                    for (int e = 0; e < EPL; ++e) d[e] += din[e];
+                    delta_store<EPL>(srow, hl, d);
+                }
+                __syncwarp();
+            } else if (valid) {
                 if constexpr (kBf16) {
                     srs = srs * 1664525u + 1013904223u;
                     add_delta_raw<EPL>(ix_row + hl * EPL, ix_raw, din, srs);
@@ -661,6 +786,22 @@ __device__ __forceinline__ long long hw_train_walk(const TrainView<T> &a, const 
             }
         }
         loss_fx += __float2ll_rn(closs * kLossScaleF);
+        __syncwarp();
+    }
+    if constexpr (STAGE) {
+        // the last window: positions max(0, L - W - 1) .. L - 1 are still staged
+        uint32_t rw = 0;
+        if constexpr (kBf16)
+            rw = philox(a.seed, static_cast<uint32_t>(lane), static_cast<uint32_t>(wi),
+                        (a.round << 16) | static_cast<uint32_t>(L), kStreamSR).x | 1u;
+        int sq = sbase;  // slot of position L - 1 - W
+        for (int q = L - 1 - W; q < L; ++q) {
+            if (q >= 0) {
+                rw = rw * 1664525u + 1013904223u;
+                flush(q, sq, rw);
+            }
+            sq = sq + 1 == R ? 0 : sq + 1;
+        }
         __syncwarp();
     }
     return loss_fx;
