@@ -93,6 +93,7 @@ def lib() -> ctypes.CDLL:
             "oracle_psi_node": (f64, [P, P, P, i32, i32, u64, i32, i32]),
             "oracle_feedback": (i64, [P, P, i32, P, i32, P, u64, i32, P, P, P]),
             "oracle_embed": (i32, [P, P, i32, i32, i32, P, P, i32, i64, u64, P, P, P]),
+            "oracle_embed_lag": (i32, [P, P, i32, i32, i32, P, P, i32, i64, u64, i32, P, P, P]),
             "oracle_auc_pairs": (f64, [P, i64, P, i64]),
             "oracle_link_scores": (None, [P, i32, P, i64, P]),
         }
@@ -298,10 +299,12 @@ def feedback(offsets, cols, phi: np.ndarray, active_in, enabled: bool, mu: float
 
 def embed(offsets, cols, L: int, wpr: int, dim: int, window: int, negatives: int, lr0: float,
           feedback_enabled: bool, mu: float, ks: int, max_rounds: int, reactivate: bool,
-          seed: int, mode: str = "serial", B: int = 4096, T: int = 0):
+          seed: int, mode: str = "serial", B: int = 4096, T: int = 0, feedback_lag: int = 0):
     """Algorithm 1 end to end; returns (phi_in, phi_out, stats[rounds, 4]).
     mode: "serial", "minibatch" (B positions per batch) or "tile" (tiles of
-    128 - 2 window centers with B shared negatives, row averaging)."""
+    128 - 2 window centers with B shared negatives, row averaging).
+    feedback_lag = 1: V_a^{r+1} from Psi on the table as round r's training
+    starts (the round-interleaved reading of Section 5.3)."""
     off, col = _c(offsets, np.int32), _c(cols, np.int32)
     n = off.shape[0] - 1
     phi_in = np.empty((n, dim), np.float64)
@@ -309,9 +312,9 @@ def embed(offsets, cols, L: int, wpr: int, dim: int, window: int, negatives: int
     stats = np.zeros((max_rounds, 4), np.float64)
     tp = _tp(dim, window, negatives, lr0, T)
     fp = _FeedbackParams(int(feedback_enabled), mu, ks, max_rounds, int(reactivate))
-    rounds = lib().oracle_embed(_p(off), _p(col), n, L, wpr, ctypes.byref(tp), ctypes.byref(fp),
-                                {"serial": 0, "minibatch": 1, "tile": 2}[mode], B, seed, _p(phi_in), _p(phi_out),
-                                _p(stats))
+    rounds = lib().oracle_embed_lag(_p(off), _p(col), n, L, wpr, ctypes.byref(tp), ctypes.byref(fp),
+                                    {"serial": 0, "minibatch": 1, "tile": 2}[mode], B, seed, int(feedback_lag),
+                                    _p(phi_in), _p(phi_out), _p(stats))
     return phi_in, phi_out, stats[:rounds]
 
 

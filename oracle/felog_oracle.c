@@ -775,11 +775,18 @@ int64_t oracle_feedback(const int32_t *offsets, const int32_t *cols, int32_t n, 
 /* phi_in / phi_out are filled by the initialiser.  Per-round statistics:    */
 /* stats[r*4 + 0] = |V_a^r|, +1 = tokens, +2 = loss, +3 = |V_a^{r+1}|.       */
 /* Returns the number of rounds run.                                         */
+/*                                                                           */
+/* feedback_lag = 1 is the round-interleaved reading of Section 5.3: the    */
+/* feedback that fixes V_a^{r+1} is computed on the embedding snapshot of   */
+/* phi_in taken when round r's training starts (the table after round      */
+/* r - 1), so sampling round r + 1 does not wait for round r's training.    */
+/* feedback_lag = 0 is Algorithm 1 as printed (Psi after round r's         */
+/* training).                                                                */
 /* ------------------------------------------------------------------------ */
-int32_t oracle_embed(const int32_t *offsets, const int32_t *cols, int32_t n, int32_t L, int32_t wpr,
-                     const oracle_train_params *tp_in, const oracle_feedback_params *fp,
-                     int32_t mode, int64_t B, uint64_t seed, double *phi_in, double *phi_out,
-                     double *stats) {
+int32_t oracle_embed_lag(const int32_t *offsets, const int32_t *cols, int32_t n, int32_t L, int32_t wpr,
+                         const oracle_train_params *tp_in, const oracle_feedback_params *fp,
+                         int32_t mode, int64_t B, uint64_t seed, int32_t feedback_lag, double *phi_in,
+                         double *phi_out, double *stats) {
     oracle_train_params tp = *tp_in;
     const int32_t d = tp.dim;
     oracle_init_tables(n, d, seed, phi_in, phi_out);
@@ -790,6 +797,7 @@ int32_t oracle_embed(const int32_t *offsets, const int32_t *cols, int32_t n, int
     uint64_t *W = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(n > 0 ? n : 1));
     uint64_t *thr = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(n > 0 ? n : 1));
     int32_t *alias = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    double *snap = feedback_lag ? (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * d) : NULL;
     int64_t n_live = 0;
     for (int32_t v = 0; v < n; ++v) {
         active[v] = offsets[v + 1] > offsets[v];
@@ -810,6 +818,7 @@ int32_t oracle_embed(const int32_t *offsets, const int32_t *cols, int32_t n, int
         oracle_counts(walks, n_walks * L, n, counts);
         uint64_t S;
         oracle_noise_table(counts, n, W, thr, alias, &S);
+        if (snap) memcpy(snap, phi_in, sizeof(double) * (size_t)n * d);  /* the table as training starts */
         double loss;
         if (mode == 0)
             loss = oracle_sgns_serial(walks, n_walks, L, n, &tp, thr, alias, S, seed, r, clock,
@@ -821,7 +830,7 @@ int32_t oracle_embed(const int32_t *offsets, const int32_t *cols, int32_t n, int
             loss = oracle_sgns_tile(walks, n_walks, L, n, &tp, 128 - 2 * tp.window, (int32_t)B, 1,
                                     thr, alias, S, seed, r, clock, phi_in, phi_out, NULL);
         clock += n_walks * L;
-        int64_t na = oracle_feedback(offsets, cols, n, phi_in, d, fp, seed, r, active, next, NULL);
+        int64_t na = oracle_feedback(offsets, cols, n, snap ? snap : phi_in, d, fp, seed, r, active, next, NULL);
         if (stats) {
             stats[r * 4 + 0] = ns;
             stats[r * 4 + 1] = (double)(n_walks * L);
@@ -831,8 +840,15 @@ int32_t oracle_embed(const int32_t *offsets, const int32_t *cols, int32_t n, int
         memcpy(active, next, (size_t)n);
         free(walks);
     }
-    free(active); free(next); free(starts); free(counts); free(W); free(thr); free(alias);
+    free(active); free(next); free(starts); free(counts); free(W); free(thr); free(alias); free(snap);
     return r;
+}
+
+int32_t oracle_embed(const int32_t *offsets, const int32_t *cols, int32_t n, int32_t L, int32_t wpr,
+                     const oracle_train_params *tp_in, const oracle_feedback_params *fp,
+                     int32_t mode, int64_t B, uint64_t seed, double *phi_in, double *phi_out,
+                     double *stats) {
+    return oracle_embed_lag(offsets, cols, n, L, wpr, tp_in, fp, mode, B, seed, 0, phi_in, phi_out, stats);
 }
 
 /* ------------------------------------------------------------------------ */

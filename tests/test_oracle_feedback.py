@@ -108,3 +108,27 @@ def test_algorithm1_token_counter_and_termination(orc):
     assert np.all(np.diff(st[:, 0]) <= 0)
     if st.shape[0] < 6:
         assert st[-1, 3] == 0  # stopped because the active set emptied
+
+
+def test_lagged_feedback_option(orc):
+    """feedback_lag = 1 (V_a^{r+1} decided on the table as round r's training
+    starts): with feedback off it changes nothing; with feedback on, the first
+    decision is Eq. 5 applied to Psi of the untrained (initial) table, and the
+    active sets still shrink monotonically."""
+    from paper_2606_22180_b300 import inputs
+
+    g = inputs.rmat(10, 8, seed=3)
+    args = (g.offsets, g.cols, 12, 1, 16, 3, 3, 0.025)
+    a0 = orc.embed(*args, False, 0.9, 8, 4, False, 5, mode="minibatch", B=500, feedback_lag=0)
+    a1 = orc.embed(*args, False, 0.9, 8, 4, False, 5, mode="minibatch", B=500, feedback_lag=1)
+    for x, y in zip(a0, a1):
+        assert np.array_equal(x, y)
+    mu = 0.5
+    _, _, st = orc.embed(*args, True, mu, 8, 5, False, 5, mode="minibatch", B=500, feedback_lag=1)
+    _, _, st0 = orc.embed(*args, True, mu, 8, 5, False, 5, mode="minibatch", B=500, feedback_lag=0)
+    live = (g.degrees() > 0).astype(np.uint8)
+    ri, _ = orc.init_tables(g.n, 16, 5)
+    psi, nxt, cnt = orc.feedback(g.offsets, g.cols, ri, live, True, mu, 8, False, 5, 0)
+    assert st[0, 3] == cnt and st[1, 0] == cnt
+    assert st0[0, 3] != cnt  # the trained table decides differently: the option is visible
+    assert all(st[r + 1, 0] <= st[r, 0] for r in range(st.shape[0] - 1))
