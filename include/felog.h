@@ -314,6 +314,40 @@ felog_status felog_embed(const felog_csr *g, const felog_walk_params *wp,
                          void *stream);
 
 /* ------------------------------------------------------------------------
+ * Round-interleaved pipeline (Section 5.3): Algorithm 1 with its operators
+ * in two pipelines on one GPU.  The caller's stream trains (T_r); a stream
+ * the library creates computes Psi_r and V_a^{r+1}, compacts it, samples
+ * round r + 1 (walks, counts) and builds its noise table into a second set of
+ * round buffers.  feedback_lag = 1 takes Section 5.3's stale-snapshot
+ * reading: Psi_r reads a copy of phi_in taken as T_r starts (the table after
+ * round r - 1), so round r + 1's sampling overlaps T_r; feedback_lag = 0 is
+ * Algorithm 1 as printed (Psi_r after T_r; no overlap).  Results, per
+ * round, equal those of a serial run with the same feedback rule (the
+ * oracle's Algorithm 1 with the same lag).  The call synchronises once per
+ * round, with the sample stream only.  Stats: per round as felog_embed, with
+ * ms_train = T_r on the train stream and ms_feedback = the sample stream's
+ * work after T_r starts (walk and noise times are folded into it).
+ * TILE-mode training waits for its launch (see felog_train), which
+ * serialises the two streams.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    double wall_ms;        /* first sample to last round's end, CUDA events */
+    double train_busy_ms;  /* sum of T_r */
+    double sample_busy_ms; /* sum of the sample stream's work */
+    double overlap_ms;     /* time both streams were busy */
+    int32_t rounds;
+    int32_t feedback_lag;
+} felog_pipeline_stats;
+
+size_t felog_pipeline_workspace_bytes(int32_t n, const felog_walk_params *wp, const felog_train_params *tp,
+                                      int32_t max_rounds, int32_t feedback_lag);
+felog_status felog_embed_pipelined(const felog_csr *g, const felog_walk_params *wp,
+                                   const felog_train_params *tp, const felog_feedback_params *fp,
+                                   int32_t feedback_lag, uint64_t seed, void *phi_in, void *phi_out,
+                                   felog_round_stats *stats, felog_pipeline_stats *pstats, int32_t *rounds_run,
+                                   void *workspace, size_t workspace_bytes, void *stream);
+
+/* ------------------------------------------------------------------------
  * FaBC (Section 5.2.2, Eq. 7, Eq. 8): frequency-aware bitmap compression of
  * a walk corpus, to persist it or move it off the GPU.
  *
@@ -364,9 +398,13 @@ felog_status felog_fabc_decode(const uint8_t *in, size_t in_bytes, int64_t n_seq
  * of launches with no host synchronisation, each job at its own round index,
  * so felog_batch_run can capture all rounds in one CUDA graph.  A job's walks,
  * alias tables and Psi are exactly those of the single-graph calls with the
- * same seed; its training is the half-warp Hogwild step (dim <= 128,
- * negatives <= 7, HOGWILD mode only), with at most
- * n_j / hogwild_rows_per_warp warps on job j at once.
+ * same seed.  Training (dim <= 128, negatives <= 7): HOGWILD mode runs the
+ * half-warp Hogwild step with at most n_j / hogwild_rows_per_warp warps on
+ * job j at once; MINIBATCH mode (the deterministic form) runs one
+ * synchronous batch per round and job (tp->minibatch is ignored), so every
+ * job's tables, |V_a| and losses equal, bit for bit, felog_embed's for that
+ * job alone with a minibatch covering the round; it needs 16 * dim + 8 more
+ * bytes of device memory per node (fixed-point accumulators and marks).
  * ------------------------------------------------------------------------ */
 typedef struct {
     felog_csr graph;          /* device CSR, node ids local to the job */
@@ -450,7 +488,7 @@ typedef struct {
     int32_t max_resident;       /* cap on resident jobs (<= 0: none) */
     int32_t drain_on_destroy;   /* 1: destroy finishes queued and resident jobs first */
     felog_walk_params walk;
-    felog_train_params train;   /* dim ignored (per job); HOGWILD, negatives <= 7 */
+    felog_train_params train;   /* dim ignored (per job); HOGWILD or MINIBATCH (as the batching form), negatives <= 7 */
     felog_feedback_params feedback;
 } felog_server_config;
 

@@ -99,6 +99,7 @@ __global__ void k_b_lr(BArgs a) {
     int64_t T = a.lr_total_tokens;
     if (T <= 0) T = static_cast<int64_t>(a.max_rounds) * a.wpr * st.n_live * a.L;
     if (T <= 0) T = 1;
+    st.T_total = T;
     st.inv_T = static_cast<float>(1.0 / static_cast<double>(T));
     st.done = st.n_live == 0 || a.max_rounds == 0;
     st.phase = 1;
@@ -402,6 +403,66 @@ __global__ void __launch_bounds__(kSgnsThreads, 2) k_b_sgns(BArgs a, int64_t ite
 }
 
 // ---------------------------------------------------------------------------
+// MINIBATCH (the deterministic form): one synchronous batch per round and
+// job.  Token x of the flat space over the jobs of one dim (a job's span is
+// its n * wpr walk slots times L) is center position p of walk slot wi; slots
+// past the job's active walks are idle.  eta is that of the round's first
+// position, formed in binary64 as felog_train does for a batch; the per-center
+// and per-row routines are the single-graph kernels' own, so a job's round
+// equals felog_train's minibatch form over the round with minibatch >= its
+// tokens, bit for bit.
+// ---------------------------------------------------------------------------
+template <int D, class T>
+__global__ void __launch_bounds__(kSgnsThreads) k_b_mb_grad(BArgs a, int64_t tok_lo, int64_t tok_hi) {
+    extern __shared__ int32_t smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    int32_t *negs = smem + wib * (2 * a.window * a.K);
+    const int64_t warps = static_cast<int64_t>(gridDim.x) * kWarps;
+    for (int64_t x = tok_lo + static_cast<int64_t>(blockIdx.x) * kWarps + wib; x < tok_hi; x += warps) {
+        const int j = find_job(a.slot_prefix, a.n_jobs, x / a.L);
+        const BState &st = *a.jobs[j].st;
+        if (st.done) continue;
+        const BJob &jb = a.jobs[j];
+        const int64_t t = x - a.slot_prefix[j] * a.L;
+        const int64_t wi = t / a.L;
+        if (wi >= static_cast<int64_t>(st.n_active) * a.wpr) continue;
+        const int p = static_cast<int>(t - wi * a.L);
+        const double f = 1.0 - static_cast<double>(st.clock) / static_cast<double>(st.T_total);
+        const float eta = static_cast<float>(static_cast<double>(a.lr0) * (f < 1e-4 ? 1e-4 : f));
+        const MbView v{jb.thr, jb.alias, static_cast<uint64_t>(jb.n), st.S, jb.seed, static_cast<uint32_t>(st.round),
+                       a.window, a.K, a.L};
+        const MbState ms{jb.acc_in, jb.acc_out, jb.mark_in, jb.mark_out, nullptr, nullptr, nullptr};
+        const float closs = mb_grad_center<D, T, 8>(v, jb.walks + wi * a.L, wi, p, eta,
+                                                    static_cast<const T *>(jb.phi_in),
+                                                    static_cast<const T *>(jb.phi_out), ms, negs);
+        long long loss_fx = __float2ll_rn(closs * kLossScaleF);
+        for (int o = 16; o; o >>= 1) loss_fx += __shfl_xor_sync(kFull, loss_fx, o);
+        if (lane == 0 && loss_fx != 0) atomicAdd(&jb.st->loss_acc, static_cast<unsigned long long>(loss_fx));
+    }
+}
+
+// every marked row of the jobs [node_lo, node_hi) of one dim, both tables
+template <int D, class T>
+__global__ void __launch_bounds__(256) k_b_mb_apply(BArgs a, int64_t node_lo, int64_t node_hi) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x / 32);
+    for (int64_t i = node_lo * 2 + static_cast<int64_t>(blockIdx.x) * (blockDim.x / 32) + (threadIdx.x >> 5);
+         i < node_hi * 2; i += warps) {
+        const int64_t x = i >> 1;
+        const bool is_in = (i & 1) == 0;
+        const int j = find_job(a.node_prefix, a.n_jobs, x);
+        const BState &st = *a.jobs[j].st;
+        if (st.done) continue;
+        const BJob &jb = a.jobs[j];
+        const int32_t r = static_cast<int32_t>(x - a.node_prefix[j]);
+        uint32_t *mark = is_in ? jb.mark_in : jb.mark_out;
+        if (!mark[r]) continue;
+        mb_apply_row<D, T>(static_cast<T *>(is_in ? jb.phi_in : jb.phi_out), is_in ? jb.acc_in : jb.acc_out, mark, r,
+                           is_in, jb.seed, static_cast<uint32_t>(st.round) << 20, lane);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Psi and V_a^{r+1} (same values as felog_feedback)
 // ---------------------------------------------------------------------------
 template <class T>
@@ -463,11 +524,17 @@ __global__ void k_b_gather(BArgs a, BState *st_out, int32_t *rna, int32_t *rnn, 
 // ---------------------------------------------------------------------------
 // host side: job memory, plans (a membership of jobs), init and step
 // ---------------------------------------------------------------------------
-size_t job_work_bytes(int32_t n, const BParams &p) {
+size_t job_work_bytes(int32_t n, int32_t dim, const BParams &p) {
     const size_t nn = n > 0 ? static_cast<size_t>(n) : 1;
     const size_t R = static_cast<size_t>(std::max(p.max_rounds, 1));
     size_t b = 0;
     auto add = [&](size_t x) { b += align_up(x, 256); };
+    if (p.mode == FELOG_SGNS_MINIBATCH) {
+        add(8 * nn * dim);  // acc_in
+        add(8 * nn * dim);  // acc_out
+        add(4 * nn);        // mark_in
+        add(4 * nn);        // mark_out
+    }
     add(sizeof(BState));
     add(4 * R);                                            // rec_n_active
     add(4 * R);                                            // rec_n_next
@@ -493,6 +560,12 @@ void job_carve(BJob &jb, void *mem, int32_t n, const BParams &p) {
     const size_t R = static_cast<size_t>(std::max(p.max_rounds, 1));
     char *q = static_cast<char *>(mem);
     auto take = [&](size_t bytes) { char *r = q; q += align_up(bytes, 256); return r; };
+    if (p.mode == FELOG_SGNS_MINIBATCH) {
+        jb.acc_in = reinterpret_cast<long long *>(take(8 * nn * jb.dim));
+        jb.acc_out = reinterpret_cast<long long *>(take(8 * nn * jb.dim));
+        jb.mark_in = reinterpret_cast<uint32_t *>(take(4 * nn));
+        jb.mark_out = reinterpret_cast<uint32_t *>(take(4 * nn));
+    }
     jb.st = reinterpret_cast<BState *>(take(sizeof(BState)));
     jb.rec_n_active = reinterpret_cast<int32_t *>(take(4 * R));
     jb.rec_n_next = reinterpret_cast<int32_t *>(take(4 * R));
@@ -516,6 +589,13 @@ void job_carve(BJob &jb, void *mem, int32_t n, const BParams &p) {
 felog_status job_clear_state(const BJob &jb, const BParams &p, cudaStream_t s) {
     const size_t R = static_cast<size_t>(std::max(p.max_rounds, 1));
     const size_t bytes = align_up(sizeof(BState), 256) + 2 * align_up(4 * R, 256) + 8 * R;
+    if (p.mode == FELOG_SGNS_MINIBATCH) {
+        // the accumulators and marks lie in front of the state, contiguous
+        const size_t nn = jb.n > 0 ? static_cast<size_t>(jb.n) : 1;
+        const size_t mb = 2 * align_up(8 * nn * jb.dim, 256) + 2 * align_up(4 * nn, 256);
+        felog_status st = record_cuda_error(cudaMemsetAsync(jb.acc_in, 0, mb, s), "job accumulators");
+        if (st) return st;
+    }
     return record_cuda_error(cudaMemsetAsync(jb.st, 0, bytes, s), "job state");
 }
 
@@ -577,6 +657,8 @@ felog_status plan_build(BatchPlan &plan, const std::vector<BJob> &jobs_in, const
     }
     plan.n_jobs = n_jobs;
     plan.item_prefix = item_prefix;
+    plan.slot_prefix = slot_prefix;
+    plan.node_prefix = node_prefix;
     plan.jobs = jobs;
     BArgs &a = plan.args;
     a.jobs = reinterpret_cast<const BJob *>(base + o_jobs);
@@ -630,6 +712,33 @@ void launch_b_sgns(const BatchPlan &plan, const BParams &p, const HostTuning &t,
     const int blocks = static_cast<int>(
         std::max<int64_t>(1, std::min<int64_t>(want, static_cast<int64_t>(t.sgns_blocks_per_sm) * sm_count())));
     kern<<<blocks, kSgnsThreads, smem, s>>>(plan.args, lo, hi);
+}
+
+template <int D, class T>
+void launch_b_mb(const BatchPlan &plan, const BParams &p, int32_t j0, int32_t j1, cudaStream_t s) {
+    const int64_t tok_lo = plan.slot_prefix[j0] * p.L, tok_hi = plan.slot_prefix[j1] * p.L;
+    if (tok_hi <= tok_lo) return;
+    const size_t smem = sizeof(int32_t) * kWarps * (2 * p.window * p.K);
+    k_b_mb_grad<D, T><<<grid_for((tok_hi - tok_lo + kWarps - 1) / kWarps, 1, 16), kSgnsThreads, smem, s>>>(
+        plan.args, tok_lo, tok_hi);
+    const int64_t node_lo = plan.node_prefix[j0], node_hi = plan.node_prefix[j1];
+    k_b_mb_apply<D, T><<<grid_for((2 * (node_hi - node_lo) + 7) / 8, 1, 16), 256, 0, s>>>(plan.args, node_lo,
+                                                                                          node_hi);
+}
+
+template <class T>
+void launch_mb_all(const BatchPlan &plan, const BParams &p, cudaStream_t s) {
+    int32_t j = 0;
+    while (j < plan.n_jobs) {
+        int32_t k = j;
+        while (k < plan.n_jobs && plan.dims[k] == plan.dims[j]) ++k;
+        switch (plan.dims[j]) {
+            case 32: launch_b_mb<32, T>(plan, p, j, k, s); break;
+            case 64: launch_b_mb<64, T>(plan, p, j, k, s); break;
+            case 128: launch_b_mb<128, T>(plan, p, j, k, s); break;
+        }
+        j = k;
+    }
 }
 
 template <class T>
@@ -687,8 +796,14 @@ felog_status plan_step(const BatchPlan &plan, const BParams &p, const HostTuning
         k_b_noise_finish<<<grid_for(a.n_nodes, 256, 8), 256, 0, s>>>(a);
     }
     if (phases & 8) {
-        if (p.precision == FELOG_FP32) launch_sgns_all<float>(plan, p, t, s);
-        else launch_sgns_all<__nv_bfloat16>(plan, p, t, s);
+        if (p.mode == FELOG_SGNS_MINIBATCH) {
+            if (p.precision == FELOG_FP32) launch_mb_all<float>(plan, p, s);
+            else launch_mb_all<__nv_bfloat16>(plan, p, s);
+        } else if (p.precision == FELOG_FP32) {
+            launch_sgns_all<float>(plan, p, t, s);
+        } else {
+            launch_sgns_all<__nv_bfloat16>(plan, p, t, s);
+        }
     }
     if (phases & 16) {
         const int grid = static_cast<int>(std::max<int64_t>(
@@ -742,6 +857,7 @@ BParams make_params(const felog_walk_params *wp, const felog_train_params *tp, c
     p.lr0 = tp->lr0;
     p.lr_total_tokens = tp->lr_total_tokens;
     p.rows_per_warp = tp->hogwild_rows_per_warp > 0 ? tp->hogwild_rows_per_warp : 16;
+    p.mode = tp->mode;
     return p;
 }
 
@@ -750,7 +866,7 @@ felog_status check_params(const felog_walk_params *wp, const felog_train_params 
     if (wp->length < 1 || wp->walks_per_round < 1) return FELOG_ERR_INVALID_ARG;
     if (tp->window < 1 || tp->window > 16 || tp->negatives < 1 || tp->negatives > 7)
         return FELOG_ERR_UNSUPPORTED;  // the batched trainer is the half-warp form
-    if (tp->mode != FELOG_SGNS_HOGWILD) return FELOG_ERR_UNSUPPORTED;
+    if (tp->mode != FELOG_SGNS_HOGWILD && tp->mode != FELOG_SGNS_MINIBATCH) return FELOG_ERR_UNSUPPORTED;
     if (tp->precision != FELOG_FP32 && tp->precision != FELOG_BF16_SR) return FELOG_ERR_INVALID_ARG;
     if (!(tp->lr0 >= 0.f)) return FELOG_ERR_INVALID_ARG;
     if (fp->ks < 1 || fp->ks > kMaxKs || fp->max_rounds < 0 || fp->max_rounds >= 65536) return FELOG_ERR_INVALID_ARG;
@@ -846,7 +962,7 @@ extern "C" felog_status felog_batch_create(const felog_job *jobs, int32_t n_jobs
     size_t total = 0;
     for (int32_t i = 0; i < n_jobs; ++i) {
         offs[i] = total;
-        total += job_work_bytes(jobs[order[i]].graph.n, b->p);
+        total += job_work_bytes(jobs[order[i]].graph.n, jobs[order[i]].dim, b->p);
     }
     st = record_cuda_error(cudaMalloc(&b->blob, total), "felog_batch_create");
     if (st) {

@@ -32,6 +32,8 @@ struct BJob {
     int32_t *heavy_idx;
     u128 *heavy_E;
     int32_t tile_base, n_tiles;
+    long long *acc_in, *acc_out;           // MINIBATCH: fixed-point increments [n][dim]
+    uint32_t *mark_in, *mark_out;          // MINIBATCH: touched rows [n]
     struct BState *st;                     // this job's state (in the job's own memory)
     int32_t *rec_n_active, *rec_n_next;    // [max_rounds]
     double *rec_loss;                      // [max_rounds]
@@ -41,6 +43,7 @@ struct BState {
     int32_t round, cur, n_active, n_next;
     int32_t done, phase;  // phase 0: tables and V_a not initialised yet
     int64_t clock, n_live;
+    int64_t T_total;  // the learning-rate horizon (tokens)
     float inv_T, pad1;
     unsigned long long S;
     uint32_t cmax, pad2;
@@ -67,6 +70,7 @@ struct BArgs {
 
 struct BParams {
     int32_t L, wpr, window, K, max_rounds, ks, enabled, reactivate, precision;
+    int32_t mode;  // FELOG_SGNS_HOGWILD or FELOG_SGNS_MINIBATCH (one synchronous batch per round)
     double mu;
     float lr0;
     int64_t lr_total_tokens, rows_per_warp;
@@ -85,13 +89,14 @@ struct BatchPlan {
     size_t bytes = 0;
     size_t o_gst = 0, o_gna = 0, o_gnn = 0, o_gl = 0;  // gather staging
     BArgs args{};
-    std::vector<int64_t> item_prefix;  // host copy
+    std::vector<int64_t> item_prefix;  // host copies
+    std::vector<int64_t> slot_prefix, node_prefix;
     std::vector<int32_t> dims;         // host, plan order
     std::vector<BJob> jobs;            // host copy of the job table
 };
 
-size_t job_work_bytes(int32_t n, const BParams &p);
-void job_carve(BJob &jb, void *mem, int32_t n, const BParams &p);
+size_t job_work_bytes(int32_t n, int32_t dim, const BParams &p);
+void job_carve(BJob &jb, void *mem, int32_t n, const BParams &p);  // jb.dim set first
 felog_status job_clear_state(const BJob &jb, const BParams &p, cudaStream_t s);
 felog_status plan_build(BatchPlan &plan, const std::vector<BJob> &jobs, const BParams &p, cudaStream_t s);
 void plan_release(BatchPlan &plan, cudaStream_t s);

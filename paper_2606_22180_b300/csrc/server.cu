@@ -102,7 +102,7 @@ felog_status upload_job(felog_server *sv, Resident &r) {
     int32_t *cols = reinterpret_cast<int32_t *>(take(4 * std::max<size_t>(q.nnz, 1)));
     void *phi_in = take(table_bytes(q.n, q.dim, sv->p.precision));
     void *phi_out = take(table_bytes(q.n, q.dim, sv->p.precision));
-    void *work = take(job_work_bytes(q.n, sv->p));
+    void *work = take(job_work_bytes(q.n, q.dim, sv->p));
     felog_status st = record_cuda_error(
         cudaMemcpyAsync(offsets, q.offsets.data(), 4 * (static_cast<size_t>(q.n) + 1), cudaMemcpyHostToDevice, s), "upload");
     if (!st && q.nnz)
@@ -125,7 +125,7 @@ felog_status upload_job(felog_server *sv, Resident &r) {
 
 size_t job_device_bytes(const BParams &p, int32_t n, int64_t nnz, int32_t dim) {
     return align_up(4 * (static_cast<size_t>(n) + 1), 256) + align_up(4 * std::max<size_t>(nnz, 1), 256) +
-           2 * align_up(table_bytes(n, dim, p.precision), 256) + job_work_bytes(n, p);
+           2 * align_up(table_bytes(n, dim, p.precision), 256) + job_work_bytes(n, dim, p);
 }
 
 felog_status rebuild_plan(felog_server *sv) {

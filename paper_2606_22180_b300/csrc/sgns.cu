@@ -216,143 +216,22 @@ __global__ void __launch_bounds__(kSgnsThreads, 2)
 
 
 // ----------------------------------------------------------------------------
-// MINIBATCH: one warp per center position of the batch [b0, b1).  Tables are
-// read only; increments go to 64-bit fixed-point accumulators (2^-40 units),
-// which makes the per-row sums exact and order independent.
+// MINIBATCH: one warp per center position of the batch [b0, b1) (the per-center
+// and per-row routines are in sgns_core.cuh, shared with the batched trainer).
 // ----------------------------------------------------------------------------
-struct MbState {
-    long long *acc_in, *acc_out;  // [n][D]
-    uint32_t *mark_in, *mark_out; // [n]
-    int32_t *list_in, *list_out;  // [n]
-    int32_t *counters;            // [0] = |list_in|, [1] = |list_out|, [2] = apply ticket
-};
-
-template <int EPL>
-__device__ __forceinline__ void add_fixed(long long *__restrict__ p, const float (&x)[EPL]) {
-#pragma unroll
-    for (int e = 0; e < EPL; ++e) {
-        const long long q = __float2ll_rn(x[e] * kDeltaScale);
-        if (q) atomicAdd(reinterpret_cast<unsigned long long *>(p + e), static_cast<unsigned long long>(q));
-    }
-}
-
-__device__ __forceinline__ void mark_row(uint32_t *mark, int32_t *list, int32_t *counter, int32_t r) {
-    if (atomicExch(mark + r, 1u) == 0u) list[atomicAdd(counter, 1)] = r;
-}
-
 template <int D, class T, int MAXT>
 __global__ void __launch_bounds__(kSgnsThreads)
     k_sgns_mb_grad(SgnsArgs a, int64_t b0, int64_t b1, float eta, const T *__restrict__ phi_in,
                    const T *__restrict__ phi_out, MbState st) {
-    constexpr int EPL = D / 32;
     extern __shared__ int32_t smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int W = a.window, K = a.K, L = a.L;
-    int32_t *negs = smem + wib * (2 * W * K);
-    const uint64_t S = *a.S;
-    const uint64_t n = static_cast<uint64_t>(a.n);
-    const int my_t = target_of_lane<MAXT>(lane);
-    const bool loss_lane = (lane & ((32 / MAXT) - 1)) == 0;
+    int32_t *negs = smem + wib * (2 * a.window * a.K);
     const int64_t tok = b0 + static_cast<int64_t>(blockIdx.x) * kWarps + wib;
     if (tok >= b1) return;
-    const int64_t wi = tok / L;
-    const int p = static_cast<int>(tok - wi * L);
-    const int32_t *row = a.walks + wi * L;
-    const int32_t c = walk_id(row[p], n);
-    if (c < 0) return;
-    for (int idx = lane; idx < 2 * W * K; idx += 32) {
-        const int q = idx / K, k = idx - q * K;
-        negs[idx] = draw_negative(a.thr, a.alias, n, S, a.seed, a.round, static_cast<uint32_t>(wi),
-                                  static_cast<uint32_t>(p), static_cast<uint32_t>(q),
-                                  static_cast<uint32_t>(k));
-    }
-    __syncwarp();
-    float oc[EPL], doc[EPL];
-    load_row<EPL>(phi_out + static_cast<int64_t>(c) * D + lane * EPL, oc);
-#pragma unroll
-    for (int e = 0; e < EPL; ++e) doc[e] = 0.f;
-    float closs = 0.f;
-    bool any = false;
-    for (int o = -W; o <= W; ++o) {
-        if (o == 0) continue;
-        const int pp = p + o;
-        if (pp < 0 || pp >= L) continue;
-        const int32_t x = walk_id(row[pp], n);
-        if (x < 0) continue;
-        any = true;
-        const int q = o < 0 ? o + W : o + W - 1;
-        int32_t nid[MAXT];
-        nid[0] = c;
-#pragma unroll
-        for (int t = 1; t < MAXT; ++t) {
-            int32_t v = -1;
-            if (t <= K) {
-                v = negs[q * K + t - 1];
-                if (v == c) v = -1;
-            }
-            nid[t] = v;
-        }
-        float ix[EPL];
-        load_row<EPL>(phi_in + static_cast<int64_t>(x) * D + lane * EPL, ix);
-        float nr[MAXT][EPL];
-#pragma unroll
-        for (int t = 1; t < MAXT; ++t) {
-            if (nid[t] >= 0) load_row<EPL>(phi_out + static_cast<int64_t>(nid[t]) * D + lane * EPL, nr[t]);
-            else {
-#pragma unroll
-                for (int e = 0; e < EPL; ++e) nr[t][e] = 0.f;
-            }
-        }
-#pragma unroll
-        for (int e = 0; e < EPL; ++e) nr[0][e] = oc[e];
-        float pd[MAXT];
-#pragma unroll
-        for (int t = 0; t < MAXT; ++t) {
-            float s = 0.f;
-#pragma unroll
-            for (int e = 0; e < EPL; ++e) s = fmaf(ix[e], nr[t][e], s);
-            pd[t] = s;
-        }
-        const float dot = reduce_scatter<MAXT>(pd, lane);
-        int32_t my_id = nid[0];
-#pragma unroll
-        for (int t = 1; t < MAXT; ++t)
-            if (t == my_t) my_id = nid[t];
-        float g = 0.f;
-        if (my_id >= 0) {
-            const float label = my_t == 0 ? 1.f : 0.f;
-            const float sig = 1.f / (1.f + expf(-dot));
-            g = eta * (label - sig);
-            if (loss_lane) closs += my_t == 0 ? softplus_neg(dot) : softplus_neg(-dot);
-        }
-        float gt[MAXT];
-#pragma unroll
-        for (int t = 0; t < MAXT; ++t) gt[t] = __shfl_sync(kFull, g, t << (5 - (MAXT == 8 ? 3 : 4)));
-        float din[EPL];
-#pragma unroll
-        for (int e = 0; e < EPL; ++e) {
-            din[e] = gt[0] * oc[e];
-            doc[e] = fmaf(gt[0], ix[e], doc[e]);
-        }
-#pragma unroll
-        for (int t = 1; t < MAXT; ++t) {
-            if (nid[t] < 0) continue;
-            float dn[EPL];
-#pragma unroll
-            for (int e = 0; e < EPL; ++e) {
-                din[e] = fmaf(gt[t], nr[t][e], din[e]);
-                dn[e] = gt[t] * ix[e];
-            }
-            add_fixed<EPL>(st.acc_out + static_cast<int64_t>(nid[t]) * D + lane * EPL, dn);
-            if (lane == 0) mark_row(st.mark_out, st.list_out, st.counters + 1, nid[t]);
-        }
-        add_fixed<EPL>(st.acc_in + static_cast<int64_t>(x) * D + lane * EPL, din);
-        if (lane == 0) mark_row(st.mark_in, st.list_in, st.counters + 0, x);
-    }
-    if (any) {
-        add_fixed<EPL>(st.acc_out + static_cast<int64_t>(c) * D + lane * EPL, doc);
-        if (lane == 0) mark_row(st.mark_out, st.list_out, st.counters + 1, c);
-    }
+    const int64_t wi = tok / a.L;
+    const int p = static_cast<int>(tok - wi * a.L);
+    const MbView v{a.thr, a.alias, static_cast<uint64_t>(a.n), *a.S, a.seed, a.round, a.window, a.K, a.L};
+    const float closs = mb_grad_center<D, T, MAXT>(v, a.walks + wi * a.L, wi, p, eta, phi_in, phi_out, st, negs);
     long long loss_fx = __float2ll_rn(closs * kLossScaleF);
     for (int o = 16; o; o >>= 1) loss_fx += __shfl_xor_sync(kFull, loss_fx, o);
     if (lane == 0 && loss_fx != 0) atomicAdd(a.loss_acc, static_cast<unsigned long long>(loss_fx));
@@ -364,7 +243,6 @@ template <int D, class T>
 __global__ void __launch_bounds__(256)
     k_sgns_mb_apply(T *__restrict__ phi_in, T *__restrict__ phi_out, MbState st, uint64_t seed,
                     uint32_t batch_key) {
-    constexpr int EPL = D / 32;
     const int lane = threadIdx.x & 31;
     const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x / 32);
     const int32_t n_in = st.counters[0], n_out = st.counters[1];
@@ -372,22 +250,8 @@ __global__ void __launch_bounds__(256)
          i < static_cast<int64_t>(n_in) + n_out; i += warps) {
         const bool is_in = i < n_in;
         const int32_t r = is_in ? st.list_in[i] : st.list_out[i - n_in];
-        T *tab = is_in ? phi_in : phi_out;
-        long long *acc = (is_in ? st.acc_in : st.acc_out) + static_cast<int64_t>(r) * D + lane * EPL;
-        float v[EPL];
-        load_row<EPL>(tab + static_cast<int64_t>(r) * D + lane * EPL, v);
-#pragma unroll
-        for (int e = 0; e < EPL; ++e) {
-            const long long q = acc[e];
-            acc[e] = 0;
-            v[e] += __ll2float_rn(q) * kDeltaUnscale;
-        }
-        uint32_t rr = 0;
-        if constexpr (!std::is_same<T, float>::value)
-            rr = philox(seed, static_cast<uint32_t>(lane) | (is_in ? 0u : 0x100u),
-                        static_cast<uint32_t>(r), batch_key, kStreamSR).x;
-        store_row<EPL>(tab + static_cast<int64_t>(r) * D + lane * EPL, v, rr);
-        if (lane == 0) (is_in ? st.mark_in : st.mark_out)[r] = 0u;
+        mb_apply_row<D, T>(is_in ? phi_in : phi_out, is_in ? st.acc_in : st.acc_out, is_in ? st.mark_in : st.mark_out,
+                           r, is_in, seed, batch_key, lane);
     }
     __shared__ bool last;
     __syncthreads();

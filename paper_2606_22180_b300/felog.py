@@ -32,6 +32,7 @@ SYMBOLS = [
     "felog_feedback",
     "felog_embed_workspace_bytes", "felog_embed",
     "felog_walk_node2vec",
+    "felog_pipeline_workspace_bytes", "felog_embed_pipelined",
     "felog_fabc_max_k", "felog_fabc_workspace_bytes", "felog_fabc_max_bytes", "felog_fabc_select",
     "felog_fabc_encode", "felog_fabc_decode",
     "felog_batch_create", "felog_batch_destroy", "felog_batch_device_bytes", "felog_batch_reset",
@@ -114,6 +115,8 @@ def load() -> ctypes.CDLL:
         "felog_feedback": (st, [P, P, i32, i32, P, u64, i32, P, P, P, P, P]),
         "felog_embed_workspace_bytes": (sz, [i32, P, P]),
         "felog_embed": (st, [P, P, P, P, u64, P, P, P, P, P, sz, P]),
+        "felog_pipeline_workspace_bytes": (sz, [i32, P, P, i32, i32]),
+        "felog_embed_pipelined": (st, [P, P, P, P, i32, u64, P, P, P, P, P, P, sz, P]),
         "felog_fabc_max_k": (i32, []),
         "felog_fabc_workspace_bytes": (sz, [i64]),
         "felog_fabc_max_bytes": (sz, [i64, i32, i32]),
@@ -455,6 +458,46 @@ def felog_embed(g: DeviceGraph, length: int, walks_per_round: int, tp: _TrainPar
                            seed, _ptr(phi_in), _ptr(phi_out), stats, ctypes.byref(rounds),
                            _ptr(workspace), workspace.numel(), _stream()), "felog_embed")
     return phi_in, phi_out, [stats[i].as_dict() for i in range(rounds.value)]
+
+
+class PipelineStats(ctypes.Structure):
+    _fields_ = [("wall_ms", ctypes.c_double), ("train_busy_ms", ctypes.c_double),
+                ("sample_busy_ms", ctypes.c_double), ("overlap_ms", ctypes.c_double),
+                ("rounds", ctypes.c_int32), ("feedback_lag", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def felog_embed_pipelined(g: DeviceGraph, length: int, walks_per_round: int, tp: _TrainParams,
+                          fp: _FeedbackParams, seed: int, feedback_lag: int = 1,
+                          phi_in: torch.Tensor | None = None, phi_out: torch.Tensor | None = None,
+                          workspace: torch.Tensor | None = None):
+    """Algorithm 1 as the round-interleaved pipeline (Section 5.3); returns
+    (phi_in, phi_out, [RoundStats dicts], pipeline stats dict)."""
+    _require_cuda(phi_in, phi_out, workspace)
+    lib = load()
+    dev = g.offsets.device
+    dt = table_dtype(tp.precision)
+    if phi_in is None:
+        phi_in = torch.empty((g.n, tp.dim), dtype=dt, device=dev)
+    if phi_out is None:
+        phi_out = torch.empty((g.n, tp.dim), dtype=dt, device=dev)
+    wp = _WalkParams(length, walks_per_round)
+    need = lib.felog_pipeline_workspace_bytes(g.n, ctypes.byref(wp), ctypes.byref(tp), fp.max_rounds, feedback_lag)
+    if need == 0:
+        raise FelogError("felog_embed_pipelined: invalid parameters")
+    if workspace is None or workspace.numel() < need:
+        workspace = _workspace(need, dev)
+    stats = (RoundStats * max(fp.max_rounds, 1))()
+    ps = PipelineStats()
+    rounds = ctypes.c_int32(0)
+    csr = g._c()
+    _check(lib.felog_embed_pipelined(ctypes.byref(csr), ctypes.byref(wp), ctypes.byref(tp), ctypes.byref(fp),
+                                     feedback_lag, seed, _ptr(phi_in), _ptr(phi_out), stats, ctypes.byref(ps),
+                                     ctypes.byref(rounds), _ptr(workspace), workspace.numel(), _stream()),
+           "felog_embed_pipelined")
+    return phi_in, phi_out, [stats[i].as_dict() for i in range(rounds.value)], ps.as_dict()
 
 
 # ---------------------------------------------------------------------------

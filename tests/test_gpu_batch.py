@@ -146,3 +146,33 @@ def test_batch_rejects_unsupported(fl):
     tp = fl.train_params(64, W, K, 0.025, 0, fl.FELOG_SGNS_HOGWILD, 4096, fl.FELOG_FP32)
     with pytest.raises(fl.FelogError):
         fl.Batch([dg], [256], [1], L, 1, tp, fp)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_minibatch_equals_solo_bitwise(fl, precision):
+    """The deterministic form in the batch (one synchronous batch per round
+    and job) gives every job exactly the result of felog_embed alone with a
+    minibatch covering the round: tables, |V_a| and loss per round, bit for
+    bit, with feedback deciding a different schedule per job; captured in a
+    CUDA graph or not."""
+    gs = _graphs()[:4]
+    dgs = [fl.DeviceGraph.from_host(g) for g in gs]
+    dims = [64, 128, 32, 128]
+    seeds = [31 + 5 * i for i in range(4)]
+    tp = fl.train_params(64, W, K, 0.025, 0, fl.FELOG_SGNS_MINIBATCH, 1 << 30, precision)
+    fp = fl.feedback_params(True, 0.9, 8, 4, False)
+    for use_graph in (False, True):
+        b = fl.Batch(dgs, dims, seeds, L, 1, tp, fp)
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            b.run(use_graph=use_graph)
+        s.synchronize()
+        stats, na, loss = b.read()
+        for j in range(4):
+            tpj = fl.train_params(dims[j], W, K, 0.025, 0, fl.FELOG_SGNS_MINIBATCH, 1 << 30, precision)
+            pi, po, st = fl.felog_embed(dgs[j], L, 1, tpj, fp, seeds[j])
+            assert stats[j]["rounds"] == len(st), j
+            assert [int(x) for x in na[: len(st), j]] == [x["n_active"] for x in st], j
+            assert [float(x) for x in loss[: len(st), j]] == [x["loss"] for x in st], j
+            assert torch.equal(b.phi_in[j], pi) and torch.equal(b.phi_out[j], po), j
+        b.close()

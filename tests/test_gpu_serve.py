@@ -119,3 +119,25 @@ def test_malformed_csr_rejected_on_host(fl):
         sv.submit(OutOfRange, 64, 1)
     assert sv.stats()["submitted"] == 0
     sv.close()
+
+
+def test_served_minibatch_results_equal_solo_bitwise(fl):
+    """The deterministic form served: jobs admitted at different times and
+    trained in the mix return exactly the embedding each gets alone."""
+    splits = _jobs(4)
+    tp = fl.train_params(64, W, K, 0.025, 0, fl.FELOG_SGNS_MINIBATCH, 1 << 30, fl.FELOG_FP32)
+    fp = fl.feedback_params(True, 0.9, 8, R, False)
+    sv = fl.Server(4 << 30, L, 1, tp, fp)
+    ids = [sv.submit(sp.train, 64, 70 + i) for i, sp in enumerate(splits[:2])]
+    t0 = time.time()
+    while sv.poll(ids[0])["state"] == fl.JOB_QUEUED and time.time() - t0 < 30:
+        time.sleep(0.001)
+    ids += [sv.submit(sp.train, 64, 72 + i) for i, sp in enumerate(splits[2:])]
+    res = [sv.wait(r, 300) for r in ids]
+    embs = [sv.fetch(r) for r in ids]
+    sv.close()
+    assert all(r["state"] == fl.JOB_DONE for r in res)
+    for i, sp in enumerate(splits):
+        solo, _, st = fl.felog_embed(fl.DeviceGraph.from_host(sp.train), L, 1, tp, fp, 70 + i)
+        assert res[i]["rounds"] == len(st) and res[i]["loss_last"] == st[-1]["loss"], i
+        assert np.array_equal(np.asarray(embs[i]), solo.cpu().numpy()), i
