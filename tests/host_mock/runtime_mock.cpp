@@ -28,7 +28,7 @@ namespace felog {
 felog_status record_cuda_error(cudaError_t e, const char *) { return e == cudaSuccess ? FELOG_OK : FELOG_ERR_CUDA; }
 felog_status check_launch(const char *) { return FELOG_OK; }
 int sm_count() { return 148; }
-size_t job_work_bytes(int32_t n, const BParams &p) {
+size_t job_work_bytes(int32_t n, int32_t, const BParams &p) {
     size_t nn = n > 0 ? n : 1; size_t R = std::max(p.max_rounds, 1);
     return align_up(sizeof(BState), 256) + 2 * align_up(4 * R, 256) + align_up(8 * R, 256) + align_up(nn * 100, 256);
 }
