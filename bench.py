@@ -265,7 +265,7 @@ def _sgns_kernel_name(form, precision):
     t = "float" if precision == "fp32" else "bf16"
     if form == 1:
         return f"k_sgns_hogwild<128,{t},8,5>"
-    staged = form == 3 or (form == 0 and precision == "fp32")  # the library's automatic choice
+    staged = form == 3
     return f"k_sgns_hogwild_hw<128,{t},5,{'true' if staged else 'false'}>"
 
 
@@ -606,8 +606,10 @@ def run_serve(fl, rate=20.0, duration=20.0, max_nodes=1 << 16, pool_size=48, bud
                 "busy_s": st["busy_seconds"],
                 "busy_tokens_per_s": tokens / st["busy_seconds"] if st["busy_seconds"] else None}
 
-    out = {"workload": f"Poisson {rate}/s for {duration}s, |V| log-uniform [1e3, {max_nodes}] (pool of "
-                       f"{pool_size} SBM/R-MAT graphs), L={L}, w={WINDOW}, K={NEG}, d={DIM} bf16, "
+    lo_nodes = min(g.n for g, _ in pool)
+    out = {"workload": f"Poisson {rate:.4g}/s for {duration}s over a pool of {pool_size} SBM/R-MAT graphs "
+                       f"(|V| drawn log-uniform; the pool spans {lo_nodes}..{max_nodes} nodes), "
+                       f"L={L}, w={WINDOW}, K={NEG}, d={DIM} bf16, "
                        f"feedback mu={MU}, budget {budget >> 30} GiB",
            "stated": one(rate)}
     if sustainable:
@@ -622,10 +624,10 @@ def _gen_workers():
     return max(1, min(32, (os.cpu_count() or 1) - 1))
 
 
-def run_serve_large(fl, capacity_tokens_per_s, duration=30.0, n_lo=1 << 16, n_hi=1 << 22, pool_size=12,
+def run_serve_large(fl, capacity_tokens_per_s, duration=60.0, n_lo=1 << 15, n_hi=1 << 22, pool_size=12,
                     budget=150 << 30, seed=5):
     """Serving with large jobs: requests on graphs with |V| log-uniform in
-    [2^16, 2^22] (up to about 6 GB of device memory each), the round
+    [2^15, 2^22] (up to about 6 GB of device memory each), the round
     workload's parameters, d = 128 bf16, feedback mu = 0.65, arriving as a
     Poisson process at 0.7 x the measured capacity (capacity_tokens_per_s /
     mean tokens per job) for `duration` seconds."""

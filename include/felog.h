@@ -90,9 +90,9 @@ typedef enum {
  * phi_in increments summed in shared memory (window <= 15): a warp reads a
  * context row plus its own pending increments of that node, and a window
  * position's summed increment reaches memory when the position leaves the
- * window (other warps see it then); 0 = automatic: form 3 for float tables,
- * form 2 for bf16 tables (where dim <= 128 and negatives <= 7, window <= 15
- * for form 3), form 1 otherwise.
+ * window (other warps see it then; on power-law graphs hub rows collect many
+ * warps' delayed increments, which costs link AUC); 0 = automatic: form 2
+ * where dim <= 128 and negatives <= 7, form 1 otherwise.
  * TILE mode (dim in {32, 64, 128}): tile_negatives = shared negatives per
  * tile (128, 256, 384 or 512; 0 selects 512: each then stands for about 20
  * per-pair draws, fewer shared negatives let hub rows take oversized stale

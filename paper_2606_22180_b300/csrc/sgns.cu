@@ -370,14 +370,12 @@ static felog_status launch_train(const SgnsArgs &a, const felog_train_params *tp
     T *pout = static_cast<T *>(phi_out);
     if (!minibatch_mode(tp)) {
         // half-warp form for dim <= 128 and K + 1 <= 8, full-warp form otherwise;
-        // form 3 stages the window's phi_in increments (window <= 15), which the
-        // automatic choice takes for float tables (measured on R-MAT 20: 559 vs
-        // 613 ms per round) but not for bf16 ones (513 vs 475 ms: that kernel is
-        // bound by instruction issue, and staging adds more than it saves)
+        // form 3 stages the window's phi_in increments (window <= 15) when asked
+        // for: faster (R-MAT 20, float: 559 vs 613 ms per round), but hub rows
+        // then collect many warps' delayed increments and the link AUC of the
+        // 10-round run fell from 0.797 to 0.735, so it is not the default
         const bool half_warp = D <= 128 && MAXT == 8 && tp->hogwild_form != 1;
-        const bool stage = half_warp && (tp->hogwild_form == 3 ||
-                                         (tp->hogwild_form == 0 && std::is_same<T, float>::value &&
-                                          a.window <= kStageMaxWindow));
+        const bool stage = half_warp && tp->hogwild_form == 3;
         constexpr int DH = D <= 128 ? D : 128;
         const size_t smem = half_warp ? sizeof(int32_t) * kWarps * hw_words_per_warp(a.L, a.window, a.K, DH, stage)
                                       : sizeof(int32_t) * kWarps * (a.L + 2 * a.window * a.K);
