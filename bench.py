@@ -53,6 +53,8 @@ def _args():
     p.add_argument("--form", type=int, default=0, choices=[0, 1, 2, 3],
                    help="Hogwild kernel form: 0 automatic, 1 full warp per pair, 2 half warp per pair, "
                         "3 half warp with the window's phi_in increments staged in shared memory")
+    p.add_argument("--stage-flush", type=int, default=0,
+                   help="form 3: staged increments reach memory every this many centers (0: on leaving the window)")
     p.add_argument("--mode", default="round", choices=["round", "tile", "batch", "serve", "mu"],
                    help="round: one round of Algorithm 1 on R-MAT 20 (default); tile: rounds with the "
                         "shared-negatives tile trainer; batch: the 512-graph "
@@ -377,7 +379,8 @@ def run_native(args):
     n_live = int((g.degrees() > 0).sum())
     T = ROUNDS * WPR * n_live * L
     prec = fl.FELOG_FP32 if args.precision == "fp32" else fl.FELOG_BF16_SR
-    tp = fl.train_params(DIM, WINDOW, NEG, LR0, T, fl.FELOG_SGNS_HOGWILD, 4096, prec, 0, args.form)
+    tp = fl.train_params(DIM, WINDOW, NEG, LR0, T, fl.FELOG_SGNS_HOGWILD, 4096, prec, 0, args.form,
+                         stage_flush=args.stage_flush)
     fp_plain = fl.feedback_params(False, MU, KS, ROUNDS, False)
     runner = RoundRunner(fl, dg, tp, fp_plain, SEED + rank)
     runner.reset()
@@ -467,7 +470,7 @@ def run_native(args):
     }
 
     if not args.no_quality and rank == 0:
-        result["quality"] = _quality(fl, evaluate, dg, split, n_live)
+        result["quality"] = _quality(fl, evaluate, dg, split, n_live, args.form, args.stage_flush)
         q = result["quality"]
         result["chosen_vs_plain"] = {
             "auc_plain": q["plain"]["auc"], "auc_chosen": q["chosen"]["auc"],
@@ -848,16 +851,17 @@ def _tile_rounds(fl, dg, T, steps, warmup, scale, ctas):
     return out
 
 
-def _quality(fl, evaluate, dg, split, n_live):
-    """Full runs of Algorithm 1: plain (feedback off, fp32) and chosen
-    (feedback mu = 0.65, bf16 with stochastic rounding); AUC on the held-out
-    edges, wall time of the felog_embed call."""
+def _quality(fl, evaluate, dg, split, n_live, form=0, stage_flush=0):
+    """Full runs of Algorithm 1: plain (feedback off, fp32, the timed rounds'
+    Hogwild form) and chosen (feedback mu = 0.65, bf16 with stochastic
+    rounding); AUC on the held-out edges, wall time of the felog_embed call."""
     import torch
 
     out = {}
     T = ROUNDS * WPR * n_live * L
     forms = {
-        "plain": (fl.train_params(DIM, WINDOW, NEG, LR0, T, fl.FELOG_SGNS_HOGWILD, 4096, fl.FELOG_FP32),
+        "plain": (fl.train_params(DIM, WINDOW, NEG, LR0, T, fl.FELOG_SGNS_HOGWILD, 4096, fl.FELOG_FP32,
+                                  0, form, stage_flush=stage_flush),
                   fl.feedback_params(False, MU, KS, ROUNDS, False)),
         "chosen": (fl.train_params(DIM, WINDOW, NEG, LR0, T, fl.FELOG_SGNS_HOGWILD, 4096, fl.FELOG_BF16_SR),
                    fl.feedback_params(True, MU, KS, ROUNDS, False)),

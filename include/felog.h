@@ -113,6 +113,8 @@ typedef struct {
     int32_t hogwild_form;
     int32_t tile_negatives;
     int32_t tile_ctas;
+    int32_t stage_flush;  /* form 3: every stage_flush centers all staged increments
+                             reach memory (0: a position's when it leaves the window) */
 } felog_train_params;
 
 /* enabled = 0 is the plain method (every non-isolated node stays active);

@@ -37,6 +37,7 @@ struct SgnsArgs {
     uint64_t seed;
     uint32_t round;
     unsigned long long *loss_acc;
+    int32_t stage_flush;
 };
 
 // KFIX > 0: the number of negatives is a compile-time constant.
@@ -205,7 +206,7 @@ __global__ void __launch_bounds__(kSgnsThreads, 2)
         __syncwarp();
     }
     TrainView<T> v{phi_in, phi_out, a.thr, a.alias, static_cast<uint64_t>(a.n), *a.S, a.seed, a.round,
-                   a.lr0, a.inv_T, a.clock_base, a.window, a.K, a.L};
+                   a.lr0, a.inv_T, a.clock_base, a.window, a.K, a.L, a.stage_flush};
     long long loss_fx = 0;
     const int64_t warps = static_cast<int64_t>(gridDim.x) * kWarps;
     for (int64_t wi = static_cast<int64_t>(blockIdx.x) * kWarps + wib; wi < a.n_walks; wi += warps)
@@ -359,6 +360,7 @@ static bool params_ok(const felog_train_params *tp) {
     if (tp->hogwild_form < 0 || tp->hogwild_form > 3) return false;
     if (tp->hogwild_form >= 2 && (tp->dim > 128 || tp->negatives > 7)) return false;
     if (tp->hogwild_form == 3 && tp->window > kStageMaxWindow) return false;
+    if (tp->stage_flush < 0) return false;
     if (!(tp->lr0 >= 0.f) || tp->lr_total_tokens <= 0) return false;
     return true;
 }
@@ -497,6 +499,7 @@ extern "C" felog_status felog_train(const int32_t *walks, int64_t n_walks, int32
         a.seed = seed;
         a.round = static_cast<uint32_t>(round);
         a.loss_acc = w.loss_acc;
+        a.stage_flush = tp->stage_flush;
         st = tp->precision == FELOG_FP32 ? dispatch_dim<float>(a, tp, phi_in, phi_out, w, s)
                                          : dispatch_dim<__nv_bfloat16>(a, tp, phi_in, phi_out, w, s);
         if (st) return st;

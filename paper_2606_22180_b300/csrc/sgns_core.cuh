@@ -458,6 +458,7 @@ struct TrainView {
     float lr0, inv_T;
     int64_t clock_base;  // token clock at the start of this graph's round
     int W, K, L;
+    int stage_flush;     // STAGE: flush every staged increment every stage_flush centers (0: on leaving)
 };
 
 // Staged phi_in increments (STAGE): a warp keeps, for each of the 2W + 1
@@ -547,6 +548,10 @@ __device__ __forceinline__ long long hw_train_walk(const TrainView<T> &a, const 
             float *srow = delta + sq * D;
             float d[EPL];
             delta_load<EPL>(srow, hl, d);
+            bool nz = false;
+#pragma unroll
+            for (int e = 0; e < EPL; ++e) nz |= d[e] != 0.f;
+            if (!__any_sync(0x0000ffffu, nz)) return;  // nothing staged for this position
             const float zero[EPL] = {};
             delta_store<EPL>(srow, hl, zero);
             T *grow = phi_in + static_cast<int64_t>(y) * D;
@@ -570,11 +575,24 @@ __device__ __forceinline__ long long hw_train_walk(const TrainView<T> &a, const 
         if constexpr (STAGE) {
             // position p - W - 1 leaves the window (its slot is the one before sbase)
             if (p > 0) sbase = sbase + 1 == R ? 0 : sbase + 1;
-            const int q = p - W - 1;
-            if (q >= 0) {
-                srs = srs * 1664525u + 1013904223u;
-                flush(q, sbase == 0 ? R - 1 : sbase - 1, srs);
+            if (a.stage_flush > 0 && p > 0 && p % a.stage_flush == 0) {
+                // every position of the previous window, p - 1 - W .. p - 1 + W
+                int sq = sbase == 0 ? R - 1 : sbase - 1;
+                for (int q = p - 1 - W; q <= p - 1 + W; ++q) {
+                    if (q >= 0 && q < L) {
+                        srs = srs * 1664525u + 1013904223u;
+                        flush(q, sq, srs);
+                    }
+                    sq = sq + 1 == R ? 0 : sq + 1;
+                }
                 __syncwarp();
+            } else {
+                const int q = p - W - 1;
+                if (q >= 0) {
+                    srs = srs * 1664525u + 1013904223u;
+                    flush(q, sbase == 0 ? R - 1 : sbase - 1, srs);
+                    __syncwarp();
+                }
             }
         }
         const int32_t c = wk[p];

@@ -63,7 +63,7 @@ class _TrainParams(ctypes.Structure):
                 ("mode", ctypes.c_int32), ("minibatch", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("hogwild_rows_per_warp", ctypes.c_int32),
                 ("hogwild_form", ctypes.c_int32), ("tile_negatives", ctypes.c_int32),
-                ("tile_ctas", ctypes.c_int32)]
+                ("tile_ctas", ctypes.c_int32), ("stage_flush", ctypes.c_int32)]
 
 
 class _FeedbackParams(ctypes.Structure):
@@ -323,9 +323,9 @@ def felog_init_tables(n: int, dim: int, precision: int, seed: int, device="cuda"
 
 def train_params(dim=128, window=10, negatives=5, lr0=0.025, lr_total_tokens=1, mode=FELOG_SGNS_HOGWILD,
                  minibatch=4096, precision=FELOG_FP32, hogwild_rows_per_warp=0,
-                 hogwild_form=0, tile_negatives=0, tile_ctas=0) -> _TrainParams:
+                 hogwild_form=0, tile_negatives=0, tile_ctas=0, stage_flush=0) -> _TrainParams:
     return _TrainParams(dim, window, negatives, lr0, lr_total_tokens, mode, minibatch, precision,
-                        hogwild_rows_per_warp, hogwild_form, tile_negatives, tile_ctas)
+                        hogwild_rows_per_warp, hogwild_form, tile_negatives, tile_ctas, stage_flush)
 
 
 def feedback_params(enabled=True, mu=0.65, ks=8, max_rounds=10, reactivate=False) -> _FeedbackParams:
