@@ -436,6 +436,8 @@ typedef struct {
     int32_t sgns_blocks_per_sm;     /* resident trainer blocks per SM */
     int32_t feedback_blocks_per_sm; /* Psi blocks per SM */
     int32_t from_cache;             /* 1 when read from the cache file */
+    int32_t sgns_form;              /* trainer shape: 2 = two pairs per warp, 16 lanes per row;
+                                       1 = one pair per warp, 32 lanes per row */
 } felog_tuning;
 
 typedef struct felog_batch felog_batch;
@@ -461,9 +463,12 @@ felog_status felog_batch_run(felog_batch *b, int32_t use_graph, void *stream);
 felog_status felog_batch_read(felog_batch *b, felog_job_stats *stats, int32_t *rec_n_active,
                               double *rec_loss, void *stream);
 felog_status felog_batch_job_buffers(const felog_batch *b, int32_t job, felog_job_buffers *out);
-/* times walk block size, trainer blocks per SM and Psi blocks per SM on
- * round 0 and keeps the fastest; cache_path (may be NULL) is a text file of
- * earlier results keyed by GPU name and batch shape.  Leaves the batch reset. */
+/* times the walk kernel's block size, the trainer's shape (pairs per warp and
+ * lanes per row: felog_tuning.sgns_form) with its resident blocks per SM
+ * (HOGWILD mode), and Psi blocks per SM, each on round 0, and keeps the
+ * fastest; shapes that would change the estimator (the staged form) are not
+ * tried.  cache_path (may be NULL) is a text file of earlier results keyed
+ * by GPU name and batch shape.  Leaves the batch reset. */
 felog_status felog_batch_autotune(felog_batch *b, const char *cache_path, felog_tuning *out, void *stream);
 
 /* ------------------------------------------------------------------------

@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <cstring>
 #include <fstream>
+#include <sstream>
 #include <new>
 #include <string>
 #include <vector>
@@ -375,7 +376,9 @@ __global__ void k_b_noise_finish(BArgs a) {
 // ---------------------------------------------------------------------------
 // SGNS over training items of the jobs whose dim is D
 // ---------------------------------------------------------------------------
-template <int D, class T, int KFIX>
+// FORM 2: two pairs per warp (a half warp each, 16 lanes per row); FORM 1:
+// one pair per warp (32 lanes per row).  Same estimator, different shapes.
+template <int D, class T, int KFIX, int FORM>
 __global__ void __launch_bounds__(kSgnsThreads, 2) k_b_sgns(BArgs a, int64_t item_lo, int64_t item_hi) {
     extern __shared__ int32_t smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -394,8 +397,10 @@ __global__ void __launch_bounds__(kSgnsThreads, 2) k_b_sgns(BArgs a, int64_t ite
                        static_cast<uint64_t>(jb.n), st.S, jb.seed, static_cast<uint32_t>(st.round), a.lr0,
                        st.inv_T, st.clock, a.window, a.K, a.L};
         long long loss_fx = 0;
-        for (int64_t wl = it - a.item_prefix[j]; wl < walks; wl += c_j)
-            loss_fx += hw_train_walk<D, T, KFIX>(v, jb.walks + wl * a.L, wl, wk, negs);
+        for (int64_t wl = it - a.item_prefix[j]; wl < walks; wl += c_j) {
+            if constexpr (FORM == 1) loss_fx += fw_train_walk<D, T, 8, KFIX>(v, jb.walks + wl * a.L, wl, wk, negs);
+            else loss_fx += hw_train_walk<D, T, KFIX>(v, jb.walks + wl * a.L, wl, wk, negs);
+        }
         for (int o = 16; o; o >>= 1) loss_fx += __shfl_xor_sync(kFull, loss_fx, o);
         if (lane == 0 && loss_fx != 0)
             atomicAdd(&jb.st->loss_acc, static_cast<unsigned long long>(loss_fx));
@@ -705,7 +710,8 @@ void launch_b_sgns(const BatchPlan &plan, const BParams &p, const HostTuning &t,
                    cudaStream_t s) {
     if (hi <= lo) return;
     const size_t smem = sizeof(int32_t) * kWarps * (p.window * 2 * p.K + p.L);
-    auto kern = p.K == 5 ? k_b_sgns<D, T, 5> : k_b_sgns<D, T, 0>;
+    auto kern = t.sgns_form == 1 ? (p.K == 5 ? k_b_sgns<D, T, 5, 1> : k_b_sgns<D, T, 0, 1>)
+                                 : (p.K == 5 ? k_b_sgns<D, T, 5, 2> : k_b_sgns<D, T, 0, 2>);
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     const int64_t want = (hi - lo + kWarps - 1) / kWarps;
@@ -1108,17 +1114,19 @@ extern "C" felog_status felog_batch_autotune(felog_batch *b, const char *cache_p
                             std::to_string(b->p.K) + "|p=" + std::to_string(b->p.precision);
     if (cache_path) {
         std::ifstream in(cache_path);
-        std::string k;
-        int wb, sb, fb;
-        while (in >> k >> wb >> sb >> fb) {
-            if (k == key) {
-                b->tune.walk_block = wb;
-                b->tune.sgns_blocks_per_sm = sb;
-                b->tune.feedback_blocks_per_sm = fb;
-                drop_graph(b);
-                if (out) *out = felog_tuning{wb, sb, fb, 1};
-                return FELOG_OK;
-            }
+        std::string line;
+        while (std::getline(in, line)) {
+            std::istringstream ls(line);
+            std::string k;
+            int wb, sb, fb, form;
+            if (!(ls >> k >> wb >> sb >> fb >> form) || k != key) continue;
+            b->tune.walk_block = wb;
+            b->tune.sgns_blocks_per_sm = sb;
+            b->tune.feedback_blocks_per_sm = fb;
+            b->tune.sgns_form = form;
+            drop_graph(b);
+            if (out) *out = felog_tuning{wb, sb, fb, 1, form};
+            return FELOG_OK;
         }
     }
     cudaEvent_t e0, e1;
@@ -1144,12 +1152,23 @@ extern "C" felog_status felog_batch_autotune(felog_batch *b, const char *cache_p
     }
     b->tune.walk_block = best.walk_block;
     best_ms = 1e30f;
-    for (int sb : {1, 2}) {
-        b->tune.sgns_blocks_per_sm = sb;
-        const float ms = time_phase(1 | 2 | 4, 8);
-        if (ms < best_ms) { best_ms = ms; best.sgns_blocks_per_sm = sb; }
+    if (b->p.mode == FELOG_SGNS_HOGWILD) {
+        // trainer shape: pairs per warp and lanes per row (form), resident blocks per SM
+        for (int form : {2, 1}) {
+            for (int sb : {1, 2}) {
+                b->tune.sgns_form = form;
+                b->tune.sgns_blocks_per_sm = sb;
+                const float ms = time_phase(1 | 2 | 4, 8);
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best.sgns_blocks_per_sm = sb;
+                    best.sgns_form = form;
+                }
+            }
+        }
     }
     b->tune.sgns_blocks_per_sm = best.sgns_blocks_per_sm;
+    b->tune.sgns_form = best.sgns_form;
     best_ms = 1e30f;
     for (int fb : {4, 8, 16}) {
         b->tune.feedback_blocks_per_sm = fb;
@@ -1166,8 +1185,9 @@ extern "C" felog_status felog_batch_autotune(felog_batch *b, const char *cache_p
     if (cache_path) {
         std::ofstream o(cache_path, std::ios::app);
         o << key << " " << best.walk_block << " " << best.sgns_blocks_per_sm << " " << best.feedback_blocks_per_sm
-          << "\n";
+          << " " << best.sgns_form << "\n";
     }
-    if (out) *out = felog_tuning{best.walk_block, best.sgns_blocks_per_sm, best.feedback_blocks_per_sm, 0};
+    if (out)
+        *out = felog_tuning{best.walk_block, best.sgns_blocks_per_sm, best.feedback_blocks_per_sm, 0, best.sgns_form};
     return FELOG_OK;
 }

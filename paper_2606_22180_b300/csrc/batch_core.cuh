@@ -80,6 +80,7 @@ struct HostTuning {
     int walk_block = 256;
     int sgns_blocks_per_sm = 2;
     int feedback_blocks_per_sm = 16;
+    int sgns_form = 2;  // 2: two pairs per warp (16 lanes per row); 1: one pair per warp (32 lanes)
 };
 
 // a membership of jobs on the device: job table, index-space prefixes, tiles

@@ -44,138 +44,17 @@ struct SgnsArgs {
 template <int D, class T, int MAXT, int KFIX>
 __global__ void __launch_bounds__(kSgnsThreads, 3)
     k_sgns_hogwild(SgnsArgs a, T *__restrict__ phi_in, T *__restrict__ phi_out) {
-    constexpr int EPL = D / 32;
-    constexpr int SRC_SHIFT = 5 - (MAXT == 8 ? 3 : 4);
-    constexpr bool kBf16 = !std::is_same<T, float>::value;
     extern __shared__ int32_t smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int W = a.window, L = a.L;
     const int K = KFIX > 0 ? KFIX : a.K;
-    const int per_warp = L + 2 * W * K;
-    int32_t *wk = smem + wib * per_warp;
-    int32_t *negs = wk + L;
-    const uint64_t S = *a.S;
-    const uint64_t n = static_cast<uint64_t>(a.n);
-    const int my_t = target_of_lane<MAXT>(lane);
-    const bool loss_lane = (lane & ((32 / MAXT) - 1)) == 0;
-    long long loss_fx = 0;  // this lane's loss terms, 2^-24 units
+    int32_t *wk = smem + wib * (a.L + 2 * a.window * K);
+    int32_t *negs = wk + a.L;
+    TrainView<T> v{phi_in, phi_out, a.thr, a.alias, static_cast<uint64_t>(a.n), *a.S, a.seed, a.round,
+                   a.lr0, a.inv_T, a.clock_base, a.window, a.K, a.L, 0};
+    long long loss_fx = 0;
     const int64_t warps = static_cast<int64_t>(gridDim.x) * kWarps;
-    for (int64_t wi = static_cast<int64_t>(blockIdx.x) * kWarps + wib; wi < a.n_walks; wi += warps) {
-        const int32_t *row = a.walks + wi * L;
-        for (int p = lane; p < L; p += 32) wk[p] = walk_id(row[p], n);
-        __syncwarp();
-        for (int p = 0; p < L; ++p) {
-            const int32_t c = wk[p];
-            if (c < 0) continue;
-            // all negatives of this center, lane-parallel
-            for (int idx = lane; idx < 2 * W * K; idx += 32) {
-                const int q = idx / K, k = idx - q * K;
-                negs[idx] = draw_negative(a.thr, a.alias, n, S, a.seed, a.round,
-                                          static_cast<uint32_t>(wi), static_cast<uint32_t>(p),
-                                          static_cast<uint32_t>(q), static_cast<uint32_t>(k));
-            }
-            __syncwarp();
-            const float tclock = static_cast<float>(a.clock_base + wi * L + p);
-            const float eta = a.lr0 * fmaxf(1e-4f, 1.0f - tclock * a.inv_T);
-            float oc[EPL], oc0[EPL], doc[EPL];
-            float closs = 0.f;
-            // stochastic-rounding stream of this lane for this center (bf16 only)
-            uint32_t srs = 0;
-            if constexpr (kBf16)
-                srs = philox(a.seed, static_cast<uint32_t>(lane), static_cast<uint32_t>(wi),
-                             (a.round << 16) | static_cast<uint32_t>(p), kStreamSR).x | 1u;
-            T *oc_ptr = phi_out + static_cast<int64_t>(c) * D + lane * EPL;
-            load_row_cg<EPL>(oc_ptr, oc);
-#pragma unroll
-            for (int e = 0; e < EPL; ++e) {
-                oc0[e] = oc[e];
-                doc[e] = 0.f;
-            }
-            for (int o = -W; o <= W; ++o) {
-                if (o == 0) continue;
-                const int pp = p + o;
-                if (pp < 0 || pp >= L) continue;
-                const int32_t x = wk[pp];
-                if (x < 0) continue;
-                const int q = o < 0 ? o + W : o + W - 1;
-                int32_t nid[MAXT];
-                nid[0] = c;
-#pragma unroll
-                for (int t = 1; t < MAXT; ++t) {
-                    int32_t v = -1;
-                    if (t <= K) {
-                        v = negs[q * K + t - 1];
-                        if (v == c) v = -1;  // a negative equal to the center is skipped
-                    }
-                    nid[t] = v;
-                }
-                float ix[EPL];
-                T *ix_ptr = phi_in + static_cast<int64_t>(x) * D + lane * EPL;
-                load_row_cg<EPL>(ix_ptr, ix);
-                float nr[MAXT][EPL];
-#pragma unroll
-                for (int t = 1; t < MAXT; ++t) {
-                    if (nid[t] >= 0) {
-                        load_row_cg<EPL>(phi_out + static_cast<int64_t>(nid[t]) * D + lane * EPL, nr[t]);
-                    } else {
-#pragma unroll
-                        for (int e = 0; e < EPL; ++e) nr[t][e] = 0.f;
-                    }
-                }
-#pragma unroll
-                for (int e = 0; e < EPL; ++e) nr[0][e] = oc[e];
-                float pd[MAXT];
-#pragma unroll
-                for (int t = 0; t < MAXT; ++t) {
-                    float s = 0.f;
-#pragma unroll
-                    for (int e = 0; e < EPL; ++e) s = fmaf(ix[e], nr[t][e], s);
-                    pd[t] = s;
-                }
-                const float dot = reduce_scatter<MAXT>(pd, lane);
-                int32_t my_id = nid[0];
-#pragma unroll
-                for (int t = 1; t < MAXT; ++t)
-                    if (t == my_t) my_id = nid[t];
-                float g = 0.f;
-                if (my_id >= 0) {
-                    const bool pos = my_t == 0;
-                    const float sig = __frcp_rn(1.f + __expf(-dot));
-                    g = eta * ((pos ? 1.f : 0.f) - sig);
-                    // -log sigma(s) for the center, -log sigma(-s) = -log(1 - sigma(s)) for a negative
-                    if (loss_lane) closs -= __logf(fmaxf(pos ? sig : 1.f - sig, 1e-30f));
-                }
-                float gt[MAXT];
-#pragma unroll
-                for (int t = 0; t < MAXT; ++t) gt[t] = __shfl_sync(kFull, g, t << SRC_SHIFT);
-                float din[EPL];
-#pragma unroll
-                for (int e = 0; e < EPL; ++e) din[e] = gt[0] * oc[e];
-#pragma unroll
-                for (int t = 1; t < MAXT; ++t) {
-                    if (nid[t] < 0) continue;
-                    float dn[EPL];
-#pragma unroll
-                    for (int e = 0; e < EPL; ++e) {
-                        din[e] = fmaf(gt[t], nr[t][e], din[e]);
-                        dn[e] = gt[t] * ix[e];
-                    }
-                    add_delta<EPL>(phi_out + static_cast<int64_t>(nid[t]) * D + lane * EPL, nr[t], dn,
-                                   kBf16 ? xorshift32(srs) : 0u);
-                }
-#pragma unroll
-                for (int e = 0; e < EPL; ++e) {
-                    const float u = gt[0] * ix[e];
-                    oc[e] += u;
-                    doc[e] += u;
-                }
-                add_delta<EPL>(ix_ptr, ix, din, kBf16 ? xorshift32(srs) : 0u);
-            }
-            add_delta<EPL>(oc_ptr, oc0, doc, kBf16 ? xorshift32(srs) : 0u);
-            loss_fx += __float2ll_rn(closs * kLossScaleF);
-            __syncwarp();
-        }
-    }
+    for (int64_t wi = static_cast<int64_t>(blockIdx.x) * kWarps + wib; wi < a.n_walks; wi += warps)
+        loss_fx += fw_train_walk<D, T, MAXT, KFIX>(v, a.walks + wi * a.L, wi, wk, negs);
     // warp total of the loss, then one integer add per warp
     for (int o = 16; o; o >>= 1) loss_fx += __shfl_xor_sync(kFull, loss_fx, o);
     if (lane == 0 && loss_fx != 0) atomicAdd(a.loss_acc, static_cast<unsigned long long>(loss_fx));

@@ -461,6 +461,145 @@ struct TrainView {
     int stage_flush;     // STAGE: flush every staged increment every stage_flush centers (0: on leaving)
 };
 
+// The full-warp Hogwild trainer of one walk (any dim, K + 1 <= MAXT): one
+// pair at a time, lane l owns elements [l * EPL, (l + 1) * EPL) of a row
+// (EPL = dim / 32), the K + 1 dots are reduced by a transposed reduce-scatter
+// (lane t << (5 - log2 MAXT) ends with the dot of target t), one sigmoid per
+// lane, coefficients broadcast; updates as atomic deltas (see add_delta).
+// wk (L ints) and negs (2 W K ints) are this warp's shared memory.  Returns
+// this lane's loss in 2^-24 units.
+template <int D, class T, int MAXT, int KFIX>
+__device__ __forceinline__ long long fw_train_walk(const TrainView<T> &a, const int32_t *__restrict__ row,
+                                                   int64_t wi, int32_t *wk, int32_t *negs) {
+    constexpr int EPL = D / 32;
+    constexpr int SRC_SHIFT = 5 - (MAXT == 8 ? 3 : 4);
+    constexpr bool kBf16 = !std::is_same<T, float>::value;
+    const int lane = threadIdx.x & 31;
+    const int W = a.W, L = a.L;
+    const int K = KFIX > 0 ? KFIX : a.K;
+    const uint64_t S = a.S, n = a.n;
+    T *const phi_in = a.phi_in;
+    T *const phi_out = a.phi_out;
+    const int my_t = target_of_lane<MAXT>(lane);
+    const bool loss_lane = (lane & ((32 / MAXT) - 1)) == 0;
+    long long loss_fx = 0;  // this lane's loss terms, 2^-24 units
+    for (int p = lane; p < L; p += 32) wk[p] = walk_id(row[p], n);
+    __syncwarp();
+    for (int p = 0; p < L; ++p) {
+        const int32_t c = wk[p];
+        if (c < 0) continue;
+        // all negatives of this center, lane-parallel
+        for (int idx = lane; idx < 2 * W * K; idx += 32) {
+            const int q = idx / K, k = idx - q * K;
+            negs[idx] = draw_negative(a.thr, a.alias, n, S, a.seed, a.round,
+                                      static_cast<uint32_t>(wi), static_cast<uint32_t>(p),
+                                      static_cast<uint32_t>(q), static_cast<uint32_t>(k));
+        }
+        __syncwarp();
+        const float tclock = static_cast<float>(a.clock_base + wi * L + p);
+        const float eta = a.lr0 * fmaxf(1e-4f, 1.0f - tclock * a.inv_T);
+        float oc[EPL], oc0[EPL], doc[EPL];
+        float closs = 0.f;
+        // stochastic-rounding stream of this lane for this center (bf16 only)
+        uint32_t srs = 0;
+        if constexpr (kBf16)
+            srs = philox(a.seed, static_cast<uint32_t>(lane), static_cast<uint32_t>(wi),
+                         (a.round << 16) | static_cast<uint32_t>(p), kStreamSR).x | 1u;
+        T *oc_ptr = phi_out + static_cast<int64_t>(c) * D + lane * EPL;
+        load_row_cg<EPL>(oc_ptr, oc);
+#pragma unroll
+        for (int e = 0; e < EPL; ++e) {
+            oc0[e] = oc[e];
+            doc[e] = 0.f;
+        }
+        for (int o = -W; o <= W; ++o) {
+            if (o == 0) continue;
+            const int pp = p + o;
+            if (pp < 0 || pp >= L) continue;
+            const int32_t x = wk[pp];
+            if (x < 0) continue;
+            const int q = o < 0 ? o + W : o + W - 1;
+            int32_t nid[MAXT];
+            nid[0] = c;
+#pragma unroll
+            for (int t = 1; t < MAXT; ++t) {
+                int32_t v = -1;
+                if (t <= K) {
+                    v = negs[q * K + t - 1];
+                    if (v == c) v = -1;  // a negative equal to the center is skipped
+                }
+                nid[t] = v;
+            }
+            float ix[EPL];
+            T *ix_ptr = phi_in + static_cast<int64_t>(x) * D + lane * EPL;
+            load_row_cg<EPL>(ix_ptr, ix);
+            float nr[MAXT][EPL];
+#pragma unroll
+            for (int t = 1; t < MAXT; ++t) {
+                if (nid[t] >= 0) {
+                    load_row_cg<EPL>(phi_out + static_cast<int64_t>(nid[t]) * D + lane * EPL, nr[t]);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < EPL; ++e) nr[t][e] = 0.f;
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < EPL; ++e) nr[0][e] = oc[e];
+            float pd[MAXT];
+#pragma unroll
+            for (int t = 0; t < MAXT; ++t) {
+                float s = 0.f;
+#pragma unroll
+                for (int e = 0; e < EPL; ++e) s = fmaf(ix[e], nr[t][e], s);
+                pd[t] = s;
+            }
+            const float dot = reduce_scatter<MAXT>(pd, lane);
+            int32_t my_id = nid[0];
+#pragma unroll
+            for (int t = 1; t < MAXT; ++t)
+                if (t == my_t) my_id = nid[t];
+            float g = 0.f;
+            if (my_id >= 0) {
+                const bool pos = my_t == 0;
+                const float sig = __frcp_rn(1.f + __expf(-dot));
+                g = eta * ((pos ? 1.f : 0.f) - sig);
+                // -log sigma(s) for the center, -log sigma(-s) = -log(1 - sigma(s)) for a negative
+                if (loss_lane) closs -= __logf(fmaxf(pos ? sig : 1.f - sig, 1e-30f));
+            }
+            float gt[MAXT];
+#pragma unroll
+            for (int t = 0; t < MAXT; ++t) gt[t] = __shfl_sync(kFull, g, t << SRC_SHIFT);
+            float din[EPL];
+#pragma unroll
+            for (int e = 0; e < EPL; ++e) din[e] = gt[0] * oc[e];
+#pragma unroll
+            for (int t = 1; t < MAXT; ++t) {
+                if (nid[t] < 0) continue;
+                float dn[EPL];
+#pragma unroll
+                for (int e = 0; e < EPL; ++e) {
+                    din[e] = fmaf(gt[t], nr[t][e], din[e]);
+                    dn[e] = gt[t] * ix[e];
+                }
+                add_delta<EPL>(phi_out + static_cast<int64_t>(nid[t]) * D + lane * EPL, nr[t], dn,
+                               kBf16 ? xorshift32(srs) : 0u);
+            }
+#pragma unroll
+            for (int e = 0; e < EPL; ++e) {
+                const float u = gt[0] * ix[e];
+                oc[e] += u;
+                doc[e] += u;
+            }
+            add_delta<EPL>(ix_ptr, ix, din, kBf16 ? xorshift32(srs) : 0u);
+        }
+        add_delta<EPL>(oc_ptr, oc0, doc, kBf16 ? xorshift32(srs) : 0u);
+        loss_fx += __float2ll_rn(closs * kLossScaleF);
+        __syncwarp();
+    }
+
+    return loss_fx;
+}
+
 // Staged phi_in increments (STAGE): a warp keeps, for each of the 2W + 1
 // positions of its current window, the summed increment of that position's
 // phi_in row in shared memory (fp32, `delta`: (2W + 1) rows of D floats, slot

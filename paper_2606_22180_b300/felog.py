@@ -521,7 +521,8 @@ class _JobBuffers(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("walk_block", ctypes.c_int32), ("sgns_blocks_per_sm", ctypes.c_int32),
-                ("feedback_blocks_per_sm", ctypes.c_int32), ("from_cache", ctypes.c_int32)]
+                ("feedback_blocks_per_sm", ctypes.c_int32), ("from_cache", ctypes.c_int32),
+                ("sgns_form", ctypes.c_int32)]
 
 
 class Batch:
