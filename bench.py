@@ -309,6 +309,33 @@ def _e2e_job(fl, g, tp, fp, seed, world, barrier):
                     "phi_in out to pinned host memory", "ms": ms, "tokens": tokens}
 
 
+def _ripp(fl, evaluate, dg, split, n_live):
+    """The round-interleaved pipeline (Section 5.3) on the round workload with
+    the chosen form's feedback (mu = 0.65, bf16-SR): felog_embed_pipelined with
+    feedback_lag 0 (Algorithm 1 as printed: the streams alternate) and 1 (Psi on
+    the snapshot as training starts: sampling runs under training); wall time,
+    stream busy times and overlap from CUDA events, link AUC."""
+    import torch
+
+    T = ROUNDS * WPR * n_live * L
+    tp = fl.train_params(DIM, WINDOW, NEG, LR0, T, fl.FELOG_SGNS_HOGWILD, 4096, fl.FELOG_BF16_SR)
+    fp = fl.feedback_params(True, MU, KS, ROUNDS, False)
+    out = {"workload": _workload_name(SCALE, "bf16-SR") + f", feedback mu={MU}"}
+    for lag in (0, 1):
+        torch.cuda.synchronize()
+        pi, _, st, ps = fl.felog_embed_pipelined(dg, L, WPR, tp, fp, SEED, feedback_lag=lag)
+        torch.cuda.synchronize()
+        tokens = sum(x["tokens"] for x in st)
+        out[f"lag{lag}"] = {"wall_ms": ps["wall_ms"], "train_busy_ms": ps["train_busy_ms"],
+                            "sample_busy_ms": ps["sample_busy_ms"], "overlap_ms": ps["overlap_ms"],
+                            "train_stream_busy_frac": ps["train_busy_ms"] / ps["wall_ms"],
+                            "rounds": ps["rounds"], "tokens": tokens, "tokens_per_s": tokens / (ps["wall_ms"] / 1e3),
+                            "active_per_round": [x["n_active"] for x in st],
+                            "auc": evaluate.link_auc(pi, split.pos, split.neg)}
+        del pi
+    return out
+
+
 def _bf16_rounds(fl, dg, T, args):
     """The precision form's rounds on the round workload's graph (bf16 tables,
     stochastic rounding), timed like the plain rounds."""
@@ -498,6 +525,9 @@ def run_native(args):
         cap = result["bf16_round"]["tokens_per_s"]
         result["serving"] = run_serve(fl, rate=20.0, duration=20.0, max_nodes=1 << 16, sustainable=True)
         result["serving_large"] = run_serve_large(fl, capacity_tokens_per_s=cap)
+        dg = fl.DeviceGraph.from_host(g)
+        result["ripp"] = _ripp(fl, evaluate, dg, split, n_live)
+        del dg
     if not args.no_cpu and rank == 0:
         result["cpu_baseline"] = _cpu_baseline(split, n_live)
         result["vs_cpu_baseline"] = value / result["cpu_baseline"]["value"]
