@@ -965,6 +965,274 @@ __device__ __forceinline__ long long hw_train_walk(const TrainView<T> &a, const 
 }
 
 // ----------------------------------------------------------------------------
+// HOGWILD, half-warp form with the next step's rows prefetched (form 4): the
+// context row and the K negative rows of step j + 1 are copied to shared
+// memory with cp.async (16-byte chunks, bypassing L1; invalid rows zero-filled)
+// while step j computes, so the L2 latency of a step's rows overlaps the
+// previous step's dots, sigmoid and reductions.  Rows live in a per-warp
+// double buffer: [2 stages][2 halves][K + 1 rows][D values of T]; lane l of a
+// half copies and later reads the same 16-byte chunks of each row (chunks l
+// and l + 16 for a 512-byte row, chunk l for a 256-byte row), so a lane
+// needs only its own copies to complete.  The arithmetic is form 2's; a
+// step's rows are read one step earlier than form 2 reads them (before the
+// previous step's updates of the same rows, if any, reach memory).  Chunks of
+// 16 bytes per lane: float rows of dim 64 or 128, bf16 rows of dim 128.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16_zfill(uint32_t dst, const void *src, bool valid) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_none() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+template <int D, class T>
+constexpr bool kPfSupported = (std::is_same<T, float>::value && (D == 64 || D == 128)) ||
+                              (!std::is_same<T, float>::value && D == 128);
+
+template <int D, class T, int KFIX>
+__device__ __forceinline__ long long hw_train_walk_pf(const TrainView<T> &a, const int32_t *__restrict__ row,
+                                                      int64_t wi, int32_t *wk, int32_t *negs, char *rowbuf) {
+    constexpr int EPL = D / 16;
+    constexpr int MAXT = 8;
+    constexpr bool kBf16 = !std::is_same<T, float>::value;
+    constexpr int ROWB = D * static_cast<int>(sizeof(T));  // bytes of a row
+    constexpr int CHUNKS = ROWB / 256;                     // 16-byte chunks per lane: 2 (512 B) or 1 (256 B)
+    static_assert(kPfSupported<D, T>, "16-byte chunks per lane");
+    const int lane = threadIdx.x & 31;
+    const int h = lane >> 4, hl = lane & 15;
+    const int W = a.W, L = a.L;
+    const int K = KFIX > 0 ? KFIX : a.K;
+    const uint64_t S = a.S, n = a.n;
+    T *const phi_in = a.phi_in;
+    T *const phi_out = a.phi_out;
+    const int my_t = hl >> 1;
+    const bool loss_lane = (hl & 1) == 0;
+    long long loss_fx = 0;
+    const uint32_t buf0 = static_cast<uint32_t>(__cvta_generic_to_shared(rowbuf));
+    // shared-memory address of row t of half h in stage s
+    auto slot = [&](int s, int t) -> uint32_t {
+        return buf0 + static_cast<uint32_t>(((s * 2 + h) * (K + 1) + t) * ROWB);
+    };
+    auto slot_ptr = [&](int s, int t) -> const char * {
+        return rowbuf + ((s * 2 + h) * (K + 1) + t) * ROWB;
+    };
+
+    for (int p = lane; p < L; p += 32) wk[p] = walk_id(row[p], n);
+    __syncwarp();
+    for (int p = 0; p < L; ++p) {
+        uint32_t srs = 0;
+        if constexpr (kBf16)
+            srs = philox(a.seed, static_cast<uint32_t>(lane), static_cast<uint32_t>(wi),
+                         (a.round << 16) | static_cast<uint32_t>(p), kStreamSR).x | 1u;
+        const int32_t c = wk[p];
+        if (c < 0) continue;
+        for (int idx = lane; idx < 2 * W * K; idx += 32) {
+            const int q = idx / K, k = idx - q * K;
+            negs[idx] = draw_negative(a.thr, a.alias, n, S, a.seed, a.round,
+                                      static_cast<uint32_t>(wi), static_cast<uint32_t>(p),
+                                      static_cast<uint32_t>(q), static_cast<uint32_t>(k));
+        }
+        __syncwarp();
+        const float tclock = static_cast<float>(a.clock_base + wi * L + p);
+        const float eta = a.lr0 * fmaxf(1e-4f, 1.0f - tclock * a.inv_T);
+        T *oc_row = phi_out + static_cast<int64_t>(c) * D;
+        float oc[EPL], doc[EPL];
+        uint32_t oc_raw[kBf16 ? EPL / 2 : 1];
+        if constexpr (kBf16) {
+            load_raw<EPL>(oc_row + hl * EPL, oc_raw);
+            unpack_bf16<EPL>(oc_raw, oc);
+        } else {
+            hw_load<EPL>(reinterpret_cast<const float *>(oc_row), hl, oc);
+        }
+#pragma unroll
+        for (int e = 0; e < EPL; ++e) doc[e] = 0.f;
+        float closs = 0.f;
+        const int lo = max(-W, -p), hi = min(W, L - 1 - p);
+        const int npairs = hi - lo;
+        const int steps = (npairs + 1) >> 1;
+        // the pair of this half in step j: offset o, context x, negatives nid[1..K]
+        auto pair_of = [&](int j, int &o, int32_t &x, int32_t (&nid)[MAXT]) -> bool {
+            const int jj = 2 * j + h;
+            o = lo + jj;
+            if (o >= 0) ++o;
+            bool valid = jj < npairs;
+            x = valid ? wk[p + o] : -1;
+            valid = valid && x >= 0;
+            const int q = o < 0 ? o + W : o + W - 1;
+            nid[0] = valid ? c : -1;
+#pragma unroll
+            for (int t = 1; t < MAXT; ++t) {
+                int32_t v = -1;
+                if (t <= K && valid) {
+                    v = negs[q * K + t - 1];
+                    if (v == c) v = -1;
+                }
+                nid[t] = v;
+            }
+            return valid;
+        };
+        // copies of step j's rows (context, then negatives) into stage j & 1
+        auto issue = [&](int j) {
+            int o;
+            int32_t x, nid[MAXT];
+            const bool valid = pair_of(j, o, x, nid);
+            const int s = j & 1;
+            const char *ix_src = reinterpret_cast<const char *>(phi_in + static_cast<int64_t>(valid ? x : 0) * D);
+#pragma unroll
+            for (int ch = 0; ch < CHUNKS; ++ch)
+                cp_async16_zfill(slot(s, 0) + (ch * 16 + hl) * 16, ix_src + (ch * 16 + hl) * 16, valid);
+#pragma unroll
+            for (int t = 1; t < MAXT; ++t) {
+                if (t > K) break;
+                const bool ok = nid[t] >= 0;
+                const char *src = reinterpret_cast<const char *>(phi_out + static_cast<int64_t>(ok ? nid[t] : 0) * D);
+#pragma unroll
+                for (int ch = 0; ch < CHUNKS; ++ch)
+                    cp_async16_zfill(slot(s, t) + (ch * 16 + hl) * 16, src + (ch * 16 + hl) * 16, ok);
+            }
+            cp_async_commit_group();
+        };
+        // this lane's values of row t of stage s (the chunks it copied), as floats and raw bf16 words
+        auto read_row = [&](int s, int t, float (&v)[EPL], uint32_t (&raw)[kBf16 ? EPL / 2 : 1]) {
+            const char *base = slot_ptr(s, t);
+            if constexpr (kBf16) {
+                const uint4 w = *reinterpret_cast<const uint4 *>(base + hl * 16);
+                raw[0] = w.x; raw[1] = w.y; raw[2] = w.z; raw[3] = w.w;
+                unpack_bf16<EPL>(raw, v);
+            } else if constexpr (EPL == 8) {
+                const float4 u = *reinterpret_cast<const float4 *>(base + hl * 16);
+                const float4 w = *reinterpret_cast<const float4 *>(base + 256 + hl * 16);
+                v[0] = u.x; v[1] = u.y; v[2] = u.z; v[3] = u.w;
+                v[4] = w.x; v[5] = w.y; v[6] = w.z; v[7] = w.w;
+            } else {
+                const float4 u = *reinterpret_cast<const float4 *>(base + hl * 16);
+                v[0] = u.x; v[1] = u.y; v[2] = u.z; v[3] = u.w;
+            }
+        };
+
+        if (steps > 0) issue(0);
+        for (int j = 0; j < steps; ++j) {
+            if (j + 1 < steps) issue(j + 1);
+            else cp_async_commit_group();  // an empty group: wait_group 1 below then means step j
+            cp_async_wait_prev();
+            const int s = j & 1;
+            int o;
+            int32_t x, nid[MAXT];
+            const bool valid = pair_of(j, o, x, nid);
+            float ix[EPL];
+            uint32_t ix_raw[kBf16 ? EPL / 2 : 1];
+            read_row(s, 0, ix, ix_raw);
+            float pd[MAXT];
+#pragma unroll
+            for (int t = 0; t < MAXT; ++t) {
+                float r[EPL];
+                uint32_t rr[kBf16 ? EPL / 2 : 1];
+                if (t == 0) {
+#pragma unroll
+                    for (int e = 0; e < EPL; ++e) r[e] = oc[e];
+                } else if (t <= K) {
+                    read_row(s, t, r, rr);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < EPL; ++e) r[e] = 0.f;
+                }
+                float2 s2 = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int e = 0; e < EPL; e += 2)
+                    s2 = __ffma2_rn(make_float2(ix[e], ix[e + 1]), make_float2(r[e], r[e + 1]), s2);
+                pd[t] = s2.x + s2.y;
+            }
+            const float dot = reduce_scatter16(pd, hl);
+            int32_t my_id = nid[0];
+#pragma unroll
+            for (int t = 1; t < MAXT; ++t)
+                if (t == my_t) my_id = nid[t];
+            float g = 0.f;
+            if (my_id >= 0) {
+                const bool pos = my_t == 0;
+                const float sig = __frcp_rn(1.f + __expf(-dot));
+                g = eta * ((pos ? 1.f : 0.f) - sig);
+                if (loss_lane) closs -= __logf(fmaxf(pos ? sig : 1.f - sig, 1e-30f));
+            }
+            float gt[MAXT];
+#pragma unroll
+            for (int t = 0; t < MAXT; ++t) {
+                gt[t] = 0.f;
+                if (t <= K) gt[t] = __shfl_sync(kFull, g, (h << 4) | (t << 1));
+            }
+            float din[EPL];
+#pragma unroll
+            for (int e = 0; e < EPL; e += 2) {
+                const float2 r2 = __fmul2_rn(make_float2(gt[0], gt[0]), make_float2(oc[e], oc[e + 1]));
+                din[e] = r2.x;
+                din[e + 1] = r2.y;
+            }
+#pragma unroll
+            for (int t = 1; t < MAXT; ++t) {
+                if (t > K || nid[t] < 0) continue;
+                float nr[EPL];
+                uint32_t nr_raw[kBf16 ? EPL / 2 : 1];
+                read_row(s, t, nr, nr_raw);
+                float dn[EPL];
+#pragma unroll
+                for (int e = 0; e < EPL; e += 2) {
+                    const float2 gg = make_float2(gt[t], gt[t]);
+                    const float2 r2 = __ffma2_rn(gg, make_float2(nr[e], nr[e + 1]), make_float2(din[e], din[e + 1]));
+                    din[e] = r2.x;
+                    din[e + 1] = r2.y;
+                    const float2 u = __fmul2_rn(gg, make_float2(ix[e], ix[e + 1]));
+                    dn[e] = u.x;
+                    dn[e + 1] = u.y;
+                }
+                T *nrow = phi_out + static_cast<int64_t>(nid[t]) * D;
+                if constexpr (kBf16) {
+                    srs = srs * 1664525u + 1013904223u;
+                    add_delta_raw<EPL>(nrow + hl * EPL, nr_raw, dn, srs);
+                } else {
+                    hw_add<EPL>(reinterpret_cast<float *>(nrow), hl, dn);
+                }
+            }
+            // both pairs of this step update phi_out[c]: each half adds its own
+            // increment and the other half's, so the next step sees both
+#pragma unroll
+            for (int e = 0; e < EPL; e += 2) {
+                const float2 gg = make_float2(gt[0], gt[0]);
+                const float2 u = __fmul2_rn(gg, make_float2(ix[e], ix[e + 1]));
+                const float v0 = __shfl_xor_sync(kFull, u.x, 16), v1 = __shfl_xor_sync(kFull, u.y, 16);
+                oc[e] += u.x + v0;
+                oc[e + 1] += u.y + v1;
+                doc[e] += u.x + v0;
+                doc[e + 1] += u.y + v1;
+            }
+            if (valid) {
+                T *ix_row = phi_in + static_cast<int64_t>(x) * D;
+                if constexpr (kBf16) {
+                    srs = srs * 1664525u + 1013904223u;
+                    add_delta_raw<EPL>(ix_row + hl * EPL, ix_raw, din, srs);
+                } else {
+                    hw_add<EPL>(reinterpret_cast<float *>(ix_row), hl, din);
+                }
+            }
+            __syncwarp();  // stage s is refilled by the issue of step j + 2
+        }
+        cp_async_wait_none();
+        // the summed increment of phi_out[c] (identical in both halves), added by half 0
+        if (h == 0) {
+            if constexpr (kBf16) {
+                srs = srs * 1664525u + 1013904223u;
+                add_delta_raw<EPL>(oc_row + hl * EPL, oc_raw, doc, srs);
+            } else {
+                hw_add<EPL>(reinterpret_cast<float *>(oc_row), hl, doc);
+            }
+        }
+        loss_fx += __float2ll_rn(closs * kLossScaleF);
+        __syncwarp();
+    }
+    return loss_fx;
+}
+
+// ----------------------------------------------------------------------------
 // Synchronous minibatch (the deterministic form), shared by the single-graph
 // kernels (sgns.cu) and the batched ones (batch.cu): one warp per center
 // position; the tables are read only; increments go to 64-bit fixed-point

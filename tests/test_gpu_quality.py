@@ -34,7 +34,8 @@ def runs(fl, orc):
         fp = fl.feedback_params(False, 0.65, 8, R, False)
         out = {"oracle": a_or}
         for name, prec, form in [("hogwild", fl.FELOG_FP32, 0), ("bf16", fl.FELOG_BF16_SR, 0),
-                                 ("staged", fl.FELOG_FP32, 3), ("staged_bf16", fl.FELOG_BF16_SR, 3)]:
+                                 ("staged", fl.FELOG_FP32, 3), ("staged_bf16", fl.FELOG_BF16_SR, 3),
+                                 ("prefetch", fl.FELOG_FP32, 4), ("prefetch_bf16", fl.FELOG_BF16_SR, 4)]:
             tp = fl.train_params(DIM, W, K, 0.025, 0, fl.FELOG_SGNS_HOGWILD, 4096, prec, hogwild_form=form)
             pi, _, _ = fl.felog_embed(dg, L, 1, tp, fp, seed)
             out[name] = evaluate.link_auc(pi, sp.pos, sp.neg)
@@ -64,10 +65,12 @@ def test_bf16_auc_within_tolerance_of_serial_oracle(runs):
     assert abs(d.mean()) <= 0.005
 
 
-@pytest.mark.parametrize("form", ["staged", "staged_bf16"])
-def test_staged_hogwild_auc_within_tolerance_of_serial_oracle(runs, form):
+@pytest.mark.parametrize("form", ["staged", "staged_bf16", "prefetch", "prefetch_bf16"])
+def test_other_hogwild_forms_auc_within_tolerance_of_serial_oracle(runs, form):
     """The staged form (window phi_in increments summed in shared memory and
-    added when a position leaves the window) keeps the per-pair estimator."""
+    added when a position leaves the window) and the prefetching form (rows of
+    the next step copied to shared memory during this one) keep the per-pair
+    estimator."""
     d = np.array([r[form] - r["oracle"] for r in runs])
     print(f"{form} - oracle AUC per seed:", d.round(4))
     assert abs(d.mean()) <= 0.005
