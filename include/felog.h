@@ -458,8 +458,14 @@ size_t felog_batch_device_bytes(const felog_batch *b);
 felog_status felog_batch_reset(felog_batch *b, void *stream);
 /* one round of every unfinished job */
 felog_status felog_batch_step(felog_batch *b, void *stream);
-/* reset + max_rounds steps; use_graph = 1 captures them in one CUDA graph
- * (instantiated on first use, relaunched afterwards; needs a non-NULL stream) */
+/* reset + max_rounds steps.  use_graph = 0: ordinary launches; 1: the
+ * launches captured in one CUDA graph (instantiated on first use, relaunched
+ * afterwards; needs a non-NULL stream); 2: one persistent kernel for all
+ * rounds (every phase of every job, separated by grid-wide barriers; a
+ * cooperative launch of as many blocks as can be resident, the trainer in
+ * its two-pairs-per-warp shape).  Every form computes the same values.  A
+ * barrier gives up after about a minute without progress; felog_batch_read
+ * then returns FELOG_ERR_TIMEOUT. */
 felog_status felog_batch_run(felog_batch *b, int32_t use_graph, void *stream);
 /* synchronises `stream`; stats [n_jobs] (caller order), per-round |V_a| and
  * loss [max_rounds][n_jobs] (each may be NULL) */

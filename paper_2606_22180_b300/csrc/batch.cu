@@ -109,101 +109,113 @@ __global__ void k_b_lr(BArgs a) {
 // ---------------------------------------------------------------------------
 // compaction of each job's V_a (tiles never span jobs)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kBThreads) k_b_compact_count(BArgs a) {
+// Every per-round kernel of the batch is a phase function over (block b of
+// g blocks) with a thin kernel around it, so that one persistent kernel can
+// run all phases of all rounds (k_b_persistent) with the same arithmetic.
+__device__ __forceinline__ void ph_compact_count(const BArgs &a, int b, int g) {
     __shared__ int32_t warp_sum[kBWarps];
-    const int t = blockIdx.x;
-    const int j = a.tile_job[t];
-    const BJob &jb = a.jobs[j];
-    const BState &st = *a.jobs[j].st;
-    int32_t c = 0;
-    if (!st.done) {
-        const int32_t start = a.tile_start[t];
-        const uint8_t *act = jb.active[st.cur];
-        for (int i = threadIdx.x; i < kBTile; i += kBThreads) {
-            const int32_t v = start + i;
-            if (v < jb.n) {
-                c += act[v] != 0;
-                jb.counts[v] = 0u;
+    for (int t = b; t < a.n_tiles; t += g) {
+        const int j = a.tile_job[t];
+        const BJob &jb = a.jobs[j];
+        const BState &st = *a.jobs[j].st;
+        int32_t c = 0;
+        if (!st.done) {
+            const int32_t start = a.tile_start[t];
+            const uint8_t *act = jb.active[st.cur];
+            for (int i = threadIdx.x; i < kBTile; i += kBThreads) {
+                const int32_t v = start + i;
+                if (v < jb.n) {
+                    c += act[v] != 0;
+                    jb.counts[v] = 0u;
+                }
             }
         }
-    }
-    c = __reduce_add_sync(kFull, c);
-    if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = c;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int32_t s = 0;
-        for (int w = 0; w < kBWarps; ++w) s += warp_sum[w];
-        a.tile_count[t] = s;
+        c = __reduce_add_sync(kFull, c);
+        if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = c;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int32_t s = 0;
+            for (int w = 0; w < kBWarps; ++w) s += warp_sum[w];
+            a.tile_count[t] = s;
+        }
+        __syncthreads();
     }
 }
+__global__ void __launch_bounds__(kBThreads) k_b_compact_count(BArgs a) { ph_compact_count(a, blockIdx.x, gridDim.x); }
 
 // one thread per job: exclusive scan of its tile counts, |V_a|, round reset
-__global__ void k_b_compact_scan(BArgs a) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= a.n_jobs) return;
-    BState &st = *a.jobs[j].st;
-    st.S = 0;
-    st.cmax = 0;
-    st.loss_acc = 0;
-    st.n_next = 0;
-    if (st.done) {
-        st.n_active = 0;
-        return;
-    }
-    const BJob &jb = a.jobs[j];
-    int32_t run = 0;
-    for (int32_t t = jb.tile_base; t < jb.tile_base + jb.n_tiles; ++t) {
-        const int32_t c = a.tile_count[t];
-        a.tile_count[t] = run;
-        run += c;
-    }
-    st.n_active = run;
-    if (run == 0 || st.round >= a.max_rounds) {
-        st.done = 1;
-        st.n_active = 0;
+__device__ __forceinline__ void ph_compact_scan(const BArgs &a, int b, int g) {
+    for (int j = b * blockDim.x + threadIdx.x; j < a.n_jobs; j += g * blockDim.x) {
+        BState &st = *a.jobs[j].st;
+        st.S = 0;
+        st.cmax = 0;
+        st.loss_acc = 0;
+        st.n_next = 0;
+        if (st.done) {
+            st.n_active = 0;
+            continue;
+        }
+        const BJob &jb = a.jobs[j];
+        int32_t run = 0;
+        for (int32_t t = jb.tile_base; t < jb.tile_base + jb.n_tiles; ++t) {
+            const int32_t c = a.tile_count[t];
+            a.tile_count[t] = run;
+            run += c;
+        }
+        st.n_active = run;
+        if (run == 0 || st.round >= a.max_rounds) {
+            st.done = 1;
+            st.n_active = 0;
+        }
     }
 }
+__global__ void k_b_compact_scan(BArgs a) { ph_compact_scan(a, blockIdx.x, gridDim.x); }
 
-__global__ void __launch_bounds__(kBThreads) k_b_compact_scatter(BArgs a) {
+__device__ __forceinline__ void ph_compact_scatter(const BArgs &a, int b, int g) {
     __shared__ int32_t warp_tot[kBWarps];
-    const int t = blockIdx.x;
-    const int j = a.tile_job[t];
-    const BJob &jb = a.jobs[j];
-    const BState &st = *a.jobs[j].st;
-    if (st.done) return;  // uniform over the block
-    const uint8_t *act = jb.active[st.cur];
-    const int32_t my = a.tile_start[t] + threadIdx.x * kBTileItems;
-    uint32_t bits = 0;
+    for (int t = b; t < a.n_tiles; t += g) {
+        const int j = a.tile_job[t];
+        const BJob &jb = a.jobs[j];
+        const BState &st = *a.jobs[j].st;
+        if (st.done) continue;  // uniform over the block
+        const uint8_t *act = jb.active[st.cur];
+        const int32_t my = a.tile_start[t] + threadIdx.x * kBTileItems;
+        uint32_t bits = 0;
 #pragma unroll
-    for (int k = 0; k < kBTileItems; ++k) {
-        const int32_t v = my + k;
-        if (v < jb.n && act[v]) bits |= 1u << k;
+        for (int k = 0; k < kBTileItems; ++k) {
+            const int32_t v = my + k;
+            if (v < jb.n && act[v]) bits |= 1u << k;
+        }
+        const int32_t c = __popc(bits);
+        int32_t incl = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(kFull, incl, o);
+            if ((threadIdx.x & 31) >= o) incl += y;
+        }
+        if ((threadIdx.x & 31) == 31) warp_tot[threadIdx.x >> 5] = incl;
+        __syncthreads();
+        int32_t warp_excl = 0;
+        for (int w = 0; w < (threadIdx.x >> 5); ++w) warp_excl += warp_tot[w];
+        int32_t pos = a.tile_count[t] + warp_excl + incl - c;
+        while (bits) {
+            const int k = __ffs(bits) - 1;
+            bits &= bits - 1;
+            jb.starts[pos++] = my + k;
+        }
+        __syncthreads();
     }
-    const int32_t c = __popc(bits);
-    int32_t incl = c;
-    for (int o = 1; o < 32; o <<= 1) {
-        const int32_t y = __shfl_up_sync(kFull, incl, o);
-        if ((threadIdx.x & 31) >= o) incl += y;
-    }
-    if ((threadIdx.x & 31) == 31) warp_tot[threadIdx.x >> 5] = incl;
-    __syncthreads();
-    int32_t warp_excl = 0;
-    for (int w = 0; w < (threadIdx.x >> 5); ++w) warp_excl += warp_tot[w];
-    int32_t pos = a.tile_count[t] + warp_excl + incl - c;
-    while (bits) {
-        const int k = __ffs(bits) - 1;
-        bits &= bits - 1;
-        jb.starts[pos++] = my + k;
-    }
+}
+__global__ void __launch_bounds__(kBThreads) k_b_compact_scatter(BArgs a) {
+    ph_compact_scatter(a, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------------------
 // walks (counts fused); walk row o of job j = rep * |V_a| + i, as in felog_walk
 // ---------------------------------------------------------------------------
 template <bool VEC>
-__global__ void k_b_walk(BArgs a) {
-    for (int64_t x = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; x < a.n_slots;
-         x += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+__device__ __forceinline__ void ph_walk(const BArgs &a, int b, int g) {
+    for (int64_t x = static_cast<int64_t>(b) * blockDim.x + threadIdx.x; x < a.n_slots;
+         x += static_cast<int64_t>(g) * blockDim.x) {
         const int j = find_job(a.slot_prefix, a.n_jobs, x);
         const BState &st = *a.jobs[j].st;
         const int64_t o = x - a.slot_prefix[j];
@@ -217,147 +229,162 @@ __global__ void k_b_walk(BArgs a) {
                                  jb.counts);
     }
 }
+template <bool VEC>
+__global__ void k_b_walk(BArgs a) { ph_walk<VEC>(a, blockIdx.x, gridDim.x); }
 
 // ---------------------------------------------------------------------------
 // per-job alias tables of the round's corpus (same integers as felog_noise_table)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kBThreads) k_b_noise_max(BArgs a) {
-    const int t = blockIdx.x;
-    const int j = a.tile_job[t];
-    if (a.jobs[j].st->done) return;
-    const BJob &jb = a.jobs[j];
-    uint32_t m = 0;
-    const int32_t start = a.tile_start[t];
-    for (int i = threadIdx.x; i < kBTile; i += kBThreads)
-        if (start + i < jb.n) m = max(m, jb.counts[start + i]);
-    m = __reduce_max_sync(kFull, m);
-    if ((threadIdx.x & 31) == 0 && m) atomicMax(&a.jobs[j].st->cmax, m);
+__device__ __forceinline__ void ph_noise_max(const BArgs &a, int b, int g) {
+    for (int t = b; t < a.n_tiles; t += g) {
+        const int j = a.tile_job[t];
+        if (a.jobs[j].st->done) continue;
+        const BJob &jb = a.jobs[j];
+        uint32_t m = 0;
+        const int32_t start = a.tile_start[t];
+        for (int i = threadIdx.x; i < kBTile; i += kBThreads)
+            if (start + i < jb.n) m = max(m, jb.counts[start + i]);
+        m = __reduce_max_sync(kFull, m);
+        if ((threadIdx.x & 31) == 0 && m) atomicMax(&a.jobs[j].st->cmax, m);
+    }
 }
+__global__ void __launch_bounds__(kBThreads) k_b_noise_max(BArgs a) { ph_noise_max(a, blockIdx.x, gridDim.x); }
 
-__global__ void __launch_bounds__(kBThreads) k_b_noise_weights(BArgs a) {
-    const int t = blockIdx.x;
-    const int j = a.tile_job[t];
-    if (a.jobs[j].st->done) return;
-    const BJob &jb = a.jobs[j];
-    const uint32_t cm = a.jobs[j].st->cmax;
-    const double wmax = cm ? three_quarter_power(cm) : 1.0;
-    unsigned long long local = 0;
-    const int32_t start = a.tile_start[t];
-    for (int i = threadIdx.x; i < kBTile; i += kBThreads) {
-        const int32_t v = start + i;
-        if (v >= jb.n) break;
-        const uint32_t c = jb.counts[v];
-        uint64_t w = 0;
-        if (c) {
-            const double q = floor(__dmul_rn(__ddiv_rn(three_quarter_power(c), wmax), 4294967296.0));
-            w = static_cast<uint64_t>(q);
-            if (w < 1) w = 1;
+__device__ __forceinline__ void ph_noise_weights(const BArgs &a, int b, int g) {
+    for (int t = b; t < a.n_tiles; t += g) {
+        const int j = a.tile_job[t];
+        if (a.jobs[j].st->done) continue;
+        const BJob &jb = a.jobs[j];
+        const uint32_t cm = a.jobs[j].st->cmax;
+        const double wmax = cm ? three_quarter_power(cm) : 1.0;
+        unsigned long long local = 0;
+        const int32_t start = a.tile_start[t];
+        for (int i = threadIdx.x; i < kBTile; i += kBThreads) {
+            const int32_t v = start + i;
+            if (v >= jb.n) break;
+            const uint32_t c = jb.counts[v];
+            uint64_t w = 0;
+            if (c) {
+                const double q = floor(__dmul_rn(__ddiv_rn(three_quarter_power(c), wmax), 4294967296.0));
+                w = static_cast<uint64_t>(q);
+                if (w < 1) w = 1;
+            }
+            jb.W[v] = w;
+            local += w;
         }
-        jb.W[v] = w;
-        local += w;
+        for (int o = 16; o; o >>= 1) local += __shfl_xor_sync(kFull, local, o);
+        if ((threadIdx.x & 31) == 0 && local) atomicAdd(&a.jobs[j].st->S, local);
     }
-    for (int o = 16; o; o >>= 1) local += __shfl_xor_sync(kFull, local, o);
-    if ((threadIdx.x & 31) == 0 && local) atomicAdd(&a.jobs[j].st->S, local);
 }
+__global__ void __launch_bounds__(kBThreads) k_b_noise_weights(BArgs a) { ph_noise_weights(a, blockIdx.x, gridDim.x); }
 
-__global__ void __launch_bounds__(kBThreads) k_b_noise_agg(BArgs a) {
+__device__ __forceinline__ void ph_noise_agg(const BArgs &a, int b, int gb) {
     __shared__ NoiseAgg part[kBThreads];
-    const int t = blockIdx.x;
-    const int j = a.tile_job[t];
-    if (a.jobs[j].st->done) return;
-    const BJob &jb = a.jobs[j];
-    const uint64_t S = a.jobs[j].st->S;
-    const int32_t my = a.tile_start[t] + threadIdx.x * kBTileItems;
-    NoiseAgg g{0, 0, 0, 0};
-    for (int k = 0; k < kBTileItems; ++k) {
-        const int32_t v = my + k;
-        if (v >= jb.n) break;
-        bool light;
-        uint64_t amt;
-        classify(jb.W[v], static_cast<uint64_t>(jb.n), S, light, amt);
-        if (light) { g.D += amt; g.nL += 1; }
-        else { g.E += amt; g.nH += 1; }
-    }
-    part[threadIdx.x] = g;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        NoiseAgg s{0, 0, 0, 0};
-        for (int i = 0; i < kBThreads; ++i) {
-            s.D += part[i].D; s.E += part[i].E; s.nL += part[i].nL; s.nH += part[i].nH;
+    for (int t = b; t < a.n_tiles; t += gb) {
+        const int j = a.tile_job[t];
+        if (a.jobs[j].st->done) continue;
+        const BJob &jb = a.jobs[j];
+        const uint64_t S = a.jobs[j].st->S;
+        const int32_t my = a.tile_start[t] + threadIdx.x * kBTileItems;
+        NoiseAgg g{0, 0, 0, 0};
+        for (int k = 0; k < kBTileItems; ++k) {
+            const int32_t v = my + k;
+            if (v >= jb.n) break;
+            bool light;
+            uint64_t amt;
+            classify(jb.W[v], static_cast<uint64_t>(jb.n), S, light, amt);
+            if (light) { g.D += amt; g.nL += 1; }
+            else { g.E += amt; g.nH += 1; }
         }
-        a.tile_agg[t] = s;
+        part[threadIdx.x] = g;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            NoiseAgg s{0, 0, 0, 0};
+            for (int i = 0; i < kBThreads; ++i) {
+                s.D += part[i].D; s.E += part[i].E; s.nL += part[i].nL; s.nH += part[i].nH;
+            }
+            a.tile_agg[t] = s;
+        }
+        __syncthreads();
     }
 }
+__global__ void __launch_bounds__(kBThreads) k_b_noise_agg(BArgs a) { ph_noise_agg(a, blockIdx.x, gridDim.x); }
 
-__global__ void k_b_noise_scan(BArgs a) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= a.n_jobs || a.jobs[j].st->done) return;
-    const BJob &jb = a.jobs[j];
-    NoiseAgg run{0, 0, 0, 0};
-    for (int32_t t = jb.tile_base; t < jb.tile_base + jb.n_tiles; ++t) {
-        const NoiseAgg x = a.tile_agg[t];
-        a.tile_agg[t] = run;
-        run.D += x.D; run.E += x.E; run.nL += x.nL; run.nH += x.nH;
-    }
-    a.jobs[j].st->total = run;
-}
-
-__global__ void __launch_bounds__(kBThreads) k_b_noise_scatter(BArgs a) {
-    __shared__ NoiseAgg part[kBThreads];
-    const int t = blockIdx.x;
-    const int j = a.tile_job[t];
-    if (a.jobs[j].st->done) return;
-    const BJob &jb = a.jobs[j];
-    const uint64_t S = a.jobs[j].st->S;
-    const int32_t my = a.tile_start[t] + threadIdx.x * kBTileItems;
-    NoiseAgg g{0, 0, 0, 0};
-    for (int k = 0; k < kBTileItems; ++k) {
-        const int32_t v = my + k;
-        if (v >= jb.n) break;
-        bool light;
-        uint64_t amt;
-        classify(jb.W[v], static_cast<uint64_t>(jb.n), S, light, amt);
-        if (light) { g.D += amt; g.nL += 1; }
-        else { g.E += amt; g.nH += 1; }
-    }
-    part[threadIdx.x] = g;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        NoiseAgg run = a.tile_agg[t];
-        for (int i = 0; i < kBThreads; ++i) {
-            const NoiseAgg x = part[i];
-            part[i] = run;
+__device__ __forceinline__ void ph_noise_scan(const BArgs &a, int b, int g) {
+    for (int j = b * blockDim.x + threadIdx.x; j < a.n_jobs; j += g * blockDim.x) {
+        if (a.jobs[j].st->done) continue;
+        const BJob &jb = a.jobs[j];
+        NoiseAgg run{0, 0, 0, 0};
+        for (int32_t t = jb.tile_base; t < jb.tile_base + jb.n_tiles; ++t) {
+            const NoiseAgg x = a.tile_agg[t];
+            a.tile_agg[t] = run;
             run.D += x.D; run.E += x.E; run.nL += x.nL; run.nH += x.nH;
         }
+        a.jobs[j].st->total = run;
     }
-    __syncthreads();
-    NoiseAgg run = part[threadIdx.x];
-    for (int k = 0; k < kBTileItems; ++k) {
-        const int32_t v = my + k;
-        if (v >= jb.n) break;
-        bool light;
-        uint64_t amt;
-        classify(jb.W[v], static_cast<uint64_t>(jb.n), S, light, amt);
-        if (light) {
-            jb.key[v] = run.D;
-            jb.light_D[run.nL] = run.D;
-            jb.rank[v] = run.nL;
-            run.D += amt;
-            run.nL += 1;
-        } else {
-            run.E += amt;
-            jb.key[v] = run.E;
-            jb.heavy_idx[run.nH] = v;
-            jb.heavy_E[run.nH] = run.E;
-            jb.rank[v] = run.nH;
-            run.nH += 1;
+}
+__global__ void k_b_noise_scan(BArgs a) { ph_noise_scan(a, blockIdx.x, gridDim.x); }
+
+__device__ __forceinline__ void ph_noise_scatter(const BArgs &a, int b, int gb) {
+    __shared__ NoiseAgg part[kBThreads];
+    for (int t = b; t < a.n_tiles; t += gb) {
+        const int j = a.tile_job[t];
+        if (a.jobs[j].st->done) continue;
+        const BJob &jb = a.jobs[j];
+        const uint64_t S = a.jobs[j].st->S;
+        const int32_t my = a.tile_start[t] + threadIdx.x * kBTileItems;
+        NoiseAgg g{0, 0, 0, 0};
+        for (int k = 0; k < kBTileItems; ++k) {
+            const int32_t v = my + k;
+            if (v >= jb.n) break;
+            bool light;
+            uint64_t amt;
+            classify(jb.W[v], static_cast<uint64_t>(jb.n), S, light, amt);
+            if (light) { g.D += amt; g.nL += 1; }
+            else { g.E += amt; g.nH += 1; }
         }
+        part[threadIdx.x] = g;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            NoiseAgg run = a.tile_agg[t];
+            for (int i = 0; i < kBThreads; ++i) {
+                const NoiseAgg x = part[i];
+                part[i] = run;
+                run.D += x.D; run.E += x.E; run.nL += x.nL; run.nH += x.nH;
+            }
+        }
+        __syncthreads();
+        NoiseAgg run = part[threadIdx.x];
+        for (int k = 0; k < kBTileItems; ++k) {
+            const int32_t v = my + k;
+            if (v >= jb.n) break;
+            bool light;
+            uint64_t amt;
+            classify(jb.W[v], static_cast<uint64_t>(jb.n), S, light, amt);
+            if (light) {
+                jb.key[v] = run.D;
+                jb.light_D[run.nL] = run.D;
+                jb.rank[v] = run.nL;
+                run.D += amt;
+                run.nL += 1;
+            } else {
+                run.E += amt;
+                jb.key[v] = run.E;
+                jb.heavy_idx[run.nH] = v;
+                jb.heavy_E[run.nH] = run.E;
+                jb.rank[v] = run.nH;
+                run.nH += 1;
+            }
+        }
+        __syncthreads();
     }
 }
 
-__global__ void k_b_noise_finish(BArgs a) {
-    for (int64_t x = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; x < a.n_nodes;
-         x += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+__global__ void __launch_bounds__(kBThreads) k_b_noise_scatter(BArgs a) { ph_noise_scatter(a, blockIdx.x, gridDim.x); }
+
+__device__ __forceinline__ void ph_noise_finish(const BArgs &a, int b, int g) {
+    for (int64_t x = static_cast<int64_t>(b) * blockDim.x + threadIdx.x; x < a.n_nodes;
+         x += static_cast<int64_t>(g) * blockDim.x) {
         const int j = find_job(a.node_prefix, a.n_jobs, x);
         const BState &st = *a.jobs[j].st;
         if (st.done) continue;
@@ -372,21 +399,22 @@ __global__ void k_b_noise_finish(BArgs a) {
                     st.total.nL, jb.heavy_idx, jb.heavy_E, st.total.nH, st.total.D, jb.thr + v, jb.alias + v);
     }
 }
+__global__ void k_b_noise_finish(BArgs a) { ph_noise_finish(a, blockIdx.x, gridDim.x); }
 
 // ---------------------------------------------------------------------------
 // SGNS over training items of the jobs whose dim is D
 // ---------------------------------------------------------------------------
 // FORM 2: two pairs per warp (a half warp each, 16 lanes per row); FORM 1:
 // one pair per warp (32 lanes per row).  Same estimator, different shapes.
-template <int D, class T, int KFIX, int FORM>
-__global__ void __launch_bounds__(kSgnsThreads, 2) k_b_sgns(BArgs a, int64_t item_lo, int64_t item_hi) {
+template <int D, class T, int KFIX, int FORM, bool NC>
+__device__ __forceinline__ void ph_sgns(const BArgs &a, int64_t item_lo, int64_t item_hi, int b, int g) {
     extern __shared__ int32_t smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int K = KFIX > 0 ? KFIX : a.K;
     int32_t *wk = smem + wib * (a.L + 2 * a.window * K);
     int32_t *negs = wk + a.L;
-    const int64_t warps = static_cast<int64_t>(gridDim.x) * kWarps;
-    for (int64_t it = item_lo + static_cast<int64_t>(blockIdx.x) * kWarps + wib; it < item_hi; it += warps) {
+    const int64_t warps = static_cast<int64_t>(g) * kWarps;
+    for (int64_t it = item_lo + static_cast<int64_t>(b) * kWarps + wib; it < item_hi; it += warps) {
         const int j = find_job(a.item_prefix, a.n_jobs, it);
         const BState &st = *a.jobs[j].st;
         if (st.done) continue;
@@ -398,13 +426,19 @@ __global__ void __launch_bounds__(kSgnsThreads, 2) k_b_sgns(BArgs a, int64_t ite
                        st.inv_T, st.clock, a.window, a.K, a.L};
         long long loss_fx = 0;
         for (int64_t wl = it - a.item_prefix[j]; wl < walks; wl += c_j) {
-            if constexpr (FORM == 1) loss_fx += fw_train_walk<D, T, 8, KFIX>(v, jb.walks + wl * a.L, wl, wk, negs);
-            else loss_fx += hw_train_walk<D, T, KFIX>(v, jb.walks + wl * a.L, wl, wk, negs);
+            if constexpr (FORM == 1)
+                loss_fx += fw_train_walk<D, T, 8, KFIX, NC>(v, jb.walks + wl * a.L, wl, wk, negs);
+            else
+                loss_fx += hw_train_walk<D, T, KFIX, false, NC>(v, jb.walks + wl * a.L, wl, wk, negs);
         }
         for (int o = 16; o; o >>= 1) loss_fx += __shfl_xor_sync(kFull, loss_fx, o);
         if (lane == 0 && loss_fx != 0)
             atomicAdd(&jb.st->loss_acc, static_cast<unsigned long long>(loss_fx));
     }
+}
+template <int D, class T, int KFIX, int FORM>
+__global__ void __launch_bounds__(kSgnsThreads, 2) k_b_sgns(BArgs a, int64_t item_lo, int64_t item_hi) {
+    ph_sgns<D, T, KFIX, FORM, true>(a, item_lo, item_hi, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -417,13 +451,13 @@ __global__ void __launch_bounds__(kSgnsThreads, 2) k_b_sgns(BArgs a, int64_t ite
 // equals felog_train's minibatch form over the round with minibatch >= its
 // tokens, bit for bit.
 // ---------------------------------------------------------------------------
-template <int D, class T>
-__global__ void __launch_bounds__(kSgnsThreads) k_b_mb_grad(BArgs a, int64_t tok_lo, int64_t tok_hi) {
+template <int D, class T, bool NC>
+__device__ __forceinline__ void ph_mb_grad(const BArgs &a, int64_t tok_lo, int64_t tok_hi, int b, int g) {
     extern __shared__ int32_t smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     int32_t *negs = smem + wib * (2 * a.window * a.K);
-    const int64_t warps = static_cast<int64_t>(gridDim.x) * kWarps;
-    for (int64_t x = tok_lo + static_cast<int64_t>(blockIdx.x) * kWarps + wib; x < tok_hi; x += warps) {
+    const int64_t warps = static_cast<int64_t>(g) * kWarps;
+    for (int64_t x = tok_lo + static_cast<int64_t>(b) * kWarps + wib; x < tok_hi; x += warps) {
         const int j = find_job(a.slot_prefix, a.n_jobs, x / a.L);
         const BState &st = *a.jobs[j].st;
         if (st.done) continue;
@@ -437,7 +471,7 @@ __global__ void __launch_bounds__(kSgnsThreads) k_b_mb_grad(BArgs a, int64_t tok
         const MbView v{jb.thr, jb.alias, static_cast<uint64_t>(jb.n), st.S, jb.seed, static_cast<uint32_t>(st.round),
                        a.window, a.K, a.L};
         const MbState ms{jb.acc_in, jb.acc_out, jb.mark_in, jb.mark_out, nullptr, nullptr, nullptr};
-        const float closs = mb_grad_center<D, T, 8>(v, jb.walks + wi * a.L, wi, p, eta,
+        const float closs = mb_grad_center<D, T, 8, NC>(v, jb.walks + wi * a.L, wi, p, eta,
                                                     static_cast<const T *>(jb.phi_in),
                                                     static_cast<const T *>(jb.phi_out), ms, negs);
         long long loss_fx = __float2ll_rn(closs * kLossScaleF);
@@ -445,13 +479,17 @@ __global__ void __launch_bounds__(kSgnsThreads) k_b_mb_grad(BArgs a, int64_t tok
         if (lane == 0 && loss_fx != 0) atomicAdd(&jb.st->loss_acc, static_cast<unsigned long long>(loss_fx));
     }
 }
+template <int D, class T>
+__global__ void __launch_bounds__(kSgnsThreads) k_b_mb_grad(BArgs a, int64_t tok_lo, int64_t tok_hi) {
+    ph_mb_grad<D, T, true>(a, tok_lo, tok_hi, blockIdx.x, gridDim.x);
+}
 
 // every marked row of the jobs [node_lo, node_hi) of one dim, both tables
 template <int D, class T>
-__global__ void __launch_bounds__(256) k_b_mb_apply(BArgs a, int64_t node_lo, int64_t node_hi) {
+__device__ __forceinline__ void ph_mb_apply(const BArgs &a, int64_t node_lo, int64_t node_hi, int b, int g) {
     const int lane = threadIdx.x & 31;
-    const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x / 32);
-    for (int64_t i = node_lo * 2 + static_cast<int64_t>(blockIdx.x) * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int64_t warps = static_cast<int64_t>(g) * (blockDim.x / 32);
+    for (int64_t i = node_lo * 2 + static_cast<int64_t>(b) * (blockDim.x / 32) + (threadIdx.x >> 5);
          i < node_hi * 2; i += warps) {
         const int64_t x = i >> 1;
         const bool is_in = (i & 1) == 0;
@@ -466,17 +504,21 @@ __global__ void __launch_bounds__(256) k_b_mb_apply(BArgs a, int64_t node_lo, in
                            is_in, jb.seed, static_cast<uint32_t>(st.round) << 20, lane);
     }
 }
+template <int D, class T>
+__global__ void __launch_bounds__(256) k_b_mb_apply(BArgs a, int64_t node_lo, int64_t node_hi) {
+    ph_mb_apply<D, T>(a, node_lo, node_hi, blockIdx.x, gridDim.x);
+}
 
 // ---------------------------------------------------------------------------
 // Psi and V_a^{r+1} (same values as felog_feedback)
 // ---------------------------------------------------------------------------
 template <class T>
-__global__ void __launch_bounds__(kBThreads) k_b_feedback(BArgs a) {
+__device__ __forceinline__ void ph_feedback(const BArgs &a, int b, int g) {
     __shared__ int32_t sub_s[kBWarps][kMaxKs];
     __shared__ int32_t sorted_s[kBWarps][kMaxKs];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int64_t warps = static_cast<int64_t>(gridDim.x) * kBWarps;
-    for (int64_t x = static_cast<int64_t>(blockIdx.x) * kBWarps + wib; x < a.n_nodes; x += warps) {
+    const int64_t warps = static_cast<int64_t>(g) * kBWarps;
+    for (int64_t x = static_cast<int64_t>(b) * kBWarps + wib; x < a.n_nodes; x += warps) {
         const int j = find_job(a.node_prefix, a.n_jobs, x);
         const BState &st = *a.jobs[j].st;
         if (st.done) continue;
@@ -496,21 +538,110 @@ __global__ void __launch_bounds__(kBThreads) k_b_feedback(BArgs a) {
         }
     }
 }
+template <class T>
+__global__ void __launch_bounds__(kBThreads) k_b_feedback(BArgs a) { ph_feedback<T>(a, blockIdx.x, gridDim.x); }
 
-__global__ void k_b_round_end(BArgs a) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= a.n_jobs) return;
-    BState &st = *a.jobs[j].st;
-    if (st.done) return;
-    const int r = st.round;
-    const BJob &jb = a.jobs[j];
-    jb.rec_n_active[r] = st.n_active;
-    jb.rec_n_next[r] = st.n_next;
-    jb.rec_loss[r] = static_cast<double>(static_cast<long long>(st.loss_acc)) / kLossScale;
-    st.clock += static_cast<int64_t>(st.n_active) * a.wpr * a.L;
-    st.round = r + 1;
-    st.cur ^= 1;
-    if (st.n_next == 0 || st.round >= a.max_rounds) st.done = 1;
+__device__ __forceinline__ void ph_round_end(const BArgs &a, int b, int g) {
+    for (int j = b * blockDim.x + threadIdx.x; j < a.n_jobs; j += g * blockDim.x) {
+        BState &st = *a.jobs[j].st;
+        if (st.done) continue;
+        const int r = st.round;
+        const BJob &jb = a.jobs[j];
+        jb.rec_n_active[r] = st.n_active;
+        jb.rec_n_next[r] = st.n_next;
+        jb.rec_loss[r] = static_cast<double>(static_cast<long long>(st.loss_acc)) / kLossScale;
+        st.clock += static_cast<int64_t>(st.n_active) * a.wpr * a.L;
+        st.round = r + 1;
+        st.cur ^= 1;
+        if (st.n_next == 0 || st.round >= a.max_rounds) st.done = 1;
+    }
+}
+__global__ void k_b_round_end(BArgs a) { ph_round_end(a, blockIdx.x, gridDim.x); }
+
+// ---------------------------------------------------------------------------
+// One persistent kernel for a whole run: every phase of every round of every
+// job, the phases separated by a grid-wide barrier.  The grid is launched
+// cooperatively (all blocks resident), so a barrier only waits for blocks
+// that are running; each wait is still bounded (kGridWaitLimit polls about a
+// microsecond apart, over a minute), after which the error word is set and
+// every block returns at its next barrier.  Phase data written by other
+// blocks is read after the barrier's release/acquire fences; the alias
+// table, rebuilt every round, is read through L2 rather than the read-only
+// cache (NC = false), which a kernel only refreshes at its launch.
+// ---------------------------------------------------------------------------
+constexpr unsigned kGridWaitLimit = 1u << 26;
+
+__device__ __forceinline__ bool grid_sync(GridBarrier *bar) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = &bar->gen;
+        volatile int *verr = &bar->error;
+        const unsigned g0 = *vgen;
+        __threadfence();
+        if (atomicAdd(&bar->count, 1u) == gridDim.x - 1) {
+            bar->count = 0;  // every block has arrived: reset, then release them
+            __threadfence();
+            atomicAdd(&bar->gen, 1u);
+        } else {
+            unsigned it = 0;
+            while (*vgen == g0 && !*verr) {
+                if (++it > kGridWaitLimit) {
+                    atomicExch(&bar->error, 1);
+                    break;
+                }
+                __nanosleep(1000);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return *reinterpret_cast<volatile int *>(&bar->error) == 0;
+}
+
+template <class T, int KFIX, bool MB>
+__global__ void __launch_bounds__(kBThreads, 2) k_b_persistent(BArgs a, GridBarrier *bar) {
+    const int b = blockIdx.x, g = gridDim.x;
+    for (int r = 0; r < a.max_rounds; ++r) {
+        ph_compact_count(a, b, g);
+        if (!grid_sync(bar)) return;
+        ph_compact_scan(a, b, g);
+        if (!grid_sync(bar)) return;
+        ph_compact_scatter(a, b, g);
+        if (!grid_sync(bar)) return;
+        if (a.L % 4 == 0) ph_walk<true>(a, b, g);
+        else ph_walk<false>(a, b, g);
+        if (!grid_sync(bar)) return;
+        ph_noise_max(a, b, g);
+        if (!grid_sync(bar)) return;
+        ph_noise_weights(a, b, g);
+        if (!grid_sync(bar)) return;
+        ph_noise_agg(a, b, g);
+        if (!grid_sync(bar)) return;
+        ph_noise_scan(a, b, g);
+        if (!grid_sync(bar)) return;
+        ph_noise_scatter(a, b, g);
+        if (!grid_sync(bar)) return;
+        ph_noise_finish(a, b, g);
+        if (!grid_sync(bar)) return;
+        if constexpr (MB) {
+            ph_mb_grad<32, T, false>(a, a.tok_lo[0], a.tok_hi[0], b, g);
+            ph_mb_grad<64, T, false>(a, a.tok_lo[1], a.tok_hi[1], b, g);
+            ph_mb_grad<128, T, false>(a, a.tok_lo[2], a.tok_hi[2], b, g);
+            if (!grid_sync(bar)) return;
+            ph_mb_apply<32, T>(a, a.node_lo[0], a.node_hi[0], b, g);
+            ph_mb_apply<64, T>(a, a.node_lo[1], a.node_hi[1], b, g);
+            ph_mb_apply<128, T>(a, a.node_lo[2], a.node_hi[2], b, g);
+        } else {
+            ph_sgns<32, T, KFIX, 2, false>(a, a.item_lo[0], a.item_hi[0], b, g);
+            ph_sgns<64, T, KFIX, 2, false>(a, a.item_lo[1], a.item_hi[1], b, g);
+            ph_sgns<128, T, KFIX, 2, false>(a, a.item_lo[2], a.item_hi[2], b, g);
+        }
+        if (!grid_sync(bar)) return;
+        ph_feedback<T>(a, b, g);
+        if (!grid_sync(bar)) return;
+        ph_round_end(a, b, g);
+        if (!grid_sync(bar)) return;
+    }
 }
 
 // gathers every job's state and round records into contiguous arrays
@@ -643,11 +774,14 @@ felog_status plan_build(BatchPlan &plan, const std::vector<BJob> &jobs_in, const
     plan.o_gna = slot(sizeof(int32_t) * R * n_jobs);
     plan.o_gnn = slot(sizeof(int32_t) * R * n_jobs);
     plan.o_gl = slot(sizeof(double) * R * n_jobs);
+    plan.o_bar = slot(sizeof(GridBarrier));
     felog_status st = record_cuda_error(cudaMallocAsync(&plan.mem, off, s), "plan");
     if (st) return st;
     plan.bytes = off;
     char *base = static_cast<char *>(plan.mem);
-    st = record_cuda_error(cudaMemcpyAsync(base + o_jobs, jobs.data(), sizeof(BJob) * n_jobs, cudaMemcpyHostToDevice, s), "plan");
+    st = record_cuda_error(cudaMemsetAsync(base + plan.o_bar, 0, sizeof(GridBarrier), s), "plan");
+    if (!st)
+        st = record_cuda_error(cudaMemcpyAsync(base + o_jobs, jobs.data(), sizeof(BJob) * n_jobs, cudaMemcpyHostToDevice, s), "plan");
     if (!st) st = record_cuda_error(cudaMemcpyAsync(base + o_sp, slot_prefix.data(), sizeof(int64_t) * (n_jobs + 1), cudaMemcpyHostToDevice, s), "plan");
     if (!st) st = record_cuda_error(cudaMemcpyAsync(base + o_np, node_prefix.data(), sizeof(int64_t) * (n_jobs + 1), cudaMemcpyHostToDevice, s), "plan");
     if (!st) st = record_cuda_error(cudaMemcpyAsync(base + o_ip, item_prefix.data(), sizeof(int64_t) * (n_jobs + 1), cudaMemcpyHostToDevice, s), "plan");
@@ -690,6 +824,19 @@ felog_status plan_build(BatchPlan &plan, const std::vector<BJob> &jobs_in, const
     a.mu = p.mu;
     a.lr0 = p.lr0;
     a.lr_total_tokens = p.lr_total_tokens;
+    for (int k = 0; k < 3; ++k) {
+        const int32_t d = 32 << k;
+        int32_t j0 = 0;
+        while (j0 < n_jobs && plan.dims[j0] < d) ++j0;
+        int32_t j1 = j0;
+        while (j1 < n_jobs && plan.dims[j1] == d) ++j1;
+        a.item_lo[k] = item_prefix[j0];
+        a.item_hi[k] = item_prefix[j1];
+        a.tok_lo[k] = slot_prefix[j0] * p.L;
+        a.tok_hi[k] = slot_prefix[j1] * p.L;
+        a.node_lo[k] = node_prefix[j0];
+        a.node_hi[k] = node_prefix[j1];
+    }
     return FELOG_OK;
 }
 
@@ -1023,10 +1170,54 @@ extern "C" felog_status felog_batch_step(felog_batch *b, void *stream) {
     return plan_step(b->plan, b->p, b->tune, static_cast<cudaStream_t>(stream), 0x3f);
 }
 
+namespace {
+
+// All rounds of every job in one cooperative launch of k_b_persistent (after
+// the usual reset).  The grid is as many blocks as can be resident.
+template <class T>
+felog_status launch_persistent(felog_batch *b, cudaStream_t s) {
+    const BatchPlan &plan = b->plan;
+    const BParams &p = b->p;
+    GridBarrier *bar = reinterpret_cast<GridBarrier *>(static_cast<char *>(plan.mem) + plan.o_bar);
+    felog_status st = record_cuda_error(cudaMemsetAsync(bar, 0, sizeof(GridBarrier), s), "persistent");
+    if (st) return st;
+    const bool mb = p.mode == FELOG_SGNS_MINIBATCH;
+    void (*kern)(BArgs, GridBarrier *) = mb ? k_b_persistent<T, 0, true>
+                                            : (p.K == 5 ? k_b_persistent<T, 5, false> : k_b_persistent<T, 0, false>);
+    const size_t smem = sizeof(int32_t) * kWarps * (p.L + 2 * p.window * p.K);
+    if (smem > 48 * 1024) {
+        st = record_cuda_error(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    static_cast<int>(smem)), "persistent");
+        if (st) return st;
+    }
+    int per_sm = 0;
+    st = record_cuda_error(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBThreads, smem), "persistent");
+    if (st) return st;
+    if (per_sm < 1) return FELOG_ERR_UNSUPPORTED;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(per_sm * sm_count()));
+    cfg.blockDim = dim3(kBThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return record_cuda_error(cudaLaunchKernelEx(&cfg, kern, plan.args, bar), "persistent launch");
+}
+
+}  // namespace
+
 extern "C" felog_status felog_batch_run(felog_batch *b, int32_t use_graph, void *stream) {
-    if (!b) return FELOG_ERR_INVALID_ARG;
+    if (!b || use_graph < 0 || use_graph > 2) return FELOG_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int R = b->p.max_rounds;
+    if (use_graph == 2) {
+        felog_status st = batch_reset(b, s);
+        if (st) return st;
+        return b->p.precision == FELOG_FP32 ? launch_persistent<float>(b, s) : launch_persistent<__nv_bfloat16>(b, s);
+    }
     if (!use_graph || s == nullptr) {
         felog_status st = batch_reset(b, s);
         for (int r = 0; !st && r < R; ++r) st = plan_step(b->plan, b->p, b->tune, s, 0x3f);
@@ -1060,6 +1251,12 @@ extern "C" felog_status felog_batch_read(felog_batch *b, felog_job_stats *stats,
     std::vector<double> rl;
     felog_status st = plan_gather(b->plan, b->p, static_cast<cudaStream_t>(stream), sts, rna, rnn, rl);
     if (st) return st;
+    // a persistent run whose grid barrier gave up waiting has failed
+    GridBarrier bar{};
+    st = record_cuda_error(cudaMemcpy(&bar, static_cast<char *>(b->plan.mem) + b->plan.o_bar, sizeof bar,
+                                      cudaMemcpyDeviceToHost), "felog_batch_read");
+    if (st) return st;
+    if (bar.error) return FELOG_ERR_TIMEOUT;
     const int n = b->n_jobs;
     for (int32_t c = 0; c < n; ++c) {
         const int32_t i = b->position[c];

@@ -66,6 +66,17 @@ struct BArgs {
     double mu;
     float lr0;
     int64_t lr_total_tokens;
+    // ranges of the jobs of dim 32, 64, 128 (jobs are ordered by dim): training
+    // items, minibatch tokens (walk slots times L) and nodes
+    int64_t item_lo[3], item_hi[3], tok_lo[3], tok_hi[3], node_lo[3], node_hi[3];
+};
+
+// Grid-wide barrier of the persistent batched kernel (device memory, zero
+// before a launch): arrivals, generation, and an error word set when a
+// bounded wait ran out.
+struct GridBarrier {
+    unsigned int count, gen;
+    int error, pad;
 };
 
 struct BParams {
@@ -89,6 +100,7 @@ struct BatchPlan {
     void *mem = nullptr;
     size_t bytes = 0;
     size_t o_gst = 0, o_gna = 0, o_gnn = 0, o_gl = 0;  // gather staging
+    size_t o_bar = 0;                                   // grid barrier of the persistent kernel
     BArgs args{};
     std::vector<int64_t> item_prefix;  // host copies
     std::vector<int64_t> slot_prefix, node_prefix;

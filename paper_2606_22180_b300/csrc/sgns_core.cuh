@@ -162,6 +162,10 @@ __device__ __forceinline__ float softplus_neg(float s) {
     return s >= 0.f ? log1pf(__expf(-s)) : -s + log1pf(__expf(s));
 }
 
+// NC: read the alias table through the read-only data cache (right for a
+// kernel that does not write the table; a persistent kernel that rebuilds it
+// every round passes false and reads it through L2).
+template <bool NC = true>
 __device__ __forceinline__ int32_t draw_negative(const uint64_t *__restrict__ thr,
                                                  const int32_t *__restrict__ alias, uint64_t n,
                                                  uint64_t S, uint64_t seed, uint32_t round,
@@ -170,8 +174,9 @@ __device__ __forceinline__ int32_t draw_negative(const uint64_t *__restrict__ th
     const u32x4 r = philox(seed, (q << 8) | k, walk, (round << 16) | pos, kStreamNeg);
     const uint64_t b = mulhi64(lo64(r), n);
     const uint64_t coin = mulhi64(hi64(r), S);
-    const uint64_t t = __ldg(reinterpret_cast<const unsigned long long *>(thr) + b);
-    const int32_t a = __ldg(alias + b);
+    const uint64_t t = NC ? __ldg(reinterpret_cast<const unsigned long long *>(thr) + b)
+                          : __ldcg(reinterpret_cast<const unsigned long long *>(thr) + b);
+    const int32_t a = NC ? __ldg(alias + b) : __ldcg(alias + b);
     // b < n always; an alias outside [0, n) (a damaged table) falls back to b
     return coin < t || static_cast<uint64_t>(static_cast<uint32_t>(a)) >= n ? static_cast<int32_t>(b) : a;
 }
@@ -468,7 +473,7 @@ struct TrainView {
 // lane, coefficients broadcast; updates as atomic deltas (see add_delta).
 // wk (L ints) and negs (2 W K ints) are this warp's shared memory.  Returns
 // this lane's loss in 2^-24 units.
-template <int D, class T, int MAXT, int KFIX>
+template <int D, class T, int MAXT, int KFIX, bool NC = true>
 __device__ __forceinline__ long long fw_train_walk(const TrainView<T> &a, const int32_t *__restrict__ row,
                                                    int64_t wi, int32_t *wk, int32_t *negs) {
     constexpr int EPL = D / 32;
@@ -491,7 +496,7 @@ __device__ __forceinline__ long long fw_train_walk(const TrainView<T> &a, const 
         // all negatives of this center, lane-parallel
         for (int idx = lane; idx < 2 * W * K; idx += 32) {
             const int q = idx / K, k = idx - q * K;
-            negs[idx] = draw_negative(a.thr, a.alias, n, S, a.seed, a.round,
+            negs[idx] = draw_negative<NC>(a.thr, a.alias, n, S, a.seed, a.round,
                                       static_cast<uint32_t>(wi), static_cast<uint32_t>(p),
                                       static_cast<uint32_t>(q), static_cast<uint32_t>(k));
         }
@@ -658,7 +663,7 @@ inline size_t stage_floats(int window, int dim) { return static_cast<size_t>(2 *
 // token clock).  wk (L ints) and negs (2 W K ints) are this warp's shared
 // memory, and with STAGE delta ((2W + 1) * D floats, all zero on entry and
 // on return).  Returns this lane's loss in 2^-24 units.
-template <int D, class T, int KFIX, bool STAGE = false>
+template <int D, class T, int KFIX, bool STAGE = false, bool NC = true>
 __device__ __forceinline__ long long hw_train_walk(const TrainView<T> &a, const int32_t *__restrict__ row,
                                                    int64_t wi, int32_t *wk, int32_t *negs,
                                                    float *delta = nullptr) {
@@ -738,7 +743,7 @@ __device__ __forceinline__ long long hw_train_walk(const TrainView<T> &a, const 
         if (c < 0) continue;
         for (int idx = lane; idx < 2 * W * K; idx += 32) {
             const int q = idx / K, k = idx - q * K;
-            negs[idx] = draw_negative(a.thr, a.alias, n, S, a.seed, a.round,
+            negs[idx] = draw_negative<NC>(a.thr, a.alias, n, S, a.seed, a.round,
                                       static_cast<uint32_t>(wi), static_cast<uint32_t>(p),
                                       static_cast<uint32_t>(q), static_cast<uint32_t>(k));
         }
@@ -1274,7 +1279,7 @@ __device__ __forceinline__ void mark_row(uint32_t *mark, int32_t *list, int32_t 
 // All pairs of center position p of walk wi (row = its L ids); eta is the
 // batch's rate; negs: this warp's 2 W K ints of shared memory.  Returns this
 // lane's share of the loss.
-template <int D, class T, int MAXT>
+template <int D, class T, int MAXT, bool NC = true>
 __device__ __forceinline__ float mb_grad_center(const MbView &a, const int32_t *__restrict__ row, int64_t wi, int p,
                                                 float eta, const T *__restrict__ phi_in,
                                                 const T *__restrict__ phi_out, const MbState &st, int32_t *negs) {
@@ -1288,7 +1293,7 @@ __device__ __forceinline__ float mb_grad_center(const MbView &a, const int32_t *
     if (c < 0) return 0.f;
     for (int idx = lane; idx < 2 * W * K; idx += 32) {
         const int q = idx / K, k = idx - q * K;
-        negs[idx] = draw_negative(a.thr, a.alias, n, a.S, a.seed, a.round, static_cast<uint32_t>(wi),
+        negs[idx] = draw_negative<NC>(a.thr, a.alias, n, a.S, a.seed, a.round, static_cast<uint32_t>(wi),
                                   static_cast<uint32_t>(p), static_cast<uint32_t>(q), static_cast<uint32_t>(k));
     }
     __syncwarp();

@@ -572,8 +572,11 @@ class Batch:
     def step(self):
         _check(self.lib.felog_batch_step(self.handle, _stream()), "felog_batch_step")
 
-    def run(self, use_graph: bool = True):
-        _check(self.lib.felog_batch_run(self.handle, int(use_graph), _stream()), "felog_batch_run")
+    def run(self, use_graph: bool | int = True, persistent: bool = False):
+        """All rounds: ordinary launches (use_graph False), one CUDA graph (True),
+        or one persistent kernel (persistent=True)."""
+        mode = 2 if persistent else int(bool(use_graph))
+        _check(self.lib.felog_batch_run(self.handle, mode, _stream()), "felog_batch_run")
 
     def autotune(self, cache_path: str | None = None) -> dict:
         t = Tuning()

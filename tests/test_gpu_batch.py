@@ -153,19 +153,19 @@ def test_batch_minibatch_equals_solo_bitwise(fl, precision):
     """The deterministic form in the batch (one synchronous batch per round
     and job) gives every job exactly the result of felog_embed alone with a
     minibatch covering the round: tables, |V_a| and loss per round, bit for
-    bit, with feedback deciding a different schedule per job; captured in a
-    CUDA graph or not."""
+    bit, with feedback deciding a different schedule per job; as ordinary
+    launches, captured in a CUDA graph, or as one persistent kernel."""
     gs = _graphs()[:4]
     dgs = [fl.DeviceGraph.from_host(g) for g in gs]
     dims = [64, 128, 32, 128]
     seeds = [31 + 5 * i for i in range(4)]
     tp = fl.train_params(64, W, K, 0.025, 0, fl.FELOG_SGNS_MINIBATCH, 1 << 30, precision)
     fp = fl.feedback_params(True, 0.9, 8, 4, False)
-    for use_graph in (False, True):
+    for use_graph, persistent in ((False, False), (True, False), (False, True)):
         b = fl.Batch(dgs, dims, seeds, L, 1, tp, fp)
         s = torch.cuda.Stream()
         with torch.cuda.stream(s):
-            b.run(use_graph=use_graph)
+            b.run(use_graph=use_graph, persistent=persistent)
         s.synchronize()
         stats, na, loss = b.read()
         for j in range(4):
@@ -176,3 +176,51 @@ def test_batch_minibatch_equals_solo_bitwise(fl, precision):
             assert [float(x) for x in loss[: len(st), j]] == [x["loss"] for x in st], j
             assert torch.equal(b.phi_in[j], pi) and torch.equal(b.phi_out[j], po), j
         b.close()
+
+
+def test_batch_persistent_hogwild(fl, orc):
+    """The persistent kernel in the Hogwild form: the last round's walks and
+    alias tables (rebuilt inside the kernel every round) equal the oracle's,
+    every job runs its rounds, and each job's link AUC is within 0.005 of the
+    same job trained alone (mean of 2 seeds)."""
+    from paper_2606_22180_b300 import evaluate
+
+    gs, splits = [], []
+    for i in range(4):
+        g, _ = inputs.sbm(1000 + 700 * i, 8, 0.04, 0.002, seed=500 + i)
+        sp = inputs.link_split(g, 0.1, i)
+        gs.append(sp.train)
+        splits.append(sp)
+    dgs = [fl.DeviceGraph.from_host(g) for g in gs]
+    dims = [64, 128, 64, 128]
+    for prec in (fl.FELOG_BF16_SR, fl.FELOG_FP32):
+        tp = fl.train_params(64, W, K, 0.025, 0, fl.FELOG_SGNS_HOGWILD, 4096, prec)
+        fp = fl.feedback_params(False, 0.65, 8, 6, False)
+        diffs = np.zeros((2, 4))
+        for rep in range(2):
+            seeds = [9 + i + 100 * rep for i in range(4)]
+            b = fl.Batch(dgs, dims, seeds, L, 1, tp, fp)
+            s = torch.cuda.Stream()
+            with torch.cuda.stream(s):
+                b.run(persistent=True)
+            s.synchronize()
+            stats, na, loss = b.read()
+            for j, g in enumerate(gs):
+                live_ids = np.nonzero(g.degrees() > 0)[0].astype(np.int32)
+                live = live_ids.shape[0]
+                assert stats[j]["rounds"] == 6 and stats[j]["tokens"] == 6 * live * L
+                assert np.all(np.isfinite(loss[:, j]))
+                ref = orc.walk(g.offsets, g.cols, live_ids, L, 1, seeds[j], 5)  # feedback off: all live nodes
+                assert np.array_equal(b.job_walks(j, live).cpu().numpy(), ref), j
+                thr, alias, _ = b.job_table(j)
+                _, thr_r, alias_r, _ = orc.noise_table(orc.counts(ref, g.n))
+                assert np.array_equal(thr.cpu().numpy().astype(np.uint64), thr_r), j
+                assert np.array_equal(alias.cpu().numpy(), alias_r), j
+                tpj = fl.train_params(dims[j], W, K, 0.025, 0, fl.FELOG_SGNS_HOGWILD, 4096, prec)
+                solo, _, _ = fl.felog_embed(dgs[j], L, 1, tpj, fp, seeds[j])
+                diffs[rep, j] = (evaluate.link_auc(b.phi_in[j], splits[j].pos, splits[j].neg)
+                                 - evaluate.link_auc(solo, splits[j].pos, splits[j].neg))
+            b.close()
+        per_job = diffs.mean(0)
+        print("persistent - solo AUC per job:", prec, np.round(per_job, 4))
+        assert np.all(np.abs(per_job) <= 0.005), per_job
