@@ -546,7 +546,7 @@ def run_native(args):
 BATCH_L, BATCH_W, BATCH_K, BATCH_ROUNDS = 40, 5, 5, 10
 
 
-def run_batch(fl, jobs=512, n_hi=200000, warmup=1, steps=1, autotune=True, seed=3):
+def run_batch(fl, jobs=512, n_hi=200000, warmup=1, steps=1, autotune=True, seed=3, persistent=True):
     """The batching workload: `jobs` graphs (half planted partitions with
     4..32 communities, half R-MAT), node counts log-uniform in [1e3, n_hi],
     average degree 8..32, d in {64, 128}, bf16 tables, 10 walks per node of
@@ -567,25 +567,33 @@ def run_batch(fl, jobs=512, n_hi=200000, warmup=1, steps=1, autotune=True, seed=
     os.makedirs(os.path.join(ROOT, "_build"), exist_ok=True)
     tuning = b.autotune(os.path.join(ROOT, "_build", "felog_tune.txt")) if autotune else None
     stream = torch.cuda.Stream()
-    with torch.cuda.stream(stream):
-        for _ in range(warmup):
-            b.run(use_graph=True)
+
+    def timed(persistent):
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                b.run(use_graph=True, persistent=persistent)
+            stream.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                b.run(use_graph=True, persistent=persistent)
+            e1.record(stream)
         stream.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(steps):
-            b.run(use_graph=True)
-        e1.record(stream)
-    stream.synchronize()
-    ms = e0.elapsed_time(e1) / steps
-    stats, na, _ = b.read()
-    tokens = sum(s["tokens"] for s in stats)
+        ms = e0.elapsed_time(e1) / steps
+        stats, _, _ = b.read()
+        return ms, sum(s["tokens"] for s in stats)
+
+    ms, tokens = timed(False)
     out = {"workload": f"{jobs} graphs (SBM/R-MAT), |V| log-uniform [1e3, {n_hi}], deg 8-32, d 64/128 bf16, "
                        f"L={BATCH_L}, {BATCH_ROUNDS} rounds, w={BATCH_W}, K={BATCH_K}",
            "nodes": int(sum(g.n for g, _ in mix)), "tokens_per_run": int(tokens),
            "ms_per_run": ms, "tokens_per_s": tokens / (ms / 1e3), "launch": "one CUDA graph per run",
            "warmup_runs": warmup, "timed_runs": steps, "tuning": tuning, "graph_gen_s": gen_s,
            "device_bytes": b.device_bytes()}
+    if persistent:
+        pms, ptok = timed(True)
+        out["persistent"] = {"launch": "one persistent kernel per run (all rounds, grid-wide barriers)",
+                             "ms_per_run": pms, "tokens_per_run": int(ptok), "tokens_per_s": ptok / (pms / 1e3)}
     b.close()
     return out
 
