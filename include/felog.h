@@ -464,9 +464,24 @@ felog_status felog_batch_step(felog_batch *b, void *stream);
  * rounds (every phase of every job, separated by grid-wide barriers; a
  * cooperative launch of as many blocks as can be resident, the trainer in
  * its two-pairs-per-warp shape).  Every form computes the same values.  A
- * barrier gives up after about a minute without progress; felog_batch_read
- * then returns FELOG_ERR_TIMEOUT. */
+ * barrier wait gives up once it has waited the batch's wait limit (60 s
+ * unless felog_batch_set_wait_limit says otherwise); every block then leaves
+ * at its next barrier and felog_batch_read returns FELOG_ERR_TIMEOUT. */
 felog_status felog_batch_run(felog_batch *b, int32_t use_graph, void *stream);
+/* budget of each grid-barrier wait of the persistent form, in seconds of the
+ * GPU's global timer; 0 < seconds <= 3600, else FELOG_ERR_INVALID_ARG.  It
+ * must exceed the longest phase (a round's training of every job). */
+felog_status felog_batch_set_wait_limit(felog_batch *b, double seconds);
+/* Check of the persistent form's grid barrier on its own: a cooperative
+ * launch of as many blocks as can be resident passes `passes` (1..1024)
+ * barriers that each expect `phantom` (0..1024) arrivals more than there are
+ * blocks.  phantom = 0: returns FELOG_OK and *where = -1.  phantom > 0: the
+ * first barrier never releases, every wait gives up after `seconds`
+ * (0 < seconds <= 60) and the call returns FELOG_ERR_TIMEOUT with *where = 0,
+ * the index of the barrier that ran out; the context stays usable.  Allocates
+ * 16 bytes stream-ordered and synchronises `stream`. */
+felog_status felog_grid_barrier_check(int32_t phantom, int32_t passes, double seconds, int32_t *where,
+                                      void *stream);
 /* synchronises `stream`; stats [n_jobs] (caller order), per-round |V_a| and
  * loss [max_rounds][n_jobs] (each may be NULL) */
 felog_status felog_batch_read(felog_batch *b, felog_job_stats *stats, int32_t *rec_n_active,

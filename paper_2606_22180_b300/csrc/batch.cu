@@ -562,31 +562,45 @@ __global__ void k_b_round_end(BArgs a) { ph_round_end(a, blockIdx.x, gridDim.x);
 // One persistent kernel for a whole run: every phase of every round of every
 // job, the phases separated by a grid-wide barrier.  The grid is launched
 // cooperatively (all blocks resident), so a barrier only waits for blocks
-// that are running; each wait is still bounded (kGridWaitLimit polls about a
-// microsecond apart, over a minute), after which the error word is set and
-// every block returns at its next barrier.  Phase data written by other
-// blocks is read after the barrier's release/acquire fences; the alias
-// table, rebuilt every round, is read through L2 rather than the read-only
-// cache (NC = false), which a kernel only refreshes at its launch.
+// that are running.  Each wait is still bounded: it gives up once the
+// nanosecond global timer has advanced by the run's budget (60 s unless the
+// caller sets another), or after kGridPollLimit polls about a microsecond
+// apart, whichever comes first; it then sets the error word (and the tag of
+// the barrier) and every block returns at its next barrier.  Phase data
+// written by other blocks is read after the barrier's release/acquire
+// fences; the alias table, rebuilt every round, is read through L2 rather
+// than the read-only cache (NC = false), which a kernel only refreshes at
+// its launch.
 // ---------------------------------------------------------------------------
-constexpr unsigned kGridWaitLimit = 1u << 26;
+constexpr unsigned kGridPollLimit = 1u << 31;
+constexpr double kDefaultGridWaitS = 60.0;
 
-__device__ __forceinline__ bool grid_sync(GridBarrier *bar) {
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// `expected` arrivals release the barrier (gridDim.x in the persistent
+// kernel); returns false once any wait of this barrier has run out.
+__device__ __forceinline__ bool grid_sync(GridBarrier *bar, unsigned expected, unsigned long long budget_ns,
+                                          int tag) {
     __syncthreads();
     if (threadIdx.x == 0) {
         volatile unsigned *vgen = &bar->gen;
         volatile int *verr = &bar->error;
         const unsigned g0 = *vgen;
         __threadfence();
-        if (atomicAdd(&bar->count, 1u) == gridDim.x - 1) {
+        if (atomicAdd(&bar->count, 1u) == expected - 1) {
             bar->count = 0;  // every block has arrived: reset, then release them
             __threadfence();
             atomicAdd(&bar->gen, 1u);
         } else {
+            const unsigned long long t0 = global_ns();
             unsigned it = 0;
             while (*vgen == g0 && !*verr) {
-                if (++it > kGridWaitLimit) {
-                    atomicExch(&bar->error, 1);
+                if (++it > kGridPollLimit || global_ns() - t0 > budget_ns) {
+                    if (atomicCAS(&bar->error, 0, 1) == 0) bar->where = tag;
                     break;
                 }
                 __nanosleep(1000);
@@ -599,35 +613,39 @@ __device__ __forceinline__ bool grid_sync(GridBarrier *bar) {
 }
 
 template <class T, int KFIX, bool MB>
-__global__ void __launch_bounds__(kBThreads, 2) k_b_persistent(BArgs a, GridBarrier *bar) {
+__global__ void __launch_bounds__(kBThreads, 2)
+    k_b_persistent(BArgs a, GridBarrier *bar, unsigned long long budget_ns) {
     const int b = blockIdx.x, g = gridDim.x;
+    int tag = 0;
+    auto sync = [&]() { return grid_sync(bar, gridDim.x, budget_ns, tag++); };
     for (int r = 0; r < a.max_rounds; ++r) {
+        tag = 16 * r;
         ph_compact_count(a, b, g);
-        if (!grid_sync(bar)) return;
+        if (!sync()) return;
         ph_compact_scan(a, b, g);
-        if (!grid_sync(bar)) return;
+        if (!sync()) return;
         ph_compact_scatter(a, b, g);
-        if (!grid_sync(bar)) return;
+        if (!sync()) return;
         if (a.L % 4 == 0) ph_walk<true>(a, b, g);
         else ph_walk<false>(a, b, g);
-        if (!grid_sync(bar)) return;
+        if (!sync()) return;
         ph_noise_max(a, b, g);
-        if (!grid_sync(bar)) return;
+        if (!sync()) return;
         ph_noise_weights(a, b, g);
-        if (!grid_sync(bar)) return;
+        if (!sync()) return;
         ph_noise_agg(a, b, g);
-        if (!grid_sync(bar)) return;
+        if (!sync()) return;
         ph_noise_scan(a, b, g);
-        if (!grid_sync(bar)) return;
+        if (!sync()) return;
         ph_noise_scatter(a, b, g);
-        if (!grid_sync(bar)) return;
+        if (!sync()) return;
         ph_noise_finish(a, b, g);
-        if (!grid_sync(bar)) return;
+        if (!sync()) return;
         if constexpr (MB) {
             ph_mb_grad<32, T, false>(a, a.tok_lo[0], a.tok_hi[0], b, g);
             ph_mb_grad<64, T, false>(a, a.tok_lo[1], a.tok_hi[1], b, g);
             ph_mb_grad<128, T, false>(a, a.tok_lo[2], a.tok_hi[2], b, g);
-            if (!grid_sync(bar)) return;
+            if (!sync()) return;
             ph_mb_apply<32, T>(a, a.node_lo[0], a.node_hi[0], b, g);
             ph_mb_apply<64, T>(a, a.node_lo[1], a.node_hi[1], b, g);
             ph_mb_apply<128, T>(a, a.node_lo[2], a.node_hi[2], b, g);
@@ -636,12 +654,22 @@ __global__ void __launch_bounds__(kBThreads, 2) k_b_persistent(BArgs a, GridBarr
             ph_sgns<64, T, KFIX, 2, false>(a, a.item_lo[1], a.item_hi[1], b, g);
             ph_sgns<128, T, KFIX, 2, false>(a, a.item_lo[2], a.item_hi[2], b, g);
         }
-        if (!grid_sync(bar)) return;
+        if (!sync()) return;
         ph_feedback<T>(a, b, g);
-        if (!grid_sync(bar)) return;
+        if (!sync()) return;
         ph_round_end(a, b, g);
-        if (!grid_sync(bar)) return;
+        if (!sync()) return;
     }
+}
+
+// The persistent kernel's barrier on its own: `passes` barriers of a
+// resident grid that expects `phantom` arrivals more than it has blocks.
+// With phantom = 0 every barrier releases; with phantom > 0 the first one
+// never does, and every wait runs out after budget_ns.
+__global__ void __launch_bounds__(kBThreads) k_grid_barrier_check(GridBarrier *bar, unsigned phantom, int passes,
+                                                                   unsigned long long budget_ns) {
+    for (int k = 0; k < passes; ++k)
+        if (!grid_sync(bar, gridDim.x + phantom, budget_ns, k)) return;
 }
 
 // gathers every job's state and round records into contiguous arrays
@@ -1051,6 +1079,7 @@ struct felog_batch {
     HostTuning tune;
     cudaGraphExec_t graph = nullptr;
     int graph_rounds = -1;
+    double wait_s = kDefaultGridWaitS;  // budget of each grid-barrier wait (persistent form)
 };
 
 namespace {
@@ -1174,6 +1203,8 @@ namespace {
 
 // All rounds of every job in one cooperative launch of k_b_persistent (after
 // the usual reset).  The grid is as many blocks as can be resident.
+unsigned long long wait_budget_ns(double seconds) { return static_cast<unsigned long long>(seconds * 1e9); }
+
 template <class T>
 felog_status launch_persistent(felog_batch *b, cudaStream_t s) {
     const BatchPlan &plan = b->plan;
@@ -1182,8 +1213,8 @@ felog_status launch_persistent(felog_batch *b, cudaStream_t s) {
     felog_status st = record_cuda_error(cudaMemsetAsync(bar, 0, sizeof(GridBarrier), s), "persistent");
     if (st) return st;
     const bool mb = p.mode == FELOG_SGNS_MINIBATCH;
-    void (*kern)(BArgs, GridBarrier *) = mb ? k_b_persistent<T, 0, true>
-                                            : (p.K == 5 ? k_b_persistent<T, 5, false> : k_b_persistent<T, 0, false>);
+    void (*kern)(BArgs, GridBarrier *, unsigned long long) =
+        mb ? k_b_persistent<T, 0, true> : (p.K == 5 ? k_b_persistent<T, 5, false> : k_b_persistent<T, 0, false>);
     const size_t smem = sizeof(int32_t) * kWarps * (p.L + 2 * p.window * p.K);
     if (smem > 48 * 1024) {
         st = record_cuda_error(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1204,7 +1235,8 @@ felog_status launch_persistent(felog_batch *b, cudaStream_t s) {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return record_cuda_error(cudaLaunchKernelEx(&cfg, kern, plan.args, bar), "persistent launch");
+    return record_cuda_error(cudaLaunchKernelEx(&cfg, kern, plan.args, bar, wait_budget_ns(b->wait_s)),
+                             "persistent launch");
 }
 
 }  // namespace
@@ -1241,6 +1273,53 @@ extern "C" felog_status felog_batch_run(felog_batch *b, int32_t use_graph, void 
         b->graph_rounds = R;
     }
     return record_cuda_error(cudaGraphLaunch(b->graph, s), "graph launch");
+}
+
+extern "C" felog_status felog_batch_set_wait_limit(felog_batch *b, double seconds) {
+    if (!b || !(seconds > 0.0) || seconds > 3600.0) return FELOG_ERR_INVALID_ARG;
+    b->wait_s = seconds;
+    return FELOG_OK;
+}
+
+extern "C" felog_status felog_grid_barrier_check(int32_t phantom, int32_t passes, double seconds,
+                                                 int32_t *where, void *stream) {
+    if (phantom < 0 || phantom > 1024 || passes < 1 || passes > 1024 || !(seconds > 0.0) || seconds > 60.0)
+        return FELOG_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    GridBarrier *bar = nullptr;
+    felog_status st = record_cuda_error(cudaMallocAsync(&bar, sizeof(GridBarrier), s), "felog_grid_barrier_check");
+    if (st) return st;
+    st = record_cuda_error(cudaMemsetAsync(bar, 0, sizeof(GridBarrier), s), "felog_grid_barrier_check");
+    int per_sm = 0;
+    if (!st)
+        st = record_cuda_error(
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid_barrier_check, kBThreads, 0),
+            "felog_grid_barrier_check");
+    if (!st && per_sm < 1) st = FELOG_ERR_UNSUPPORTED;
+    if (!st) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(static_cast<unsigned>(per_sm * sm_count()));
+        cfg.blockDim = dim3(kBThreads);
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        st = record_cuda_error(cudaLaunchKernelEx(&cfg, k_grid_barrier_check, bar, static_cast<unsigned>(phantom),
+                                                  static_cast<int>(passes), wait_budget_ns(seconds)),
+                               "felog_grid_barrier_check");
+    }
+    GridBarrier h{};
+    if (!st)
+        st = record_cuda_error(cudaMemcpyAsync(&h, bar, sizeof h, cudaMemcpyDeviceToHost, s),
+                               "felog_grid_barrier_check");
+    felog_status st2 = record_cuda_error(cudaFreeAsync(bar, s), "felog_grid_barrier_check");
+    if (!st) st = record_cuda_error(cudaStreamSynchronize(s), "felog_grid_barrier_check");
+    if (st) return st;
+    if (st2) return st2;
+    if (where) *where = h.error ? h.where : -1;
+    return h.error ? FELOG_ERR_TIMEOUT : FELOG_OK;
 }
 
 extern "C" felog_status felog_batch_read(felog_batch *b, felog_job_stats *stats, int32_t *rec_n_active,

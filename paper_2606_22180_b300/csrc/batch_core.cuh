@@ -72,11 +72,12 @@ struct BArgs {
 };
 
 // Grid-wide barrier of the persistent batched kernel (device memory, zero
-// before a launch): arrivals, generation, and an error word set when a
-// bounded wait ran out.
+// before a launch): arrivals, generation, an error word set when a bounded
+// wait ran out, and the tag of the barrier where that happened (phase index
+// + 16 * round for the persistent kernel).
 struct GridBarrier {
     unsigned int count, gen;
-    int error, pad;
+    int error, where;
 };
 
 struct BParams {

@@ -16,6 +16,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libfelog.so")
 
 FELOG_OK = 0
+FELOG_ERR_TIMEOUT = 6
 FELOG_SGNS_HOGWILD, FELOG_SGNS_MINIBATCH, FELOG_SGNS_TILE = 0, 1, 2
 FELOG_FP32, FELOG_BF16_SR = 0, 1
 
@@ -37,7 +38,7 @@ SYMBOLS = [
     "felog_fabc_encode", "felog_fabc_decode",
     "felog_batch_create", "felog_batch_destroy", "felog_batch_device_bytes", "felog_batch_reset",
     "felog_batch_step", "felog_batch_run", "felog_batch_read", "felog_batch_job_buffers",
-    "felog_batch_autotune",
+    "felog_batch_autotune", "felog_batch_set_wait_limit", "felog_grid_barrier_check",
     "felog_server_create", "felog_server_destroy", "felog_server_now", "felog_server_job_bytes",
     "felog_server_submit", "felog_server_poll", "felog_server_wait", "felog_server_fetch",
     "felog_server_drain", "felog_server_get_stats",
@@ -132,6 +133,8 @@ def load() -> ctypes.CDLL:
         "felog_batch_read": (st, [P, P, P, P, P]),
         "felog_batch_job_buffers": (st, [P, i32, P]),
         "felog_batch_autotune": (st, [P, ctypes.c_char_p, P, P]),
+        "felog_batch_set_wait_limit": (st, [P, f64]),
+        "felog_grid_barrier_check": (st, [i32, i32, f64, P, P]),
         "felog_server_create": (st, [P, P]),
         "felog_server_destroy": (st, [P]),
         "felog_server_now": (f64, [P]),
@@ -231,6 +234,21 @@ def felog_validate_csr(g: DeviceGraph, starts: torch.Tensor | None = None,
     _check(lib.felog_validate_csr(ctypes.byref(csr), _ptr(starts), n_starts, _ptr(status), _stream()),
            "felog_validate_csr")
     return status
+
+
+def felog_grid_barrier_check(phantom: int = 0, passes: int = 1, seconds: float = 1.0) -> tuple[int, int]:
+    """The persistent batched kernel's grid barrier on its own (see felog.h):
+    returns (status, where); status is FELOG_OK or FELOG_ERR_TIMEOUT, and
+    where the index of the barrier whose wait ran out (-1 if none).  Other
+    statuses raise."""
+    if not torch.cuda.is_available():
+        raise FelogError("no CUDA device: the FeLoG path has no CPU fallback")
+    lib = load()
+    where = ctypes.c_int32(-2)
+    st = lib.felog_grid_barrier_check(int(phantom), int(passes), float(seconds), ctypes.byref(where), _stream())
+    if st not in (FELOG_OK, FELOG_ERR_TIMEOUT):
+        _check(st, "felog_grid_barrier_check")
+    return int(st), int(where.value)
 
 
 def felog_compact_active(active: torch.Tensor):
@@ -577,6 +595,10 @@ class Batch:
         or one persistent kernel (persistent=True)."""
         mode = 2 if persistent else int(bool(use_graph))
         _check(self.lib.felog_batch_run(self.handle, mode, _stream()), "felog_batch_run")
+
+    def set_wait_limit(self, seconds: float):
+        """Budget of each grid-barrier wait of the persistent form."""
+        _check(self.lib.felog_batch_set_wait_limit(self.handle, float(seconds)), "felog_batch_set_wait_limit")
 
     def autotune(self, cache_path: str | None = None) -> dict:
         t = Tuning()

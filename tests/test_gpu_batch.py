@@ -224,3 +224,40 @@ def test_batch_persistent_hogwild(fl, orc):
         per_job = diffs.mean(0)
         print("persistent - solo AUC per job:", prec, np.round(per_job, 4))
         assert np.all(np.abs(per_job) <= 0.005), per_job
+
+
+def test_grid_barrier_wait_runs_out_and_reports(fl):
+    """The persistent kernel's grid barrier: with every block arriving it
+    releases; with one phantom arrival that nothing provides, every wait gives
+    up after its budget, the call reports FELOG_ERR_TIMEOUT at barrier 0, and
+    the context stays usable (a barrier check and a persistent batch run
+    afterwards succeed).  No wait is unbounded."""
+    import time
+
+    st, where = fl.felog_grid_barrier_check(0, 64, 5.0)
+    assert (st, where) == (fl.FELOG_OK, -1)
+    t0 = time.perf_counter()
+    st, where = fl.felog_grid_barrier_check(1, 4, 0.05)
+    elapsed = time.perf_counter() - t0
+    assert (st, where) == (fl.FELOG_ERR_TIMEOUT, 0)
+    assert elapsed < 5.0
+    st, where = fl.felog_grid_barrier_check(0, 8, 5.0)
+    assert (st, where) == (fl.FELOG_OK, -1)
+    with pytest.raises(fl.FelogError):
+        fl.felog_grid_barrier_check(0, 1, 0.0)
+
+    g, _ = inputs.sbm(1200, 8, 0.04, 0.002, seed=77)
+    dg = fl.DeviceGraph.from_host(g)
+    tp = fl.train_params(64, W, K, 0.025, 0, fl.FELOG_SGNS_HOGWILD, 4096, fl.FELOG_FP32)
+    fp = fl.feedback_params(False, 0.65, 8, 2, False)
+    b = fl.Batch([dg], [64], [3], L, 1, tp, fp)
+    with pytest.raises(fl.FelogError):
+        b.set_wait_limit(-1.0)
+    b.set_wait_limit(30.0)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        b.run(persistent=True)
+    s.synchronize()
+    stats, _, _ = b.read()
+    assert stats[0]["rounds"] == 2
+    b.close()
