@@ -66,6 +66,8 @@ def _args():
     p.add_argument("--duration", type=float, default=20.0, help="serve mode: seconds of arrivals")
     p.add_argument("--max-nodes", type=int, default=1 << 16, help="serve mode: largest job in nodes")
     p.add_argument("--no-forms", action="store_true", help="round mode: skip the small batch/serve runs")
+    p.add_argument("--no-persistent", action="store_true",
+                   help="batch mode: time only the CUDA-graph launch form, not the persistent kernel")
     p.add_argument("--precision", default="fp32", choices=["fp32", "bf16"],
                    help="table precision of the timed rounds (fp32 = the plain form)")
     return p.parse_args()
@@ -268,7 +270,7 @@ def _sgns_kernel_name(form, precision):
     t = "float" if precision == "fp32" else "bf16"
     if form == 1:
         return f"k_sgns_hogwild<128,{t},8,5>"
-    if form == 4:
+    if form == 4 or (form == 0 and t == "bf16"):  # the automatic form for bf16 tables of dim 128
         return f"k_sgns_hogwild_pf<128,{t},5>"
     staged = form == 3
     return f"k_sgns_hogwild_hw<128,{t},5,{'true' if staged else 'false'}>"
@@ -894,8 +896,9 @@ def _tile_rounds(fl, dg, T, steps, warmup, scale, ctas):
 
 def _quality(fl, evaluate, dg, split, n_live, form=0, stage_flush=0):
     """Full runs of Algorithm 1: plain (feedback off, fp32, the timed rounds'
-    Hogwild form) and chosen (feedback mu = 0.65, bf16 with stochastic
-    rounding); AUC on the held-out edges, wall time of the felog_embed call."""
+    Hogwild form), plain_bf16 (the same in bf16 with stochastic rounding) and
+    chosen (feedback mu = 0.65, bf16 with stochastic rounding, the automatic
+    form); AUC on the held-out edges, wall time of the felog_embed call."""
     import torch
 
     out = {}
@@ -904,6 +907,9 @@ def _quality(fl, evaluate, dg, split, n_live, form=0, stage_flush=0):
         "plain": (fl.train_params(DIM, WINDOW, NEG, LR0, T, fl.FELOG_SGNS_HOGWILD, 4096, fl.FELOG_FP32,
                                   0, form, stage_flush=stage_flush),
                   fl.feedback_params(False, MU, KS, ROUNDS, False)),
+        "plain_bf16": (fl.train_params(DIM, WINDOW, NEG, LR0, T, fl.FELOG_SGNS_HOGWILD, 4096, fl.FELOG_BF16_SR,
+                                       0, form, stage_flush=stage_flush),
+                       fl.feedback_params(False, MU, KS, ROUNDS, False)),
         "chosen": (fl.train_params(DIM, WINDOW, NEG, LR0, T, fl.FELOG_SGNS_HOGWILD, 4096, fl.FELOG_BF16_SR),
                    fl.feedback_params(True, MU, KS, ROUNDS, False)),
         "tile": (fl.train_params(DIM, WINDOW, NEG, LR0, T, fl.FELOG_SGNS_TILE, 1, fl.FELOG_BF16_SR,
@@ -1056,7 +1062,7 @@ def run_form(args):
                 "data": "synthetic (seeded R-MAT graph; no dataset)", "config": {"workload": r["workload"]},
                 "tile_form": r}
     elif args.mode == "batch":
-        r = run_batch(fl, jobs=args.jobs, warmup=1, steps=1)
+        r = run_batch(fl, jobs=args.jobs, warmup=1, steps=1, persistent=not args.no_persistent)
         line = {"metric": "SGNS tokens/s, batching form", "value": r["tokens_per_s"], "unit": "tokens/s",
                 "n_gpus": 1, "higher_is_better": True, "dtype": "bf16 tables, f32 math",
                 "data": "synthetic (seeded SBM/R-MAT mix)", "config": {"workload": r["workload"]}, "batching": r}

@@ -19,6 +19,15 @@ def fl():
     return felog
 
 
+# (name, precision: 0 float / 1 bf16-SR, hogwild_form, dim).  Form 0 is the
+# automatic choice: form 2 at dim 64, and for bf16 at dim 128 the prefetching
+# form 4, which needs 16-byte row chunks per lane (float dim 64/128, bf16 dim
+# 128); the bf16 forms at dim 128 are held to the dim-128 oracle.
+FORMS = [("hogwild", 0, 0, DIM), ("bf16", 1, 0, DIM), ("staged", 0, 3, DIM), ("staged_bf16", 1, 3, DIM),
+         ("prefetch", 0, 4, DIM), ("prefetch_128", 0, 4, 128), ("prefetch_bf16", 1, 0, 128),
+         ("bf16_128", 1, 2, 128)]
+
+
 @pytest.fixture(scope="module")
 def runs(fl, orc):
     from paper_2606_22180_b300 import evaluate
@@ -28,15 +37,15 @@ def runs(fl, orc):
         g, _ = inputs.workload_sbm1000(seed)
         sp = inputs.link_split(g, 0.1, seed)
         tr = sp.train
-        ri, _, _ = orc.embed(tr.offsets, tr.cols, L, 1, DIM, W, K, 0.025, False, 0.65, 8, R, False, seed)
-        a_or = orc.link_auc(ri, sp.pos, sp.neg)
+        out = {}
+        for d in (DIM, 128):
+            ri, _, _ = orc.embed(tr.offsets, tr.cols, L, 1, d, W, K, 0.025, False, 0.65, 8, R, False, seed)
+            out[f"oracle{d}"] = orc.link_auc(ri, sp.pos, sp.neg)
+        out["oracle"] = out[f"oracle{DIM}"]
         dg = fl.DeviceGraph.from_host(tr)
         fp = fl.feedback_params(False, 0.65, 8, R, False)
-        out = {"oracle": a_or}
-        for name, prec, form in [("hogwild", fl.FELOG_FP32, 0), ("bf16", fl.FELOG_BF16_SR, 0),
-                                 ("staged", fl.FELOG_FP32, 3), ("staged_bf16", fl.FELOG_BF16_SR, 3),
-                                 ("prefetch", fl.FELOG_FP32, 4), ("prefetch_bf16", fl.FELOG_BF16_SR, 4)]:
-            tp = fl.train_params(DIM, W, K, 0.025, 0, fl.FELOG_SGNS_HOGWILD, 4096, prec, hogwild_form=form)
+        for name, prec, form, d in FORMS:
+            tp = fl.train_params(d, W, K, 0.025, 0, fl.FELOG_SGNS_HOGWILD, 4096, prec, hogwild_form=form)
             pi, _, _ = fl.felog_embed(dg, L, 1, tp, fp, seed)
             out[name] = evaluate.link_auc(pi, sp.pos, sp.neg)
         # tile form: 3 rounds, 128 shared negatives on both sides (the serial
@@ -65,13 +74,15 @@ def test_bf16_auc_within_tolerance_of_serial_oracle(runs):
     assert abs(d.mean()) <= 0.005
 
 
-@pytest.mark.parametrize("form", ["staged", "staged_bf16", "prefetch", "prefetch_bf16"])
+@pytest.mark.parametrize("form", ["staged", "staged_bf16", "prefetch", "prefetch_128", "prefetch_bf16",
+                                  "bf16_128"])
 def test_other_hogwild_forms_auc_within_tolerance_of_serial_oracle(runs, form):
     """The staged form (window phi_in increments summed in shared memory and
     added when a position leaves the window) and the prefetching form (rows of
     the next step copied to shared memory during this one) keep the per-pair
-    estimator."""
-    d = np.array([r[form] - r["oracle"] for r in runs])
+    estimator.  Each is held to the oracle of its own dimension."""
+    dim = next(f[3] for f in FORMS if f[0] == form)
+    d = np.array([r[form] - r[f"oracle{dim}"] for r in runs])
     print(f"{form} - oracle AUC per seed:", d.round(4))
     assert abs(d.mean()) <= 0.005
 
