@@ -441,7 +441,10 @@ typedef struct {
     int32_t feedback_blocks_per_sm; /* Psi blocks per SM */
     int32_t from_cache;             /* 1 when read from the cache file */
     int32_t sgns_form;              /* trainer shape: 2 = two pairs per warp, 16 lanes per row;
-                                       1 = one pair per warp, 32 lanes per row */
+                                       1 = one pair per warp, 32 lanes per row; 4 = shape 2 with
+                                       each step's rows copied to shared memory one step ahead
+                                       (jobs whose rows give a lane 16 bytes: float dim 64/128,
+                                       bf16 dim 128; other jobs run shape 2) */
 } felog_tuning;
 
 typedef struct felog_batch felog_batch;
@@ -488,13 +491,19 @@ felog_status felog_grid_barrier_check(int32_t phantom, int32_t passes, double se
 felog_status felog_batch_read(felog_batch *b, felog_job_stats *stats, int32_t *rec_n_active,
                               double *rec_loss, void *stream);
 felog_status felog_batch_job_buffers(const felog_batch *b, int32_t job, felog_job_buffers *out);
-/* times the walk kernel's block size, the trainer's shape (pairs per warp and
- * lanes per row: felog_tuning.sgns_form) with its resident blocks per SM
- * (HOGWILD mode), and Psi blocks per SM, each on round 0, and keeps the
- * fastest; shapes that would change the estimator (the staged form) are not
- * tried.  cache_path (may be NULL) is a text file of earlier results keyed
- * by GPU name and batch shape.  Leaves the batch reset. */
+/* times the walk kernel's block size, the trainer's shape (pairs per warp,
+ * lanes per row, rows prefetched or not: felog_tuning.sgns_form) with its
+ * resident blocks per SM (HOGWILD mode), and Psi blocks per SM, each on
+ * round 0, and keeps the fastest; shapes that would change the estimator
+ * (the staged form) are not tried.  cache_path (may be NULL) is a text file
+ * of earlier results keyed by GPU name and batch shape.  Leaves the batch
+ * reset. */
 felog_status felog_batch_autotune(felog_batch *b, const char *cache_path, felog_tuning *out, void *stream);
+/* sets the launch shapes (from_cache ignored): walk_block a multiple of 32
+ * in [32, 1024], sgns_blocks_per_sm 1..8, feedback_blocks_per_sm 1..32,
+ * sgns_form 1, 2 or 4; else FELOG_ERR_INVALID_ARG.  Values are unchanged by
+ * any shape. */
+felog_status felog_batch_set_tuning(felog_batch *b, const felog_tuning *t);
 
 /* ------------------------------------------------------------------------
  * Serving form: a request loop over embedding jobs with continuous batching.

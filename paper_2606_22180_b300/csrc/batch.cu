@@ -405,13 +405,25 @@ __global__ void k_b_noise_finish(BArgs a) { ph_noise_finish(a, blockIdx.x, gridD
 // SGNS over training items of the jobs whose dim is D
 // ---------------------------------------------------------------------------
 // FORM 2: two pairs per warp (a half warp each, 16 lanes per row); FORM 1:
-// one pair per warp (32 lanes per row).  Same estimator, different shapes.
+// one pair per warp (32 lanes per row); FORM 4: FORM 2 with each step's rows
+// copied to shared memory one step ahead (cp.async; tables whose rows give a
+// lane 16 bytes: float dim 64/128, bf16 dim 128).  Same estimator, different
+// shapes.
 template <int D, class T, int KFIX, int FORM, bool NC>
 __device__ __forceinline__ void ph_sgns(const BArgs &a, int64_t item_lo, int64_t item_hi, int b, int g) {
-    extern __shared__ int32_t smem[];
+    extern __shared__ __align__(16) int32_t smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int K = KFIX > 0 ? KFIX : a.K;
-    int32_t *wk = smem + wib * (a.L + 2 * a.window * K);
+    int32_t *wk;
+    char *rows = nullptr;
+    if constexpr (FORM == 4) {
+        char *base = reinterpret_cast<char *>(smem) +
+                     wib * pf_bytes_per_warp(a.L, a.window, K, D, static_cast<int>(sizeof(T)));
+        wk = reinterpret_cast<int32_t *>(base);
+        rows = base + 4 * ((a.L + 2 * a.window * K + 3) & ~3);
+    } else {
+        wk = smem + wib * (a.L + 2 * a.window * K);
+    }
     int32_t *negs = wk + a.L;
     const int64_t warps = static_cast<int64_t>(g) * kWarps;
     for (int64_t it = item_lo + static_cast<int64_t>(b) * kWarps + wib; it < item_hi; it += warps) {
@@ -428,6 +440,8 @@ __device__ __forceinline__ void ph_sgns(const BArgs &a, int64_t item_lo, int64_t
         for (int64_t wl = it - a.item_prefix[j]; wl < walks; wl += c_j) {
             if constexpr (FORM == 1)
                 loss_fx += fw_train_walk<D, T, 8, KFIX, NC>(v, jb.walks + wl * a.L, wl, wk, negs);
+            else if constexpr (FORM == 4)
+                loss_fx += hw_train_walk_pf<D, T, KFIX>(v, jb.walks + wl * a.L, wl, wk, negs, rows);
             else
                 loss_fx += hw_train_walk<D, T, KFIX, false, NC>(v, jb.walks + wl * a.L, wl, wk, negs);
         }
@@ -514,28 +528,47 @@ __global__ void __launch_bounds__(256) k_b_mb_apply(BArgs a, int64_t node_lo, in
 // ---------------------------------------------------------------------------
 template <class T>
 __device__ __forceinline__ void ph_feedback(const BArgs &a, int b, int g) {
-    __shared__ int32_t sub_s[kBWarps][kMaxKs];
-    __shared__ int32_t sorted_s[kBWarps][kMaxKs];
+    __shared__ PsiScratch scratch[kBWarps];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    PsiScratch &w = scratch[wib];
+    const int GN = psi_group_size(a.ks);
     const int64_t warps = static_cast<int64_t>(g) * kBWarps;
-    for (int64_t x = static_cast<int64_t>(b) * kBWarps + wib; x < a.n_nodes; x += warps) {
-        const int j = find_job(a.node_prefix, a.n_jobs, x);
-        const BState &st = *a.jobs[j].st;
-        if (st.done) continue;
-        const BJob &jb = a.jobs[j];
-        const int32_t v = static_cast<int32_t>(x - a.node_prefix[j]);
-        const int32_t lo = jb.offsets[v], hi = jb.offsets[v + 1];
-        const int64_t deg = lo >= 0 && hi <= jb.nnz ? static_cast<int64_t>(hi) - lo : 0;
-        const bool evaluate = deg > 0 && (a.reactivate || jb.active[st.cur][v]);
-        double psi = 0.0;
-        if (evaluate)
-            psi = psi_node<T>(jb.cols, static_cast<const T *>(jb.phi_in), jb.n, jb.dim, a.ks, jb.seed,
-                              static_cast<uint32_t>(st.round), v, lo, deg, sub_s[wib], sorted_s[wib]);
-        const uint8_t next = a.enabled ? (evaluate && psi < a.mu) : (deg > 0);
-        if (lane == 0) {
-            jb.active[st.cur ^ 1][v] = next;
-            if (next) atomicAdd(&jb.st->n_next, 1);
+    // groups of GN consecutive flat nodes (they may span jobs): totals node
+    // by node, then cosines and means lane-parallel, as felog_feedback does
+    for (int64_t base = (static_cast<int64_t>(b) * kBWarps + wib) * GN; base < a.n_nodes; base += warps * GN) {
+        const int cnt = static_cast<int>(a.n_nodes - base < GN ? a.n_nodes - base : GN);
+        for (int i = 0; i < cnt; ++i) {
+            const int64_t x = base + i;
+            const int j = find_job(a.node_prefix, a.n_jobs, x);
+            const BState &st = *a.jobs[j].st;
+            const BJob &jb = a.jobs[j];
+            const int32_t v = static_cast<int32_t>(x - a.node_prefix[j]);
+            const int32_t lo = jb.offsets[v], hi = jb.offsets[v + 1];
+            const int64_t deg = lo >= 0 && hi <= jb.nnz ? static_cast<int64_t>(hi) - lo : 0;
+            const bool evaluate = !st.done && deg > 0 && (a.reactivate || jb.active[st.cur][v]);
+            if (evaluate)
+                psi_node_totals<T>(jb.cols, static_cast<const T *>(jb.phi_in), jb.n, jb.dim, a.ks, jb.seed,
+                                   static_cast<uint32_t>(st.round), v, lo, deg, w, i);
+            else if (lane == 0) w.m[i] = 0;
         }
+        const double psi = psi_group_finish(w, cnt, a.ks);
+        if (lane < cnt) {
+            const int64_t x = base + lane;
+            const int j = find_job(a.node_prefix, a.n_jobs, x);
+            const BState &st = *a.jobs[j].st;
+            if (!st.done) {
+                const BJob &jb = a.jobs[j];
+                const int32_t v = static_cast<int32_t>(x - a.node_prefix[j]);
+                const int32_t lo = jb.offsets[v], hi = jb.offsets[v + 1];
+                const bool live = lo >= 0 && hi <= jb.nnz && hi > lo;
+                const bool evaluated = w.m[lane] > 0;
+                const uint8_t next = a.enabled ? static_cast<uint8_t>(evaluated && psi < a.mu)
+                                               : static_cast<uint8_t>(live);
+                jb.active[st.cur ^ 1][v] = next;
+                if (next) atomicAdd(&jb.st->n_next, 1);
+            }
+        }
+        __syncwarp();
     }
 }
 template <class T>
@@ -884,9 +917,17 @@ template <int D, class T>
 void launch_b_sgns(const BatchPlan &plan, const BParams &p, const HostTuning &t, int64_t lo, int64_t hi,
                    cudaStream_t s) {
     if (hi <= lo) return;
-    const size_t smem = sizeof(int32_t) * kWarps * (p.window * 2 * p.K + p.L);
-    auto kern = t.sgns_form == 1 ? (p.K == 5 ? k_b_sgns<D, T, 5, 1> : k_b_sgns<D, T, 0, 1>)
-                                 : (p.K == 5 ? k_b_sgns<D, T, 5, 2> : k_b_sgns<D, T, 0, 2>);
+    // form 4 where a lane's share of a row is 16 bytes, else form 2
+    const int form = t.sgns_form == 1 ? 1 : (t.sgns_form == 4 && kPfSupported<D, T> ? 4 : 2);
+    size_t smem = sizeof(int32_t) * kWarps * (p.window * 2 * p.K + p.L);
+    void (*kern)(BArgs, int64_t, int64_t) = form == 1 ? (p.K == 5 ? k_b_sgns<D, T, 5, 1> : k_b_sgns<D, T, 0, 1>)
+                                                      : (p.K == 5 ? k_b_sgns<D, T, 5, 2> : k_b_sgns<D, T, 0, 2>);
+    if constexpr (kPfSupported<D, T>) {
+        if (form == 4) {
+            smem = static_cast<size_t>(kWarps) * pf_bytes_per_warp(p.L, p.window, p.K, D, static_cast<int>(sizeof(T)));
+            kern = p.K == 5 ? k_b_sgns<D, T, 5, 4> : k_b_sgns<D, T, 0, 4>;
+        }
+    }
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     const int64_t want = (hi - lo + kWarps - 1) / kWarps;
@@ -988,7 +1029,7 @@ felog_status plan_step(const BatchPlan &plan, const BParams &p, const HostTuning
     }
     if (phases & 16) {
         const int grid = static_cast<int>(std::max<int64_t>(
-            1, std::min<int64_t>((a.n_nodes + kBWarps - 1) / kBWarps,
+            1, std::min<int64_t>((a.n_nodes + kBWarps * psi_group_size(p.ks) - 1) / (kBWarps * psi_group_size(p.ks)),
                                  static_cast<int64_t>(sm_count()) * t.feedback_blocks_per_sm)));
         if (p.precision == FELOG_FP32) k_b_feedback<float><<<grid, kBThreads, 0, s>>>(a);
         else k_b_feedback<__nv_bfloat16><<<grid, kBThreads, 0, s>>>(a);
@@ -1368,10 +1409,26 @@ extern "C" felog_status felog_batch_job_buffers(const felog_batch *b, int32_t jo
     return FELOG_OK;
 }
 
-// Autotuner: times the walk launch shape, the trainer's blocks per SM and the
-// Psi blocks per SM on round 0 of this batch (the batch is re-initialised
-// before each probe) and keeps the fastest of each.  With cache_path, results
-// are looked up and stored in a text file keyed by GPU name and batch shape.
+extern "C" felog_status felog_batch_set_tuning(felog_batch *b, const felog_tuning *t) {
+    if (!b || !t) return FELOG_ERR_INVALID_ARG;
+    if (t->walk_block < 32 || t->walk_block > 1024 || t->walk_block % 32 != 0) return FELOG_ERR_INVALID_ARG;
+    if (t->sgns_blocks_per_sm < 1 || t->sgns_blocks_per_sm > 8) return FELOG_ERR_INVALID_ARG;
+    if (t->feedback_blocks_per_sm < 1 || t->feedback_blocks_per_sm > 32) return FELOG_ERR_INVALID_ARG;
+    if (t->sgns_form != 1 && t->sgns_form != 2 && t->sgns_form != 4) return FELOG_ERR_INVALID_ARG;
+    b->tune.walk_block = t->walk_block;
+    b->tune.sgns_blocks_per_sm = t->sgns_blocks_per_sm;
+    b->tune.feedback_blocks_per_sm = t->feedback_blocks_per_sm;
+    b->tune.sgns_form = t->sgns_form;
+    drop_graph(b);
+    return FELOG_OK;
+}
+
+// Autotuner: times the walk launch shape, the trainer's shape (pairs per
+// warp, lanes per row, rows prefetched to shared memory or not) with its
+// blocks per SM, and the Psi blocks per SM on round 0 of this batch (the
+// batch is re-initialised before each probe) and keeps the fastest of each.
+// With cache_path, results are looked up and stored in a text file keyed by
+// GPU name and batch shape.
 extern "C" felog_status felog_batch_autotune(felog_batch *b, const char *cache_path, felog_tuning *out,
                                              void *stream) {
     if (!b) return FELOG_ERR_INVALID_ARG;
@@ -1384,7 +1441,7 @@ extern "C" felog_status felog_batch_autotune(felog_batch *b, const char *cache_p
     for (int32_t d : b->plan.dims) dsum += d;
     std::string gpu(prop.name);
     std::replace(gpu.begin(), gpu.end(), ' ', '_');  // the cache file is whitespace separated
-    const std::string key = gpu + "|n=" + std::to_string(b->plan.args.n_nodes) + "|jobs=" +
+    const std::string key = gpu + "|tuner=2|n=" + std::to_string(b->plan.args.n_nodes) + "|jobs=" +
                             std::to_string(b->n_jobs) + "|dsum=" + std::to_string(dsum) + "|L=" +
                             std::to_string(b->p.L) + "|w=" + std::to_string(b->p.window) + "|K=" +
                             std::to_string(b->p.K) + "|p=" + std::to_string(b->p.precision);
@@ -1429,8 +1486,10 @@ extern "C" felog_status felog_batch_autotune(felog_batch *b, const char *cache_p
     b->tune.walk_block = best.walk_block;
     best_ms = 1e30f;
     if (b->p.mode == FELOG_SGNS_HOGWILD) {
-        // trainer shape: pairs per warp and lanes per row (form), resident blocks per SM
-        for (int form : {2, 1}) {
+        // trainer shape (form: 2 = two pairs per warp, 16 lanes per row; 1 = one
+        // pair per warp, 32 lanes; 4 = form 2 with rows prefetched to shared
+        // memory, where the dims allow it), resident blocks per SM
+        for (int form : {2, 1, 4}) {
             for (int sb : {1, 2}) {
                 b->tune.sgns_form = form;
                 b->tune.sgns_blocks_per_sm = sb;

@@ -1,5 +1,5 @@
 // Feedback: neighbourhood-consistency score Psi (Eq. 4) and next active set
-// (Eq. 5), one warp per evaluated node.
+// (Eq. 5); a warp takes groups of consecutive nodes (feedback_core.cuh).
 //
 // The neighbour subset is all neighbours when deg <= ks, else ks distinct
 // CSR positions chosen by Floyd's algorithm (Bentley and Floyd, CACM 1987)
@@ -32,29 +32,39 @@ __global__ void __launch_bounds__(kPsiThreads)
                int32_t reactivate, uint64_t seed, uint32_t round, const uint8_t *__restrict__ active_in,
                uint8_t *__restrict__ active_out, double *__restrict__ psi_out,
                int32_t *__restrict__ n_next) {
-    __shared__ int32_t sub_s[kPsiWarps][kMaxKs];
-    __shared__ int32_t sorted_s[kPsiWarps][kMaxKs];
+    __shared__ PsiScratch scratch[kPsiWarps];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    int32_t *sub = sub_s[wib];
-    int32_t *sorted = sorted_s[wib];
+    PsiScratch &w = scratch[wib];
+    const int GN = psi_group_size(ks);
     int32_t count = 0;
     const int64_t warps = static_cast<int64_t>(gridDim.x) * kPsiWarps;
-    for (int64_t v = static_cast<int64_t>(blockIdx.x) * kPsiWarps + wib; v < n; v += warps) {
-        const int32_t lo = offsets[v], hi = offsets[v + 1];
-        // a row outside [0, nnz] (a malformed graph) is treated as isolated
-        const int64_t deg = lo >= 0 && hi <= nnz ? static_cast<int64_t>(hi) - lo : 0;
-        const bool evaluate = deg > 0 && (reactivate || active_in[v]);
-        double psi = __longlong_as_double(0x7ff8000000000000LL);  // quiet NaN
-        if (evaluate) psi = psi_node<T>(cols, phi, n, dim, ks, seed, round, v, lo, deg, sub, sorted);
-        uint8_t next;
-        if (!enabled) next = deg > 0;
-        else next = evaluate && psi < mu;
-        if (lane == 0) {
+    // a warp takes GN consecutive nodes at a time: their totals one node after
+    // the other, then their cosines and means lane-parallel
+    for (int64_t base = (static_cast<int64_t>(blockIdx.x) * kPsiWarps + wib) * GN; base < n; base += warps * GN) {
+        const int cnt = static_cast<int>(n - base < GN ? n - base : GN);
+        for (int i = 0; i < cnt; ++i) {
+            const int64_t v = base + i;
+            const int32_t lo = offsets[v], hi = offsets[v + 1];
+            // a row outside [0, nnz] (a malformed graph) is treated as isolated
+            const int64_t deg = lo >= 0 && hi <= nnz ? static_cast<int64_t>(hi) - lo : 0;
+            const bool evaluate = deg > 0 && (reactivate || active_in[v]);
+            if (evaluate) psi_node_totals<T>(cols, phi, n, dim, ks, seed, round, v, lo, deg, w, i);
+            else if (lane == 0) w.m[i] = 0;
+        }
+        const double psi = psi_group_finish(w, cnt, ks);  // NaN for nodes not evaluated
+        if (lane < cnt) {
+            const int64_t v = base + lane;
+            const int32_t lo = offsets[v], hi = offsets[v + 1];
+            const bool live = lo >= 0 && hi <= nnz && hi > lo;
+            const bool evaluated = w.m[lane] > 0;  // m, not Psi, marks an evaluated node
+            const uint8_t next = enabled ? static_cast<uint8_t>(evaluated && psi < mu) : static_cast<uint8_t>(live);
             active_out[v] = next;
             if (psi_out) psi_out[v] = psi;
+            count += next;
         }
-        count += next;
+        __syncwarp();
     }
+    for (int o = 16; o; o >>= 1) count += __shfl_xor_sync(kFull, count, o);
     if (lane == 0 && count) atomicAdd(n_next, count);
 }
 
@@ -75,7 +85,7 @@ extern "C" felog_status felog_feedback(const felog_csr *g, const void *phi_in, i
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     felog_status st = record_cuda_error(cudaMemsetAsync(n_next, 0, sizeof(int32_t), s), "feedback");
     if (st || g->n == 0) return st;
-    const int grid = std::min(ceil_div(g->n, kPsiWarps), sm_count() * 16);
+    const int grid = std::min(ceil_div(g->n, kPsiWarps * psi_group_size(fp->ks)), sm_count() * 16);
     if (precision == FELOG_FP32)
         k_feedback<float><<<grid, kPsiThreads, 0, s>>>(
             g->offsets, g->cols, g->n, g->nnz, static_cast<const float *>(phi_in), dim, fp->enabled, fp->mu,

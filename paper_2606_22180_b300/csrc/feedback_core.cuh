@@ -9,9 +9,23 @@ namespace felog {
 
 constexpr int kMaxKs = 32;
 
-__device__ __forceinline__ double elem(const float *p, int64_t i) { return static_cast<double>(p[i]); }
+// binary32 -> binary64, exactly, by moving the fields of a normal number:
+// the sign stays, the 8-bit exponent is rebiased by 1023 - 127 = 896 into
+// 11 bits, and the 23 fraction bits become the top of the 52.  This keeps the
+// conversions (one per row element) off the FP64 pipe, which on this GPU
+// issues two instructions per clock per SM and is what bounds Psi.  Zeros,
+// subnormals, infinities and NaNs take the ordinary conversion.
+__device__ __forceinline__ double f32_to_f64(float f) {
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t e = (b >> 23) & 0xffu;
+    if (e - 1u >= 254u) return static_cast<double>(f);
+    const uint32_t hi = (b & 0x80000000u) | (((b >> 3) & 0x0fffffffu) + (896u << 20));
+    return __hiloint2double(static_cast<int>(hi), static_cast<int>(b << 29));
+}
+
+__device__ __forceinline__ double elem(const float *p, int64_t i) { return f32_to_f64(p[i]); }
 __device__ __forceinline__ double elem(const __nv_bfloat16 *p, int64_t i) {
-    return static_cast<double>(__bfloat162float(p[i]));
+    return f32_to_f64(__bfloat162float(p[i]));
 }
 
 __device__ __forceinline__ double butterfly(double s) {
@@ -40,15 +54,46 @@ __device__ __forceinline__ double reduce_scatter16_f64(double (&v)[16], int lane
     return __dadd_rn(v[0], __shfl_xor_sync(kFull, v[0], 1));
 }
 
-// Psi of node v (deg > 0) on a warp; sub / sorted are this warp's kMaxKs-int
-// shared buffers.  Every lane returns the same value.  A neighbour id outside
-// [0, n) (a malformed graph) counts as a zero row, so nothing is read out of
-// range; on a well-formed graph it never occurs.
+// Psi is computed for a group of nodes on one warp in two parts.
+//
+// psi_node_totals (per node, all lanes): the neighbour subset, |x|^2 and,
+// for each subset neighbour u_a, |u_a|^2 and x . u_a, each a binary64 sum in
+// the fixed order; they are left in the warp's scratch.
+//
+// psi_group_finish (per group): the cosines of every (node, neighbour) slot,
+// one slot per lane, then on lane i the mean of node i's cosines in
+// ascending subset order.  The square roots and divisions of a node thus run
+// on one lane instead of the whole warp, with the same operations in the
+// same order, so the values are those of the one-node-per-warp form bit for
+// bit.
+//
+// Scratch of one warp (shared memory): nv[kPsiGroup] = |x|^2 per node,
+// m[kPsiGroup] = subset size (0: not evaluated), and u2 / xu
+// [kPsiGroup * ks <= kPsiSlots]: the totals of slot i * ks + a.
+constexpr int kPsiGroup = 32;
+constexpr int kPsiSlots = 256;
+
+__host__ __device__ inline int psi_group_size(int ks) { return ks * kPsiGroup <= kPsiSlots ? kPsiGroup : kPsiSlots / ks; }
+
+struct PsiScratch {
+    double nv[kPsiGroup];
+    double u2[kPsiSlots];
+    double xu[kPsiSlots];
+    int32_t m[kPsiGroup];
+    int32_t sub[kMaxKs];
+    int32_t sorted[kMaxKs];
+};
+
+// Totals of node v (deg > 0) into slot row `row` of the scratch; returns the
+// subset size.  A neighbour id outside [0, n) (a malformed graph) counts as a
+// zero row, so nothing is read out of range; on a well-formed graph it never
+// occurs.
 template <class T>
-__device__ __forceinline__ double psi_node(const int32_t *__restrict__ cols, const T *__restrict__ phi,
-                                           int64_t n, int32_t dim, int32_t ks, uint64_t seed, uint32_t round,
-                                           int64_t v, int32_t lo, int64_t deg, int32_t *sub, int32_t *sorted) {
+__device__ __forceinline__ int32_t psi_node_totals(const int32_t *__restrict__ cols, const T *__restrict__ phi,
+                                                   int64_t n, int32_t dim, int32_t ks, uint64_t seed, uint32_t round,
+                                                   int64_t v, int32_t lo, int64_t deg, PsiScratch &w, int row) {
     const int lane = threadIdx.x & 31;
+    int32_t *sub = w.sub, *sorted = w.sorted;
     int32_t m;
     if (deg <= ks) {
         m = static_cast<int32_t>(deg);
@@ -93,15 +138,14 @@ __device__ __forceinline__ double psi_node(const int32_t *__restrict__ cols, con
     for (int c = 0; c < 8; ++c)
         if (c < per_lane) nv = __fma_rn(xv[c], xv[c], nv);
     nv = butterfly(nv);
-    const double sq_nv = __dsqrt_rn(nv);
+    if (lane == 0) w.nv[row] = nv;
     // neighbours in chunks of 8: their row loads overlap, and the 16 partial
     // sums of a chunk (|u|^2 and x.u per neighbour) are reduced together by a
     // reduce-scatter that adds the same pairs as the xor butterfly (so each
-    // total is bit-identical to it) with 16 instead of 80 additions per lane;
-    // lane 4b then forms the cosine of neighbour b, and the cosines are added
-    // in ascending subset order
+    // total is bit-identical to it) with 16 instead of 80 additions per lane
     constexpr int G = 8;
-    double sum = 0.0;
+    double *u2 = w.u2 + row * ks;
+    double *xu = w.xu + row * ks;
     for (int a0 = 0; a0 < m; a0 += G) {
         const T *pu[G];
         bool inside[G];
@@ -114,31 +158,58 @@ __device__ __forceinline__ double psi_node(const int32_t *__restrict__ cols, con
         double part[2 * G];  // part[2b] = |u_b|^2, part[2b + 1] = x . u_b
 #pragma unroll
         for (int i = 0; i < 2 * G; ++i) part[i] = 0.0;
+        // slots past the subset (m - a0 < G, warp-uniform) keep their zero
+        // partials: the FMAs they would run add +0 exactly, so they are skipped
+        const int live = min(G, m - a0);
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
             if (c >= per_lane) break;
             double y[G];
 #pragma unroll
-            for (int b = 0; b < G; ++b) y[b] = inside[b] ? elem(pu[b], lane + 32 * c) : 0.0;
+            for (int b = 0; b < G; ++b) y[b] = b < live && inside[b] ? elem(pu[b], lane + 32 * c) : 0.0;
 #pragma unroll
             for (int b = 0; b < G; ++b) {
+                if (b >= live) break;
                 part[2 * b] = __fma_rn(y[b], y[b], part[2 * b]);
                 part[2 * b + 1] = __fma_rn(xv[c], y[b], part[2 * b + 1]);
             }
         }
         const double tot = reduce_scatter16_f64(part, lane);  // lanes 2t, 2t+1: total t
-        const double d2 = __shfl_down_sync(kFull, tot, 2);    // at lane 4b: x . u_b
-        double cs = 0.0;
+        // lane 4b holds |u_b|^2, lane 4b + 2 holds x . u_b
         const int b_mine = lane >> 2;
-        if ((lane & 3) == 0 && a0 + b_mine < m && nv > 0.0 && tot > 0.0)
-            cs = __ddiv_rn(d2, __dmul_rn(sq_nv, __dsqrt_rn(tot)));
-#pragma unroll
-        for (int b = 0; b < G; ++b) {
-            const double cb = __shfl_sync(kFull, cs, 4 * b);
-            if (a0 + b < m) sum = __dadd_rn(sum, cb);
+        if ((lane & 1) == 0 && b_mine < live) ((lane & 2) ? xu : u2)[a0 + b_mine] = tot;
+    }
+    if (lane == 0) w.m[row] = m;
+    __syncwarp();
+    return m;
+}
+
+// Cosines and means of rows 0..count-1 (count <= psi_group_size(ks)); lane i
+// < count returns Psi of row i (NaN where m[i] == 0, a node not evaluated).
+__device__ __forceinline__ double psi_group_finish(PsiScratch &w, int count, int32_t ks) {
+    const int lane = threadIdx.x & 31;
+    __syncwarp();
+    // cos = x.u / (sqrt(|x|^2) * sqrt(|u|^2)), 0 for a zero row; written over xu
+    for (int s = lane; s < count * ks; s += 32) {
+        const int i = s / ks, a = s - i * ks;
+        if (a < w.m[i]) {
+            const double nv = w.nv[i], tot = w.u2[s];
+            double cs = 0.0;
+            if (nv > 0.0 && tot > 0.0) cs = __ddiv_rn(w.xu[s], __dmul_rn(__dsqrt_rn(nv), __dsqrt_rn(tot)));
+            w.xu[s] = cs;
         }
     }
-    const double psi = __ddiv_rn(sum, static_cast<double>(m));
+    __syncwarp();
+    double psi = __longlong_as_double(0x7ff8000000000000LL);  // quiet NaN
+    if (lane < count) {
+        const int32_t m = w.m[lane];
+        if (m > 0) {
+            const double *cs = w.xu + lane * ks;
+            double sum = 0.0;
+            for (int a = 0; a < m; ++a) sum = __dadd_rn(sum, cs[a]);
+            psi = __ddiv_rn(sum, static_cast<double>(m));
+        }
+    }
     __syncwarp();
     return psi;
 }

@@ -62,12 +62,7 @@ __global__ void __launch_bounds__(kSgnsThreads, 3)
 
 
 // Form 4: the half-warp trainer with each step's rows prefetched to shared
-// memory (hw_train_walk_pf); per warp the walk and negative ids (rounded up
-// to 16 bytes), then the double buffer of rows.
-__host__ __device__ inline int pf_bytes_per_warp(int L, int window, int K, int dim, int elem) {
-    const int ids = 4 * ((L + 2 * window * K + 3) & ~3);
-    return ids + 2 * 2 * (K + 1) * dim * elem;
-}
+// memory (hw_train_walk_pf; shared-memory layout in pf_bytes_per_warp).
 
 template <int D, class T, int KFIX>
 __global__ void __launch_bounds__(kSgnsThreads, 2)

@@ -995,6 +995,13 @@ template <int D, class T>
 constexpr bool kPfSupported = (std::is_same<T, float>::value && (D == 64 || D == 128)) ||
                               (!std::is_same<T, float>::value && D == 128);
 
+// Shared memory of one warp of the prefetching form: the walk and negative
+// ids (rounded up to 16 bytes), then the double buffer of rows.
+__host__ __device__ inline int pf_bytes_per_warp(int L, int window, int K, int dim, int elem) {
+    const int ids = 4 * ((L + 2 * window * K + 3) & ~3);
+    return ids + 2 * 2 * (K + 1) * dim * elem;
+}
+
 template <int D, class T, int KFIX>
 __device__ __forceinline__ long long hw_train_walk_pf(const TrainView<T> &a, const int32_t *__restrict__ row,
                                                       int64_t wi, int32_t *wk, int32_t *negs, char *rowbuf) {

@@ -38,7 +38,7 @@ SYMBOLS = [
     "felog_fabc_encode", "felog_fabc_decode",
     "felog_batch_create", "felog_batch_destroy", "felog_batch_device_bytes", "felog_batch_reset",
     "felog_batch_step", "felog_batch_run", "felog_batch_read", "felog_batch_job_buffers",
-    "felog_batch_autotune", "felog_batch_set_wait_limit", "felog_grid_barrier_check",
+    "felog_batch_autotune", "felog_batch_set_tuning", "felog_batch_set_wait_limit", "felog_grid_barrier_check",
     "felog_server_create", "felog_server_destroy", "felog_server_now", "felog_server_job_bytes",
     "felog_server_submit", "felog_server_poll", "felog_server_wait", "felog_server_fetch",
     "felog_server_drain", "felog_server_get_stats",
@@ -133,6 +133,7 @@ def load() -> ctypes.CDLL:
         "felog_batch_read": (st, [P, P, P, P, P]),
         "felog_batch_job_buffers": (st, [P, i32, P]),
         "felog_batch_autotune": (st, [P, ctypes.c_char_p, P, P]),
+        "felog_batch_set_tuning": (st, [P, P]),
         "felog_batch_set_wait_limit": (st, [P, f64]),
         "felog_grid_barrier_check": (st, [i32, i32, f64, P, P]),
         "felog_server_create": (st, [P, P]),
@@ -595,6 +596,12 @@ class Batch:
         or one persistent kernel (persistent=True)."""
         mode = 2 if persistent else int(bool(use_graph))
         _check(self.lib.felog_batch_run(self.handle, mode, _stream()), "felog_batch_run")
+
+    def set_tuning(self, walk_block: int = 256, sgns_blocks_per_sm: int = 2, feedback_blocks_per_sm: int = 16,
+                   sgns_form: int = 2):
+        """Launch shapes of the batched kernels (see felog_tuning)."""
+        t = Tuning(walk_block, sgns_blocks_per_sm, feedback_blocks_per_sm, 0, sgns_form)
+        _check(self.lib.felog_batch_set_tuning(self.handle, ctypes.byref(t)), "felog_batch_set_tuning")
 
     def set_wait_limit(self, seconds: float):
         """Budget of each grid-barrier wait of the persistent form."""

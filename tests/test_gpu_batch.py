@@ -118,6 +118,53 @@ def test_batch_hogwild_quality_equals_solo(fl):
     assert np.all(np.abs(per_job) <= 0.005), per_job
 
 
+@pytest.mark.parametrize("form", [1, 2, 4])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_trainer_shapes_quality_equal_solo(fl, form, precision):
+    """Every trainer shape the autotuner may pick (1: one pair per warp;
+    2: two pairs per warp; 4: shape 2 with rows prefetched to shared memory)
+    keeps each dim-128 job's link AUC within 0.005 of the job trained alone
+    (mean of 2 seeds per job; every job checked)."""
+    from paper_2606_22180_b300 import evaluate
+
+    gs, splits = [], []
+    for i in range(4):
+        g, _ = inputs.sbm(1200 + 600 * i, 8, 0.04, 0.002, seed=700 + i)
+        sp = inputs.link_split(g, 0.1, i)
+        gs.append(sp.train)
+        splits.append(sp)
+    dgs = [fl.DeviceGraph.from_host(g) for g in gs]
+    tp = fl.train_params(128, W, K, 0.025, 0, fl.FELOG_SGNS_HOGWILD, 4096, precision)
+    fp = fl.feedback_params(False, 0.65, 8, 8, False)
+    diffs = np.zeros((2, 4))
+    for rep in range(2):
+        seeds = [21 + i + 100 * rep for i in range(4)]
+        b = fl.Batch(dgs, [128] * 4, seeds, L, 1, tp, fp)
+        b.set_tuning(sgns_form=form)
+        b.run(use_graph=True)
+        stats, _, _ = b.read()
+        assert all(s["rounds"] == 8 for s in stats)
+        for j in range(4):
+            solo, _, _ = fl.felog_embed(dgs[j], L, 1, tp, fp, seeds[j])
+            diffs[rep, j] = (evaluate.link_auc(b.phi_in[j], splits[j].pos, splits[j].neg)
+                             - evaluate.link_auc(solo, splits[j].pos, splits[j].neg))
+        b.close()
+    per_job = diffs.mean(0)
+    print(f"shape {form} precision {precision}: batch - solo AUC per job:", np.round(per_job, 4))
+    assert np.all(np.abs(per_job) <= 0.005), per_job
+
+
+def test_batch_set_tuning_rejects_bad_shapes(fl):
+    g = _graphs()[0]
+    tp = fl.train_params(64, W, K, 0.025, 0, fl.FELOG_SGNS_HOGWILD, 4096, fl.FELOG_FP32)
+    fp = fl.feedback_params(False, 0.65, 8, 2, False)
+    b = fl.Batch([fl.DeviceGraph.from_host(g)], [64], [1], L, 1, tp, fp)
+    for bad in ({"sgns_form": 3}, {"walk_block": 100}, {"sgns_blocks_per_sm": 0}, {"feedback_blocks_per_sm": 64}):
+        with pytest.raises(fl.FelogError):
+            b.set_tuning(**bad)
+    b.close()
+
+
 def test_batch_autotune_and_cache(fl, tmp_path):
     gs = _graphs()[:4]
     dgs = [fl.DeviceGraph.from_host(g) for g in gs]

@@ -318,7 +318,7 @@ def test_feedback_bit_exact(fl, orc, rmat14, precision, reactivate, enabled):
     pt = torch.from_numpy(phi).cuda()
     if precision == 1:
         pt = pt.to(torch.bfloat16)
-    phi64 = pt.double().cpu().numpy()
+    phi64 = pt.cpu().double().numpy()
     live = (g.degrees() > 0).astype(np.uint8)
     active = live * (rng.random(g.n) < 0.7).astype(np.uint8)
     dg = fl.DeviceGraph.from_host(g)
@@ -333,6 +333,40 @@ def test_feedback_bit_exact(fl, orc, rmat14, precision, reactivate, enabled):
         assert np.array_equal(psi[ok].view(np.int64), psi_ref[ok].view(np.int64))
         assert np.array_equal(nxt.cpu().numpy(), nxt_ref)
         assert int(cnt.item()) == cnt_ref
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_feedback_bit_exact_wide_exponents(fl, orc, rmat14, precision):
+    """Psi on tables whose entries span the whole finite binary32 range that
+    keeps the sums finite: random sign and fraction, exponent field 0..167
+    (zeros, subnormals, and normals up to 2^40), plus exact +0 and -0.  The
+    kernel widens each entry to binary64 by moving its fields (the ordinary
+    conversion for zeros and subnormals); Psi must still equal the oracle's
+    bit for bit."""
+    g = rmat14
+    rng = np.random.default_rng(11 + precision)
+    dim = 64
+    sign = rng.integers(0, 2, size=(g.n, dim), dtype=np.uint32) << 31
+    expo = rng.integers(0, 168, size=(g.n, dim), dtype=np.uint32)
+    expo[rng.random((g.n, dim)) < 0.05] = 0  # more subnormals and zeros
+    frac = rng.integers(0, 1 << 23, size=(g.n, dim), dtype=np.uint32)
+    frac[rng.random((g.n, dim)) < 0.02] = 0
+    phi = (sign | (expo << 23) | frac).view(np.float32)
+    assert np.all(np.isfinite(phi)) and np.any(phi == 0) and np.any((phi != 0) & (np.abs(phi) < 2.0 ** -126))
+    pt = torch.from_numpy(phi).cuda()
+    if precision == 1:
+        pt = pt.to(torch.bfloat16)
+    phi64 = pt.cpu().double().numpy()
+    active = (g.degrees() > 0).astype(np.uint8)
+    fp = fl.feedback_params(True, 0.2, 8, 10, False)
+    psi, nxt, cnt = fl.felog_feedback(fl.DeviceGraph.from_host(g), pt, precision, fp, SEED, 2, _dev(active))
+    psi_ref, nxt_ref, cnt_ref = orc.feedback(g.offsets, g.cols, phi64, active, True, 0.2, 8, False, SEED, 2)
+    psi = psi.cpu().numpy()
+    assert np.array_equal(np.isnan(psi), np.isnan(psi_ref))
+    ok = ~np.isnan(psi_ref)
+    assert np.array_equal(psi[ok].view(np.int64), psi_ref[ok].view(np.int64))
+    assert np.array_equal(nxt.cpu().numpy(), nxt_ref)
+    assert int(cnt.item()) == cnt_ref
 
 
 @pytest.mark.parametrize("ks", [1, 5, 32])
