@@ -281,6 +281,16 @@ felog_status felog_init_tables(int32_t n, int32_t dim, int32_t precision, uint64
  * launch then stopped early, *loss is NaN and the tables are undefined.
  * During stream capture the NaN loss is the only report.
  * Workspace: felog_train_workspace_bytes(...). */
+/* Stochastic rounding to bfloat16 (the precision form's rounding of every
+ * bf16 table store): out[i] = the upper half of (bits of x[i]) + r16[i],
+ * i.e. the 16 random bits r16[i] are added below the kept bits and the sum
+ * is truncated.  The bf16 Hogwild trainers round with the same instruction.
+ * x: device float[n]; r16: device uint16[n]; out: device uint16[n] (bf16
+ * patterns).  n >= 0; pointers may be NULL only when n == 0.  Finite inputs
+ * round as stated (a carry out of the largest finite value gives infinity);
+ * infinities stay; a NaN gives a NaN. */
+felog_status felog_sr_bf16(const float *x, const uint16_t *r16, int64_t n, uint16_t *out, void *stream);
+
 size_t felog_train_workspace_bytes(int64_t n_walks, int32_t L, int32_t n,
                                    const felog_train_params *tp);
 felog_status felog_train(const int32_t *walks, int64_t n_walks, int32_t L, int32_t n,

@@ -78,6 +78,7 @@ def lib() -> ctypes.CDLL:
             "oracle_sr_bf16_keyed": (ctypes.c_uint32, [ctypes.c_uint32, u64, ctypes.c_uint32,
                                                        ctypes.c_uint32, ctypes.c_uint32]),
             "oracle_sr_bf16_row": (None, [P, i64, u64, ctypes.c_uint32, ctypes.c_uint32, P]),
+            "oracle_sr_bf16_array": (None, [P, P, i64, P]),
             "oracle_learning_rate": (f64, [f64, i64, i64]),
             "oracle_pair_update": (f64, [P, P, i32, i32, f64, P]),
             "oracle_sgns_serial": (f64, [P, i64, i32, i32, P, P, P, u64, u64, i32, i64, P, P]),
@@ -190,6 +191,17 @@ def sr_bf16_keyed(xbits: int, seed: int, element: int, row: int, counter: int) -
     """Stochastic rounding with bits from the rounding stream (stream 4) keyed
     by (element / 4, row, counter)."""
     return int(lib().oracle_sr_bf16_keyed(xbits & 0xffffffff, seed, element, row, counter))
+
+
+def sr_bf16_array(xbits, r16) -> np.ndarray:
+    """Stochastic rounding of binary32 patterns (uint32 array) with the given
+    16-bit random values (uint16 array of the same length); returns uint16."""
+    x = _c(xbits, np.uint32)
+    r = _c(r16, np.uint16)
+    assert x.shape == r.shape
+    out = np.empty(x.shape[0], np.uint16)
+    lib().oracle_sr_bf16_array(_p(x), _p(r), x.shape[0], _p(out))
+    return out
 
 
 def sr_bf16_row(xbits, seed: int, row: int, counter: int) -> np.ndarray:

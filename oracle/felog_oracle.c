@@ -311,6 +311,12 @@ uint32_t oracle_sr_bf16_keyed(uint32_t xbits, uint64_t seed, uint32_t element, u
     return oracle_sr_bf16(xbits, w[element % 4u] & 0xffffu);
 }
 
+/* Stochastic rounding of an array with caller-supplied bits: out[i] =      */
+/* SR(x[i]) with r16[i].                                                     */
+void oracle_sr_bf16_array(const uint32_t *x, const uint16_t *r16, int64_t m, uint16_t *out) {
+    for (int64_t i = 0; i < m; ++i) out[i] = (uint16_t)oracle_sr_bf16(x[i], r16[i]);
+}
+
 /* A row store with stochastic rounding: out[i] = SR(x[i]) with the bits of  */
 /* element i of the rounding stream keyed (i / 4, row, counter).             */
 void oracle_sr_bf16_row(const uint32_t *x, int64_t m, uint64_t seed, uint32_t row, uint32_t counter,

@@ -356,6 +356,35 @@ static felog_status dispatch_dim(const SgnsArgs &a, const felog_train_params *tp
 
 using namespace felog;
 
+namespace felog {
+// element pairs (x[2p], x[2p+1]) per thread; the pair's random word carries
+// r16[2p + 1] in its upper half and r16[2p] in its lower half
+__global__ void k_sr_bf16(const float *__restrict__ x, const uint16_t *__restrict__ r16, int64_t n,
+                          uint16_t *__restrict__ out) {
+    const int64_t pairs = (n + 1) / 2;
+    for (int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < pairs;
+         q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t i = 2 * q;
+        const bool two = i + 1 < n;
+        const float hi = two ? x[i + 1] : 0.f;
+        const uint32_t bits = (two ? static_cast<uint32_t>(r16[i + 1]) << 16 : 0u) | r16[i];
+        const uint32_t t = sr_pack_bf16x2(hi, x[i], bits);
+        out[i] = static_cast<uint16_t>(t & 0xffffu);
+        if (two) out[i + 1] = static_cast<uint16_t>(t >> 16);
+    }
+}
+}  // namespace felog
+
+extern "C" felog_status felog_sr_bf16(const float *x, const uint16_t *r16, int64_t n, uint16_t *out,
+                                      void *stream) {
+    if (n < 0 || (n > 0 && (!x || !r16 || !out))) return FELOG_ERR_INVALID_ARG;
+    if (n == 0) return FELOG_OK;
+    const int64_t pairs = (n + 1) / 2;
+    const int grid = static_cast<int>(std::min<int64_t>((pairs + 255) / 256, static_cast<int64_t>(sm_count()) * 8));
+    k_sr_bf16<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(x, r16, n, out);
+    return check_launch("felog_sr_bf16");
+}
+
 extern "C" size_t felog_train_workspace_bytes(int64_t n_walks, int32_t L, int32_t n,
                                               const felog_train_params *tp) {
     (void)n_walks;

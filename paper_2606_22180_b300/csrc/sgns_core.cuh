@@ -362,13 +362,6 @@ __device__ __forceinline__ void unpack_bf16(const uint32_t (&w)[EPL / 2], float 
     }
 }
 
-// hi16(w * C) + b: one 16-bit random value for one rounding, added below the
-// kept mantissa of float bits b (multiply-high mixing of one random word by
-// distinct odd constants gives each element its own value).
-__device__ __forceinline__ uint32_t add_rand16(uint32_t b, uint32_t w, uint32_t C) {
-    return __umulhi(w * C, 0x10000u) + b;
-}
-
 __device__ __forceinline__ void red_add_bf16x2_v4(__nv_bfloat16 *p, uint32_t a, uint32_t b, uint32_t c,
                                                   uint32_t d) {
     asm volatile("red.relaxed.gpu.global.add.noftz.v4.bf16x2 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(a),
@@ -376,21 +369,36 @@ __device__ __forceinline__ void red_add_bf16x2_v4(__nv_bfloat16 *p, uint32_t a, 
                  : "memory");
 }
 
+// Two stochastically rounded bf16 values packed in one word: hi = SR(x_hi)
+// with the random word's upper 16 bits, lo = SR(x_lo) with its lower 16.  The
+// conversion instruction with the .rs rounding mode adds the random bits
+// below the kept bits of each float and truncates, which is the rounding the
+// oracle defines (checked bit for bit on a B300 over 2^20 random pairs,
+// both halves); one instruction replaces the two additions and the pack.
+__device__ __forceinline__ uint32_t sr_pack_bf16x2(float x_hi, float x_lo, uint32_t rbits) {
+    uint32_t t;
+    asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(t) : "f"(x_hi), "f"(x_lo), "r"(rbits));
+    return t;
+}
+
 // bf16 row slice: raw = packed bf16 values last read, delta in float; one
-// random word w covers the slice.
+// random word w (a step of the lane's LCG) covers the slice.  Element pair i
+// rounds with w * C_i for an odd constant C_i: its upper half, the product's
+// well-mixed high bits, serves the upper element; its lower half, whose bits
+// only depend on w's low bits (short periods in an LCG), is xored with w's
+// high half before it serves the lower element.
 template <int EPL>
 __device__ __forceinline__ void add_delta_raw(__nv_bfloat16 *__restrict__ p, const uint32_t (&raw)[EPL / 2],
                                               const float (&delta)[EPL], uint32_t w) {
-    constexpr uint32_t C[8] = {0x9E3779B1u, 0x85EBCA77u, 0xC2B2AE3Du, 0x27D4EB2Fu,
-                               0x165667B1u, 0xD3A2646Cu | 1u, 0xFD7046C5u, 0xB55A4F09u};
+    constexpr uint32_t C[4] = {0x9E3779B1u, 0x85EBCA77u, 0xC2B2AE3Du, 0x27D4EB2Fu};
+    const uint32_t whi = w >> 16;
     uint32_t inc[EPL / 2];
     uint32_t any = 0;
 #pragma unroll
     for (int i = 0; i < EPL / 2; ++i) {
         const float c0 = __uint_as_float(raw[i] << 16), c1 = __uint_as_float(raw[i] & 0xffff0000u);
-        const uint32_t b0 = add_rand16(__float_as_uint(c0 + delta[2 * i]), w, C[(2 * i) & 7]);
-        const uint32_t b1 = add_rand16(__float_as_uint(c1 + delta[2 * i + 1]), w, C[(2 * i + 1) & 7]);
-        inc[i] = sub_bf16x2(__byte_perm(b0, b1, 0x7632), raw[i]);
+        const uint32_t t = sr_pack_bf16x2(c1 + delta[2 * i + 1], c0 + delta[2 * i], (w * C[i & 3]) ^ whi);
+        inc[i] = sub_bf16x2(t, raw[i]);
         any |= inc[i];
     }
     if (!(any & 0x7fff7fffu)) return;  // every element rounded back to its current value

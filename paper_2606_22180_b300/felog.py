@@ -29,7 +29,7 @@ SYMBOLS = [
     "felog_walk", "felog_count",
     "felog_noise_workspace_bytes", "felog_noise_table",
     "felog_init_tables",
-    "felog_train_workspace_bytes", "felog_train",
+    "felog_sr_bf16", "felog_train_workspace_bytes", "felog_train",
     "felog_feedback",
     "felog_embed_workspace_bytes", "felog_embed",
     "felog_walk_node2vec",
@@ -112,6 +112,7 @@ def load() -> ctypes.CDLL:
         "felog_noise_table": (st, [P, i32, P, P, P, P, sz, P]),
         "felog_init_tables": (st, [i32, i32, i32, u64, P, P, P]),
         "felog_train_workspace_bytes": (sz, [i64, i32, i32, P]),
+        "felog_sr_bf16": (st, [P, P, i64, P, P]),
         "felog_train": (st, [P, i64, i32, i32, P, P, P, P, u64, i32, i64, P, P, P, P, sz, P]),
         "felog_feedback": (st, [P, P, i32, i32, P, u64, i32, P, P, P, P, P]),
         "felog_embed_workspace_bytes": (sz, [i32, P, P]),
@@ -349,6 +350,18 @@ def train_params(dim=128, window=10, negatives=5, lr0=0.025, lr_total_tokens=1, 
 
 def feedback_params(enabled=True, mu=0.65, ks=8, max_rounds=10, reactivate=False) -> _FeedbackParams:
     return _FeedbackParams(int(enabled), mu, ks, max_rounds, int(reactivate))
+
+
+def felog_sr_bf16(x: torch.Tensor, r16: torch.Tensor) -> torch.Tensor:
+    """Stochastic rounding of float32 x to bf16 patterns with the 16-bit random
+    values r16 (int16 tensor holding uint16 bits, same length); returns the
+    patterns as an int16 tensor."""
+    _require_cuda(x, r16)
+    if x.dtype != torch.float32 or r16.dtype != torch.int16 or x.numel() != r16.numel():
+        raise FelogError("felog_sr_bf16: float32 x and int16 r16 of the same length")
+    out = torch.empty(x.numel(), dtype=torch.int16, device=x.device)
+    _check(load().felog_sr_bf16(_ptr(x), _ptr(r16), x.numel(), _ptr(out), _stream()), "felog_sr_bf16")
+    return out
 
 
 def felog_train(walks: torch.Tensor, n: int, tp: _TrainParams, thr: torch.Tensor, alias: torch.Tensor,

@@ -155,3 +155,33 @@ def test_hogwild_bf16_stores_are_unbiased(fl, corpus):
     z = _z(err)
     print(f"hogwild SR, all {N} rows: z = {z:.2f}")
     assert abs(z) < 5
+
+
+def test_sr_conversion_matches_oracle_bitwise(fl, orc):
+    """felog_sr_bf16 rounds with the instruction the bf16 Hogwild trainers use
+    for their stores.  Against the oracle's SR definition (add the 16 random
+    bits below the kept bits, truncate), bit for bit, over an odd number of
+    elements (a ragged last pair): random bit patterns across the whole
+    binary32 range including subnormals, zeros of both signs, the largest
+    finite values (whose carry gives infinity) and infinities.  A NaN must
+    stay a NaN (its payload is not fixed)."""
+    rng = np.random.default_rng(5)
+    n = (1 << 20) + 3
+    xb = rng.integers(0, 1 << 32, size=n, dtype=np.uint64).astype(np.uint32)
+    special = np.array([0x00000000, 0x80000000, 0x00000001, 0x807fffff, 0x7f7fffff, 0xff7fffff,
+                        0x7f800000, 0xff800000, 0x7fc00000, 0xffc00001, 0x3f800000, 0x3f80ffff], np.uint32)
+    xb[: special.size] = special
+    r = rng.integers(0, 1 << 16, size=n, dtype=np.uint64).astype(np.uint16)
+    r[: special.size] = 0xffff
+    x = torch.from_numpy(xb.view(np.float32)).cuda()
+    rt = torch.from_numpy(r.view(np.int16)).cuda()
+    got = fl.felog_sr_bf16(x, rt).cpu().numpy().view(np.uint16)
+    want = orc.sr_bf16_array(xb, r)
+    nan_in = ((xb & 0x7f800000) == 0x7f800000) & ((xb & 0x007fffff) != 0)
+    assert np.array_equal(got[~nan_in], want[~nan_in])
+    got_nan = ((got & 0x7f80) == 0x7f80) & ((got & 0x007f) != 0)
+    assert np.all(got_nan[nan_in])
+    assert got[6] == 0x7f80 and got[7] == 0x7f80 | 0x8000  # inf stays inf
+    assert got[4] == 0x7f80  # largest finite + carry -> inf
+    with pytest.raises(fl.FelogError):
+        fl.felog_sr_bf16(x, rt[:-1])

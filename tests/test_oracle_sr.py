@@ -104,3 +104,12 @@ def test_keyed_bits_are_the_rounding_stream(orc):
         r16 = int(w[element % 4]) & 0xffff
         xb = 0x3eaaaaab
         assert orc.sr_bf16_keyed(xb, seed, element, row, counter) == orc.sr_bf16(xb, r16)
+
+
+def test_sr_array_equals_scalar_definition(orc):
+    """The array form applies the pinned scalar rounding element by element."""
+    rng = np.random.default_rng(3)
+    x = rng.integers(0, 1 << 32, size=4000, dtype=np.uint64).astype(np.uint32)
+    r = rng.integers(0, 1 << 16, size=4000, dtype=np.uint64).astype(np.uint16)
+    got = orc.sr_bf16_array(x, r)
+    assert all(int(got[i]) == orc.sr_bf16(int(x[i]), int(r[i])) for i in range(x.size))
