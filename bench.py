@@ -50,7 +50,7 @@ def _args():
     p.add_argument("--scale", type=int, default=SCALE, help="R-MAT scale (20 = the benchmark workload)")
     p.add_argument("--no-quality", action="store_true", help="skip the full-run AUC comparison")
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
-    p.add_argument("--form", type=int, default=0, choices=[0, 1, 2, 3, 4],
+    p.add_argument("--form", type=int, default=0, choices=[0, 1, 2, 3, 4, 5],
                    help="Hogwild kernel form: 0 automatic, 1 full warp per pair, 2 half warp per pair, "
                         "3 half warp with the window's phi_in increments staged in shared memory, "
                         "4 half warp with the next step's rows prefetched to shared memory")
@@ -272,6 +272,8 @@ def _sgns_kernel_name(form, precision):
         return f"k_sgns_hogwild<128,{t},8,5>"
     if form == 4 or (form == 0 and t == "bf16"):  # the automatic form for bf16 tables of dim 128
         return f"k_sgns_hogwild_pf<128,{t},5>"
+    if form == 5 and t == "float":
+        return "k_sgns_hogwild_bulk<128,5>"
     staged = form == 3
     return f"k_sgns_hogwild_hw<128,{t},5,{'true' if staged else 'false'}>"
 

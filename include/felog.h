@@ -94,7 +94,10 @@ typedef enum {
  * warps' delayed increments, which costs link AUC), 4 = form 2 with the
  * next step's context and negative rows copied to shared memory (cp.async)
  * while the current step computes (float tables of dim 64 or 128, bf16
- * tables of dim 128; other shapes run form 2); 0 = automatic: form 4 for
+ * tables of dim 128; other shapes run form 2), 5 = form 2 on float tables
+ * with each step's row increments written to shared memory and added to the
+ * tables by the bulk-copy engine (cp.reduce.async.bulk, one per row; other
+ * precisions run form 2); 0 = automatic: form 4 for
  * bf16 tables of dim 128 with negatives <= 7, form 2 for other shapes with
  * dim <= 128 and negatives <= 7, form 1 otherwise.
  * TILE mode (dim in {32, 64, 128}): tile_negatives = shared negatives per

@@ -87,6 +87,28 @@ __global__ void __launch_bounds__(kSgnsThreads, 2)
     if (lane == 0 && loss_fx != 0) atomicAdd(a.loss_acc, static_cast<unsigned long long>(loss_fx));
 }
 
+// Form 5: the half-warp trainer on float tables with each step's row
+// increments added by the bulk-copy engine (hw_train_walk<..., BULK>).
+template <int D, int KFIX>
+__global__ void __launch_bounds__(kSgnsThreads, 2)
+    k_sgns_hogwild_bulk(SgnsArgs a, float *__restrict__ phi_in, float *__restrict__ phi_out) {
+    extern __shared__ __align__(16) int32_t smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int K = KFIX > 0 ? KFIX : a.K;
+    char *base = reinterpret_cast<char *>(smem) + wib * bulk_bytes_per_warp(a.L, a.window, K, D);
+    int32_t *wk = reinterpret_cast<int32_t *>(base);
+    int32_t *negs = wk + a.L;
+    float *slots = reinterpret_cast<float *>(base + 4 * ((a.L + 2 * a.window * K + 3) & ~3));
+    TrainView<float> v{phi_in, phi_out, a.thr, a.alias, static_cast<uint64_t>(a.n), *a.S, a.seed, a.round,
+                       a.lr0, a.inv_T, a.clock_base, a.window, a.K, a.L, 0};
+    long long loss_fx = 0;
+    const int64_t warps = static_cast<int64_t>(gridDim.x) * kWarps;
+    for (int64_t wi = static_cast<int64_t>(blockIdx.x) * kWarps + wib; wi < a.n_walks; wi += warps)
+        loss_fx += hw_train_walk<D, float, KFIX, false, true, true>(v, a.walks + wi * a.L, wi, wk, negs, slots);
+    for (int o = 16; o; o >>= 1) loss_fx += __shfl_xor_sync(kFull, loss_fx, o);
+    if (lane == 0 && loss_fx != 0) atomicAdd(a.loss_acc, static_cast<unsigned long long>(loss_fx));
+}
+
 // Shared memory words per warp of the half-warp trainer: walk and negative
 // ids (rounded up to 16 bytes), then with STAGE the staged phi_in increments.
 inline int hw_words_per_warp(int L, int window, int K, int dim, bool stage) {
@@ -262,7 +284,7 @@ static bool params_ok(const felog_train_params *tp) {
     }
     if (tp->precision != FELOG_FP32 && tp->precision != FELOG_BF16_SR) return false;
     if (tp->mode == FELOG_SGNS_MINIBATCH && tp->minibatch < 1) return false;
-    if (tp->hogwild_form < 0 || tp->hogwild_form > 4) return false;
+    if (tp->hogwild_form < 0 || tp->hogwild_form > 5) return false;
     if (tp->hogwild_form >= 2 && (tp->dim > 128 || tp->negatives > 7)) return false;
     if (tp->hogwild_form == 3 && tp->window > kStageMaxWindow) return false;
     if (tp->stage_flush < 0) return false;
@@ -294,11 +316,17 @@ static felog_status launch_train(const SgnsArgs &a, const felog_train_params *tp
                                 : sizeof(int32_t) * kWarps * (a.L + 2 * a.window * a.K);
         if (prefetch)
             smem = static_cast<size_t>(kWarps) * pf_bytes_per_warp(a.L, a.window, a.K, DH, static_cast<int>(sizeof(T)));
+        // form 5 (row increments added by the bulk-copy engine): float tables
+        const bool bulk = half_warp && !kBf16 && tp->hogwild_form == 5;
+        if (bulk) smem = static_cast<size_t>(kWarps) * bulk_bytes_per_warp(a.L, a.window, a.K, DH);
         if (smem > 200 * 1024) return FELOG_ERR_UNSUPPORTED;  // walk too long to stage per warp
-        auto kern = prefetch ? k_sgns_hogwild_pf<DH, T, KFIX>
-                             : stage ? k_sgns_hogwild_hw<DH, T, KFIX, true>
-                                     : (half_warp ? k_sgns_hogwild_hw<DH, T, KFIX, false>
-                                                  : k_sgns_hogwild<D, T, MAXT, KFIX>);
+        void (*kern)(SgnsArgs, T *, T *) = prefetch ? k_sgns_hogwild_pf<DH, T, KFIX>
+                                           : stage ? k_sgns_hogwild_hw<DH, T, KFIX, true>
+                                                   : (half_warp ? k_sgns_hogwild_hw<DH, T, KFIX, false>
+                                                                : k_sgns_hogwild<D, T, MAXT, KFIX>);
+        if constexpr (!kBf16) {
+            if (bulk) kern = k_sgns_hogwild_bulk<DH, KFIX>;
+        }
         if (smem > 48 * 1024)
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
         int per_sm = 0;

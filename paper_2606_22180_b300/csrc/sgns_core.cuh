@@ -666,12 +666,54 @@ constexpr int kStageMaxWindow = 15;
 // Floats of staged increments per warp.
 inline size_t stage_floats(int window, int dim) { return static_cast<size_t>(2 * window + 1) * dim; }
 
+// Bulk reductions (form 5, float tables): a step's row increments are
+// written to shared memory in the row's own layout and added to the table
+// by the bulk-copy engine, one cp.reduce.async.bulk of the whole row each,
+// instead of two vector reductions per lane.  A half's K + 1 slots (K
+// negatives, then the context) are reused every step once the engine has
+// read them (wait_group.read by the issuing lane).
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_reduce_add_f32(float *gdst, const float *ssrc, uint32_t bytes) {
+    const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(ssrc));
+    asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;" ::"l"(gdst), "r"(s),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() {
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// writes lane hl's elements of a float row increment into a shared-memory
+// slot laid out as the row itself (the layout of hw_load / hw_add)
+template <int EPL>
+__device__ __forceinline__ void slot_store(float *slot, int hl, const float (&d)[EPL]) {
+    if constexpr (EPL == 8) {
+        *reinterpret_cast<float4 *>(slot + hl * 4) = make_float4(d[0], d[1], d[2], d[3]);
+        *reinterpret_cast<float4 *>(slot + 64 + hl * 4) = make_float4(d[4], d[5], d[6], d[7]);
+    } else if constexpr (EPL == 4) {
+        *reinterpret_cast<float4 *>(slot + hl * 4) = make_float4(d[0], d[1], d[2], d[3]);
+    } else {
+        *reinterpret_cast<float2 *>(slot + hl * 2) = make_float2(d[0], d[1]);
+    }
+}
+
+// Shared memory of one warp of the bulk-reduction form: the walk and
+// negative ids (rounded up to 16 bytes), then 2 halves x (K + 1) row slots.
+__host__ __device__ inline int bulk_bytes_per_warp(int L, int window, int K, int dim) {
+    return 4 * ((L + 2 * window * K + 3) & ~3) + 2 * (K + 1) * dim * 4;
+}
+
 // Trains all pairs of one walk (row: L node ids local to the graph; wi: the
 // walk's index in the graph's round, which keys its negatives and its
 // token clock).  wk (L ints) and negs (2 W K ints) are this warp's shared
 // memory, and with STAGE delta ((2W + 1) * D floats, all zero on entry and
-// on return).  Returns this lane's loss in 2^-24 units.
-template <int D, class T, int KFIX, bool STAGE = false, bool NC = true>
+// on return); with BULK (float tables, not STAGE) `delta` is the warp's
+// 2 (K + 1) row slots instead.  Returns this lane's loss in 2^-24 units.
+template <int D, class T, int KFIX, bool STAGE = false, bool NC = true, bool BULK = false>
 __device__ __forceinline__ long long hw_train_walk(const TrainView<T> &a, const int32_t *__restrict__ row,
                                                    int64_t wi, int32_t *wk, int32_t *negs,
                                                    float *delta = nullptr) {
@@ -679,10 +721,12 @@ __device__ __forceinline__ long long hw_train_walk(const TrainView<T> &a, const 
     constexpr int MAXT = 8;
     constexpr bool kBf16 = !std::is_same<T, float>::value;
     static_assert(EPL == 2 || EPL == 4 || EPL == 8, "dim");
+    static_assert(!BULK || (!kBf16 && !STAGE), "bulk reductions: float tables, not staged");
     const int lane = threadIdx.x & 31;
     const int h = lane >> 4, hl = lane & 15;
     const int W = a.W, L = a.L;
     const int K = KFIX > 0 ? KFIX : a.K;
+    float *const slots = BULK ? delta + h * (K + 1) * D : nullptr;  // this half's K + 1 row slots
     const uint64_t S = a.S, n = a.n;
     T *const phi_in = a.phi_in;
     T *const phi_out = a.phi_out;
@@ -885,6 +929,11 @@ __device__ __forceinline__ long long hw_train_walk(const TrainView<T> &a, const 
                 gt[t] = 0.f;
                 if (t <= K) gt[t] = __shfl_sync(kFull, g, (h << 4) | (t << 1));
             }
+            if constexpr (BULK) {
+                // the engine has read the previous step's slots before they are rewritten
+                if (hl == 0) bulk_wait_read_all();
+                __syncwarp();
+            }
             float din[EPL];
 #pragma unroll
             for (int e = 0; e < EPL; e += 2) {
@@ -910,6 +959,8 @@ __device__ __forceinline__ long long hw_train_walk(const TrainView<T> &a, const 
                 if constexpr (kBf16) {
                     srs = srs * 1664525u + 1013904223u;
                     add_delta_raw<EPL>(nrow + hl * EPL, nr_raw[t], dn, srs);
+                } else if constexpr (BULK) {
+                    slot_store<EPL>(slots + (t - 1) * D, hl, dn);
                 } else {
                     hw_add<EPL>(reinterpret_cast<float *>(nrow), hl, dn);
                 }
@@ -941,8 +992,25 @@ __device__ __forceinline__ long long hw_train_walk(const TrainView<T> &a, const 
                 if constexpr (kBf16) {
                     srs = srs * 1664525u + 1013904223u;
                     add_delta_raw<EPL>(ix_row + hl * EPL, ix_raw, din, srs);
+                } else if constexpr (BULK) {
+                    slot_store<EPL>(slots + K * D, hl, din);
                 } else {
                     hw_add<EPL>(reinterpret_cast<float *>(ix_row), hl, din);
+                }
+            }
+            if constexpr (BULK) {
+                // the slots' writes reach the async proxy, then one lane per
+                // half hands every written row to the bulk-copy engine
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (hl == 0) {
+#pragma unroll
+                    for (int t = 1; t < MAXT; ++t)
+                        if (t <= K && nid[t] >= 0)
+                            bulk_reduce_add_f32(reinterpret_cast<float *>(phi_out + static_cast<int64_t>(nid[t]) * D),
+                                                slots + (t - 1) * D, D * 4);
+                    if (valid) bulk_reduce_add_f32(reinterpret_cast<float *>(ix_row), slots + K * D, D * 4);
+                    bulk_commit();
                 }
             }
         }
@@ -956,6 +1024,12 @@ __device__ __forceinline__ long long hw_train_walk(const TrainView<T> &a, const 
             }
         }
         loss_fx += __float2ll_rn(closs * kLossScaleF);
+        __syncwarp();
+    }
+    if constexpr (BULK) {
+        // every reduction of this walk has completed (the slots are free and
+        // nothing is in flight when the warp moves on or exits)
+        if (hl == 0) bulk_wait_all();
         __syncwarp();
     }
     if constexpr (STAGE) {

@@ -25,7 +25,7 @@ def fl():
 # 128); the bf16 forms at dim 128 are held to the dim-128 oracle.
 FORMS = [("hogwild", 0, 0, DIM), ("bf16", 1, 0, DIM), ("staged", 0, 3, DIM), ("staged_bf16", 1, 3, DIM),
          ("prefetch", 0, 4, DIM), ("prefetch_128", 0, 4, 128), ("prefetch_bf16", 1, 0, 128),
-         ("bf16_128", 1, 2, 128)]
+         ("bf16_128", 1, 2, 128), ("bulk", 0, 5, DIM), ("bulk_128", 0, 5, 128)]
 
 
 @pytest.fixture(scope="module")
@@ -75,11 +75,12 @@ def test_bf16_auc_within_tolerance_of_serial_oracle(runs):
 
 
 @pytest.mark.parametrize("form", ["staged", "staged_bf16", "prefetch", "prefetch_128", "prefetch_bf16",
-                                  "bf16_128"])
+                                  "bf16_128", "bulk", "bulk_128"])
 def test_other_hogwild_forms_auc_within_tolerance_of_serial_oracle(runs, form):
     """The staged form (window phi_in increments summed in shared memory and
-    added when a position leaves the window) and the prefetching form (rows of
-    the next step copied to shared memory during this one) keep the per-pair
+    added when a position leaves the window), the prefetching form (rows of
+    the next step copied to shared memory during this one) and the bulk
+    form (row increments added by the bulk-copy engine) keep the per-pair
     estimator.  Each is held to the oracle of its own dimension."""
     dim = next(f[3] for f in FORMS if f[0] == form)
     d = np.array([r[form] - r[f"oracle{dim}"] for r in runs])
