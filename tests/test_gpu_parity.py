@@ -119,6 +119,43 @@ def test_walks_rmat20_sampled(fl, orc):
     # the fused counts equal the oracle's histogram of the whole round
     full = orc.counts(orc.walk(g.offsets, g.cols, starts, 80, 1, SEED, 4), g.n)
     assert np.array_equal(counts.cpu().numpy().astype(np.uint32), full)
+    # and the round's noise table (1,048,576 entries) equals the oracle's
+    thr, alias, S = fl.felog_noise_table(counts)
+    _, thr_ref, alias_ref, S_ref = orc.noise_table(full)
+    assert int(S.item()) == S_ref
+    assert np.array_equal(thr.cpu().numpy().astype(np.uint64), thr_ref)
+    assert np.array_equal(alias.cpu().numpy(), alias_ref)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("precision", [0, 1])
+def test_feedback_rmat20_sampled(fl, orc, precision):
+    """Full-size R-MAT scale 20 with d = 128 tables, Psi of every live node
+    in the launch a round makes (ks = 8, mu = 0.65); 3000 sampled nodes are
+    recomputed by the oracle (the others inactive on its side) and must
+    agree bit for bit, with the same decision."""
+    g = inputs.workload_rmat(20, 1)
+    rng = np.random.default_rng(20 + precision)
+    phi = (rng.normal(size=(g.n, 128)) * 0.05).astype(np.float32)
+    pt = torch.from_numpy(phi).cuda()
+    if precision == 1:
+        pt = pt.to(torch.bfloat16)
+    live = (g.degrees() > 0).astype(np.uint8)
+    fp = fl.feedback_params(True, 0.65, 8, 10, False)
+    psi, nxt, _ = fl.felog_feedback(fl.DeviceGraph.from_host(g), pt, precision, fp, SEED, 3, _dev(live))
+    sample = np.sort(rng.choice(np.nonzero(live)[0], 3000, replace=False))
+    act = np.zeros(g.n, np.uint8)
+    act[sample] = 1
+    rows = pt[torch.as_tensor(sample).cuda()].cpu().double().numpy()
+    # the oracle reads only the sampled nodes' rows and their neighbours' rows
+    phi64 = np.zeros((g.n, 128))
+    nb = np.unique(np.concatenate([g.cols[g.offsets[v]:g.offsets[v + 1]] for v in sample]))
+    phi64[nb] = pt[torch.as_tensor(nb).cuda()].cpu().double().numpy()
+    phi64[sample] = rows
+    psi_ref, nxt_ref, _ = orc.feedback(g.offsets, g.cols, phi64, act, True, 0.65, 8, False, SEED, 3)
+    got = psi.cpu().numpy()[sample]
+    assert np.array_equal(got.view(np.int64), psi_ref[sample].view(np.int64))
+    assert np.array_equal(nxt.cpu().numpy()[sample], nxt_ref[sample])
 
 
 # ---------------------------------------------------------------------------
