@@ -228,6 +228,36 @@ __global__ void __launch_bounds__(kWalkThreads)
     }
 }
 
+// kWalkPerThread walks per thread in lockstep (walk_fill_rows_vec), walks
+// g * M .. g * M + M - 1 for thread-group index g; 4-step int4 stores.
+constexpr int kWalkPerThread = 2;
+
+template <bool COUNT, int M>
+__global__ void __launch_bounds__(kWalkThreads)
+    k_walk_m(const int32_t *__restrict__ offsets, const int32_t *__restrict__ cols, int32_t n, int64_t nnz,
+             const int32_t *__restrict__ starts, int32_t n_starts, int32_t L, int32_t wpr, uint64_t seed,
+             uint32_t round, int32_t *__restrict__ walks, uint32_t *__restrict__ counts) {
+    const int64_t total = static_cast<int64_t>(n_starts) * wpr;
+    const int64_t groups = (total + M - 1) / M;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t g = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; g < groups; g += stride) {
+        int32_t s[M];
+        uint32_t x2[M];
+        int32_t *rows[M];
+        const int nm = static_cast<int>(total - g * M < M ? total - g * M : M);
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const int64_t w = g * M + (m < nm ? m : 0);
+            const int32_t j = static_cast<int32_t>(w / n_starts);
+            const int32_t i = static_cast<int32_t>(w - static_cast<int64_t>(j) * n_starts);
+            s[m] = __ldg(starts + i);
+            x2[m] = round * static_cast<uint32_t>(wpr) + static_cast<uint32_t>(j);
+            rows[m] = walks + w * L;
+        }
+        walk_fill_rows_vec<COUNT, M>(offsets, cols, n, nnz, s, nm, L, seed, x2, rows, counts);
+    }
+}
+
 __global__ void k_count(const int32_t *__restrict__ tokens, int64_t n_tokens,
                         uint32_t *__restrict__ counts) {
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
@@ -329,9 +359,23 @@ extern "C" felog_status felog_walk(const felog_csr *g, const int32_t *starts, in
     const int64_t total = static_cast<int64_t>(n_starts) * wp->walks_per_round;
     const int L = wp->length;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool vec = (L % 4 == 0) && (reinterpret_cast<uintptr_t>(walks) % 16 == 0);
+    if (vec) {
+        constexpr int M = kWalkPerThread;
+        const int blocks = static_cast<int>(std::min<int64_t>(ceil_div((total + M - 1) / M, kWalkThreads),
+                                                              static_cast<int64_t>(sm_count()) * 8));
+        if (counts)
+            k_walk_m<true, M><<<blocks, kWalkThreads, 0, s>>>(g->offsets, g->cols, g->n, g->nnz, starts, n_starts, L,
+                                                              wp->walks_per_round, seed, static_cast<uint32_t>(round),
+                                                              walks, counts);
+        else
+            k_walk_m<false, M><<<blocks, kWalkThreads, 0, s>>>(g->offsets, g->cols, g->n, g->nnz, starts, n_starts,
+                                                               L, wp->walks_per_round, seed,
+                                                               static_cast<uint32_t>(round), walks, counts);
+        return check_launch("felog_walk");
+    }
     const int blocks = static_cast<int>(
         std::min<int64_t>(ceil_div(total, kWalkThreads), static_cast<int64_t>(sm_count()) * 8));
-    const bool vec = (L % 4 == 0) && (reinterpret_cast<uintptr_t>(walks) % 16 == 0);
 #define FELOG_WALK_LAUNCH(C, V)                                                                   \
     k_walk<C, V><<<blocks, kWalkThreads, 0, s>>>(g->offsets, g->cols, g->n, g->nnz, starts, n_starts, L, \
                                                  wp->walks_per_round, seed,                        \
