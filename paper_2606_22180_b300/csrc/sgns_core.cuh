@@ -411,6 +411,35 @@ __device__ __forceinline__ void add_delta_raw(__nv_bfloat16 *__restrict__ p, con
     }
 }
 
+// As add_delta_raw, with the row's current values also given as floats
+// (cur[e] = the bf16 value in raw, already unpacked by the caller), and the
+// sums cur + delta formed two at a time.
+template <int EPL>
+__device__ __forceinline__ void add_delta_vals(__nv_bfloat16 *__restrict__ p, const float (&cur)[EPL],
+                                               const uint32_t (&raw)[EPL / 2], const float (&delta)[EPL],
+                                               uint32_t w) {
+    constexpr uint32_t C[4] = {0x9E3779B1u, 0x85EBCA77u, 0xC2B2AE3Du, 0x27D4EB2Fu};
+    const uint32_t whi = w >> 16;
+    uint32_t inc[EPL / 2];
+    uint32_t any = 0;
+#pragma unroll
+    for (int i = 0; i < EPL / 2; ++i) {
+        const float2 x = __fadd2_rn(make_float2(cur[2 * i], cur[2 * i + 1]),
+                                    make_float2(delta[2 * i], delta[2 * i + 1]));
+        const uint32_t t = sr_pack_bf16x2(x.y, x.x, (w * C[i & 3]) ^ whi);
+        inc[i] = sub_bf16x2(t, raw[i]);
+        any |= inc[i];
+    }
+    if (!(any & 0x7fff7fffu)) return;  // every element rounded back to its current value
+    if constexpr (EPL == 2) {
+        red_add_bf16x2_v1(p, inc[0]);
+    } else if constexpr (EPL == 4) {
+        red_add_bf16x2_v2(p, inc[0], inc[1]);
+    } else {
+        red_add_bf16x2_v4(p, inc[0], inc[1], inc[2], inc[3]);
+    }
+}
+
 // Transposed reduction of 8 partial sums over the 16 lanes of a half warp:
 // afterwards lanes 2t and 2t+1 of the half hold the total of value t.
 __device__ __forceinline__ float reduce_scatter16(float (&v)[8], int hl) {
@@ -958,7 +987,7 @@ __device__ __forceinline__ long long hw_train_walk(const TrainView<T> &a, const 
                 T *nrow = phi_out + static_cast<int64_t>(nid[t]) * D;
                 if constexpr (kBf16) {
                     srs = srs * 1664525u + 1013904223u;
-                    add_delta_raw<EPL>(nrow + hl * EPL, nr_raw[t], dn, srs);
+                    add_delta_vals<EPL>(nrow + hl * EPL, nr[t], nr_raw[t], dn, srs);
                 } else if constexpr (BULK) {
                     slot_store<EPL>(slots + (t - 1) * D, hl, dn);
                 } else {
@@ -991,7 +1020,7 @@ __device__ __forceinline__ long long hw_train_walk(const TrainView<T> &a, const 
             } else if (valid) {
                 if constexpr (kBf16) {
                     srs = srs * 1664525u + 1013904223u;
-                    add_delta_raw<EPL>(ix_row + hl * EPL, ix_raw, din, srs);
+                    add_delta_vals<EPL>(ix_row + hl * EPL, ix, ix_raw, din, srs);
                 } else if constexpr (BULK) {
                     slot_store<EPL>(slots + K * D, hl, din);
                 } else {
@@ -1282,7 +1311,7 @@ __device__ __forceinline__ long long hw_train_walk_pf(const TrainView<T> &a, con
                 T *nrow = phi_out + static_cast<int64_t>(nid[t]) * D;
                 if constexpr (kBf16) {
                     srs = srs * 1664525u + 1013904223u;
-                    add_delta_raw<EPL>(nrow + hl * EPL, nr_raw, dn, srs);
+                    add_delta_vals<EPL>(nrow + hl * EPL, nr, nr_raw, dn, srs);
                 } else {
                     hw_add<EPL>(reinterpret_cast<float *>(nrow), hl, dn);
                 }
@@ -1303,7 +1332,7 @@ __device__ __forceinline__ long long hw_train_walk_pf(const TrainView<T> &a, con
                 T *ix_row = phi_in + static_cast<int64_t>(x) * D;
                 if constexpr (kBf16) {
                     srs = srs * 1664525u + 1013904223u;
-                    add_delta_raw<EPL>(ix_row + hl * EPL, ix_raw, din, srs);
+                    add_delta_vals<EPL>(ix_row + hl * EPL, ix, ix_raw, din, srs);
                 } else {
                     hw_add<EPL>(reinterpret_cast<float *>(ix_row), hl, din);
                 }
