@@ -124,20 +124,23 @@ def test_batch_trainer_shapes_quality_equal_solo(fl, form, precision):
     """Every trainer shape the autotuner may pick (1: one pair per warp;
     2: two pairs per warp; 4: shape 2 with rows prefetched to shared memory)
     keeps each dim-128 job's link AUC within 0.005 of the job trained alone
-    (mean of 2 seeds per job; every job checked)."""
+    (mean of 4 seeds per job; every job checked).  Lock-free training is
+    not reproducible, and on graphs of a few thousand nodes one bf16 run's
+    AUC moves by about 0.005 from seed to seed, so a job's mean over fewer
+    seeds would not separate a real gap from that spread."""
     from paper_2606_22180_b300 import evaluate
 
     gs, splits = [], []
     for i in range(4):
-        g, _ = inputs.sbm(1200 + 600 * i, 8, 0.04, 0.002, seed=700 + i)
+        g, _ = inputs.sbm(2000 + 1000 * i, 8, 0.04, 0.002, seed=700 + i)
         sp = inputs.link_split(g, 0.1, i)
         gs.append(sp.train)
         splits.append(sp)
     dgs = [fl.DeviceGraph.from_host(g) for g in gs]
     tp = fl.train_params(128, W, K, 0.025, 0, fl.FELOG_SGNS_HOGWILD, 4096, precision)
     fp = fl.feedback_params(False, 0.65, 8, 8, False)
-    diffs = np.zeros((2, 4))
-    for rep in range(2):
+    diffs = np.zeros((4, 4))
+    for rep in range(4):
         seeds = [21 + i + 100 * rep for i in range(4)]
         b = fl.Batch(dgs, [128] * 4, seeds, L, 1, tp, fp)
         b.set_tuning(sgns_form=form)
@@ -150,7 +153,8 @@ def test_batch_trainer_shapes_quality_equal_solo(fl, form, precision):
                              - evaluate.link_auc(solo, splits[j].pos, splits[j].neg))
         b.close()
     per_job = diffs.mean(0)
-    print(f"shape {form} precision {precision}: batch - solo AUC per job:", np.round(per_job, 4))
+    print(f"shape {form} precision {precision}: batch - solo AUC per job:", np.round(per_job, 4),
+          "spread", np.round(diffs.std(0), 4))
     assert np.all(np.abs(per_job) <= 0.005), per_job
 
 
@@ -229,7 +233,7 @@ def test_batch_persistent_hogwild(fl, orc):
     """The persistent kernel in the Hogwild form: the last round's walks and
     alias tables (rebuilt inside the kernel every round) equal the oracle's,
     every job runs its rounds, and each job's link AUC is within 0.005 of the
-    same job trained alone (mean of 2 seeds)."""
+    same job trained alone (mean of 4 seeds)."""
     from paper_2606_22180_b300 import evaluate
 
     gs, splits = [], []
@@ -243,8 +247,8 @@ def test_batch_persistent_hogwild(fl, orc):
     for prec in (fl.FELOG_BF16_SR, fl.FELOG_FP32):
         tp = fl.train_params(64, W, K, 0.025, 0, fl.FELOG_SGNS_HOGWILD, 4096, prec)
         fp = fl.feedback_params(False, 0.65, 8, 6, False)
-        diffs = np.zeros((2, 4))
-        for rep in range(2):
+        diffs = np.zeros((4, 4))
+        for rep in range(4):
             seeds = [9 + i + 100 * rep for i in range(4)]
             b = fl.Batch(dgs, dims, seeds, L, 1, tp, fp)
             s = torch.cuda.Stream()
