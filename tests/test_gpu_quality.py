@@ -8,6 +8,7 @@ from paper_2606_22180_b300 import inputs
 pytestmark = pytest.mark.gpu
 
 L, DIM, W, K, R = 40, 64, 5, 5, 10
+SEEDS = 8
 TILE_R, TILE_NS = 3, 128
 
 
@@ -33,7 +34,10 @@ def runs(fl, orc):
     from paper_2606_22180_b300 import evaluate
 
     res = []
-    for seed in range(5):
+    # 8 seeds: one lock-free bf16 run's AUC on this 1,000-node graph moves by
+    # about 0.005 from seed to seed, so a mean over 5 would sit within a few
+    # standard errors of the 0.005 bound by chance alone
+    for seed in range(SEEDS):
         g, _ = inputs.workload_sbm1000(seed)
         sp = inputs.link_split(g, 0.1, seed)
         tr = sp.train
