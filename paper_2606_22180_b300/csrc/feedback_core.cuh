@@ -34,15 +34,20 @@ __device__ __forceinline__ double butterfly(double s) {
     return s;
 }
 
-// Reduce-scatter of 16 per-lane partial sums over the warp: each total is
-// formed from the same pairs of partials as butterfly() (xor distance 16,
-// 8, 4, 2, 1), so it is bit-identical to the butterfly's; afterwards lanes
-// 2t and 2t + 1 hold total t.
-__device__ __forceinline__ double reduce_scatter16_f64(double (&v)[16], int lane) {
+// Reduce-scatter of the first NP (2, 4, 8 or 16) per-lane partial sums over
+// the warp: each total is formed from the same pairs of partials as
+// butterfly() (xor distance 16, 8, 4, 2, 1), so it is bit-identical to the
+// butterfly's.  The first log2(NP) levels halve the partials a lane carries,
+// the remaining levels add the one it keeps; afterwards the 32 / NP lanes
+// lane / (32 / NP) == t hold total t.
+template <int NP>
+__device__ __forceinline__ double reduce_scatter_f64(double (&v)[16], int lane) {
+    constexpr int S = NP == 16 ? 4 : NP == 8 ? 3 : NP == 4 ? 2 : 1;
+    static_assert(NP == 2 << (S - 1), "NP: 2, 4, 8 or 16");
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
+    for (int s = 0; s < S; ++s) {
         const int dist = 16 >> s;
-        const int half = 8 >> s;
+        const int half = (NP / 2) >> s;
         const bool upper = (lane & dist) != 0;
 #pragma unroll
         for (int i = 0; i < half; ++i) {
@@ -51,7 +56,10 @@ __device__ __forceinline__ double reduce_scatter16_f64(double (&v)[16], int lane
             v[i] = __dadd_rn(keep, __shfl_xor_sync(kFull, send, dist));
         }
     }
-    return __dadd_rn(v[0], __shfl_xor_sync(kFull, v[0], 1));
+    double t = v[0];
+#pragma unroll
+    for (int d = 16 >> S; d >= 1; d >>= 1) t = __dadd_rn(t, __shfl_xor_sync(kFull, t, d));
+    return t;
 }
 
 // Psi is computed for a group of nodes on one warp in two parts.
@@ -139,10 +147,11 @@ __device__ __forceinline__ int32_t psi_node_totals(const int32_t *__restrict__ c
         if (c < per_lane) nv = __fma_rn(xv[c], xv[c], nv);
     nv = butterfly(nv);
     if (lane == 0) w.nv[row] = nv;
-    // neighbours in chunks of 8: their row loads overlap, and the 16 partial
+    // neighbours in chunks of 8: their row loads overlap, and the partial
     // sums of a chunk (|u|^2 and x.u per neighbour) are reduced together by a
     // reduce-scatter that adds the same pairs as the xor butterfly (so each
     // total is bit-identical to it) with 16 instead of 80 additions per lane
+    // for a full chunk
     constexpr int G = 8;
     double *u2 = w.u2 + row * ks;
     double *xu = w.xu + row * ks;
@@ -174,10 +183,27 @@ __device__ __forceinline__ int32_t psi_node_totals(const int32_t *__restrict__ c
                 part[2 * b + 1] = __fma_rn(xv[c], y[b], part[2 * b + 1]);
             }
         }
-        const double tot = reduce_scatter16_f64(part, lane);  // lanes 2t, 2t+1: total t
-        // lane 4b holds |u_b|^2, lane 4b + 2 holds x . u_b
-        const int b_mine = lane >> 2;
-        if ((lane & 1) == 0 && b_mine < live) ((lane & 2) ? xu : u2)[a0 + b_mine] = tot;
+        // only the 2 * live partials of the live slots are reduced (fewer
+        // halving levels for a short chunk; the same tree for each total)
+        double tot;
+        int grp;  // lanes per total: total t sits in lanes [t * grp, t * grp + grp)
+        if (live > 4) {
+            tot = reduce_scatter_f64<16>(part, lane);
+            grp = 2;
+        } else if (live > 2) {
+            tot = reduce_scatter_f64<8>(part, lane);
+            grp = 4;
+        } else if (live > 1) {
+            tot = reduce_scatter_f64<4>(part, lane);
+            grp = 8;
+        } else {
+            tot = reduce_scatter_f64<2>(part, lane);
+            grp = 16;
+        }
+        // total 2b is |u_b|^2, total 2b + 1 is x . u_b
+        const int t_mine = lane / grp;
+        const int b_mine = t_mine >> 1;
+        if (lane % grp == 0 && b_mine < live) ((t_mine & 1) ? xu : u2)[a0 + b_mine] = tot;
     }
     if (lane == 0) w.m[row] = m;
     __syncwarp();
