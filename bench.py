@@ -385,7 +385,7 @@ def _bf16_rounds(fl, dg, T, args):
                          "traffic": traffic,
                          "dram_frac": traffic / train_s / 1e9 / peak if traffic else None,
                          "note": "algorithmic row bytes (256-byte bf16 rows) per launch / CUDA-event time; "
-                                 "the launch is bound by instruction issue (ncu: 70 % issue active), "
+                                 "the launch is bound by instruction issue (ncu: 66 % issue active), "
                                  "not by DRAM or the L2 request path"}}
 
 
