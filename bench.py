@@ -521,7 +521,11 @@ def run_native(args):
         "clocks": clocks,
     }
 
-    if not args.no_quality and rank == 0:
+    # the quality runs, the other forms and the CPU baseline belong to the
+    # single-GPU line; under torchrun (N > 1) only the replicated rounds run,
+    # so the N GPUs are not held while rank 0 runs them
+    single = world == 1
+    if not args.no_quality and single:
         result["quality"] = _quality(fl, evaluate, dg, split, n_live, args.form, args.stage_flush)
         q = result["quality"]
         result["chosen_vs_plain"] = {
@@ -532,7 +536,7 @@ def run_native(args):
             "tokens_plain": q["plain"]["tokens"], "tokens_chosen": q["chosen"]["tokens"],
             "chosen": "feedback mu=0.65 + bf16-SR tables, same graph and split",
         }
-    if not args.no_forms and rank == 0:
+    if not args.no_forms and single:
         na = int(runner.n_active_h.item())
         result["fabc"] = _fabc_form(fl, runner.walks[: na * WPR * L].view(-1, L), runner.counts)
         result["node2vec"] = _node2vec_form(fl, dg, runner.starts[:na], runner.walks, runner.counts)
@@ -553,7 +557,7 @@ def run_native(args):
         dg = fl.DeviceGraph.from_host(g)
         result["ripp"] = _ripp(fl, evaluate, dg, split, n_live)
         del dg
-    if not args.no_cpu and rank == 0:
+    if not args.no_cpu and single:
         result["cpu_baseline"] = _cpu_baseline(split, n_live)
         result["vs_cpu_baseline"] = value / result["cpu_baseline"]["value"]
     if rank == 0:
