@@ -923,8 +923,10 @@ void launch_b_sgns(const BatchPlan &plan, const BParams &p, const HostTuning &t,
     void (*kern)(BArgs, int64_t, int64_t) = form == 1 ? (p.K == 5 ? k_b_sgns<D, T, 5, 1> : k_b_sgns<D, T, 0, 1>)
                                                       : (p.K == 5 ? k_b_sgns<D, T, 5, 2> : k_b_sgns<D, T, 0, 2>);
     if constexpr (kPfSupported<D, T>) {
-        if (form == 4) {
-            smem = static_cast<size_t>(kWarps) * pf_bytes_per_warp(p.L, p.window, p.K, D, static_cast<int>(sizeof(T)));
+        const size_t pf_smem =
+            static_cast<size_t>(kWarps) * pf_bytes_per_warp(p.L, p.window, p.K, D, static_cast<int>(sizeof(T)));
+        if (form == 4 && pf_smem <= 200 * 1024) {  // longer walks than fit run shape 2
+            smem = pf_smem;
             kern = p.K == 5 ? k_b_sgns<D, T, 5, 4> : k_b_sgns<D, T, 0, 4>;
         }
     }
@@ -1175,6 +1177,7 @@ extern "C" felog_status felog_batch_create(const felog_job *jobs, int32_t n_jobs
     if (!b) return FELOG_ERR_INVALID_ARG;
     b->n_jobs = n_jobs;
     b->p = make_params(wp, tp, fp);
+    b->tune.sgns_form = default_sgns_form(tp);
     // plan order: by dim (stable), so each dim's training items are contiguous
     std::vector<int32_t> order(n_jobs);
     for (int32_t i = 0; i < n_jobs; ++i) order[i] = i;

@@ -92,8 +92,20 @@ struct HostTuning {
     int walk_block = 256;
     int sgns_blocks_per_sm = 2;
     int feedback_blocks_per_sm = 16;
-    int sgns_form = 2;  // 2: two pairs per warp (16 lanes per row); 1: one pair per warp (32 lanes)
+    int sgns_form = 2;  // 2: two pairs per warp (16 lanes per row); 1: one pair per warp (32 lanes);
+                        // 4: shape 2 with rows prefetched to shared memory
 };
+
+// Trainer shape before any tuning: the train parameters' hogwild_form where
+// the batched trainer has it (1, 2, 4), else for the automatic form 0 the
+// single-graph rule (4 for bf16 tables, which falls back to 2 for dims it
+// does not cover; 2 for float tables), else 2.
+inline int default_sgns_form(const felog_train_params *tp) {
+    const int f = tp->hogwild_form;
+    if (f == 1 || f == 2 || f == 4) return f;
+    if (f == 0 && tp->precision == FELOG_BF16_SR) return 4;
+    return 2;
+}
 
 // a membership of jobs on the device: job table, index-space prefixes, tiles
 struct BatchPlan {

@@ -333,6 +333,7 @@ extern "C" felog_status felog_server_create(const felog_server_config *cfg, felo
     if (!sv) return FELOG_ERR_INVALID_ARG;
     sv->cfg = *cfg;
     sv->p = make_params(&cfg->walk, &cfg->train, &cfg->feedback);
+    sv->tune.sgns_form = default_sgns_form(&cfg->train);
     sv->t0 = Clock::now();
     st = record_cuda_error(cudaGetDevice(&sv->device), "felog_server_create");
     if (!st) st = record_cuda_error(cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking), "felog_server_create");
