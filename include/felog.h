@@ -93,8 +93,8 @@ typedef enum {
  * window (other warps see it then; on power-law graphs hub rows collect many
  * warps' delayed increments, which costs link AUC), 4 = form 2 with the
  * next step's context and negative rows copied to shared memory (cp.async)
- * while the current step computes (float tables of dim 64 or 128, bf16
- * tables of dim 128; other shapes run form 2), 5 = form 2 on float tables
+ * while the current step computes (float tables of dim 32, 64 or 128, bf16
+ * tables of dim 64 or 128; other shapes run form 2), 5 = form 2 on float tables
  * with each step's row increments written to shared memory and added to the
  * tables by the bulk-copy engine (cp.reduce.async.bulk, one per row; other
  * precisions run form 2); 0 = automatic: form 4 for
@@ -456,8 +456,8 @@ typedef struct {
     int32_t sgns_form;              /* trainer shape: 2 = two pairs per warp, 16 lanes per row;
                                        1 = one pair per warp, 32 lanes per row; 4 = shape 2 with
                                        each step's rows copied to shared memory one step ahead
-                                       (jobs whose rows give a lane 16 bytes: float dim 64/128,
-                                       bf16 dim 128; other jobs run shape 2) */
+                                       (jobs with rows of 128 to 512 bytes: float dim 32/64/128,
+                                       bf16 dim 64/128; other jobs run shape 2) */
 } felog_tuning;
 
 typedef struct felog_batch felog_batch;

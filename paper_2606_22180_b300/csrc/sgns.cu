@@ -311,7 +311,7 @@ static felog_status launch_train(const SgnsArgs &a, const felog_train_params *tp
         // round, same link AUC), not for float tables (687 against 608 ms)
         constexpr bool kBf16 = !std::is_same<T, float>::value;
         const bool prefetch = half_warp && kPfSupported<DH, T> &&
-                              (tp->hogwild_form == 4 || (tp->hogwild_form == 0 && kBf16));
+                              (tp->hogwild_form == 4 || (tp->hogwild_form == 0 && kBf16 && DH == 128));
         size_t smem = half_warp ? sizeof(int32_t) * kWarps * hw_words_per_warp(a.L, a.window, a.K, DH, stage)
                                 : sizeof(int32_t) * kWarps * (a.L + 2 * a.window * a.K);
         if (prefetch)

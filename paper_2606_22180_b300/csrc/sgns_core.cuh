@@ -1102,9 +1102,10 @@ __device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async
 __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_none() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
+// rows of 128, 256 or 512 bytes: float dim 32/64/128, bf16 dim 64/128
 template <int D, class T>
-constexpr bool kPfSupported = (std::is_same<T, float>::value && (D == 64 || D == 128)) ||
-                              (!std::is_same<T, float>::value && D == 128);
+constexpr bool kPfSupported = (std::is_same<T, float>::value && (D == 32 || D == 64 || D == 128)) ||
+                              (!std::is_same<T, float>::value && (D == 64 || D == 128));
 
 // Shared memory of one warp of the prefetching form: the walk and negative
 // ids (rounded up to 16 bytes), then the double buffer of rows.
@@ -1120,8 +1121,9 @@ __device__ __forceinline__ long long hw_train_walk_pf(const TrainView<T> &a, con
     constexpr int MAXT = 8;
     constexpr bool kBf16 = !std::is_same<T, float>::value;
     constexpr int ROWB = D * static_cast<int>(sizeof(T));  // bytes of a row
-    constexpr int CHUNKS = ROWB / 256;                     // 16-byte chunks per lane: 2 (512 B) or 1 (256 B)
-    static_assert(kPfSupported<D, T>, "16-byte chunks per lane");
+    constexpr int CHUNKS = ROWB / 256;  // 16-byte copies per lane: 2 (512 B), 1 (256 B); 0: 128-byte rows,
+                                        // copied by the half's first 8 lanes, 16 bytes each
+    static_assert(kPfSupported<D, T>, "rows of 128, 256 or 512 bytes");
     const int lane = threadIdx.x & 31;
     const int h = lane >> 4, hl = lane & 15;
     const int W = a.W, L = a.L;
@@ -1202,6 +1204,9 @@ __device__ __forceinline__ long long hw_train_walk_pf(const TrainView<T> &a, con
             const bool valid = pair_of(j, o, x, nid);
             const int s = j & 1;
             const char *ix_src = reinterpret_cast<const char *>(phi_in + static_cast<int64_t>(valid ? x : 0) * D);
+            if constexpr (CHUNKS == 0) {
+                if (hl < 8) cp_async16_zfill(slot(s, 0) + hl * 16, ix_src + hl * 16, valid);
+            }
 #pragma unroll
             for (int ch = 0; ch < CHUNKS; ++ch)
                 cp_async16_zfill(slot(s, 0) + (ch * 16 + hl) * 16, ix_src + (ch * 16 + hl) * 16, valid);
@@ -1210,6 +1215,9 @@ __device__ __forceinline__ long long hw_train_walk_pf(const TrainView<T> &a, con
                 if (t > K) break;
                 const bool ok = nid[t] >= 0;
                 const char *src = reinterpret_cast<const char *>(phi_out + static_cast<int64_t>(ok ? nid[t] : 0) * D);
+                if constexpr (CHUNKS == 0) {
+                    if (hl < 8) cp_async16_zfill(slot(s, t) + hl * 16, src + hl * 16, ok);
+                }
 #pragma unroll
                 for (int ch = 0; ch < CHUNKS; ++ch)
                     cp_async16_zfill(slot(s, t) + (ch * 16 + hl) * 16, src + (ch * 16 + hl) * 16, ok);
@@ -1219,10 +1227,17 @@ __device__ __forceinline__ long long hw_train_walk_pf(const TrainView<T> &a, con
         // this lane's values of row t of stage s (the chunks it copied), as floats and raw bf16 words
         auto read_row = [&](int s, int t, float (&v)[EPL], uint32_t (&raw)[kBf16 ? EPL / 2 : 1]) {
             const char *base = slot_ptr(s, t);
-            if constexpr (kBf16) {
+            if constexpr (kBf16 && EPL == 4) {
+                const uint2 w = *reinterpret_cast<const uint2 *>(base + hl * 8);
+                raw[0] = w.x; raw[1] = w.y;
+                unpack_bf16<EPL>(raw, v);
+            } else if constexpr (kBf16) {
                 const uint4 w = *reinterpret_cast<const uint4 *>(base + hl * 16);
                 raw[0] = w.x; raw[1] = w.y; raw[2] = w.z; raw[3] = w.w;
                 unpack_bf16<EPL>(raw, v);
+            } else if constexpr (EPL == 2) {
+                const float2 u = *reinterpret_cast<const float2 *>(base + hl * 8);
+                v[0] = u.x; v[1] = u.y;
             } else if constexpr (EPL == 8) {
                 const float4 u = *reinterpret_cast<const float4 *>(base + hl * 16);
                 const float4 w = *reinterpret_cast<const float4 *>(base + 256 + hl * 16);

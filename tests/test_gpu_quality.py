@@ -22,11 +22,11 @@ def fl():
 
 # (name, precision: 0 float / 1 bf16-SR, hogwild_form, dim).  Form 0 is the
 # automatic choice: form 2 at dim 64, and for bf16 at dim 128 the prefetching
-# form 4, which needs 16-byte row chunks per lane (float dim 64/128, bf16 dim
-# 128); the bf16 forms at dim 128 are held to the dim-128 oracle.
+# form 4 (which covers rows of 128 to 512 bytes: float dim 32/64/128, bf16 dim
+# 64/128); the forms at dim 128 are held to the dim-128 oracle.
 FORMS = [("hogwild", 0, 0, DIM), ("bf16", 1, 0, DIM), ("staged", 0, 3, DIM), ("staged_bf16", 1, 3, DIM),
          ("prefetch", 0, 4, DIM), ("prefetch_128", 0, 4, 128), ("prefetch_bf16", 1, 0, 128),
-         ("bf16_128", 1, 2, 128), ("bulk", 0, 5, DIM), ("bulk_128", 0, 5, 128)]
+         ("bf16_128", 1, 2, 128), ("bulk", 0, 5, DIM), ("bulk_128", 0, 5, 128), ("prefetch_bf16_64", 1, 4, DIM)]
 
 
 @pytest.fixture(scope="module")
@@ -79,7 +79,7 @@ def test_bf16_auc_within_tolerance_of_serial_oracle(runs):
 
 
 @pytest.mark.parametrize("form", ["staged", "staged_bf16", "prefetch", "prefetch_128", "prefetch_bf16",
-                                  "bf16_128", "bulk", "bulk_128"])
+                                  "bf16_128", "bulk", "bulk_128", "prefetch_bf16_64"])
 def test_other_hogwild_forms_auc_within_tolerance_of_serial_oracle(runs, form):
     """The staged form (window phi_in increments summed in shared memory and
     added when a position leaves the window), the prefetching form (rows of
