@@ -456,8 +456,8 @@ typedef struct {
     int32_t sgns_form;              /* trainer shape: 2 = two pairs per warp, 16 lanes per row;
                                        1 = one pair per warp, 32 lanes per row; 4 = shape 2 with
                                        each step's rows copied to shared memory one step ahead
-                                       (jobs with rows of 128 to 512 bytes: float dim 32/64/128,
-                                       bf16 dim 64/128; other jobs run shape 2) */
+                                       (jobs with rows of 256 or 512 bytes: float dim 64/128,
+                                       bf16 dim 128; other jobs run shape 2) */
 } felog_tuning;
 
 typedef struct felog_batch felog_batch;

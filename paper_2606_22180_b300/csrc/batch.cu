@@ -917,12 +917,15 @@ template <int D, class T>
 void launch_b_sgns(const BatchPlan &plan, const BParams &p, const HostTuning &t, int64_t lo, int64_t hi,
                    cudaStream_t s) {
     if (hi <= lo) return;
-    // form 4 where a lane's share of a row is 16 bytes, else form 2
-    const int form = t.sgns_form == 1 ? 1 : (t.sgns_form == 4 && kPfSupported<D, T> ? 4 : 2);
+    // form 4 for rows of 256 bytes or more (bf16 dim 128, float dim 64 and 128), else form 2: on the
+    // 512-graph mix the dim-64 bf16 jobs (128-byte rows) trained no faster prefetched
+    // (2.40e8 against 2.44e8 tokens/s for the whole batch)
+    constexpr bool kPfHere = kPfSupported<D, T> && D * sizeof(T) >= 256;
+    const int form = t.sgns_form == 1 ? 1 : (t.sgns_form == 4 && kPfHere ? 4 : 2);
     size_t smem = sizeof(int32_t) * kWarps * (p.window * 2 * p.K + p.L);
     void (*kern)(BArgs, int64_t, int64_t) = form == 1 ? (p.K == 5 ? k_b_sgns<D, T, 5, 1> : k_b_sgns<D, T, 0, 1>)
                                                       : (p.K == 5 ? k_b_sgns<D, T, 5, 2> : k_b_sgns<D, T, 0, 2>);
-    if constexpr (kPfSupported<D, T>) {
+    if constexpr (kPfHere) {
         const size_t pf_smem =
             static_cast<size_t>(kWarps) * pf_bytes_per_warp(p.L, p.window, p.K, D, static_cast<int>(sizeof(T)));
         if (form == 4 && pf_smem <= 200 * 1024) {  // longer walks than fit run shape 2
