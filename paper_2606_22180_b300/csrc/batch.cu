@@ -406,8 +406,8 @@ __global__ void k_b_noise_finish(BArgs a) { ph_noise_finish(a, blockIdx.x, gridD
 // ---------------------------------------------------------------------------
 // FORM 2: two pairs per warp (a half warp each, 16 lanes per row); FORM 1:
 // one pair per warp (32 lanes per row); FORM 4: FORM 2 with each step's rows
-// copied to shared memory one step ahead (cp.async; tables whose rows give a
-// lane 16 bytes: float dim 64/128, bf16 dim 128).  Same estimator, different
+// copied to shared memory one step ahead (cp.async; used for rows of 256 or
+// 512 bytes: float dim 64/128, bf16 dim 128).  Same estimator, different
 // shapes.
 template <int D, class T, int KFIX, int FORM, bool NC>
 __device__ __forceinline__ void ph_sgns(const BArgs &a, int64_t item_lo, int64_t item_hi, int b, int g) {

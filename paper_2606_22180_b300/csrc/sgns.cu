@@ -306,9 +306,9 @@ static felog_status launch_train(const SgnsArgs &a, const felog_train_params *tp
         const bool half_warp = D <= 128 && MAXT == 8 && tp->hogwild_form != 1;
         const bool stage = half_warp && tp->hogwild_form == 3;
         constexpr int DH = D <= 128 ? D : 128;
-        // form 4 (rows prefetched with cp.async) where a lane's chunk of a row is 16 bytes;
-        // the automatic choice for bf16 tables of dim 128 (R-MAT 20: 451 against 473 ms per
-        // round, same link AUC), not for float tables (687 against 608 ms)
+        // form 4 (rows prefetched with cp.async) for rows of 128 to 512 bytes; the automatic
+        // choice for bf16 tables of dim 128 (R-MAT 20: 412 against 423 ms per round for
+        // form 2, same link AUC), not for float tables (687 against 608 ms)
         constexpr bool kBf16 = !std::is_same<T, float>::value;
         const bool prefetch = half_warp && kPfSupported<DH, T> &&
                               (tp->hogwild_form == 4 || (tp->hogwild_form == 0 && kBf16 && DH == 128));

@@ -1089,10 +1089,13 @@ __device__ __forceinline__ long long hw_train_walk(const TrainView<T> &a, const 
 // double buffer: [2 stages][2 halves][K + 1 rows][D values of T]; lane l of a
 // half copies and later reads the same 16-byte chunks of each row (chunks l
 // and l + 16 for a 512-byte row, chunk l for a 256-byte row), so a lane
-// needs only its own copies to complete.  The arithmetic is form 2's; a
-// step's rows are read one step earlier than form 2 reads them (before the
-// previous step's updates of the same rows, if any, reach memory).  Chunks of
-// 16 bytes per lane: float rows of dim 64 or 128, bf16 rows of dim 128.
+// needs only its own copies to complete; a 128-byte row is copied by the
+// half's first 8 lanes, 16 bytes each, and read 8 bytes per lane, so every
+// lane waits for the whole half's copies (cp.async.wait_group, then the
+// warp's __syncwarp).  The arithmetic is form 2's; a step's rows are read one
+// step earlier than form 2 reads them (before the previous step's updates of
+// the same rows, if any, reach memory).  Rows of 128, 256 or 512 bytes: float
+// dim 32, 64 or 128, bf16 dim 64 or 128.
 // ----------------------------------------------------------------------------
 __device__ __forceinline__ void cp_async16_zfill(uint32_t dst, const void *src, bool valid) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
@@ -1254,6 +1257,9 @@ __device__ __forceinline__ long long hw_train_walk_pf(const TrainView<T> &a, con
             if (j + 1 < steps) issue(j + 1);
             else cp_async_commit_group();  // an empty group: wait_group 1 below then means step j
             cp_async_wait_prev();
+            // a 128-byte row is read by lanes other than the 8 that copied it: every
+            // lane's copies of step j have landed before any lane reads
+            if constexpr (CHUNKS == 0) __syncwarp();
             const int s = j & 1;
             int o;
             int32_t x, nid[MAXT];
