@@ -61,6 +61,18 @@ def test_host_side_argument_checks(lib):
     wp = felog._WalkParams(4, 1)
     assert lib.felog_walk(ctypes.byref(csr_bad), 1, 1, ctypes.byref(wp), 0, 0, 1, None, None) == 2
     assert lib.felog_embed_workspace_bytes(10, ctypes.byref(wp), ctypes.byref(bad)) == 0
+    # stochastic rounding: negative length or missing buffers rejected, empty input is a no-op
+    assert lib.felog_sr_bf16(None, None, -1, None, None) == 1
+    assert lib.felog_sr_bf16(None, None, 5, None, None) == 1
+    assert lib.felog_sr_bf16(None, None, 0, None, None) == 0
+    # grid-barrier check and batch knobs: out-of-range arguments rejected before any CUDA call
+    assert lib.felog_grid_barrier_check(-1, 1, 1.0, None, None) == 1
+    assert lib.felog_grid_barrier_check(0, 0, 1.0, None, None) == 1
+    assert lib.felog_grid_barrier_check(0, 1, 0.0, None, None) == 1
+    assert lib.felog_grid_barrier_check(0, 1, 61.0, None, None) == 1
+    t = felog.Tuning(256, 2, 16, 0, 2)
+    assert lib.felog_batch_set_tuning(None, ctypes.byref(t)) == 1
+    assert lib.felog_batch_set_wait_limit(None, 1.0) == 1
 
 
 def test_product_path_has_no_cpu_fallback():
