@@ -13,6 +13,14 @@
  *   felog_feedback        Psi (Eq. 4) and the next active set (Eq. 5; Alg. 1 Feedback)
  *   felog_embed           Algorithm 1 end to end
  *
+ * and around them: felog_validate_csr (the graph checked on the device),
+ * felog_embed_pipelined (round-interleaved pipeline, Section 5.3),
+ * felog_walk_node2vec (second-order walks, a Sample variant of Section 5.4),
+ * felog_fabc_* (walk compression, Section 5.2.2, Eq. 7, Eq. 8),
+ * felog_sr_bf16 (the bf16 stores' stochastic rounding on its own),
+ * felog_batch_* (many graphs in one launch sequence) and felog_server_*
+ * (a request loop with continuous batching), felog_compact_active_noalloc.
+ *
  * Conventions (every call):
  *   - Pointers documented "device" point to CUDA device memory owned by the
  *     caller; the library never frees caller memory and allocates none of
@@ -29,7 +37,8 @@
  *
  * Random numbers: Philox4x32-10 keyed by the 64-bit seed with counter
  * (x0, x1, x2, stream); stream 0 = walks, 1 = Psi subsets, 2 = negatives,
- * 3 = table initialisation, 4 = stochastic rounding.
+ * 3 = table initialisation, 4 = stochastic rounding, 7 = shared tile
+ * negatives, 8 = node2vec attempts.
  */
 #ifndef FELOG_H_
 #define FELOG_H_
