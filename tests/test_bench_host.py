@@ -45,3 +45,21 @@ def test_profile_traffic_only_for_the_captured_source(bench, tmp_path, monkeypat
     src.write_text("kernel v2\n")
     assert bench._profile_traffic([str(src)], "p.md") is None
     assert bench._profile_traffic([str(src)], "missing.md") is None
+
+
+def test_profile_commands_parse(bench, monkeypatch):
+    """Every bench.py command quoted in a committed profile summary is one the
+    current bench.py accepts (the summaries say how to reproduce them)."""
+    import glob
+    import re
+    import shlex
+
+    cmds = []
+    for path in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        text = open(path).read().replace("\\\n", " ")
+        for m in re.finditer(r"python bench\.py([^>&\n`\"]*)", text):
+            cmds.append((os.path.basename(path), shlex.split(m.group(1))))
+    assert len(cmds) >= 10
+    for name, argv in cmds:
+        monkeypatch.setattr("sys.argv", ["bench.py"] + argv)
+        bench._args()  # argparse exits on an unknown option or value
